@@ -1,0 +1,198 @@
+/*
+ * topo.h - C ABI of the GB300 SIMP state-solve library (libtopo.so).
+ *
+ * The library computes, on one GPU, the state solve, compliance and element
+ * sensitivities of density-based (SIMP) compliance topology optimisation on a
+ * structured grid of trilinear 8-node bricks (arXiv 2605.04735):
+ *
+ *   E_e = Emin + rho_e^p (E0 - Emin)                        Sec. 2.1, Eq. (1)
+ *   K(rho) U = F,  J = F^T U = U^T K U = sum_e u_e^T k_e u_e Sec. 2.1.1, Eq. (2)
+ *   dJ/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e     Sec. 2.1.2, Eq. (3)
+ *
+ * k0 is the 24x24 matrix of the unit cube brick for unit Young's modulus
+ * (Sec. 2.1.2), exact (2x2x2-point) integration of the trilinear element,
+ * isotropic material with Poisson ratio nu; an element of edge h uses h*k0.
+ * The paper does not say how K U = F is solved: the library solves it with
+ * matrix-free preconditioned conjugate gradients (Jacobi or a geometric
+ * multigrid V-cycle), either all in FP64 or in FP32 inside FP64 iterative
+ * refinement, always to a true FP64 relative residual.
+ *
+ * Numbering (both for inputs and outputs):
+ *   node    n = i + (nx+1) * (j + (ny+1) * k),  0 <= i <= nx, ...
+ *   DOF     3 n + c, c = 0 (x), 1 (y), 2 (z)     (displacements: n_dof = 3 * nodes)
+ *   element e = i + nx * (j + ny * k),           0 <= i < nx, ...
+ *   local nodes of an element: (0,0,0) (1,0,0) (1,1,0) (0,1,0)
+ *                              (0,0,1) (1,0,1) (1,1,1) (0,1,1)
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a topo_status; nothing throws across the ABI.
+ *   - The library owns the mesh and all device memory it allocates; caller
+ *     arrays are only read or written during the call (inputs are copied).
+ *   - on_device != 0: the pointer is a device pointer on the mesh's device;
+ *     on_device == 0: it is a host pointer (pageable or pinned).
+ *   - Work runs on the CUDA stream given to topo_create_mesh (NULL: the
+ *     library's own stream).  Calls that return host values synchronise
+ *     that stream; the others only enqueue work.  One mesh must not be used
+ *     from two host threads at once; different meshes are independent.
+ *   - Sizes are checked: a count that differs from the mesh's size returns
+ *     TOPO_ERR_INVALID and touches nothing.
+ */
+#ifndef TOPO_H
+#define TOPO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct topo_mesh topo_mesh; /* opaque, library-owned */
+
+typedef enum {
+  TOPO_OK = 0,
+  TOPO_ERR_INVALID = -1,       /* bad argument, size or option */
+  TOPO_ERR_OOM = -2,           /* device or host allocation failed */
+  TOPO_ERR_CUDA = -3,          /* a CUDA runtime/driver call failed */
+  TOPO_ERR_NO_DENSITY = -4,    /* solve before set_density */
+  TOPO_ERR_NOT_SOLVED = -5,    /* compliance/sensitivity before a solve */
+  TOPO_ERR_NOT_CONVERGED = -6, /* iteration limits reached above rtol */
+  TOPO_ERR_NAN = -7,           /* NaN/Inf or out-of-range density, or a NaN in the solve */
+  TOPO_ERR_TIMEOUT = -8        /* a bounded device-side wait ran out */
+} topo_status;
+
+/* Boundary conditions (zero displacement on the listed DOFs). */
+enum {
+  TOPO_BC_CANTILEVER = 0, /* every component of every node with i = 0 */
+  TOPO_BC_MBB = 1,        /* u_x on i = 0; u_z on (i = nx, k = 0); u_y at (nx, ny/2, 0); ny even */
+  TOPO_BC_ROLLER_BOX = 2  /* u_x on i = 0, u_y on j = 0, u_z on k = 0 (test problem) */
+};
+
+/* Loads (consistent nodal forces; total magnitude params.load). */
+enum {
+  TOPO_LOAD_EDGE_XL_BOTTOM = 0,  /* -z along the line i = nx, k = 0 */
+  TOPO_LOAD_EDGE_X0_TOP = 1,     /* -z along the line i = 0, k = nz */
+  TOPO_LOAD_FACE_XL_TRACTION = 2 /* uniform +x traction (per unit area) on i = nx */
+};
+
+/* Arithmetic of the inner (preconditioned CG) solve. */
+enum {
+  TOPO_PREC_FP64 = 0, /* plain FP64 PCG (the reference GPU path) */
+  TOPO_PREC_FP32 = 1  /* FP32 PCG inside FP64 iterative refinement */
+};
+
+enum {
+  TOPO_PRECOND_JACOBI = 0, /* D^-1, D = diag K */
+  TOPO_PRECOND_GMG = 1     /* one geometric multigrid V-cycle (2:1 vertex-nested grids) */
+};
+
+typedef struct {
+  double E0;    /* solid Young's modulus (default 1) */
+  double Emin;  /* void modulus (default 1e-9) */
+  double nu;    /* Poisson ratio (default 0.3), 0 <= nu < 0.5 */
+  double penal; /* SIMP exponent p (default 3), p >= 1 */
+  double h;     /* element edge length (default 1) */
+  double load;  /* total edge load, or traction per unit area (default 1) */
+} topo_params;
+
+typedef struct {
+  int precision;     /* TOPO_PREC_* (default FP32) */
+  int precond;       /* TOPO_PRECOND_* (default GMG) */
+  double rtol;       /* target ||f - K u||_2 / ||f||_2 over free DOFs, in FP64 (default 1e-8) */
+  double inner_rtol; /* relative residual reduction of each inner solve (default 1e-5) */
+  int max_iter;      /* cap on inner CG iterations summed over the solve (default 100000) */
+  int max_outer;     /* cap on refinement steps (default 12) */
+  int warm_start;    /* 1: start from the stored displacement, 0: from zero */
+  int gmg_levels;    /* 0: as many 2:1 levels as the grid allows (coarsest <= ~3000 DOF) */
+  int smooth_degree; /* Chebyshev smoother degree per pre/post smoothing (default 3) */
+  int check_every;   /* inner iterations between host convergence checks (default 16) */
+} topo_solve_opts;
+
+typedef struct {
+  int iters;           /* inner CG iterations (all refinement steps) */
+  int outer;           /* FP64 refinement steps (residual evaluations after the first) */
+  int status;          /* the topo_status the call returned */
+  double rel_residual; /* final true FP64 relative residual */
+  double seconds;      /* wall time of the call */
+} topo_solve_info;
+
+/* Defaults as documented above. */
+void topo_default_params(topo_params* p);
+void topo_default_opts(topo_solve_opts* o);
+
+/* Create a mesh of nx*ny*nz elements (each >= 1) with the given boundary
+ * condition and load, on the current CUDA device.  stream: a cudaStream_t
+ * (NULL = the library creates its own).  Allocates all device state of the
+ * FP32/FP64 Jacobi paths; the multigrid hierarchy is built on first use.
+ * Cites Eq. (2): K is assembled implicitly (matrix-free) from E_e k0. */
+topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
+                             void* stream, topo_mesh** out);
+
+/* Set element densities rho (n_elem float32 values in [0, 1], element
+ * order) and derive E_e by Eq. (1).  NaN/Inf or values outside [0, 1] give
+ * TOPO_ERR_NAN (checked on the device; the call synchronises).  Invalidates
+ * the stored solution's compliance/sensitivity until the next solve; the
+ * displacement itself is kept for warm starts. */
+topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int on_device);
+
+/* Solve K(rho) u = f (Eq. (2)) to opts->rtol in the true FP64 residual.
+ * opts NULL = defaults.  info may be NULL; when given it is always filled.
+ * Returns TOPO_ERR_NOT_CONVERGED (u kept, info->rel_residual set) if the
+ * iteration caps are reached first. */
+topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_info* info);
+
+/* Compliance J = f^T u (Eq. (2)) of the last solve, computed in FP64. */
+topo_status topo_compliance(topo_mesh* m, double* c);
+
+/* Compliance J = sum_e E_e u_e^T k0 u_e (Eq. (2), element form) of the last
+ * solve; equals topo_compliance at equilibrium. */
+topo_status topo_compliance_energy(topo_mesh* m, double* c);
+
+/* Element sensitivities dJ/drho_e (Eq. (3)) of the last solve, FP64,
+ * n_elem values in element order. */
+topo_status topo_sensitivity(topo_mesh* m, double* dc, size_t n_elem, int on_device);
+
+/* Copy the stored FP64 displacement out (n_dof = 3 * nodes, DOF order). */
+topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_device);
+
+/* Replace the stored displacement (warm start, checkpoint restore).
+ * Entries on fixed DOFs are ignored (held at zero). */
+topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, int on_device);
+
+/* y = M K M x with M the diagonal mask of free DOFs: entries of x on fixed
+ * DOFs are taken as 0 and y is 0 there (the operator the solver inverts on
+ * the free DOFs, Eq. (2)).  K comes from the current densities.  precision
+ * TOPO_PREC_FP64 or TOPO_PREC_FP32 selects the kernel (FP32 rounds x to
+ * float and returns y widened to double).  n_dof values in DOF order. */
+topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, size_t n_dof,
+                       int on_device);
+
+/* Launch the fine-grid FP32 (or FP64) operator kernel `reps` times on the
+ * mesh's stream over the mesh's internal vectors (no copies, no sync), for
+ * timing.  Cites Eq. (2) (K u). */
+topo_status topo_apply_internal(topo_mesh* m, int precision, int reps);
+
+/* Sizes and memory: nodes, free DOFs, bytes of device memory held. */
+topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_free_dof,
+                           long long* device_bytes);
+
+/* Device bytes a mesh of this size would hold after a solve with opts
+ * (NULL = defaults), for admission control.  No allocation. */
+long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* opts);
+
+/* Kernel timing: when enabled, the library records CUDA events around every
+ * launch of the fine-grid FP32 operator kernel during topo_solve and sums
+ * their durations; read (and reset) the total and the launch count. */
+topo_status topo_profile_enable(topo_mesh* m, int enable);
+topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches, int reset);
+
+/* Release everything the mesh holds (NULL-safe). */
+void topo_free(topo_mesh* m);
+
+/* Static string for a status code. */
+const char* topo_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOPO_H */

@@ -1,0 +1,231 @@
+// Shared device-side definitions of the SIMP state-solve library.
+//
+// Data layout in HBM (one mesh, one grid level):
+//   * vectors (displacement-like, 3 components) are SoA: component c lives at
+//     c * comp_stride; inside a component, node (i, j, k) with -1 <= i <= nx+1
+//     etc. is at (i+1) + px * ((j+1) + (ny+3) * (k+1)).  The ring i = -1,
+//     i = nx+1 (and likewise in j, k) is a ghost layer that always holds 0, so
+//     the 27-node gather never needs a bounds test, and px (a multiple of 4)
+//     keeps every row 16-byte aligned;
+//   * element arrays (E, rho) use the same idea with one ghost layer:
+//     element (i, j, k), -1 <= i <= nx, at (i+1) + ex * ((j+1) + (ny+2) * (k+1)),
+//     ghost elements hold E = 0, so they contribute nothing.
+//   Every vector entry of a fixed (Dirichlet) DOF is kept at 0 by all
+//   kernels, which is what lets the operator skip input masking.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace topo {
+
+enum Bc { BC_CANTILEVER = 0, BC_MBB = 1, BC_ROLLER_BOX = 2 };
+
+// k0 as a kernel parameter: 24x24 row-major, unit Young's modulus.  Read
+// with compile-time indices only, so every access is a constant-bank
+// operand of the FMA that uses it.
+template <typename T>
+struct K0 {
+  T v[576];
+};
+
+struct Dims {
+  int nx, ny, nz;    // elements per direction
+  int px;            // node row pitch (entries), >= nx + 3, multiple of 4
+  int ex;            // element row pitch, >= nx + 2, multiple of 4
+  int bc;            // Bc
+  int pin_j;         // MBB: j index of the single u_y pin (ny / 2)
+  long long comp;    // entries per vector component = px * (ny+3) * (nz+3)
+  long long ecount;  // entries of an element array = ex * (ny+2) * (nz+2)
+  __host__ __device__ long long node(int i, int j, int k) const {
+    return (long long)(i + 1) + (long long)px * ((j + 1) + (long long)(ny + 3) * (k + 1));
+  }
+  __host__ __device__ long long elem(int i, int j, int k) const {
+    return (long long)(i + 1) + (long long)ex * ((j + 1) + (long long)(ny + 2) * (k + 1));
+  }
+  __host__ __device__ long long row_stride() const { return px; }
+  __host__ __device__ long long plane_stride() const { return (long long)px * (ny + 3); }
+  __host__ __device__ long long erow() const { return ex; }
+  __host__ __device__ long long eplane() const { return (long long)ex * (ny + 2); }
+  // Is DOF c of node (i, j, k) held at zero?
+  __host__ __device__ bool fixed(int c, int i, int j, int k) const {
+    switch (bc) {
+      case BC_CANTILEVER:
+        return i == 0;
+      case BC_MBB:
+        return (c == 0 && i == 0) || (c == 2 && i == nx && k == 0) ||
+               (c == 1 && i == nx && k == 0 && j == pin_j);
+      default:
+        return (c == 0 && i == 0) || (c == 1 && j == 0) || (c == 2 && k == 0);
+    }
+  }
+};
+
+// Device-resident scalars of one preconditioned CG run.  All decisions
+// (alpha, beta, convergence) are taken on the device, so the host only reads
+// this struct once per chunk of iterations.
+struct PcgScalars {
+  double rz;      // r . z of the current iterate
+  double pq;      // p . A p
+  double alpha, beta;
+  double rr;      // r . r of the current iterate (recursive residual)
+  double rr0;     // r . r at the start
+  double tol2;    // stop when rr <= tol2
+  double aux[4];  // results of stand-alone reductions (dots, norms)
+  int iter;       // iterations done
+  int max_iter;   // stop (not converged) when iter reaches it
+  int done;       // 1: converged or stopped; every loop kernel returns at once
+  int status;     // 0 ok, 1 hit max_iter, 2 breakdown / non-finite
+  unsigned counter[8];  // last-block counters of the reductions (reset by the last block)
+};
+
+enum FinalizeOp {
+  FIN_NONE = 0,
+  FIN_ALPHA = 1,     // v0 = p.q           -> alpha = rz / pq
+  FIN_UPDATE = 2,    // v0 = r.z, v1 = r.r -> beta, iter++, convergence test
+  FIN_INIT = 3,      // v0 = r.z, v1 = r.r -> start values, tol2
+  FIN_AUX = 4,       // v0.. -> aux[0..]
+  FIN_RR_ONLY = 5,   // v0 = r.r           -> rr (used before a separate z = M r)
+  FIN_RZ_BETA = 6    // v0 = r.z           -> beta, iter++, convergence test on rr
+};
+
+constexpr int kMaxPartials = 16384;  // block partials per reduced value
+
+struct Red {
+  double* partials;   // [NV][kMaxPartials]
+  PcgScalars* sc;
+  int slot;           // which counter
+  int op;             // FinalizeOp
+  double rtol2;       // FIN_INIT: relative tolerance squared
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void finalize(const Red& red, const double* tot, int nv) {
+  PcgScalars* s = red.sc;
+  switch (red.op) {
+    case FIN_ALPHA: {
+      s->pq = tot[0];
+      double a = s->rz / tot[0];
+      if (!(tot[0] > 0.0) || !isfinite(a)) {  // breakdown: stop with status 2
+        s->status = 2;
+        s->done = 1;
+        a = 0.0;
+      }
+      s->alpha = a;
+      break;
+    }
+    case FIN_UPDATE:
+    case FIN_RZ_BETA: {
+      double rz_new = tot[0];
+      if (red.op == FIN_UPDATE && nv > 1) s->rr = tot[1];
+      s->beta = rz_new / s->rz;
+      s->rz = rz_new;
+      s->iter += 1;
+      if (!isfinite(s->rr) || !isfinite(rz_new)) {
+        s->status = 2;
+        s->done = 1;
+      } else if (s->rr <= s->tol2) {
+        s->done = 1;
+      } else if (s->iter >= s->max_iter) {
+        s->status = 1;
+        s->done = 1;
+      }
+      break;
+    }
+    case FIN_INIT: {
+      s->rz = tot[0];
+      s->rr = tot[nv - 1];
+      s->rr0 = tot[nv - 1];
+      s->tol2 = red.rtol2 * tot[nv - 1];
+      s->iter = 0;
+      s->status = 0;
+      s->done = (tot[nv - 1] <= 0.0) ? 1 : 0;
+      break;
+    }
+    case FIN_AUX:
+      for (int q = 0; q < nv && q < 4; ++q) s->aux[q] = tot[q];
+      break;
+    case FIN_RR_ONLY:
+      s->rr = tot[0];
+      if (!isfinite(tot[0])) {
+        s->status = 2;
+        s->done = 1;
+      } else if (tot[0] <= s->tol2) {  // converged: skip the preconditioner
+        s->iter += 1;
+        s->done = 1;
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+// Deterministic block-partial reduction of NV doubles with a last-block
+// finalisation: every block writes its partials, the last block to arrive
+// sums them in block order (fixed order => bitwise reproducible) and calls
+// finalize().  Must be called by every thread of every block.
+template <int NV>
+__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const Red& red) {
+  __shared__ double sh[NV][32];
+  __shared__ bool last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int warp = tid >> 5;
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int nwarps = (nthreads + 31) >> 5;
+  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double w = warp_sum(v[q]);
+    if ((tid & 31) == 0) sh[q][warp] = w;
+  }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double acc = 0.0;
+      for (int w = 0; w < nwarps; ++w) acc += sh[q][w];
+      red.partials[q * kMaxPartials + bid] = acc;
+    }
+    __threadfence();
+    unsigned prev = atomicAdd(&red.sc->counter[red.slot], 1u);
+    last = (prev == (unsigned)(nblocks - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tot[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double acc = 0.0;
+    for (int b = tid; b < nblocks; b += nthreads)
+      acc += __ldcg(&red.partials[q * kMaxPartials + b]);
+    tot[q] = acc;
+  }
+  __syncthreads();  // sh reuse
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double w = warp_sum(tot[q]);
+    if ((tid & 31) == 0) sh[q][warp] = w;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double fin[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double acc = 0.0;
+      for (int w = 0; w < nwarps; ++w) acc += sh[q][w];
+      fin[q] = acc;
+    }
+    finalize(red, fin, NV);
+    red.sc->counter[red.slot] = 0u;
+    __threadfence();
+  }
+}
+
+}  // namespace topo

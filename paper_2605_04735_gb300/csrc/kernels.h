@@ -1,0 +1,66 @@
+// Host-side launchers of the library's kernels (one declaration per kernel
+// family; definitions live in the .cu file of that family).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace topo {
+
+// ---- operator (operator.cu) -------------------------------------------
+enum ApplyMode {
+  APPLY_PLAIN = 0,  // y = A x
+  APPLY_DOT = 1,    // y = A x, reduce x . y
+  APPLY_RESID = 2   // y = f - A x (0 on fixed DOFs), reduce y . y
+};
+template <typename T>
+cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
+                         const Red& red, int mode, const int* done, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s);
+
+// ---- vectors (vectors.cu) -----------------------------------------------
+cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s);
+// n = total entries of one vector (3 * comp); all arrays 16-byte aligned
+template <typename T>
+cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, long long n,
+                            const Red& red, bool jacobi, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
+                              const Red& red, bool jacobi, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
+                        cudaStream_t s);
+// b32 = float(r64 * scale), scale = 1 / sqrt(sc->aux[0]) read on the device
+cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
+                                 cudaStream_t s);
+// u64 += scale * x, scale = sqrt(sc->aux[0]) read on the device (T = float or double)
+template <typename T>
+cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgScalars* sc,
+                              bool scaled, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s);
+
+// ---- mesh data (meshdata.cu) -------------------------------------------
+// rho (dense element order) -> ghosted rho32, E32, E64; counts bad values into *bad
+cudaError_t launch_simp(const float* rho, float* rho_g, float* E32, double* E64, const Dims& d,
+                        double E0, double Emin, double penal, double hscale, int* bad,
+                        cudaStream_t s);
+cudaError_t launch_build_load(double* f, const Dims& d, int load, double magnitude, double h,
+                              cudaStream_t s);
+// AoS (3n + c, dense node order) <-> ghosted SoA; unpack zeroes fixed DOFs
+template <typename T>
+cudaError_t launch_pack(const T* soa, double* aos, const Dims& d, cudaStream_t s);
+template <typename T>
+cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t s);
+cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
+                               const Dims& d, const K0<double>& k0, double penal, double dE,
+                               const Red& red, cudaStream_t s);
+
+}  // namespace topo

@@ -1,0 +1,193 @@
+// Per-element and per-node data kernels: SIMP interpolation (Eq. (1)),
+// the load vector, layout conversion at the ABI boundary, and the adjoint
+// sensitivity of the compliance (Eq. (3)) with the element-energy form of
+// the compliance (Eq. (2)) fused into the same pass.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace topo {
+
+namespace {
+
+__host__ __device__ constexpr int lidx(int dx, int dy, int dz) {
+  return 4 * dz + (dy ? (dx ? 2 : 3) : (dx ? 1 : 0));
+}
+
+// Eq. (1): E_e = Emin + rho_e^p (E0 - Emin), evaluated in FP64 and stored
+// both in FP64 and rounded to FP32; each scaled by the element size h
+// (k0 of an element of edge h is h times the unit-cube k0 in 3-D).
+__global__ void k_simp(const float* __restrict__ rho, float* __restrict__ rho_g,
+                       float* __restrict__ E32, double* __restrict__ E64, const Dims d, double E0,
+                       double Emin, double penal, double hscale, int* __restrict__ bad) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  int nbad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % d.nx);
+    const int j = (int)((e / d.nx) % d.ny);
+    const int k = (int)(e / ((long long)d.nx * d.ny));
+    float r = rho[e];
+    if (!(r >= 0.0f && r <= 1.0f)) {  // catches NaN too
+      ++nbad;
+      r = 0.0f;
+    }
+    const double rp = (penal == 3.0) ? (double)r * r * r : pow((double)r, penal);
+    const double Ee = (Emin + rp * (E0 - Emin)) * hscale;
+    const long long o = d.elem(i, j, k);
+    rho_g[o] = r;
+    E64[o] = Ee;
+    E32[o] = (float)Ee;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+// Consistent nodal forces of the load cases (component-major ghosted layout).
+__global__ void k_build_load(double* __restrict__ f, const Dims d, int load, double mag, double h) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (load == 0 || load == 1) {
+    // total `mag` in -z along a line of ny segments: ends get half a share
+    if (t > d.ny) return;
+    const int i = (load == 0) ? d.nx : 0;
+    const int k = (load == 0) ? 0 : d.nz;
+    const double share = mag / d.ny;
+    const double v = (t == 0 || t == d.ny) ? 0.5 * share : share;
+    f[2 * d.comp + d.node(i, t, k)] = -v;
+  } else {
+    // uniform +x traction `mag` per unit area on x = L: each face quad of
+    // area h^2 sends a quarter of its force to each of its corners
+    const int nyz = (d.ny + 1) * (d.nz + 1);
+    if (t >= nyz) return;
+    const int j = t % (d.ny + 1);
+    const int k = t / (d.ny + 1);
+    const int cj = (j == 0 || j == d.ny) ? 1 : 2;
+    const int ck = (k == 0 || k == d.nz) ? 1 : 2;
+    f[d.node(d.nx, j, k)] = mag * h * h * 0.25 * cj * ck;
+  }
+}
+
+template <typename T>
+__global__ void k_pack(const T* __restrict__ soa, double* __restrict__ aos, const Dims d) {
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (d.nx + 1));
+    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
+    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    const long long o = d.node(i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) aos[3 * n + c] = (double)soa[c * d.comp + o];
+  }
+}
+
+template <typename T>
+__global__ void k_unpack(const double* __restrict__ aos, T* __restrict__ soa, const Dims d) {
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (d.nx + 1));
+    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
+    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    const long long o = d.node(i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) soa[c * d.comp + o] = d.fixed(c, i, j, k) ? T(0) : (T)aos[3 * n + c];
+  }
+}
+
+// Eq. (3): dc_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e, FP64 throughout
+// (u_e^T k0 u_e as the symmetric quadratic form: 300 FMAs instead of 576);
+// also reduces sum_e E_e u_e^T k0 u_e (Eq. (2), element form) -> aux[0].
+__global__ void __launch_bounds__(256)
+    k_sensitivity(const double* __restrict__ u, const float* __restrict__ rho_g,
+                  const double* __restrict__ E64, double* __restrict__ dc, const Dims d,
+                  const __grid_constant__ K0<double> k0, double penal, double dE, const Red red) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  double part = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % d.nx);
+    const int j = (int)((e / d.nx) % d.ny);
+    const int k = (int)(e / ((long long)d.nx * d.ny));
+    double ue[24];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const long long o = d.node(i + dx, j + dy, k + dz);
+          const int a = lidx(dx, dy, dz);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ue[3 * a + c] = __ldg(u + c * d.comp + o);
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 24; ++a) {
+      double t = 0.5 * k0.v[a * 24 + a] * ue[a];
+#pragma unroll
+      for (int b = a + 1; b < 24; ++b) t = fma(k0.v[a * 24 + b], ue[b], t);
+      s = fma(2.0 * ue[a], t, s);
+    }
+    const long long og = d.elem(i, j, k);
+    const double r = (double)rho_g[og];
+    const double rp1 = (penal == 3.0) ? r * r : pow(r, penal - 1.0);
+    dc[e] = -penal * rp1 * dE * s;
+    part = fma(E64[og], s, part);
+  }
+  double v[1] = {part};
+  reduce_finalize<1>(v, red);
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_simp(const float* rho, float* rho_g, float* E32, double* E64, const Dims& d,
+                        double E0, double Emin, double penal, double hscale, int* bad,
+                        cudaStream_t s) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  k_simp<<<grid_for(n, 256), 256, 0, s>>>(rho, rho_g, E32, E64, d, E0, Emin, penal, hscale, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_load(double* f, const Dims& d, int load, double magnitude, double h,
+                              cudaStream_t s) {
+  const long long n = (load == 2) ? (long long)(d.ny + 1) * (d.nz + 1) : d.ny + 1;
+  k_build_load<<<(int)((n + 255) / 256), 256, 0, s>>>(f, d, load, magnitude, h);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pack(const T* soa, double* aos, const Dims& d, cudaStream_t s) {
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  k_pack<T><<<grid_for(nn, 256), 256, 0, s>>>(soa, aos, d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t s) {
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  k_unpack<T><<<grid_for(nn, 256), 256, 0, s>>>(aos, soa, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
+                               const Dims& d, const K0<double>& k0, double penal, double dE,
+                               const Red& red, cudaStream_t s) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  k_sensitivity<<<grid_for(n, 256), 256, 0, s>>>(u, rho_g, E64, dc, d, k0, penal, dE, red);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pack<float>(const float*, double*, const Dims&, cudaStream_t);
+template cudaError_t launch_pack<double>(const double*, double*, const Dims&, cudaStream_t);
+template cudaError_t launch_unpack<float>(const double*, float*, const Dims&, cudaStream_t);
+template cudaError_t launch_unpack<double>(const double*, double*, const Dims&, cudaStream_t);
+
+}  // namespace topo

@@ -1,0 +1,697 @@
+// Host runtime and C ABI of the SIMP state-solve library (include/topo.h).
+//
+// The runtime owns one mesh's device state and drives the solver:
+//   * FP64 iterative refinement (outer loop): r = f - K u in FP64 on the
+//     device, stop when ||r|| / ||f|| <= rtol, else solve K d = r / ||r||
+//     approximately with preconditioned CG and set u += ||r|| d;
+//   * the inner preconditioned CG runs in FP32 (or, for the plain FP64
+//     reference path, in FP64 to the final tolerance in one outer step);
+//     alpha, beta and the convergence test are taken on the device, and the
+//     host only reads the scalars once every `check_every` iterations.
+// The paper (Sec. 2.1.1) states the equilibrium K(rho) U = F but not how it
+// is solved; the refinement loop and CG are this library's choice.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/topo.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace topo;
+
+namespace {
+
+// --------------------------------------------------------------------------
+// k0 of the unit cube for E = 1 (Sec. 2.1.2), built from exact 1-D integrals
+// of the linear hat functions on [0, 1]:
+//   K[(a,p),(b,q)] = lam I(a,b; p,q) + mu I(a,b; q,p) + mu delta_pq sum_r I(a,b; r,r),
+//   I(a,b; s,t) = int dN_a/dx_s dN_b/dx_t dV = prod over directions of
+//   {int N'N', int N'N, int N N', int N N} of the 1-D factors.
+// --------------------------------------------------------------------------
+void build_k0(double nu, double* k) {
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double mu = 1.0 / (2.0 * (1.0 + nu));
+  const double M[2][2] = {{1.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 1.0 / 3.0}};  // int N_a N_b
+  const double S[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};                      // int N_a' N_b'
+  const double L[2][2] = {{-0.5, -0.5}, {0.5, 0.5}};                      // int N_a' N_b
+  static const int loc[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+  auto I = [&](int a, int b, int s, int t) {
+    double v = 1.0;
+    for (int r = 0; r < 3; ++r) {
+      const int ia = loc[a][r], ib = loc[b][r];
+      if (r == s && r == t)
+        v *= S[ia][ib];
+      else if (r == s)
+        v *= L[ia][ib];
+      else if (r == t)
+        v *= L[ib][ia];
+      else
+        v *= M[ia][ib];
+    }
+    return v;
+  };
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          double v = lam * I(a, b, p, q) + mu * I(a, b, q, p);
+          if (p == q) v += mu * (I(a, b, 0, 0) + I(a, b, 1, 1) + I(a, b, 2, 2));
+          k[(3 * a + p) * 24 + 3 * b + q] = v;
+        }
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double seconds() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+struct topo_mesh {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Dims d{};
+  topo_params prm{};
+  K0<double> k0d{};
+  K0<float> k0f{};
+  long long nvec = 0;  // entries of one 3-component vector (3 * comp)
+
+  // element data (ghosted)
+  float* rho_g = nullptr;
+  float* E32 = nullptr;
+  double* E64 = nullptr;
+  // FP64 state
+  double* f64 = nullptr;
+  double* u64 = nullptr;
+  double* r64 = nullptr;
+  // FP32 inner CG
+  float *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr,
+        *b32 = nullptr, *dinv32 = nullptr;
+  // FP64 inner CG (allocated on first FP64 solve)
+  double *x64 = nullptr, *s64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr,
+         *dinv64 = nullptr;
+  // scratch
+  PcgScalars* sc = nullptr;
+  PcgScalars* h_sc = nullptr;  // pinned mirror
+  double* partials = nullptr;
+  int* flags = nullptr;
+  double* aos = nullptr;       // n_dof doubles (ABI transfers)
+  double* dc = nullptr;        // n_elem doubles
+  float* rho_in = nullptr;     // n_elem floats (host-density staging)
+
+  bool has_density = false, solved = false, diag32 = false, diag64 = false;
+  double fnorm2 = 0.0;
+  long long bytes = 0;
+
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  double prof_ms = 0.0;
+  long long prof_launches = 0;
+};
+
+namespace {
+
+topo_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TOPO_OK;
+  if (e == cudaErrorMemoryAllocation) return TOPO_ERR_OOM;
+  return TOPO_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t err__ = (call);                   \
+    if (err__ != cudaSuccess) return cuda_status(err__); \
+  } while (0)
+
+template <typename T>
+topo_status dalloc(topo_mesh* m, T** p, long long count) {
+  const size_t bytes = (size_t)count * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TOPO_ERR_OOM;
+  }
+  e = cudaMemsetAsync(q, 0, bytes, m->stream);
+  if (e != cudaSuccess) {
+    cudaFree(q);
+    return TOPO_ERR_CUDA;
+  }
+  *p = static_cast<T*>(q);
+  m->bytes += (long long)bytes;
+  return TOPO_OK;
+}
+
+#define CKS(call)                        \
+  do {                                   \
+    topo_status st__ = (call);           \
+    if (st__ != TOPO_OK) return st__;    \
+  } while (0)
+
+Dims make_dims(int nx, int ny, int nz, int bc) {
+  Dims d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.px = ((nx + 3) + 3) / 4 * 4;
+  d.ex = ((nx + 2) + 3) / 4 * 4;
+  d.bc = bc;
+  d.pin_j = ny / 2;
+  d.comp = (long long)d.px * (ny + 3) * (nz + 3);
+  d.ecount = (long long)d.ex * (ny + 2) * (nz + 2);
+  return d;
+}
+
+Red red_of(topo_mesh* m, int op, double rtol2 = 0.0) {
+  Red r{};
+  r.partials = m->partials;
+  r.sc = m->sc;
+  r.slot = 0;
+  r.op = op;
+  r.rtol2 = rtol2;
+  return r;
+}
+
+topo_status sync_scalars(topo_mesh* m) {
+  CK(cudaMemcpyAsync(m->h_sc, m->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status ensure_fp64_inner(topo_mesh* m) {
+  if (m->x64) return TOPO_OK;
+  CKS(dalloc(m, &m->x64, m->nvec));
+  CKS(dalloc(m, &m->s64, m->nvec));
+  CKS(dalloc(m, &m->z64, m->nvec));
+  CKS(dalloc(m, &m->p64, m->nvec));
+  CKS(dalloc(m, &m->q64, m->nvec));
+  CKS(dalloc(m, &m->dinv64, m->nvec));
+  return TOPO_OK;
+}
+
+topo_status ensure_profile_events(topo_mesh* m, int n) {
+  while ((int)m->ev.size() < 2 * n) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    m->ev.push_back(e);
+  }
+  return TOPO_OK;
+}
+
+// Preconditioned CG on A x = b (A = masked stiffness operator in precision
+// T), from x = 0, to ||r|| <= rtol ||b||; returns iterations in *iters and
+// the device status (0 converged, 1 iteration cap, 2 breakdown).
+template <typename T>
+topo_status inner_pcg(topo_mesh* m, const T* b, T* x, T* r, T* z, T* p, T* q, const T* dinv,
+                      const T* E, const K0<T>& k0, double rtol, int max_iter, int check_every,
+                      bool profile, int* iters, int* dev_status) {
+  cudaStream_t s = m->stream;
+  CK(launch_set_max_iter(m->sc, max_iter, s));
+  CK(launch_pcg_init<T>(b, x, r, z, p, dinv, m->nvec, red_of(m, FIN_INIT, rtol * rtol), true, s));
+  const int* done = &m->sc->done;
+  int it_before = 0;
+  if (profile) CKS(ensure_profile_events(m, check_every));
+  for (;;) {
+    for (int c = 0; c < check_every; ++c) {
+      if (profile) CK(cudaEventRecord(m->ev[2 * c], s));
+      CK(launch_apply<T>(p, q, E, nullptr, m->d, k0, red_of(m, FIN_ALPHA), APPLY_DOT, done, s));
+      if (profile) CK(cudaEventRecord(m->ev[2 * c + 1], s));
+      CK(launch_pcg_update<T>(x, r, z, p, q, dinv, m->nvec, red_of(m, FIN_UPDATE), true, s));
+      CK(launch_pcg_direction<T>(p, z, m->nvec, m->sc, s));
+    }
+    CKS(sync_scalars(m));
+    if (profile) {
+      const int worked = std::min(check_every, m->h_sc->iter - it_before);
+      for (int c = 0; c < worked; ++c) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
+        m->prof_ms += ms;
+        m->prof_launches += 1;
+      }
+    }
+    if (m->h_sc->done) break;
+    if (m->h_sc->iter == it_before) return TOPO_ERR_CUDA;  // no progress without a stop: bug
+    it_before = m->h_sc->iter;
+  }
+  *iters = m->h_sc->iter;
+  *dev_status = m->h_sc->status;
+  return TOPO_OK;
+}
+
+topo_status residual64(topo_mesh* m, double* rr) {
+  CK(launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
+                          APPLY_RESID, nullptr, m->stream));
+  CKS(sync_scalars(m));
+  *rr = m->h_sc->aux[0];
+  return TOPO_OK;
+}
+
+topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* info) {
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  if (o->precision != TOPO_PREC_FP64 && o->precision != TOPO_PREC_FP32) return TOPO_ERR_INVALID;
+  if (o->precond != TOPO_PRECOND_JACOBI) return TOPO_ERR_INVALID;
+  if (!(o->rtol > 0.0) || o->max_iter < 1 || o->max_outer < 1 || o->check_every < 1 ||
+      o->check_every > 1024)
+    return TOPO_ERR_INVALID;
+  cudaStream_t s = m->stream;
+  const bool fp64 = (o->precision == TOPO_PREC_FP64);
+  if (fp64) {
+    CKS(ensure_fp64_inner(m));
+    if (!m->diag64) {
+      CK(launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, s));
+      m->diag64 = true;
+    }
+  } else if (!m->diag32) {
+    CK(launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s));
+    m->diag32 = true;
+  }
+  m->solved = false;
+  double rr = 0.0;
+  if (o->warm_start) {
+    CKS(residual64(m, &rr));
+  } else {
+    CK(cudaMemsetAsync(m->u64, 0, sizeof(double) * m->nvec, s));
+    CK(cudaMemcpyAsync(m->r64, m->f64, sizeof(double) * m->nvec, cudaMemcpyDeviceToDevice, s));
+    rr = m->fnorm2;
+    // aux[0] must hold ||r||^2 for the scaled narrowing below
+    CK(launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s));
+  }
+  int total_iters = 0, outer = 0;
+  topo_status st = TOPO_OK;
+  const double fn = std::sqrt(m->fnorm2);
+  for (;;) {
+    if (!std::isfinite(rr)) {
+      st = TOPO_ERR_NAN;
+      break;
+    }
+    const double rel = fn > 0 ? std::sqrt(rr) / fn : 0.0;
+    if (info) info->rel_residual = rel;
+    if (rel <= o->rtol) break;
+    if (outer >= o->max_outer || total_iters >= o->max_iter) {
+      st = TOPO_ERR_NOT_CONVERGED;
+      break;
+    }
+    int it = 0, dst = 0;
+    const int budget = o->max_iter - total_iters;
+    if (fp64) {
+      // target the final tolerance directly (relative to this rhs), with margin
+      double inner = 0.5 * o->rtol * fn / std::sqrt(rr);
+      inner = std::min(std::max(inner, 1e-15), 0.5);
+      CKS(inner_pcg<double>(m, m->r64, m->x64, m->s64, m->z64, m->p64, m->q64, m->dinv64, m->E64,
+                            m->k0d, inner, budget, o->check_every, false, &it, &dst));
+      CK(launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, s));
+    } else {
+      CK(launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s));
+      double inner = std::max(o->inner_rtol, 0.25 * o->rtol * fn / std::sqrt(rr));
+      inner = std::min(inner, 0.5);
+      CKS(inner_pcg<float>(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32, m->E32,
+                           m->k0f, inner, budget, o->check_every, m->prof, &it, &dst));
+      // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
+      CK(launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s));
+    }
+    total_iters += it;
+    ++outer;
+    if (dst == 2) {
+      st = TOPO_ERR_NAN;
+      break;
+    }
+    CKS(residual64(m, &rr));
+  }
+  if (info) {
+    info->iters = total_iters;
+    info->outer = outer;
+  }
+  if (st == TOPO_OK) m->solved = true;
+  return st;
+}
+
+topo_status upload_f64(topo_mesh* m, const double* src, double* dst_soa, size_t n_dof,
+                       int on_device) {
+  cudaStream_t s = m->stream;
+  const double* a = src;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(m->aos, src, n_dof * sizeof(double), cudaMemcpyHostToDevice, s));
+    a = m->aos;
+  }
+  CK(launch_unpack<double>(a, dst_soa, m->d, s));
+  return TOPO_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+extern "C" {
+
+void topo_default_params(topo_params* p) {
+  if (!p) return;
+  p->E0 = 1.0;
+  p->Emin = 1e-9;
+  p->nu = 0.3;
+  p->penal = 3.0;
+  p->h = 1.0;
+  p->load = 1.0;
+}
+
+void topo_default_opts(topo_solve_opts* o) {
+  if (!o) return;
+  o->precision = TOPO_PREC_FP32;
+  o->precond = TOPO_PRECOND_JACOBI;
+  o->rtol = 1e-8;
+  o->inner_rtol = 1e-5;
+  o->max_iter = 100000;
+  o->max_outer = 12;
+  o->warm_start = 0;
+  o->gmg_levels = 0;
+  o->smooth_degree = 3;
+  o->check_every = 16;
+}
+
+const char* topo_status_string(int status) {
+  switch (status) {
+    case TOPO_OK: return "ok";
+    case TOPO_ERR_INVALID: return "invalid argument";
+    case TOPO_ERR_OOM: return "out of memory";
+    case TOPO_ERR_CUDA: return "CUDA error";
+    case TOPO_ERR_NO_DENSITY: return "no density set";
+    case TOPO_ERR_NOT_SOLVED: return "not solved";
+    case TOPO_ERR_NOT_CONVERGED: return "not converged";
+    case TOPO_ERR_NAN: return "non-finite or out-of-range value";
+    case TOPO_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+void topo_free(topo_mesh* m) {
+  if (!m) return;
+  cudaSetDevice(m->dev);
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  void* ptrs[] = {m->rho_g, m->E32,  m->E64,  m->f64, m->u64,  m->r64, m->x32, m->r32,
+                  m->z32,   m->p32,  m->q32,  m->b32, m->dinv32, m->x64, m->s64, m->z64,
+                  m->p64,   m->q64,  m->dinv64, m->sc, m->partials, m->flags, m->aos, m->dc,
+                  m->rho_in};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (m->h_sc) cudaFreeHost(m->h_sc);
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+}
+
+static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
+                               void* stream, topo_mesh* m) {
+  CK(cudaGetDevice(&m->dev));
+  if (stream) {
+    m->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+    m->own_stream = true;
+  }
+  m->d = make_dims(nx, ny, nz, bc);
+  m->nvec = 3 * m->d.comp;
+  if (prm)
+    m->prm = *prm;
+  else
+    topo_default_params(&m->prm);
+  double k[576];
+  build_k0(m->prm.nu, k);
+  for (int t = 0; t < 576; ++t) {
+    m->k0d.v[t] = k[t];
+    m->k0f.v[t] = (float)k[t];
+  }
+  const long long ne = m->d.ecount;
+  CKS(dalloc(m, &m->rho_g, ne));
+  CKS(dalloc(m, &m->E32, ne));
+  CKS(dalloc(m, &m->E64, ne));
+  CKS(dalloc(m, &m->f64, m->nvec));
+  CKS(dalloc(m, &m->u64, m->nvec));
+  CKS(dalloc(m, &m->r64, m->nvec));
+  CKS(dalloc(m, &m->x32, m->nvec));
+  CKS(dalloc(m, &m->r32, m->nvec));
+  CKS(dalloc(m, &m->z32, m->nvec));
+  CKS(dalloc(m, &m->p32, m->nvec));
+  CKS(dalloc(m, &m->q32, m->nvec));
+  CKS(dalloc(m, &m->b32, m->nvec));
+  CKS(dalloc(m, &m->dinv32, m->nvec));
+  CKS(dalloc(m, &m->sc, 1));
+  CKS(dalloc(m, &m->partials, 4LL * kMaxPartials));
+  CKS(dalloc(m, &m->flags, 4));
+  const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  CKS(dalloc(m, &m->aos, 3 * nn));
+  CK(cudaMallocHost(&m->h_sc, sizeof(PcgScalars)));
+  std::memset(m->h_sc, 0, sizeof(PcgScalars));
+  CK(launch_build_load(m->f64, m->d, load, m->prm.load, m->prm.h, m->stream));
+  CK(launch_dot<double>(m->f64, m->f64, m->nvec, red_of(m, FIN_AUX), m->stream));
+  CKS(sync_scalars(m));
+  m->fnorm2 = m->h_sc->aux[0];
+  return TOPO_OK;
+}
+
+topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
+                             void* stream, topo_mesh** out) {
+  if (!out) return TOPO_ERR_INVALID;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
+  if (bc < 0 || bc > 2 || load < 0 || load > 2) return TOPO_ERR_INVALID;
+  if (bc == TOPO_BC_MBB && (ny % 2)) return TOPO_ERR_INVALID;
+  if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
+              !(prm->E0 > 0.0) || !(prm->Emin >= 0.0) || !(prm->Emin < prm->E0)))
+    return TOPO_ERR_INVALID;
+  topo_mesh* m = new (std::nothrow) topo_mesh();
+  if (!m) return TOPO_ERR_OOM;
+  topo_status st = create_impl(nx, ny, nz, bc, load, prm, stream, m);
+  if (st != TOPO_OK) {
+    topo_free(m);
+    return st;
+  }
+  *out = m;
+  return TOPO_OK;
+}
+
+topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int on_device) {
+  if (!m || !rho) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  CK(cudaSetDevice(m->dev));
+  cudaStream_t s = m->stream;
+  const float* src = rho;
+  if (!on_device) {
+    if (!m->rho_in) CKS(dalloc(m, &m->rho_in, ne));
+    CK(cudaMemcpyAsync(m->rho_in, rho, ne * sizeof(float), cudaMemcpyHostToDevice, s));
+    src = m->rho_in;
+  }
+  CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
+  CK(launch_simp(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin, m->prm.penal,
+                 m->prm.h, m->flags, s));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  m->diag32 = m->diag64 = false;
+  m->solved = false;
+  m->has_density = (bad == 0);
+  return bad ? TOPO_ERR_NAN : TOPO_OK;
+}
+
+topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_info* info) {
+  Timer t;
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!m) {
+    if (info) info->status = TOPO_ERR_INVALID;
+    return TOPO_ERR_INVALID;
+  }
+  topo_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    topo_default_opts(&o);
+  topo_status st;
+  if (cudaSetDevice(m->dev) != cudaSuccess)
+    st = TOPO_ERR_CUDA;
+  else
+    st = do_solve(m, &o, info);
+  if (info) {
+    info->status = st;
+    info->seconds = t.seconds();
+  }
+  return st;
+}
+
+topo_status topo_compliance(topo_mesh* m, double* c) {
+  if (!m || !c) return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  CK(cudaSetDevice(m->dev));
+  CK(launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), m->stream));
+  CKS(sync_scalars(m));
+  *c = m->h_sc->aux[0];
+  return TOPO_OK;
+}
+
+static topo_status sens_impl(topo_mesh* m) {
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if (!m->dc) CKS(dalloc(m, &m->dc, ne));
+  CK(launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->k0d, m->prm.penal,
+                        (m->prm.E0 - m->prm.Emin) * m->prm.h, red_of(m, FIN_AUX), m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_compliance_energy(topo_mesh* m, double* c) {
+  if (!m || !c) return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  CK(cudaSetDevice(m->dev));
+  CKS(sens_impl(m));
+  CKS(sync_scalars(m));
+  *c = m->h_sc->aux[0];
+  return TOPO_OK;
+}
+
+topo_status topo_sensitivity(topo_mesh* m, double* dc, size_t n_elem, int on_device) {
+  if (!m || !dc) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  CK(cudaSetDevice(m->dev));
+  CKS(sens_impl(m));
+  CK(cudaMemcpyAsync(dc, m->dc, ne * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_device) {
+  if (!m || !u) return TOPO_ERR_INVALID;
+  const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
+  CK(cudaSetDevice(m->dev));
+  double* dst = on_device ? u : m->aos;
+  CK(launch_pack<double>(m->u64, dst, m->d, m->stream));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(u, m->aos, nd * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, int on_device) {
+  if (!m || !u) return TOPO_ERR_INVALID;
+  const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
+  CK(cudaSetDevice(m->dev));
+  CKS(upload_f64(m, u, m->u64, n_dof, on_device));
+  m->solved = false;
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, size_t n_dof,
+                       int on_device) {
+  if (!m || !x || !y) return TOPO_ERR_INVALID;
+  if (precision != TOPO_PREC_FP64 && precision != TOPO_PREC_FP32) return TOPO_ERR_INVALID;
+  const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  CK(cudaSetDevice(m->dev));
+  cudaStream_t s = m->stream;
+  const double* src = x;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(m->aos, x, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = m->aos;
+  }
+  if (precision == TOPO_PREC_FP64) {
+    CKS(ensure_fp64_inner(m));
+    CK(launch_unpack<double>(src, m->p64, m->d, s));
+    CK(launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, red_of(m, FIN_NONE),
+                            APPLY_PLAIN, nullptr, s));
+    CK(launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
+  } else {
+    CK(launch_unpack<float>(src, m->p32, m->d, s));
+    CK(launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+                           APPLY_PLAIN, nullptr, s));
+    CK(launch_pack<float>(m->q32, on_device ? y : m->aos, m->d, s));
+  }
+  if (!on_device) {
+    CK(cudaMemcpyAsync(y, m->aos, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_apply_internal(topo_mesh* m, int precision, int reps) {
+  if (!m || reps < 0) return TOPO_ERR_INVALID;
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  CK(cudaSetDevice(m->dev));
+  for (int r = 0; r < reps; ++r) {
+    if (precision == TOPO_PREC_FP64) {
+      CKS(ensure_fp64_inner(m));
+      CK(launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
+                              red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->stream));
+    } else if (precision == TOPO_PREC_FP32) {
+      CK(launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+                             APPLY_PLAIN, nullptr, m->stream));
+    } else {
+      return TOPO_ERR_INVALID;
+    }
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_free_dof,
+                           long long* device_bytes) {
+  if (!m) return TOPO_ERR_INVALID;
+  const Dims& d = m->d;
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  long long fixed = 0;
+  const long long face = (long long)(d.ny + 1) * (d.nz + 1);
+  if (d.bc == BC_CANTILEVER)
+    fixed = 3 * face;
+  else if (d.bc == BC_MBB)
+    fixed = face + (d.ny + 1) + 1;
+  else
+    fixed = face + (long long)(d.nx + 1) * (d.nz + 1) + (long long)(d.nx + 1) * (d.ny + 1);
+  if (n_nodes) *n_nodes = nn;
+  if (n_free_dof) *n_free_dof = 3 * nn - fixed;
+  if (device_bytes) *device_bytes = m->bytes;
+  return TOPO_OK;
+}
+
+long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* opts) {
+  if (nx < 1 || ny < 1 || nz < 1) return -1;
+  Dims d = make_dims(nx, ny, nz, 0);
+  const long long nvec = 3 * d.comp;
+  long long b = d.ecount * (4 + 4 + 8);      // rho, E32, E64
+  b += nvec * (3 * 8 + 7 * 4);                // f, u, r (FP64) + 7 FP32 CG vectors
+  b += (long long)sizeof(PcgScalars) + 4LL * kMaxPartials * 8 + 16;
+  b += 3LL * (nx + 1) * (ny + 1) * (nz + 1) * 8;  // ABI staging
+  b += (long long)nx * ny * nz * (8 + 4);          // sensitivities + density staging
+  if (opts && opts->precision == TOPO_PREC_FP64) b += nvec * 6 * 8;
+  return b;
+}
+
+topo_status topo_profile_enable(topo_mesh* m, int enable) {
+  if (!m) return TOPO_ERR_INVALID;
+  m->prof = enable != 0;
+  return TOPO_OK;
+}
+
+topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches, int reset) {
+  if (!m) return TOPO_ERR_INVALID;
+  if (total_ms) *total_ms = m->prof_ms;
+  if (launches) *launches = m->prof_launches;
+  if (reset) {
+    m->prof_ms = 0.0;
+    m->prof_launches = 0;
+  }
+  return TOPO_OK;
+}
+
+}  // extern "C"

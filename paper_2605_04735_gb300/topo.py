@@ -1,0 +1,233 @@
+"""Python binding of libtopo.so (ctypes): argument marshalling only.
+
+Every step of the solve, compliance and sensitivity runs in the library's
+CUDA kernels.  Device memory and streams may come from PyTorch: pass CUDA
+tensors and they are handed over by pointer (no copy); numpy arrays are
+passed as host pointers and copied by the library.  There is no CPU
+fallback: if the library is missing this module raises on import use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtopo.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NO_DENSITY, ERR_NOT_SOLVED, ERR_NOT_CONVERGED, \
+    ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX = 0, 1, 2
+LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
+PREC_FP64, PREC_FP32 = 0, 1
+PRECOND_JACOBI, PRECOND_GMG = 0, 1
+
+
+class Params(C.Structure):
+    _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double),
+                ("penal", C.c_double), ("h", C.c_double), ("load", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
+                ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
+                ("warm_start", C.c_int), ("gmg_levels", C.c_int), ("smooth_degree", C.c_int),
+                ("check_every", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
+                ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+
+class TopoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libtopo.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtopo.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i, sz, d = C.c_void_p, C.c_int, C.c_size_t, C.c_double
+        sig = {
+            "topo_default_params": (None, [C.POINTER(Params)]),
+            "topo_default_opts": (None, [C.POINTER(SolveOpts)]),
+            "topo_create_mesh": (i, [i, i, i, i, i, C.POINTER(Params), vp, C.POINTER(vp)]),
+            "topo_set_density": (i, [vp, vp, sz, i]),
+            "topo_solve": (i, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+            "topo_compliance": (i, [vp, C.POINTER(d)]),
+            "topo_compliance_energy": (i, [vp, C.POINTER(d)]),
+            "topo_sensitivity": (i, [vp, vp, sz, i]),
+            "topo_get_displacement": (i, [vp, vp, sz, i]),
+            "topo_set_displacement": (i, [vp, vp, sz, i]),
+            "topo_apply": (i, [vp, i, vp, vp, sz, i]),
+            "topo_apply_internal": (i, [vp, i, i]),
+            "topo_mesh_info": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_longlong)]),
+            "topo_footprint_bytes": (C.c_longlong, [i, i, i, C.POINTER(SolveOpts)]),
+            "topo_profile_enable": (i, [vp, i]),
+            "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong), i]),
+            "topo_free": (None, [vp]),
+            "topo_status_string": (C.c_char_p, [i]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(st: int) -> str:
+    return lib().topo_status_string(int(st)).decode()
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise TopoError(st, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().topo_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().topo_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def footprint_bytes(nx, ny, nz, opts: SolveOpts | None = None) -> int:
+    return int(lib().topo_footprint_bytes(nx, ny, nz, C.byref(opts) if opts else None))
+
+
+def _ptr(a, dtype):
+    """(pointer, count, on_device) of a numpy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+        return a.ctypes.data, a.size, 0
+    # torch tensor (duck-typed so numpy users need no torch)
+    if not a.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    want = {np.float32: "torch.float32", np.float64: "torch.float64"}[dtype]
+    if str(a.dtype) != want:
+        raise TypeError(f"expected {want}, got {a.dtype}")
+    return a.data_ptr(), a.numel(), 1 if a.is_cuda else 0
+
+
+class Mesh:
+    """One structured hex8 design domain held on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, bc=BC_CANTILEVER, load=LOAD_EDGE_XL_BOTTOM,
+                 params: Params | None = None, stream=None):
+        L = lib()
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(L.topo_create_mesh(nx, ny, nz, bc, load, C.byref(params) if params else None, s,
+                                  C.byref(h)), "topo_create_mesh")
+        self._h = h
+        self.nx, self.ny, self.nz, self.bc, self.load = nx, ny, nz, bc, load
+        self.n_elem = nx * ny * nz
+        self.n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
+        self.n_dof = 3 * self.n_nodes
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().topo_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_density(self, rho):
+        p, n, dev = _ptr(rho, np.float32)
+        _check(lib().topo_set_density(self._h, p, n, dev), "topo_set_density")
+
+    def solve(self, opts: SolveOpts | None = None, check: bool = True) -> SolveInfo:
+        info = SolveInfo()
+        st = lib().topo_solve(self._h, C.byref(opts) if opts else None, C.byref(info))
+        if check:
+            _check(st, "topo_solve")
+        return info
+
+    def compliance(self) -> float:
+        c = C.c_double()
+        _check(lib().topo_compliance(self._h, C.byref(c)), "topo_compliance")
+        return c.value
+
+    def compliance_energy(self) -> float:
+        c = C.c_double()
+        _check(lib().topo_compliance_energy(self._h, C.byref(c)), "topo_compliance_energy")
+        return c.value
+
+    def sensitivity(self, out=None):
+        if out is None:
+            out = np.empty(self.n_elem, dtype=np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_sensitivity(self._h, p, n, dev), "topo_sensitivity")
+        return out
+
+    def displacement(self, out=None):
+        if out is None:
+            out = np.empty(self.n_dof, dtype=np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_get_displacement(self._h, p, n, dev), "topo_get_displacement")
+        return out
+
+    def set_displacement(self, u):
+        p, n, dev = _ptr(u, np.float64)
+        _check(lib().topo_set_displacement(self._h, p, n, dev), "topo_set_displacement")
+
+    def apply(self, x, precision=PREC_FP64, out=None):
+        if out is None:
+            out = np.empty(self.n_dof, dtype=np.float64)
+        px, n, dev = _ptr(x, np.float64)
+        py, n2, dev2 = _ptr(out, np.float64)
+        if dev != dev2:
+            raise TypeError("x and out must both be host or both be device arrays")
+        _check(lib().topo_apply(self._h, precision, px, py, n, dev), "topo_apply")
+        return out
+
+    def apply_internal(self, precision=PREC_FP32, reps=1):
+        _check(lib().topo_apply_internal(self._h, precision, reps), "topo_apply_internal")
+
+    def info(self):
+        a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(lib().topo_mesh_info(self._h, C.byref(a), C.byref(b), C.byref(c)), "topo_mesh_info")
+        return {"n_nodes": a.value, "n_free_dof": b.value, "device_bytes": c.value}
+
+    def profile(self, enable=True):
+        _check(lib().topo_profile_enable(self._h, int(enable)), "topo_profile_enable")
+
+    def profile_read(self, reset=True):
+        ms, n = C.c_double(), C.c_longlong()
+        _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), int(reset)),
+               "topo_profile_read")
+        return ms.value, n.value
