@@ -1,0 +1,354 @@
+"""Benchmark: PCG state solves/s (true FP64 relative residual 1e-8) of the
+SIMP state solve + compliance + sensitivities, on the MBB half-beam
+96x32x32 workload (cone-smoothed seeded densities), one JSON line.
+
+A step is one pass of the whole hot path over one design: density upload
+and SIMP interpolation (Eq. (1)), the state solve K(rho) u = f (Eq. (2)) to
+rel. residual 1e-8, the compliance f^T u and the element sensitivities
+(Eq. (3)).  `value` times steps with inputs already in HBM (device
+timeline, CUDA events on the library's stream, L2 flushed between steps);
+`e2e` times the same through the public API with host buffers.
+
+Under torchrun every rank solves its own independent designs (weak
+scaling); the only collectives are the timing barrier and max-reduction.
+`--impl reference` times the CPU oracle (banded Cholesky) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_04735_gb300 import inputs as I  # noqa: E402
+
+METRIC = "PCG state solves/s at true FP64 rel. residual 1e-8 (solve + compliance + sensitivity)"
+UNIT = "solves/s"
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(workload: I.Workload, budget_s: float = 20.0):
+    """The oracle (assembled K, banded Cholesky, compliance, sensitivities)
+    timed on a slab of the workload with the same y-z cross-section and fewer
+    x layers, scaled to the full problem by the number of free DOFs (the
+    banded factorisation costs n * b^2 with the same band b)."""
+    from oracle import fem
+    nx_s = max(2, min(workload.nx, 12))
+    t_tot, n = 0.0, 0
+    rho_full = workload.density().reshape(workload.nz, workload.ny, workload.nx)
+    rho = np.ascontiguousarray(rho_full[:, :, :nx_s]).reshape(-1)
+    free_s = None
+    while t_tot < budget_s / 2 or n == 0:
+        t0 = time.perf_counter()
+        P = fem.Problem(nx_s, workload.ny, workload.nz, workload.bc, workload.load, rho)
+        u = P.solve()
+        P.compliance(u)
+        P.sensitivity(u)
+        t_tot += time.perf_counter() - t0
+        n += 1
+        free_s = int((~P.fixed).sum())
+        if n >= 3:
+            break
+    g = fem.Grid(workload.nx, workload.ny, workload.nz)
+    free_full = int((~fem.fixed_dofs(g, workload.bc)).sum())
+    t_full = (t_tot / n) * free_full / free_s
+    cores = os.cpu_count() or 1
+    return {"value": 1.0 / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle solve(s) of the {nx_s}x{workload.ny}x{workload.nz} slab "
+                      f"(same cross-section and band), {t_tot / n:.2f} s each, scaled by free DOFs "
+                      f"{free_full}/{free_s}; LAPACK threads = all {cores} host cores"}
+
+
+def run_reference(args, workload):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import fem
+    nx_s = max(2, min(workload.nx, 12))
+    rho_full = workload.density().reshape(workload.nz, workload.ny, workload.nx)
+    rho = np.ascontiguousarray(rho_full[:, :, :nx_s]).reshape(-1)
+    g = fem.Grid(workload.nx, workload.ny, workload.nz)
+    free_full = int((~fem.fixed_dofs(g, workload.bc)).sum())
+    times = []
+    free_s = None
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        P = fem.Problem(nx_s, workload.ny, workload.nz, workload.bc, workload.load, rho)
+        u = P.solve()
+        P.compliance(u)
+        P.sensitivity(u)
+        dt = time.perf_counter() - t0
+        free_s = int((~P.fixed).sum())
+        if it >= args.warmup:
+            times.append(dt * free_full / free_s)
+    ms = 1e3 * float(np.mean(times))
+    value = 1e3 / ms
+    cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload.name, "nx": workload.nx, "ny": workload.ny,
+                       "nz": workload.nz, "rtol": 1e-8, "solver": "banded Cholesky (LAPACK)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: oracle solve of the {nx_s}x{workload.ny}x"
+                                       f"{workload.nz} slab, scaled by free DOFs {free_full}/"
+                                       f"{free_s}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mbb_96x32x32", choices=sorted(I.WORKLOADS))
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--precond", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    workload = I.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, workload)
+        return
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2605_04735_gb300 import build as _b
+    if not os.path.exists(os.path.join(ROOT, "paper_2605_04735_gb300", "libtopo.so")):
+        _b.build()
+    from paper_2605_04735_gb300 import topo
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = workload
+    # each rank gets its own design (independent problems: weak scaling)
+    rho_np = w.density() if rank == 0 else I.dataclasses.replace(w, seed=w.seed + 1000 * rank).density()
+    rho_dev = torch.from_numpy(rho_np).cuda()
+    dc_dev = torch.empty(w.n_elem, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    mesh = topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream)
+    opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
+
+    def step(m, opt, rho, dc):
+        m.set_density(rho)
+        info = m.solve(opt)
+        c = m.compliance()
+        m.sensitivity(dc)
+        return info, c
+
+    for _ in range(args.warmup):
+        step(mesh, opts, rho_dev, dc_dev)
+    torch.cuda.synchronize()
+    mesh.profile_read(reset=True)
+    mesh.profile(True)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict the previous step's data from L2
+            ev[k][0].record(stream)
+            info, c = step(mesh, opts, rho_dev, dc_dev)
+            ev[k][1].record(stream)
+            infos.append((info.iters, info.outer, info.rel_residual, c))
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    prof_ms, prof_n, launches = mesh.profile_read(reset=True)
+    mesh.profile(False)
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1e3)
+
+    # e2e through the public API with host buffers (pinned), same metric
+    rho_host = torch.from_numpy(rho_np).pin_memory()
+    dc_host = torch.empty(w.n_elem, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(mesh, opts, rho_host.numpy(), dc_host.numpy())
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = ws / float(np.mean(e2e_t))
+
+    # plain FP64 Jacobi-PCG GPU path on the same design (the comparison path)
+    fp64 = None
+    if args.fp64_steps > 0 and rank == 0:
+        o64 = topo.default_opts(precision=topo.PREC_FP64, precond=topo.PRECOND_JACOBI, rtol=1e-8)
+        step(mesh, o64, rho_dev, dc_dev)
+        ts, its = [], []
+        for k in range(args.fp64_steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info, _ = step(mesh, o64, rho_dev, dc_dev)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+            its.append(info.iters)
+        fp64 = {"solves_per_s": 1e3 / float(np.mean(ts)), "ms_per_solve": float(np.mean(ts)),
+                "iters": int(np.mean(its))}
+
+    if rank != 0:
+        mesh.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, peaks_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    avg_ms = prof_ms / max(prof_n, 1)
+    flop_launch = 1152.0 * w.n_elem
+    achieved = flop_launch / (avg_ms * 1e-3) / 1e12
+    gdofs = 3.0 * w.n_nodes / (avg_ms * 1e-3) / 1e9
+    iters = [x[0] for x in infos]
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == 1 else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz,
+                   "n_dof": 3 * w.n_nodes, "bc": "mbb" if w.bc == 1 else "cantilever",
+                   "density": w.recipe, "rtol": 1e-8,
+                   "solver": ("FP32 PCG + FP64 refinement" if args.precision == 1 else "FP64 PCG")
+                   + (" / Jacobi" if args.precond == 0 else " / GMG V-cycle"),
+                   "l2": "flushed between steps (256 MB write)"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "solve": {"iters_mean": float(np.mean(iters)), "outer_mean": float(np.mean([x[1] for x in infos])),
+                  "rel_residual_max": float(max(x[2] for x in infos)),
+                  "compliance": infos[-1][3]},
+        "matvec": {"kernel": "k_apply<float> (27-node gather, FP32)", "launches": prof_n,
+                   "avg_us": avg_ms * 1e3, "gdofs": gdofs},
+        "fp64_jacobi_pcg": fp64,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": f"derived: {FP32_PEAK_NOTE} (FP32 SIMT is not in "
+                                    f"MEASURED_PEAKS.json); algorithmic 1152 flop/element"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem,
+                "d2h_bytes_per_step": 8 * w.n_elem + 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    mesh.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

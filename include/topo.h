@@ -181,9 +181,13 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
 
 /* Kernel timing: when enabled, the library records CUDA events around every
  * launch of the fine-grid FP32 operator kernel during topo_solve and sums
- * their durations; read (and reset) the total and the launch count. */
+ * their durations.  topo_profile_read returns (and with reset != 0 zeroes)
+ * that total, the number of such launches, and the number of all kernel
+ * launches the mesh has made (counted whether or not timing is enabled).
+ * Any output pointer may be NULL. */
 topo_status topo_profile_enable(topo_mesh* m, int enable);
-topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches, int reset);
+topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches,
+                              long long* all_launches, int reset);
 
 /* Release everything the mesh holds (NULL-safe). */
 void topo_free(topo_mesh* m);

@@ -61,6 +61,21 @@ struct Dims {
   }
 };
 
+// Layout of a grid of nx*ny*nz elements (pitches padded to 4 entries).
+inline Dims make_dims(int nx, int ny, int nz, int bc, int pin_j) {
+  Dims d{};
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.px = ((nx + 3) + 3) / 4 * 4;
+  d.ex = ((nx + 2) + 3) / 4 * 4;
+  d.bc = bc;
+  d.pin_j = pin_j;
+  d.comp = (long long)d.px * (ny + 3) * (nz + 3);
+  d.ecount = (long long)d.ex * (ny + 2) * (nz + 2);
+  return d;
+}
+
 // Device-resident scalars of one preconditioned CG run.  All decisions
 // (alpha, beta, convergence) are taken on the device, so the host only reads
 // this struct once per chunk of iterations.
@@ -86,7 +101,8 @@ enum FinalizeOp {
   FIN_INIT = 3,      // v0 = r.z, v1 = r.r -> start values, tol2
   FIN_AUX = 4,       // v0.. -> aux[0..]
   FIN_RR_ONLY = 5,   // v0 = r.r           -> rr (used before a separate z = M r)
-  FIN_RZ_BETA = 6    // v0 = r.z           -> beta, iter++, convergence test on rr
+  FIN_RZ_BETA = 6,   // v0 = r.z           -> beta, iter++, convergence test on rr
+  FIN_SET_RZ = 7     // v0 = r.z           -> rz, beta = 0 (first direction p = z)
 };
 
 constexpr int kMaxPartials = 16384;  // block partials per reduced value
@@ -126,7 +142,7 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
       s->beta = rz_new / s->rz;
       s->rz = rz_new;
       s->iter += 1;
-      if (!isfinite(s->rr) || !isfinite(rz_new)) {
+      if (!isfinite(s->rr) || !isfinite(rz_new) || !(rz_new > 0.0)) {
         s->status = 2;
         s->done = 1;
       } else if (s->rr <= s->tol2) {
@@ -149,6 +165,14 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
     }
     case FIN_AUX:
       for (int q = 0; q < nv && q < 4; ++q) s->aux[q] = tot[q];
+      break;
+    case FIN_SET_RZ:
+      s->rz = tot[0];
+      s->beta = 0.0;
+      if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+        s->status = 2;
+        s->done = 1;
+      }
       break;
     case FIN_RR_ONLY:
       s->rr = tot[0];

@@ -1,0 +1,548 @@
+// Geometric multigrid V-cycle (see gmg.h).  All grid transfers are gathers
+// (no atomics); the Chebyshev smoother's vector updates are fused into the
+// operator kernel's epilogue, so one smoothing step is one pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "gmg.h"
+#include "kernels.h"
+#include "stencil.cuh"
+
+namespace topo {
+
+namespace {
+
+constexpr int kCoarseMaxDof = 1200;  // target size of the dense coarsest problem
+constexpr int kPT = 256;
+
+inline int grid1d(long long n) {
+  long long b = (n + kPT - 1) / kPT;
+  return (int)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+// ---------------------------------------------------------------- smoother
+// Chebyshev iteration for A x = b preconditioned by D^-1, on [lmin, lmax]
+// (theta = centre, delta = half width): d_0 = D^-1 r_0 / theta,
+// d_k = c1_k d_{k-1} + c2_k D^-1 r_k, r_k = r_{k-1} - A d_{k-1}, x += d_k.
+
+// pre-smoothing start from x = 0: r = b, d0 = D^-1 b / theta, x = d0
+__global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
+                            float* __restrict__ d0, float* __restrict__ x,
+                            const float* __restrict__ dinv, long long n4, float inv_theta,
+                            const int* __restrict__ done) {
+  if (*done) return;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const float4 bv = reinterpret_cast<const float4*>(b)[q];
+    const float4 dv = reinterpret_cast<const float4*>(dinv)[q];
+    float4 o;
+    o.x = dv.x * bv.x * inv_theta;
+    o.y = dv.y * bv.y * inv_theta;
+    o.z = dv.z * bv.z * inv_theta;
+    o.w = dv.w * bv.w * inv_theta;
+    reinterpret_cast<float4*>(r)[q] = bv;
+    reinterpret_cast<float4*>(d0)[q] = o;
+    reinterpret_cast<float4*>(x)[q] = o;
+  }
+}
+
+__global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long long n4,
+                        const int* __restrict__ done) {
+  if (*done) return;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    float4 xv = reinterpret_cast<float4*>(x)[q];
+    const float4 dv = reinterpret_cast<const float4*>(d)[q];
+    xv.x += dv.x;
+    xv.y += dv.y;
+    xv.z += dv.z;
+    xv.w += dv.w;
+    reinterpret_cast<float4*>(x)[q] = xv;
+  }
+}
+
+// one Chebyshev step, fused: gathers d_{k-1}; r -= A d_{k-1};
+// d_k = c1 d_{k-1} + c2 D^-1 r; x += d_k (+ d_{k-1} when it was not yet added)
+struct EpiChebStep {
+  static constexpr bool kReduce = false;
+  float* r;
+  float* dn;
+  float* x;
+  const float* dinv;
+  float c1, c2;
+  int add_prev;
+  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
+                                               const float (&acc)[3], const float (&ctr)[3],
+                                               const Dims& d) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long oc = c * d.comp + o;
+      const float Ad = d.fixed(c, i, j, k) ? 0.0f : acc[c];
+      const float rn = r[oc] - Ad;
+      const float dd = fmaf(c1, ctr[c], c2 * dinv[oc] * rn);
+      r[oc] = rn;
+      dn[oc] = dd;
+      x[oc] += add_prev ? (dd + ctr[c]) : dd;
+    }
+    return 0.0;
+  }
+};
+
+// r -= A d (the residual after pre-smoothing)
+struct EpiChebLast {
+  static constexpr bool kReduce = false;
+  float* r;
+  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
+                                               const float (&acc)[3], const float (&)[3],
+                                               const Dims& d) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!d.fixed(c, i, j, k)) r[c * d.comp + o] -= acc[c];
+    return 0.0;
+  }
+};
+
+// post-smoothing start: r = b - A x (gathering x), d0 = D^-1 r / theta
+struct EpiChebResid {
+  static constexpr bool kReduce = false;
+  const float* b;
+  float* r;
+  float* d0;
+  const float* dinv;
+  float inv_theta;
+  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
+                                               const float (&acc)[3], const float (&)[3],
+                                               const Dims& d) const {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long oc = c * d.comp + o;
+      const float rr = d.fixed(c, i, j, k) ? 0.0f : (b[oc] - acc[c]);
+      r[oc] = rr;
+      d0[oc] = dinv[oc] * rr * inv_theta;
+    }
+    return 0.0;
+  }
+};
+
+// ---------------------------------------------------------------- transfers
+// coarse element modulus: mean of its (up to) 8 children, times 2 for the
+// doubled edge (k0 of an element of edge 2h is 2h times the unit k0);
+// children beyond an odd fine grid are ghosts with E = 0
+__global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* __restrict__ Ec,
+                            const Dims dc) {
+  const long long n = (long long)dc.nx * dc.ny * dc.nz;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(e % dc.nx);
+    const int J = (int)((e / dc.nx) % dc.ny);
+    const int K = (int)(e / ((long long)dc.nx * dc.ny));
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + c;
+          if (i < df.nx && j < df.ny && k < df.nz) s += Ef[df.elem(i, j, k)];
+        }
+    Ec[dc.elem(I, J, K)] = 0.25f * s;
+  }
+}
+
+// b_c = P^T r_f for trilinear P: coarse node (I,J,K) sits on fine node
+// (2I,2J,2K) and collects fine neighbours with weights 1, 1/2 per axis offset
+__global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* __restrict__ bc,
+                           const Dims dc, const int* __restrict__ done) {
+  if (*done) return;
+  const long long nn = (long long)(dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(n % (dc.nx + 1));
+    const int J = (int)((n / (dc.nx + 1)) % (dc.ny + 1));
+    const int K = (int)(n / ((long long)(dc.nx + 1) * (dc.ny + 1)));
+    float s[3] = {0.f, 0.f, 0.f};
+    for (int dk = -1; dk <= 1; ++dk) {
+      const int k = 2 * K + dk;
+      if (k < 0 || k > df.nz) continue;
+      const float wk = dk ? 0.5f : 1.0f;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int j = 2 * J + dj;
+        if (j < 0 || j > df.ny) continue;
+        const float wjk = wk * (dj ? 0.5f : 1.0f);
+        for (int di = -1; di <= 1; ++di) {
+          const int i = 2 * I + di;
+          if (i < 0 || i > df.nx) continue;
+          const float wt = wjk * (di ? 0.5f : 1.0f);
+          const long long o = df.node(i, j, k);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, rf[c * df.comp + o], s[c]);
+        }
+      }
+    }
+    const long long o = dc.node(I, J, K);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bc[c * dc.comp + o] = dc.fixed(c, I, J, K) ? 0.0f : s[c];
+  }
+}
+
+// x_f += P x_c (trilinear interpolation from the coarse nodes around each
+// fine node), fixed fine DOFs untouched
+__global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float* __restrict__ xf,
+                              const Dims df, const int* __restrict__ done) {
+  if (*done) return;
+  const long long nn = (long long)(df.nx + 1) * (df.ny + 1) * (df.nz + 1);
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (df.nx + 1));
+    const int j = (int)((n / (df.nx + 1)) % (df.ny + 1));
+    const int k = (int)(n / ((long long)(df.nx + 1) * (df.ny + 1)));
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const float wi = (i & 1) ? 0.5f : 1.0f, wj = (j & 1) ? 0.5f : 1.0f,
+                wk = (k & 1) ? 0.5f : 1.0f;
+    float s[3] = {0.f, 0.f, 0.f};
+    for (int c2 = 0; c2 < nk; ++c2)
+      for (int b2 = 0; b2 < nj; ++b2)
+        for (int a2 = 0; a2 < ni; ++a2) {
+          const long long o = dc.node(i0 + a2, j0 + b2, k0 + c2);
+          const float wt = wi * wj * wk;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, xc[c * dc.comp + o], s[c]);
+        }
+    const long long o = df.node(i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (!df.fixed(c, i, j, k)) xf[c * df.comp + o] += s[c];
+  }
+}
+
+// ---------------------------------------------------------------- coarsest grid
+// dense FP64 matrix of the masked operator on the coarsest grid, one entry
+// per thread, summed over the elements shared by the two nodes (a gather:
+// deterministic, no atomics)
+__global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const float* __restrict__ E,
+                                 const __grid_constant__ K0<double> k0) {
+  const int n = 3 * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  const long long nn = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / n), col = (int)(t % n);
+    const int p = row / 3, r = row % 3, q = col / 3, s = col % 3;
+    const int pi = p % (d.nx + 1), pj = (p / (d.nx + 1)) % (d.ny + 1),
+              pk = p / ((d.nx + 1) * (d.ny + 1));
+    const int qi = q % (d.nx + 1), qj = (q / (d.nx + 1)) % (d.ny + 1),
+              qk = q / ((d.nx + 1) * (d.ny + 1));
+    double v = 0.0;
+    const bool fr = d.fixed(r, pi, pj, pk), fc = d.fixed(s, qi, qj, qk);
+    if (fr || fc) {
+      v = (row == col) ? 1.0 : 0.0;
+    } else if (abs(pi - qi) <= 1 && abs(pj - qj) <= 1 && abs(pk - qk) <= 1) {
+      for (int ek = max(max(pk, qk) - 1, 0); ek <= min(min(pk, qk), d.nz - 1); ++ek)
+        for (int ej = max(max(pj, qj) - 1, 0); ej <= min(min(pj, qj), d.ny - 1); ++ej)
+          for (int ei = max(max(pi, qi) - 1, 0); ei <= min(min(pi, qi), d.nx - 1); ++ei) {
+            const int lp = 4 * (pk - ek) + ((pj - ej) ? ((pi - ei) ? 2 : 3) : ((pi - ei) ? 1 : 0));
+            const int lq = 4 * (qk - ek) + ((qj - ej) ? ((qi - ei) ? 2 : 3) : ((qi - ei) ? 1 : 0));
+            v += (double)E[d.elem(ei, ej, ek)] * k0.v[(3 * lp + r) * 24 + 3 * lq + s];
+          }
+    }
+    A[t] = v;
+  }
+}
+
+// in-place Gauss-Jordan inversion of an SPD matrix, one kernel per pivot k;
+// the pivot row/column before step k are read from side buffers (written by
+// step k-1), so no entry is read after it was overwritten in the same step
+__global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
+                          double* __restrict__ col) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    row[t] = A[t];
+    col[t] = A[(long long)t * n];
+  }
+}
+
+__global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
+                          const double* __restrict__ colk, double* __restrict__ rown,
+                          double* __restrict__ coln) {
+  const long long nn = (long long)n * n;
+  const double p = 1.0 / rowk[k];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    double v;
+    if (i == k && j == k)
+      v = p;
+    else if (i == k)
+      v = rowk[j] * p;
+    else if (j == k)
+      v = -colk[i] * p;
+    else
+      v = A[t] - colk[i] * rowk[j] * p;
+    A[t] = v;
+    if (i == k + 1) rown[j] = v;
+    if (j == k + 1) coln[i] = v;
+  }
+}
+
+__global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, double* __restrict__ bd,
+                                const int* __restrict__ done) {
+  if (*done) return;
+  const int nn = (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
+    const int i = n % (d.nx + 1), j = (n / (d.nx + 1)) % (d.ny + 1),
+              k = n / ((d.nx + 1) * (d.ny + 1));
+    const long long o = d.node(i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bd[3 * n + c] = (double)b[c * d.comp + o];
+  }
+}
+
+// x = A^-1 b, one warp per row (A^-1 symmetric, rows read coalesced), FP64
+__global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __restrict__ bd,
+                               int n, float* __restrict__ x, const Dims d,
+                               const int* __restrict__ done) {
+  if (*done) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* a = Ainv + (long long)warp * n;
+  double s = 0.0;
+  for (int t = lane; t < n; t += 32) s = fma(a[t], bd[t], s);
+  s = warp_sum(s);
+  if (lane == 0) {
+    const int node = warp / 3, c = warp % 3;
+    const int i = node % (d.nx + 1), j = (node / (d.nx + 1)) % (d.ny + 1),
+              k = node / ((d.nx + 1) * (d.ny + 1));
+    x[c * d.comp + d.node(i, j, k)] = d.fixed(c, i, j, k) ? 0.0f : (float)s;
+  }
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, long long count, long long* bytes) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  *bytes += count * (long long)sizeof(T);
+  return cudaMemset(*p, 0, (size_t)count * sizeof(T));
+}
+
+#define GCK(call)                          \
+  do {                                     \
+    cudaError_t e__ = (call);              \
+    if (e__ != cudaSuccess) return e__;    \
+  } while (0)
+
+struct ChebCoef {
+  float inv_theta;
+  std::vector<float> c1, c2;  // index k = 1..degree-1
+};
+
+ChebCoef cheb_coef(double lmax, double ratio, int degree) {
+  const double lmin = lmax / ratio;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  ChebCoef c;
+  c.inv_theta = (float)(1.0 / theta);
+  c.c1.assign(degree, 0.f);
+  c.c2.assign(degree, 0.f);
+  double rho_prev = 1.0 / sigma;
+  for (int k = 1; k < degree; ++k) {
+    const double rho = 1.0 / (2.0 * sigma - rho_prev);
+    c.c1[k] = (float)(rho * rho_prev);
+    c.c2[k] = (float)(2.0 * rho / delta);
+    rho_prev = rho;
+  }
+  return c;
+}
+
+}  // namespace
+
+double k0_jacobi_bound(const double* k0) {
+  // power iteration on S = D^-1/2 k0 D^-1/2 (symmetric positive semidefinite)
+  double dis[24], v[24], w[24];
+  for (int a = 0; a < 24; ++a) {
+    dis[a] = 1.0 / std::sqrt(k0[a * 24 + a]);
+    v[a] = 1.0 + 0.01 * a;
+  }
+  double lam = 0.0;
+  for (int it = 0; it < 500; ++it) {
+    double nrm = 0.0;
+    for (int a = 0; a < 24; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < 24; ++b) s += dis[a] * k0[a * 24 + b] * dis[b] * v[b];
+      w[a] = s;
+      nrm += s * s;
+    }
+    nrm = std::sqrt(nrm);
+    double dot = 0.0;
+    for (int a = 0; a < 24; ++a) dot += v[a] * w[a];
+    double vn = 0.0;
+    for (int a = 0; a < 24; ++a) vn += v[a] * v[a];
+    lam = dot / vn;
+    for (int a = 0; a < 24; ++a) v[a] = w[a] / nrm;
+  }
+  return lam;
+}
+
+cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max) {
+  g.degree = std::max(1, degree);
+  g.lam_max = lam_max;
+  Dims d = fine;
+  g.lv.clear();
+  for (;;) {
+    GmgLevel L;
+    L.d = d;
+    L.nvec = 3 * d.comp;
+    g.lv.push_back(L);
+    const long long dof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    if (dof <= kCoarseMaxDof) break;
+    if (max_levels > 0 && (int)g.lv.size() >= max_levels) break;
+    const int nx = (d.nx + 1) / 2, ny = (d.ny + 1) / 2, nz = (d.nz + 1) / 2;
+    if (nx == d.nx && ny == d.ny && nz == d.nz) break;
+    d = make_dims(nx, ny, nz, d.bc, d.pin_j / 2);
+    if ((int)g.lv.size() >= 16) break;
+  }
+  const Dims& dc = g.lv.back().d;
+  g.nc = 3 * (dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
+  if ((long long)g.nc * g.nc > (1LL << 27)) return cudaErrorInvalidValue;  // > 1 GB inverse
+  for (size_t l = 0; l < g.lv.size(); ++l) {
+    GmgLevel& L = g.lv[l];
+    GCK(dmalloc(&L.r, L.nvec, &g.bytes));
+    GCK(dmalloc(&L.dv[0], L.nvec, &g.bytes));
+    GCK(dmalloc(&L.dv[1], L.nvec, &g.bytes));
+    if (l > 0) {
+      GCK(dmalloc(&L.E, L.d.ecount, &g.bytes));
+      GCK(dmalloc(&L.dinv, L.nvec, &g.bytes));
+      GCK(dmalloc(&L.b, L.nvec, &g.bytes));
+      GCK(dmalloc(&L.x, L.nvec, &g.bytes));
+    }
+  }
+  GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes));
+  GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes));
+  GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes));
+  g.ready = false;
+  return cudaSuccess;
+}
+
+cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
+                      const K0<double>& k0d, cudaStream_t s, long long* launches) {
+  g.lv[0].E = const_cast<float*>(E0);
+  g.lv[0].dinv = const_cast<float*>(dinv0);
+  for (size_t l = 1; l < g.lv.size(); ++l) {
+    const GmgLevel& F = g.lv[l - 1];
+    GmgLevel& C = g.lv[l];
+    const long long ne = (long long)C.d.nx * C.d.ny * C.d.nz;
+    k_coarsen_E<<<grid1d(ne), kPT, 0, s>>>(F.E, F.d, C.E, C.d);
+    GCK(cudaGetLastError());
+    GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s));
+    *launches += 2;
+  }
+  const GmgLevel& Lc = g.lv.back();
+  const long long nn = (long long)g.nc * g.nc;
+  k_dense_assemble<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d);
+  GCK(cudaGetLastError());
+  double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
+  k_gj_seed<<<(g.nc + kPT - 1) / kPT, kPT, 0, s>>>(g.Ainv, g.nc, buf[0][0], buf[0][1]);
+  GCK(cudaGetLastError());
+  *launches += 2;
+  for (int k = 0; k < g.nc; ++k) {
+    double** cur = buf[k & 1];
+    double** nxt = buf[(k + 1) & 1];
+    k_gj_step<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, g.nc, k, cur[0], cur[1], nxt[0], nxt[1]);
+    GCK(cudaGetLastError());
+  }
+  *launches += g.nc;
+  g.ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f, const int* done,
+                       cudaStream_t s, long long* launches) {
+  const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
+  const int m = g.degree;
+  const int nl = (int)g.lv.size();
+  Red nored{};
+  auto B = [&](int l) { return l == 0 ? b0 : g.lv[l].b; };
+  auto X = [&](int l) { return l == 0 ? x0 : g.lv[l].x; };
+  // down
+  for (int l = 0; l < nl - 1; ++l) {
+    GmgLevel& L = g.lv[l];
+    const long long n4 = L.nvec / 4;
+    k_cheb_init<<<grid1d(n4), kPT, 0, s>>>(B(l), L.r, L.dv[0], X(l), L.dinv, n4, cc.inv_theta,
+                                          done);
+    GCK(cudaGetLastError());
+    ++*launches;
+    for (int k = 1; k < m; ++k) {
+      EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
+      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, s));
+      ++*launches;
+    }
+    GCK(launch_stencil<float>(L.dv[(m - 1) & 1], L.E, L.d, k0f, EpiChebLast{L.r}, nored, done, s));
+    const GmgLevel& C = g.lv[l + 1];
+    const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
+    k_restrict<<<grid1d(nnc), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done);
+    GCK(cudaGetLastError());
+    *launches += 2;
+  }
+  // coarsest
+  {
+    const GmgLevel& C = g.lv[nl - 1];
+    const int nnc = (C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
+    k_coarse_gather<<<(nnc + kPT - 1) / kPT, kPT, 0, s>>>(B(nl - 1), C.d, g.bd, done);
+    GCK(cudaGetLastError());
+    const long long thr = 32LL * g.nc;
+    k_coarse_apply<<<(int)((thr + kPT - 1) / kPT), kPT, 0, s>>>(g.Ainv, g.bd, g.nc, X(nl - 1),
+                                                              C.d, done);
+    GCK(cudaGetLastError());
+    *launches += 2;
+  }
+  // up
+  for (int l = nl - 2; l >= 0; --l) {
+    GmgLevel& L = g.lv[l];
+    const GmgLevel& C = g.lv[l + 1];
+    const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
+    k_prolong_add<<<grid1d(nnf), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done);
+    GCK(cudaGetLastError());
+    EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
+    GCK(launch_stencil<float>(X(l), L.E, L.d, k0f, er, nored, done, s));
+    *launches += 2;
+    for (int k = 1; k < m; ++k) {
+      EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
+      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, s));
+      ++*launches;
+    }
+    if (m == 1) {
+      k_axpy1<<<grid1d(L.nvec / 4), kPT, 0, s>>>(X(l), L.dv[0], L.nvec / 4, done);
+      GCK(cudaGetLastError());
+      ++*launches;
+    }
+  }
+  return cudaSuccess;
+}
+
+void gmg_free(Gmg& g) {
+  for (size_t l = 0; l < g.lv.size(); ++l) {
+    GmgLevel& L = g.lv[l];
+    cudaFree(L.r);
+    cudaFree(L.dv[0]);
+    cudaFree(L.dv[1]);
+    if (l > 0) {
+      cudaFree(L.E);
+      cudaFree(L.dinv);
+      cudaFree(L.b);
+      cudaFree(L.x);
+    }
+  }
+  g.lv.clear();
+  cudaFree(g.Ainv);
+  cudaFree(g.side);
+  cudaFree(g.bd);
+  g.Ainv = g.side = g.bd = nullptr;
+  g.ready = false;
+}
+
+}  // namespace topo

@@ -1,0 +1,57 @@
+// Geometric multigrid V-cycle preconditioner for the masked stiffness
+// operator (the paper leaves the solver of Eq. (2) open; this is the
+// library's choice).  Grids are vertex-nested 2:1 coarsenings of the
+// structured hex grid (odd element counts round up, the extra half element
+// having E = 0); coarse operators are rediscretised with the mean child
+// modulus on elements of twice the edge; smoothing is Chebyshev-accelerated
+// Jacobi; the coarsest grid is solved with an explicit FP64 inverse.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace topo {
+
+struct GmgLevel {
+  Dims d{};
+  long long nvec = 0;
+  float* E = nullptr;     // owned for levels >= 1 (level 0 borrows the mesh's)
+  float* dinv = nullptr;  // owned for levels >= 1
+  float* b = nullptr;     // owned for levels >= 1
+  float* x = nullptr;     // owned for levels >= 1
+  float* r = nullptr;     // owned
+  float* dv[2] = {nullptr, nullptr};  // owned, Chebyshev direction double buffer
+};
+
+struct Gmg {
+  std::vector<GmgLevel> lv;
+  int degree = 3;            // Chebyshev degree per pre/post smoothing
+  double lam_max = 0.0;      // bound on lambda_max(D^-1 A) (from k0)
+  double lam_ratio = 10.0;   // smoothing interval [lam_max / lam_ratio, lam_max]
+  // coarsest level: explicit inverse
+  int nc = 0;                // dense size (3 * nodes of the coarsest grid)
+  double* Ainv = nullptr;    // nc * nc
+  double* side = nullptr;    // 4 * nc (Gauss-Jordan pivot row/column, ping-pong)
+  double* bd = nullptr;      // nc
+  long long bytes = 0;
+  bool ready = false;        // set up for the current densities
+};
+
+// Choose levels for a fine grid and allocate them (fine-level E/dinv/b/x are
+// bound later, per call).  max_levels <= 0: automatic.
+cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max);
+// Per-density setup: coarse moduli, Jacobi diagonals, coarsest inverse.
+cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
+                      const K0<double>& k0d, cudaStream_t s, long long* launches);
+// x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
+// when *done is set.
+cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f, const int* done,
+                       cudaStream_t s, long long* launches);
+void gmg_free(Gmg& g);
+// lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
+double k0_jacobi_bound(const double* k0);
+
+}  // namespace topo

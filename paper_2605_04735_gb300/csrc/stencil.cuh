@@ -1,0 +1,220 @@
+// Matrix-free application of the SIMP stiffness operator (Sec. 2.1.1,
+// Eq. (2): K(rho) = sum_e E_e k0, E_e from Eq. (1)) as a node-centric gather
+// with no atomics, with a pluggable per-node epilogue.
+//
+// FP32 kernel (k_stencil): each thread owns a column of nodes (i, j, kb..ke)
+// and marches up in z, holding the 3x3x3 node neighbourhood (3 components)
+// and the 2x2x2 surrounding element moduli in registers; per z step it loads
+// one new node plane (9 nodes) and element plane (4 elements).  For node n
+//     (K x)_n = sum_{e owns n} E_e * (k0[row block of n in e] . x_e),
+// 8 elements x 72 FMAs, k0 read as constant-bank operands (compile-time
+// indices into a __grid_constant__ parameter).
+// FP64 kernel (k_stencil_direct): same sum, no register window (81 doubles
+// would spill); the FP64 pipe bounds it, not the loads.
+//
+// The epilogue receives (K x)_n (before any masking) and x_n and decides what
+// to write; it returns the node's contribution to an optional reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace topo {
+
+// local node number of the corner at offsets (dx, dy, dz) in {0,1}^3
+__host__ __device__ constexpr int lidx(int dx, int dy, int dz) {
+  return 4 * dz + (dy ? (dx ? 2 : 3) : (dx ? 1 : 0));
+}
+
+constexpr int kStencilBX = 32;
+constexpr int kStencilBY = 8;
+
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kStencilBX* kStencilBY)
+    k_stencil(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
+              const __grid_constant__ K0<T> k0, const Epi epi, const Red red, const int zchunk,
+              const int* __restrict__ done) {
+  if (done != nullptr && *done) return;  // uniform over the grid
+  const int i = blockIdx.x * kStencilBX + threadIdx.x;
+  const int j = blockIdx.y * kStencilBY + threadIdx.y;
+  const int kb = blockIdx.z * zchunk;
+  const int ke = min(kb + zchunk, d.nz + 1);
+  const bool act = (i <= d.nx) && (j <= d.ny);
+  double part = 0.0;
+  if (act) {
+    const long long ps = d.plane_stride();
+    const long long eps = d.eplane();
+    const long long cs = d.comp;
+    T w[3][3][3][3];  // w[z][y][x][c]: node (i-1+x, j-1+y, k-1+z)
+    T e[2][2][2];     // e[z][y][x]: element (i-1+x, j-1+y, k-1+z)
+    const long long nb = d.node(i - 1, j - 1, kb - 1);
+    const long long eb = d.elem(i - 1, j - 1, kb - 1);
+#pragma unroll
+    for (int zz = 0; zz < 2; ++zz)
+#pragma unroll
+      for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx) {
+          const long long o = nb + zz * ps + yy * d.px + xx;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) w[zz][yy][xx][c] = __ldg(x + c * cs + o);
+        }
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx) e[0][yy][xx] = __ldg(E + eb + yy * d.ex + xx);
+
+    for (int k = kb; k < ke; ++k) {
+      const long long np = nb + (long long)(k - kb + 2) * ps;   // node plane k+1
+      const long long ep = eb + (long long)(k - kb + 1) * eps;  // element plane k
+#pragma unroll
+      for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx) {
+          const long long o = np + yy * d.px + xx;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) w[2][yy][xx][c] = __ldg(x + c * cs + o);
+        }
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 2; ++xx) e[1][yy][xx] = __ldg(E + ep + yy * d.ex + xx);
+
+      // Every row of k0 sums to zero per displacement component (a rigid
+      // translation is stress-free), so k0 x_e = k0 (x_e - 1 (x) x_n) for the
+      // owning node n.  Gathering the differences x_m - x_n keeps FP32 from
+      // cancelling large rigid displacements against each other, and the
+      // centre terms vanish (72 FMAs fewer, 78 subtractions more).
+      const T ctr[3] = {w[1][1][1][0], w[1][1][1][1], w[1][1][1][2]};
+      T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const int ln = lidx(1 - a, 1 - b, 1 - c);
+            T s[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+              for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                  if (a + dx == 1 && b + dy == 1 && c + dz == 1) continue;  // the node itself
+                  const int lm = lidx(dx, dy, dz);
+#pragma unroll
+                  for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                      s[r] = fma(k0.v[(3 * ln + r) * 24 + 3 * lm + q],
+                                 w[c + dz][b + dy][a + dx][q] - ctr[q], s[r]);
+                }
+            const T ee = e[c][b][a];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) acc[r] = fma(ee, s[r], acc[r]);
+          }
+      part += epi(i, j, k, d.node(i, j, k), acc, ctr, d);
+      // slide the window up one plane
+#pragma unroll
+      for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            w[0][yy][xx][c] = w[1][yy][xx][c];
+            w[1][yy][xx][c] = w[2][yy][xx][c];
+          }
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 2; ++xx) e[0][yy][xx] = e[1][yy][xx];
+    }
+  }
+  if (Epi::kReduce) {
+    double v[1] = {part};
+    reduce_finalize<1>(v, red);
+  }
+}
+
+template <typename T, class Epi>
+__global__ void __launch_bounds__(kStencilBX* kStencilBY)
+    k_stencil_direct(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
+                     const __grid_constant__ K0<T> k0, const Epi epi, const Red red,
+                     const int zchunk, const int* __restrict__ done) {
+  if (done != nullptr && *done) return;
+  const int i = blockIdx.x * kStencilBX + threadIdx.x;
+  const int j = blockIdx.y * kStencilBY + threadIdx.y;
+  const int kb = blockIdx.z * zchunk;
+  const int ke = min(kb + zchunk, d.nz + 1);
+  const bool act = (i <= d.nx) && (j <= d.ny);
+  double part = 0.0;
+  for (int k = kb; act && k < ke; ++k) {
+    const long long cs = d.comp;
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int ln = lidx(1 - a, 1 - b, 1 - c);
+          const long long ob = d.node(i - 1 + a, j - 1 + b, k - 1 + c);
+          T s[3] = {T(0), T(0), T(0)};
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+              for (int dx = 0; dx < 2; ++dx) {
+                const int lm = lidx(dx, dy, dz);
+                const long long o = ob + dz * d.plane_stride() + dy * d.px + dx;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  const T u = __ldg(x + q * cs + o);
+#pragma unroll
+                  for (int r = 0; r < 3; ++r)
+                    s[r] = fma(k0.v[(3 * ln + r) * 24 + 3 * lm + q], u, s[r]);
+                }
+              }
+          const T ee = __ldg(E + d.elem(i - 1 + a, j - 1 + b, k - 1 + c));
+#pragma unroll
+          for (int r = 0; r < 3; ++r) acc[r] = fma(ee, s[r], acc[r]);
+        }
+    const long long o = d.node(i, j, k);
+    const T ctr[3] = {x[o], x[cs + o], x[2 * cs + o]};
+    part += epi(i, j, k, o, acc, ctr, d);
+  }
+  if (Epi::kReduce) {
+    double v[1] = {part};
+    reduce_finalize<1>(v, red);
+  }
+}
+
+// z planes per thread: enough blocks for ~4 waves of 152 SMs at 2 resident
+// blocks each, a 2-plane halo reload below ~15%, and at most kMaxPartials blocks
+inline int stencil_zchunk(const Dims& d) {
+  const long long xy = (long long)((d.nx + kStencilBX) / kStencilBX) * ((d.ny + kStencilBY) / kStencilBY);
+  const int planes = d.nz + 1;
+  int z = (int)((xy * planes) / (152 * 2 * 4));
+  if (z < 2) z = 2;
+  if (z > 32) z = 32;
+  while (xy * ((planes + z - 1) / z) > kMaxPartials) ++z;
+  return z;
+}
+
+template <typename T, class Epi>
+cudaError_t launch_stencil(const T* x, const T* E, const Dims& d, const K0<T>& k0, const Epi& epi,
+                           const Red& red, const int* done, cudaStream_t s) {
+  const int z = stencil_zchunk(d);
+  dim3 block(kStencilBX, kStencilBY, 1);
+  dim3 grid((d.nx + kStencilBX) / kStencilBX, (d.ny + kStencilBY) / kStencilBY, (d.nz + z) / z);
+  if constexpr (sizeof(T) == 8)
+    k_stencil_direct<T, Epi><<<grid, block, 0, s>>>(x, E, d, k0, epi, red, z, done);
+  else
+    k_stencil<T, Epi><<<grid, block, 0, s>>>(x, E, d, k0, epi, red, z, done);
+  return cudaGetLastError();
+}
+
+}  // namespace topo

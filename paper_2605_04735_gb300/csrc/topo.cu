@@ -21,6 +21,7 @@
 
 #include "../../include/topo.h"
 #include "common.cuh"
+#include "gmg.h"
 #include "kernels.h"
 
 using namespace topo;
@@ -117,6 +118,13 @@ struct topo_mesh {
   std::vector<cudaEvent_t> ev;
   double prof_ms = 0.0;
   long long prof_launches = 0;
+  long long launches = 0;  // every kernel this mesh launched
+
+  // multigrid hierarchy (built on the first GMG solve, set up per density)
+  Gmg gmg;
+  bool gmg_built = false;
+  int gmg_levels_req = -1, gmg_degree = -1;
+  double lam_max = 0.0;
 };
 
 namespace {
@@ -152,25 +160,18 @@ topo_status dalloc(topo_mesh* m, T** p, long long count) {
   return TOPO_OK;
 }
 
+// count one kernel launch of this mesh, then check the launch
+#define LK(mesh, call)          \
+  do {                          \
+    ++(mesh)->launches;         \
+    CK(call);                   \
+  } while (0)
+
 #define CKS(call)                        \
   do {                                   \
     topo_status st__ = (call);           \
     if (st__ != TOPO_OK) return st__;    \
   } while (0)
-
-Dims make_dims(int nx, int ny, int nz, int bc) {
-  Dims d{};
-  d.nx = nx;
-  d.ny = ny;
-  d.nz = nz;
-  d.px = ((nx + 3) + 3) / 4 * 4;
-  d.ex = ((nx + 2) + 3) / 4 * 4;
-  d.bc = bc;
-  d.pin_j = ny / 2;
-  d.comp = (long long)d.px * (ny + 3) * (nz + 3);
-  d.ecount = (long long)d.ex * (ny + 2) * (nz + 2);
-  return d;
-}
 
 Red red_of(topo_mesh* m, int op, double rtol2 = 0.0) {
   Red r{};
@@ -216,18 +217,18 @@ topo_status inner_pcg(topo_mesh* m, const T* b, T* x, T* r, T* z, T* p, T* q, co
                       const T* E, const K0<T>& k0, double rtol, int max_iter, int check_every,
                       bool profile, int* iters, int* dev_status) {
   cudaStream_t s = m->stream;
-  CK(launch_set_max_iter(m->sc, max_iter, s));
-  CK(launch_pcg_init<T>(b, x, r, z, p, dinv, m->nvec, red_of(m, FIN_INIT, rtol * rtol), true, s));
+  LK(m, launch_set_max_iter(m->sc, max_iter, s));
+  LK(m, launch_pcg_init<T>(b, x, r, z, p, dinv, m->nvec, red_of(m, FIN_INIT, rtol * rtol), true, s));
   const int* done = &m->sc->done;
   int it_before = 0;
   if (profile) CKS(ensure_profile_events(m, check_every));
   for (;;) {
     for (int c = 0; c < check_every; ++c) {
       if (profile) CK(cudaEventRecord(m->ev[2 * c], s));
-      CK(launch_apply<T>(p, q, E, nullptr, m->d, k0, red_of(m, FIN_ALPHA), APPLY_DOT, done, s));
+      LK(m, launch_apply<T>(p, q, E, nullptr, m->d, k0, red_of(m, FIN_ALPHA), APPLY_DOT, done, s));
       if (profile) CK(cudaEventRecord(m->ev[2 * c + 1], s));
-      CK(launch_pcg_update<T>(x, r, z, p, q, dinv, m->nvec, red_of(m, FIN_UPDATE), true, s));
-      CK(launch_pcg_direction<T>(p, z, m->nvec, m->sc, s));
+      LK(m, launch_pcg_update<T>(x, r, z, p, q, dinv, m->nvec, red_of(m, FIN_UPDATE), true, s));
+      LK(m, launch_pcg_direction<T>(p, z, m->nvec, m->sc, s));
     }
     CKS(sync_scalars(m));
     if (profile) {
@@ -248,8 +249,76 @@ topo_status inner_pcg(topo_mesh* m, const T* b, T* x, T* r, T* z, T* p, T* q, co
   return TOPO_OK;
 }
 
+// Preconditioned CG with one V-cycle as the preconditioner (FP32).
+topo_status inner_pcg_gmg(topo_mesh* m, const float* b, float* x, float* r, float* z, float* p,
+                          float* q, double rtol, int max_iter, int check_every, bool profile,
+                          int* iters, int* dev_status) {
+  cudaStream_t s = m->stream;
+  const int* done = &m->sc->done;
+  LK(m, launch_set_max_iter(m->sc, max_iter, s));
+  LK(m, launch_pcg_init<float>(b, x, r, z, p, nullptr, m->nvec,
+                               red_of(m, FIN_INIT, rtol * rtol), false, s));
+  CK(gmg_vcycle(m->gmg, r, z, m->k0f, done, s, &m->launches));
+  LK(m, launch_dot<float>(r, z, m->nvec, red_of(m, FIN_SET_RZ), s));
+  LK(m, launch_pcg_direction<float>(p, z, m->nvec, m->sc, s));
+  int it_before = 0;
+  if (profile) CKS(ensure_profile_events(m, check_every));
+  for (;;) {
+    for (int c = 0; c < check_every; ++c) {
+      if (profile) CK(cudaEventRecord(m->ev[2 * c], s));
+      LK(m, launch_apply<float>(p, q, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_ALPHA),
+                                APPLY_DOT, done, s));
+      if (profile) CK(cudaEventRecord(m->ev[2 * c + 1], s));
+      LK(m, launch_pcg_update<float>(x, r, z, p, q, nullptr, m->nvec, red_of(m, FIN_RR_ONLY),
+                                     false, s));
+      CK(gmg_vcycle(m->gmg, r, z, m->k0f, done, s, &m->launches));
+      LK(m, launch_dot<float>(r, z, m->nvec, red_of(m, FIN_RZ_BETA), s));
+      LK(m, launch_pcg_direction<float>(p, z, m->nvec, m->sc, s));
+    }
+    CKS(sync_scalars(m));
+    if (profile) {
+      const int worked = std::min(check_every, m->h_sc->iter - it_before);
+      for (int c = 0; c < worked; ++c) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
+        m->prof_ms += ms;
+        m->prof_launches += 1;
+      }
+    }
+    if (m->h_sc->done) break;
+    if (m->h_sc->iter == it_before) return TOPO_ERR_CUDA;
+    it_before = m->h_sc->iter;
+  }
+  *iters = m->h_sc->iter;
+  *dev_status = m->h_sc->status;
+  return TOPO_OK;
+}
+
+topo_status ensure_gmg(topo_mesh* m, const topo_solve_opts* o) {
+  if (m->gmg_built && (m->gmg_levels_req != o->gmg_levels || m->gmg_degree != o->smooth_degree)) {
+    CK(cudaStreamSynchronize(m->stream));
+    m->bytes -= m->gmg.bytes;
+    gmg_free(m->gmg);
+    m->gmg = Gmg();
+    m->gmg_built = false;
+  }
+  if (!m->gmg_built) {
+    cudaError_t e = gmg_create(m->gmg, m->d, o->gmg_levels, o->smooth_degree, m->lam_max);
+    m->bytes += m->gmg.bytes;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? TOPO_ERR_OOM : TOPO_ERR_INVALID;
+    }
+    m->gmg_built = true;
+    m->gmg_levels_req = o->gmg_levels;
+    m->gmg_degree = o->smooth_degree;
+  }
+  if (!m->gmg.ready) CK(gmg_setup(m->gmg, m->E32, m->dinv32, m->k0f, m->k0d, m->stream, &m->launches));
+  return TOPO_OK;
+}
+
 topo_status residual64(topo_mesh* m, double* rr) {
-  CK(launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
+  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
                           APPLY_RESID, nullptr, m->stream));
   CKS(sync_scalars(m));
   *rr = m->h_sc->aux[0];
@@ -259,7 +328,10 @@ topo_status residual64(topo_mesh* m, double* rr) {
 topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* info) {
   if (!m->has_density) return TOPO_ERR_NO_DENSITY;
   if (o->precision != TOPO_PREC_FP64 && o->precision != TOPO_PREC_FP32) return TOPO_ERR_INVALID;
-  if (o->precond != TOPO_PRECOND_JACOBI) return TOPO_ERR_INVALID;
+  if (o->precond != TOPO_PRECOND_JACOBI && o->precond != TOPO_PRECOND_GMG) return TOPO_ERR_INVALID;
+  if (o->precond == TOPO_PRECOND_GMG &&
+      (o->precision != TOPO_PREC_FP32 || o->smooth_degree < 1 || o->smooth_degree > 8))
+    return TOPO_ERR_INVALID;
   if (!(o->rtol > 0.0) || o->max_iter < 1 || o->max_outer < 1 || o->check_every < 1 ||
       o->check_every > 1024)
     return TOPO_ERR_INVALID;
@@ -268,13 +340,14 @@ topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* in
   if (fp64) {
     CKS(ensure_fp64_inner(m));
     if (!m->diag64) {
-      CK(launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, s));
+      LK(m, launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, s));
       m->diag64 = true;
     }
   } else if (!m->diag32) {
-    CK(launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s));
+    LK(m, launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s));
     m->diag32 = true;
   }
+  if (o->precond == TOPO_PRECOND_GMG) CKS(ensure_gmg(m, o));
   m->solved = false;
   double rr = 0.0;
   if (o->warm_start) {
@@ -284,7 +357,7 @@ topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* in
     CK(cudaMemcpyAsync(m->r64, m->f64, sizeof(double) * m->nvec, cudaMemcpyDeviceToDevice, s));
     rr = m->fnorm2;
     // aux[0] must hold ||r||^2 for the scaled narrowing below
-    CK(launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s));
+    LK(m, launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s));
   }
   int total_iters = 0, outer = 0;
   topo_status st = TOPO_OK;
@@ -309,15 +382,19 @@ topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* in
       inner = std::min(std::max(inner, 1e-15), 0.5);
       CKS(inner_pcg<double>(m, m->r64, m->x64, m->s64, m->z64, m->p64, m->q64, m->dinv64, m->E64,
                             m->k0d, inner, budget, o->check_every, false, &it, &dst));
-      CK(launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, s));
+      LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, s));
     } else {
-      CK(launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s));
+      LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s));
       double inner = std::max(o->inner_rtol, 0.25 * o->rtol * fn / std::sqrt(rr));
       inner = std::min(inner, 0.5);
-      CKS(inner_pcg<float>(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32, m->E32,
-                           m->k0f, inner, budget, o->check_every, m->prof, &it, &dst));
+      if (o->precond == TOPO_PRECOND_GMG)
+        CKS(inner_pcg_gmg(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, inner, budget,
+                          o->check_every, m->prof, &it, &dst));
+      else
+        CKS(inner_pcg<float>(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32,
+                             m->E32, m->k0f, inner, budget, o->check_every, m->prof, &it, &dst));
       // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
-      CK(launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s));
+      LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s));
     }
     total_iters += it;
     ++outer;
@@ -343,7 +420,7 @@ topo_status upload_f64(topo_mesh* m, const double* src, double* dst_soa, size_t 
     CK(cudaMemcpyAsync(m->aos, src, n_dof * sizeof(double), cudaMemcpyHostToDevice, s));
     a = m->aos;
   }
-  CK(launch_unpack<double>(a, dst_soa, m->d, s));
+  LK(m, launch_unpack<double>(a, dst_soa, m->d, s));
   return TOPO_OK;
 }
 
@@ -367,7 +444,7 @@ void topo_default_params(topo_params* p) {
 void topo_default_opts(topo_solve_opts* o) {
   if (!o) return;
   o->precision = TOPO_PREC_FP32;
-  o->precond = TOPO_PRECOND_JACOBI;
+  o->precond = TOPO_PRECOND_GMG;
   o->rtol = 1e-8;
   o->inner_rtol = 1e-5;
   o->max_iter = 100000;
@@ -403,6 +480,7 @@ void topo_free(topo_mesh* m) {
                   m->rho_in};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (m->gmg_built) gmg_free(m->gmg);
   if (m->h_sc) cudaFreeHost(m->h_sc);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -418,7 +496,7 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
     CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
     m->own_stream = true;
   }
-  m->d = make_dims(nx, ny, nz, bc);
+  m->d = make_dims(nx, ny, nz, bc, ny / 2);
   m->nvec = 3 * m->d.comp;
   if (prm)
     m->prm = *prm;
@@ -430,6 +508,7 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
     m->k0d.v[t] = k[t];
     m->k0f.v[t] = (float)k[t];
   }
+  m->lam_max = k0_jacobi_bound(k);
   const long long ne = m->d.ecount;
   CKS(dalloc(m, &m->rho_g, ne));
   CKS(dalloc(m, &m->E32, ne));
@@ -451,8 +530,8 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
   CKS(dalloc(m, &m->aos, 3 * nn));
   CK(cudaMallocHost(&m->h_sc, sizeof(PcgScalars)));
   std::memset(m->h_sc, 0, sizeof(PcgScalars));
-  CK(launch_build_load(m->f64, m->d, load, m->prm.load, m->prm.h, m->stream));
-  CK(launch_dot<double>(m->f64, m->f64, m->nvec, red_of(m, FIN_AUX), m->stream));
+  LK(m, launch_build_load(m->f64, m->d, load, m->prm.load, m->prm.h, m->stream));
+  LK(m, launch_dot<double>(m->f64, m->f64, m->nvec, red_of(m, FIN_AUX), m->stream));
   CKS(sync_scalars(m));
   m->fnorm2 = m->h_sc->aux[0];
   return TOPO_OK;
@@ -492,12 +571,13 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
     src = m->rho_in;
   }
   CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
-  CK(launch_simp(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin, m->prm.penal,
+  LK(m, launch_simp(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin, m->prm.penal,
                  m->prm.h, m->flags, s));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   m->diag32 = m->diag64 = false;
+  m->gmg.ready = false;
   m->solved = false;
   m->has_density = (bad == 0);
   return bad ? TOPO_ERR_NAN : TOPO_OK;
@@ -531,7 +611,7 @@ topo_status topo_compliance(topo_mesh* m, double* c) {
   if (!m || !c) return TOPO_ERR_INVALID;
   if (!m->solved) return TOPO_ERR_NOT_SOLVED;
   CK(cudaSetDevice(m->dev));
-  CK(launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), m->stream));
+  LK(m, launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), m->stream));
   CKS(sync_scalars(m));
   *c = m->h_sc->aux[0];
   return TOPO_OK;
@@ -540,7 +620,7 @@ topo_status topo_compliance(topo_mesh* m, double* c) {
 static topo_status sens_impl(topo_mesh* m) {
   const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
   if (!m->dc) CKS(dalloc(m, &m->dc, ne));
-  CK(launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->k0d, m->prm.penal,
+  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->k0d, m->prm.penal,
                         (m->prm.E0 - m->prm.Emin) * m->prm.h, red_of(m, FIN_AUX), m->stream));
   return TOPO_OK;
 }
@@ -574,7 +654,7 @@ topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_
   if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
   CK(cudaSetDevice(m->dev));
   double* dst = on_device ? u : m->aos;
-  CK(launch_pack<double>(m->u64, dst, m->d, m->stream));
+  LK(m, launch_pack<double>(m->u64, dst, m->d, m->stream));
   if (!on_device) {
     CK(cudaMemcpyAsync(u, m->aos, nd * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
@@ -609,15 +689,15 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
   }
   if (precision == TOPO_PREC_FP64) {
     CKS(ensure_fp64_inner(m));
-    CK(launch_unpack<double>(src, m->p64, m->d, s));
-    CK(launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, red_of(m, FIN_NONE),
+    LK(m, launch_unpack<double>(src, m->p64, m->d, s));
+    LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, red_of(m, FIN_NONE),
                             APPLY_PLAIN, nullptr, s));
-    CK(launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
+    LK(m, launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
   } else {
-    CK(launch_unpack<float>(src, m->p32, m->d, s));
-    CK(launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+    LK(m, launch_unpack<float>(src, m->p32, m->d, s));
+    LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
                            APPLY_PLAIN, nullptr, s));
-    CK(launch_pack<float>(m->q32, on_device ? y : m->aos, m->d, s));
+    LK(m, launch_pack<float>(m->q32, on_device ? y : m->aos, m->d, s));
   }
   if (!on_device) {
     CK(cudaMemcpyAsync(y, m->aos, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -633,10 +713,10 @@ topo_status topo_apply_internal(topo_mesh* m, int precision, int reps) {
   for (int r = 0; r < reps; ++r) {
     if (precision == TOPO_PREC_FP64) {
       CKS(ensure_fp64_inner(m));
-      CK(launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
+      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
                               red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->stream));
     } else if (precision == TOPO_PREC_FP32) {
-      CK(launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
                              APPLY_PLAIN, nullptr, m->stream));
     } else {
       return TOPO_ERR_INVALID;
@@ -666,7 +746,7 @@ topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_
 
 long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* opts) {
   if (nx < 1 || ny < 1 || nz < 1) return -1;
-  Dims d = make_dims(nx, ny, nz, 0);
+  Dims d = make_dims(nx, ny, nz, 0, ny / 2);
   const long long nvec = 3 * d.comp;
   long long b = d.ecount * (4 + 4 + 8);      // rho, E32, E64
   b += nvec * (3 * 8 + 7 * 4);                // f, u, r (FP64) + 7 FP32 CG vectors
@@ -683,13 +763,16 @@ topo_status topo_profile_enable(topo_mesh* m, int enable) {
   return TOPO_OK;
 }
 
-topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches, int reset) {
+topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches,
+                              long long* all_launches, int reset) {
   if (!m) return TOPO_ERR_INVALID;
   if (total_ms) *total_ms = m->prof_ms;
   if (launches) *launches = m->prof_launches;
+  if (all_launches) *all_launches = m->launches;
   if (reset) {
     m->prof_ms = 0.0;
     m->prof_launches = 0;
+    m->launches = 0;
   }
   return TOPO_OK;
 }

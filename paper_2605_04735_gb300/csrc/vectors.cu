@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(kThreads)
       st4(z, q, zv);
       st4(p, q, zv);
       rz += (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z + (double)bv.w * zv.w;
+    } else {
+      st4(p, q, zero);  // the first direction is set after z = M r
     }
     rr += (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z + (double)bv.w * bv.w;
   }

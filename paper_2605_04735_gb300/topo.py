@@ -75,7 +75,8 @@ def lib():
                                    C.POINTER(C.c_longlong)]),
             "topo_footprint_bytes": (C.c_longlong, [i, i, i, C.POINTER(SolveOpts)]),
             "topo_profile_enable": (i, [vp, i]),
-            "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong), i]),
+            "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_longlong), i]),
             "topo_free": (None, [vp]),
             "topo_status_string": (C.c_char_p, [i]),
         }
@@ -227,7 +228,8 @@ class Mesh:
         _check(lib().topo_profile_enable(self._h, int(enable)), "topo_profile_enable")
 
     def profile_read(self, reset=True):
-        ms, n = C.c_double(), C.c_longlong()
-        _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), int(reset)),
+        """(summed ms of the timed operator launches, their count, all kernel launches)."""
+        ms, n, a = C.c_double(), C.c_longlong(), C.c_longlong()
+        _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(a), int(reset)),
                "topo_profile_read")
-        return ms.value, n.value
+        return ms.value, n.value, a.value

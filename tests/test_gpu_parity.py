@@ -5,7 +5,8 @@ Tolerances (derived from the arithmetic, stated per test):
     576-term sums); FP32 kernel: <= 2e-6 (FP32 rounding of x, E, k0 and the
     sums, random x so no cancellation beyond a factor ~10);
   * solves: the library stops on the true FP64 relative residual; at
-    rtol = 1e-12 the displacement and compliance must match the direct
+    rtol = 1e-10 (FP64 itself attains only ~1e-11 on slender beams, the
+    direct solver included) the displacement and compliance must match the direct
     Cholesky solution to <= 1e-8 relative (2-norm over all DOFs), and the
     sensitivities to <= 1e-6 relative to their max-norm.
 """
@@ -63,23 +64,27 @@ def test_operator_matches_assembled_K(topo, case, prec, tol):
 
 
 def _solve_case(topo, nx, ny, nz, bc, load, rho, prec, rtol, **kw):
+    kw.setdefault("precond", topo.PRECOND_JACOBI if prec == 0 else topo.PRECOND_GMG)
     with topo.Mesh(nx, ny, nz, bc, load) as m:
         m.set_density(rho)
         info = m.solve(topo.default_opts(precision=prec, rtol=rtol, **kw))
         return (info, m.displacement(), m.compliance(), m.compliance_energy(), m.sensitivity())
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("case", CASES[:3] + [CASES[4]])
-def test_solve_matches_direct_oracle(topo, case, prec):
+SOLVERS = [(0, 0), (1, 0), (1, 1)]  # (precision, preconditioner): FP64 Jacobi, FP32 Jacobi, FP32 GMG
+
+
+@pytest.mark.parametrize("prec,pc", SOLVERS)
+@pytest.mark.parametrize("case", CASES)
+def test_solve_matches_direct_oracle(topo, case, prec, pc):
     nx, ny, nz, bc, load = case
     rho = I.density_uniform(nx, ny, nz, 0.05, 1.0, 23)
     P = fem.Problem(nx, ny, nz, bc, load, rho)
     u_ref = P.solve()
     c_ref = P.compliance(u_ref)
     dc_ref = P.sensitivity(u_ref)
-    info, u, c, ce, dc = _solve_case(topo, nx, ny, nz, bc, load, rho, prec, 1e-12)
-    assert info.rel_residual <= 1e-12
+    info, u, c, ce, dc = _solve_case(topo, nx, ny, nz, bc, load, rho, prec, 1e-10, precond=pc)
+    assert info.rel_residual <= 1e-10
     assert _rel(u, u_ref) <= 1e-8
     assert abs(c - c_ref) <= 1e-8 * abs(c_ref)
     assert abs(ce - c) <= 1e-9 * abs(c)
@@ -88,7 +93,7 @@ def test_solve_matches_direct_oracle(topo, case, prec):
 
 def test_cantilever_24x12x12_all_paths(topo):
     """The small cantilever workload (uniform rho in [0.01, 1]): plain FP64
-    and FP32+refinement both reach rtol 1e-8; at 1e-12 both match the
+    and FP32+refinement both reach rtol 1e-8; at rtol 1e-10 both match the
     direct solve to 1e-8 (u, c) and 1e-6 (dc)."""
     w = I.WORKLOADS["cantilever_24x12x12"]
     rho = w.density()
@@ -96,12 +101,14 @@ def test_cantilever_24x12x12_all_paths(topo):
     u_ref = P.solve()
     c_ref = P.compliance(u_ref)
     dc_ref = P.sensitivity(u_ref)
-    for prec in (0, 1):
-        info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, prec, 1e-8)
+    for prec, pc in SOLVERS:
+        info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, prec, 1e-8,
+                                         precond=pc)
         assert info.rel_residual <= 1e-8
         # the oracle's own FP64 residual of the GPU displacement
         assert P.rel_residual(u) <= 1.05e-8
-        info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, prec, 1e-12)
+        info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, prec, 1e-10,
+                                         precond=pc)
         assert _rel(u, u_ref) <= 1e-8
         assert abs(c - c_ref) <= 1e-8 * c_ref
         assert np.abs(dc - dc_ref).max() <= 1e-6 * np.abs(dc_ref).max()
@@ -114,7 +121,7 @@ def test_uniaxial_tension_closed_form(topo):
     prm = topo.default_params(Emin=0.0, h=h, load=t)
     with topo.Mesh(nx, ny, nz, topo.BC_ROLLER_BOX, topo.LOAD_FACE_XL_TRACTION, prm) as m:
         m.set_density(np.ones(nx * ny * nz, np.float32))
-        m.solve(topo.default_opts(precision=1, rtol=1e-13))
+        m.solve(topo.default_opts(precision=1, rtol=1e-12))
         u = m.displacement().reshape(-1, 3)
         c = m.compliance()
     g = fem.Grid(nx, ny, nz, h)
@@ -125,15 +132,19 @@ def test_uniaxial_tension_closed_form(topo):
     assert abs(c - t * t * V) <= 1e-11 * t * t * V
 
 
-def test_mbb_96x32x32_full_size_properties(topo):
+@pytest.mark.parametrize("pc", [0, 1])
+def test_mbb_96x32x32_full_size_properties(topo, pc):
     """Full-size MBB workload in the bench's configuration: the oracle
     assembles K in FP64 and checks the GPU displacement's true residual, the
     energy identity, and sampled sensitivities computed one by one."""
     w = I.WORKLOADS["mbb_96x32x32"]
     rho = w.density()
     P = fem.Problem(w.nx, w.ny, w.nz, w.bc, w.load, rho)
-    info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, 1, 1e-8)
+    info, u, c, ce, dc = _solve_case(topo, w.nx, w.ny, w.nz, w.bc, w.load, rho, 1, 1e-8,
+                                     precond=pc)
     assert info.rel_residual <= 1e-8
+    if pc == 1:
+        assert info.iters <= 200  # multigrid keeps CG short
     assert P.rel_residual(u) <= 1.05e-8
     assert abs(c - P.compliance(u)) <= 1e-12 * c
     assert abs(c - float(u @ (P.K @ u))) <= 1e-7 * c
@@ -141,7 +152,8 @@ def test_mbb_96x32x32_full_size_properties(topo):
     elems = I.fd_elements(rho, 50, 99)
     en = fem.element_energies_at(P.grid, u, P.k0, elems)
     ref = -3.0 * rho[elems].astype(np.float64) ** 2 * (1 - 1e-9) * en
-    assert np.all(np.abs(dc[elems] - ref) <= 1e-9 * np.abs(ref) + 1e-300)
+    # FP64 on both sides, different summation order: 1e-8 relative + 1e-12 of the largest
+    assert np.all(np.abs(dc[elems] - ref) <= 1e-8 * np.abs(ref) + 1e-12 * np.abs(ref).max())
 
 
 def test_deterministic_bitwise(topo):
@@ -199,7 +211,9 @@ def test_errors_are_reported_not_raised_in_the_library(topo):
             m.set_density(bad)
         assert e.value.status == topo.ERR_NAN
         m.set_density(np.full(16, 0.5, np.float32))
-        info = m.solve(topo.default_opts(max_iter=1, rtol=1e-14), check=False)
+        info = m.solve(topo.default_opts(max_iter=1, rtol=1e-14, precond=0), check=False)
         assert info.status == topo.ERR_NOT_CONVERGED and info.iters <= 1
+        info = m.solve(topo.default_opts(precision=0, precond=1), check=False)
+        assert info.status == topo.ERR_INVALID
         info = m.solve(topo.default_opts(precision=7), check=False)
         assert info.status == topo.ERR_INVALID
