@@ -8,6 +8,10 @@
 
 namespace topo {
 
+// ---- host helpers (topo.cu) ---------------------------------------------
+// k0 (24x24, row-major) of the unit cube for E = 1 and Poisson ratio nu
+void build_k0(double nu, double* k);
+
 // ---- operator (operator.cu) -------------------------------------------
 enum ApplyMode {
   APPLY_PLAIN = 0,  // y = A x

@@ -26,7 +26,7 @@
 
 using namespace topo;
 
-namespace {
+namespace topo {
 
 // --------------------------------------------------------------------------
 // k0 of the unit cube for E = 1 (Sec. 2.1.2), built from exact 1-D integrals
@@ -67,6 +67,10 @@ void build_k0(double nu, double* k) {
           k[(3 * a + p) * 24 + 3 * b + q] = v;
         }
 }
+
+}  // namespace topo
+
+namespace {
 
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();

@@ -77,6 +77,7 @@ def lib():
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
+            "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
             "topo_free": (None, [vp]),
             "topo_status_string": (C.c_char_p, [i]),
         }
@@ -115,6 +116,20 @@ def default_opts(**kw) -> SolveOpts:
 
 def footprint_bytes(nx, ny, nz, opts: SolveOpts | None = None) -> int:
     return int(lib().topo_footprint_bytes(nx, ny, nz, C.byref(opts) if opts else None))
+
+
+def sensitivity_noalloc(nx, ny, nz, u, rho, dc, c, params: Params | None = None, stream=None):
+    """topo_sensitivity_noalloc on CUDA tensors (u: float64 DOFs, rho: float32
+    elements, dc: float64 elements, c: one float64); enqueued, not synchronised."""
+    pu, nu_, du = _ptr(u, np.float64)
+    pr, nr, dr = _ptr(rho, np.float32)
+    pd, nd, dd = _ptr(dc, np.float64)
+    pc, nc, dcc = _ptr(c, np.float64)
+    if not (du and dr and dd and dcc):
+        raise TypeError("topo_sensitivity_noalloc takes device arrays only")
+    s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().topo_sensitivity_noalloc(nx, ny, nz, C.byref(params) if params else None,
+                                          pu, pr, pd, pc, s), "topo_sensitivity_noalloc")
 
 
 def _ptr(a, dtype):
