@@ -30,10 +30,14 @@
  *     arrays are only read or written during the call (inputs are copied).
  *   - on_device != 0: the pointer is a device pointer on the mesh's device;
  *     on_device == 0: it is a host pointer (pageable or pinned).
- *   - Work runs on the CUDA stream given to topo_create_mesh (NULL: the
- *     library's own stream).  Calls that return host values synchronise
- *     that stream; the others only enqueue work.  One mesh must not be used
- *     from two host threads at once; different meshes are independent.
+ *   - Streams: each mesh runs its kernels on its own non-blocking stream and
+ *     fences it against the caller's stream (given to topo_create_mesh or
+ *     topo_set_stream; NULL = the legacy default stream) with events: a
+ *     call's work starts after everything already enqueued on the caller's
+ *     stream, and work the caller enqueues after the call starts after it.
+ *     Calls that return host values synchronise; the others only enqueue.
+ *     One mesh must not be used from two host threads at once; different
+ *     meshes are independent.
  *   - Sizes are checked: a count that differs from the mesh's size returns
  *     TOPO_ERR_INVALID and touches nothing.
  */
@@ -120,8 +124,8 @@ void topo_default_params(topo_params* p);
 void topo_default_opts(topo_solve_opts* o);
 
 /* Create a mesh of nx*ny*nz elements (each >= 1) with the given boundary
- * condition and load, on the current CUDA device.  stream: a cudaStream_t
- * (NULL = the library creates its own).  Allocates all device state of the
+ * condition and load, on the current CUDA device.  stream: the caller's
+ * cudaStream_t to order against (NULL = legacy default stream).  Allocates all device state of the
  * FP32/FP64 Jacobi paths; the multigrid hierarchy is built on first use.
  * Cites Eq. (2): K is assembled implicitly (matrix-free) from E_e k0. */
 topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
@@ -139,6 +143,15 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
  * Returns TOPO_ERR_NOT_CONVERGED (u kept, info->rel_residual set) if the
  * iteration caps are reached first. */
 topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_info* info);
+
+/* Solve n distinct meshes at once (same options; NULL = defaults): each
+ * mesh runs on its own stream and one host thread advances all of them, so
+ * their kernels overlap on the GPU (batched / continuous solving).  infos:
+ * NULL or n entries, each filled as by topo_solve.  Returns TOPO_OK if every
+ * solve succeeded, else the first failing status (see infos for each);
+ * TOPO_ERR_INVALID if a mesh appears twice.  Blocks until all are done. */
+topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_opts* opts,
+                            topo_solve_info* infos);
 
 /* Compliance J = f^T u (Eq. (2)) of the last solve, computed in FP64. */
 topo_status topo_compliance(topo_mesh* m, double* c);
@@ -170,6 +183,9 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
  * mesh's stream over the mesh's internal vectors (no copies, no sync), for
  * timing.  Cites Eq. (2) (K u). */
 topo_status topo_apply_internal(topo_mesh* m, int precision, int reps);
+
+/* Change the caller stream the mesh orders its calls against. */
+topo_status topo_set_stream(topo_mesh* m, void* stream);
 
 /* Sizes and memory: nodes, free DOFs, bytes of device memory held. */
 topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_free_dof,

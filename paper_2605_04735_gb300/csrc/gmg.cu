@@ -1,6 +1,7 @@
 // Geometric multigrid V-cycle (see gmg.h).  All grid transfers are gathers
 // (no atomics); the Chebyshev smoother's vector updates are fused into the
 // operator kernel's epilogue, so one smoothing step is one pass.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,7 +17,7 @@ namespace topo {
 
 namespace {
 
-constexpr int kCoarseMaxDof = 1200;  // target size of the dense coarsest problem
+constexpr int kCoarseMaxDof = 400;  // target size of the dense coarsest problem
 constexpr int kPT = 256;
 
 inline int grid1d(long long n) {
@@ -254,38 +255,47 @@ __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const flo
   }
 }
 
-// in-place Gauss-Jordan inversion of an SPD matrix, one kernel per pivot k;
-// the pivot row/column before step k are read from side buffers (written by
-// step k-1), so no entry is read after it was overwritten in the same step
-__global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
-                          double* __restrict__ col) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) {
-    row[t] = A[t];
-    col[t] = A[(long long)t * n];
-  }
-}
-
-__global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
-                          const double* __restrict__ colk, double* __restrict__ rown,
-                          double* __restrict__ coln) {
+// In-place Gauss-Jordan inversion of the SPD coarsest matrix (no pivoting
+// needed: every pivot is a Schur-complement diagonal, hence positive), as ONE
+// cooperative kernel with a grid-wide barrier between pivots.  The pivot row
+// and column as they were before step k are read from side buffers written
+// during step k-1 (ping-pong), so no entry is read after being overwritten
+// in the same step.
+__global__ void __launch_bounds__(256) k_gj_coop(double* __restrict__ A, int n,
+                                                 double* __restrict__ side) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
   const long long nn = (long long)n * n;
-  const double p = 1.0 / rowk[k];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    double v;
-    if (i == k && j == k)
-      v = p;
-    else if (i == k)
-      v = rowk[j] * p;
-    else if (j == k)
-      v = -colk[i] * p;
-    else
-      v = A[t] - colk[i] * rowk[j] * p;
-    A[t] = v;
-    if (i == k + 1) rown[j] = v;
-    if (j == k + 1) coln[i] = v;
+  const long long tid = grid.thread_rank();
+  const long long nthr = grid.size();
+  double* buf[2][2] = {{side, side + n}, {side + 2 * n, side + 3 * n}};
+  for (long long t = tid; t < n; t += nthr) {
+    buf[0][0][t] = A[t];
+    buf[0][1][t] = A[t * n];
+  }
+  grid.sync();
+  for (int k = 0; k < n; ++k) {
+    const double* rowk = buf[k & 1][0];
+    const double* colk = buf[k & 1][1];
+    double* rown = buf[(k + 1) & 1][0];
+    double* coln = buf[(k + 1) & 1][1];
+    const double p = 1.0 / rowk[k];
+    for (long long t = tid; t < nn; t += nthr) {
+      const int i = (int)(t / n), j = (int)(t % n);
+      double v;
+      if (i == k && j == k)
+        v = p;
+      else if (i == k)
+        v = rowk[j] * p;
+      else if (j == k)
+        v = -colk[i] * p;
+      else
+        v = A[t] - colk[i] * rowk[j] * p;
+      A[t] = v;
+      if (i == k + 1) rown[j] = v;
+      if (j == k + 1) coln[i] = v;
+    }
+    grid.sync();
   }
 }
 
@@ -445,23 +455,27 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
   const long long nn = (long long)g.nc * g.nc;
   k_dense_assemble<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d);
   GCK(cudaGetLastError());
-  double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
-  k_gj_seed<<<(g.nc + kPT - 1) / kPT, kPT, 0, s>>>(g.Ainv, g.nc, buf[0][0], buf[0][1]);
-  GCK(cudaGetLastError());
-  *launches += 2;
-  for (int k = 0; k < g.nc; ++k) {
-    double** cur = buf[k & 1];
-    double** nxt = buf[(k + 1) & 1];
-    k_gj_step<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, g.nc, k, cur[0], cur[1], nxt[0], nxt[1]);
-    GCK(cudaGetLastError());
-  }
-  *launches += g.nc;
+  // one cooperative launch: as many co-resident blocks as the device holds,
+  // no more than the matrix needs
+  int per_sm = 0, sms = 0, dev = 0;
+  GCK(cudaGetDevice(&dev));
+  GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kPT, 0));
+  long long blocks = std::min<long long>((long long)per_sm * sms, (nn + kPT - 1) / kPT);
+  if (blocks < 1) blocks = 1;
+  int n = g.nc;
+  double* A = g.Ainv;
+  double* side = g.side;
+  void* args[] = {&A, &n, &side};
+  GCK(cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3((unsigned)blocks), dim3(kPT), args,
+                                  0, s));
+  *launches += 1;
   g.ready = true;
   return cudaSuccess;
 }
 
 cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f, const int* done,
-                       cudaStream_t s, long long* launches) {
+                       int* errflag, cudaStream_t s, long long* launches) {
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
@@ -478,10 +492,10 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
-      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, s));
+      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, errflag, s));
       ++*launches;
     }
-    GCK(launch_stencil<float>(L.dv[(m - 1) & 1], L.E, L.d, k0f, EpiChebLast{L.r}, nored, done, s));
+    GCK(launch_stencil<float>(L.dv[(m - 1) & 1], L.E, L.d, k0f, EpiChebLast{L.r}, nored, done, errflag, s));
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     k_restrict<<<grid1d(nnc), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done);
@@ -508,11 +522,11 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     k_prolong_add<<<grid1d(nnf), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done);
     GCK(cudaGetLastError());
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
-    GCK(launch_stencil<float>(X(l), L.E, L.d, k0f, er, nored, done, s));
+    GCK(launch_stencil<float>(X(l), L.E, L.d, k0f, er, nored, done, errflag, s));
     *launches += 2;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
-      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, s));
+      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, errflag, s));
       ++*launches;
     }
     if (m == 1) {

@@ -49,7 +49,7 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 // x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
 // when *done is set.
 cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f, const int* done,
-                       cudaStream_t s, long long* launches);
+                       int* errflag, cudaStream_t s, long long* launches);
 void gmg_free(Gmg& g);
 // lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
 double k0_jacobi_bound(const double* k0);

@@ -18,9 +18,10 @@ enum ApplyMode {
   APPLY_DOT = 1,    // y = A x, reduce x . y
   APPLY_RESID = 2   // y = f - A x (0 on fixed DOFs), reduce y . y
 };
+// errflag: set to 1 by the kernel if a bounded device-side wait ran out
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
-                         const Red& red, int mode, const int* done, cudaStream_t s);
+                         const Red& red, int mode, const int* done, int* errflag, cudaStream_t s);
 template <typename T>
 cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s);
 

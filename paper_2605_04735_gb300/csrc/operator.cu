@@ -80,14 +80,15 @@ __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const 
 
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
-                         const Red& red, int mode, const int* done, cudaStream_t s) {
+                         const Red& red, int mode, const int* done, int* errflag,
+                         cudaStream_t s) {
   switch (mode) {
     case APPLY_PLAIN:
-      return launch_stencil<T>(x, E, d, k0, EpiApply<T, false>{y}, red, done, s);
+      return launch_stencil<T>(x, E, d, k0, EpiApply<T, false>{y}, red, done, errflag, s);
     case APPLY_DOT:
-      return launch_stencil<T>(x, E, d, k0, EpiApply<T, true>{y}, red, done, s);
+      return launch_stencil<T>(x, E, d, k0, EpiApply<T, true>{y}, red, done, errflag, s);
     default:
-      return launch_stencil<T>(x, E, d, k0, EpiResid<T>{y, f}, red, done, s);
+      return launch_stencil<T>(x, E, d, k0, EpiResid<T>{y, f}, red, done, errflag, s);
   }
 }
 
@@ -101,10 +102,10 @@ cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0,
 
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,
                                          const Dims&, const K0<float>&, const Red&, int,
-                                         const int*, cudaStream_t);
+                                         const int*, int*, cudaStream_t);
 template cudaError_t launch_apply<double>(const double*, double*, const double*, const double*,
                                           const Dims&, const K0<double>&, const Red&, int,
-                                          const int*, cudaStream_t);
+                                          const int*, int*, cudaStream_t);
 template cudaError_t launch_diag_inv<float>(float*, const float*, const Dims&, const K0<float>&,
                                             cudaStream_t);
 template cudaError_t launch_diag_inv<double>(double*, const double*, const Dims&,

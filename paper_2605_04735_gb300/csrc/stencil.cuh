@@ -16,9 +16,11 @@
 // to write; it returns the node's contribution to an optional reduction.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace topo {
 
@@ -87,6 +89,15 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
       // cancelling large rigid displacements against each other, and the
       // centre terms vanish (72 FMAs fewer, 78 subtractions more).
       const T ctr[3] = {w[1][1][1][0], w[1][1][1][1], w[1][1][1][2]};
+      T t[3][3][3][3];  // shifted window, formed once per node (each entry feeds up to 8 elements)
+#pragma unroll
+      for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+        for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+          for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[zz][yy][xx][c] = w[zz][yy][xx][c] - ctr[c];
       T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int c = 0; c < 2; ++c)
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
                       s[r] = fma(k0.v[(3 * ln + r) * 24 + 3 * lm + q],
-                                 w[c + dz][b + dy][a + dx][q] - ctr[q], s[r]);
+                                 t[c + dz][b + dy][a + dx][q], s[r]);
                 }
             const T ee = e[c][b][a];
 #pragma unroll
@@ -192,6 +203,183 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-staged FP32 variant.  A CTA owns a 32 x 8 tile of node columns and a
+// z range; node planes (36 x 10 halo box, 3 components) and element planes
+// (36 x 9 box) stream through a kTmaStages-deep shared-memory ring, each
+// stage filled by one elected thread with cp.async.bulk.tensor and
+// completed on an mbarrier.  Threads copy their 3x3 node and 2x2 element
+// neighbourhoods from the stage into the same register window as above, the
+// slot is refilled right away (kTmaStages - 1 planes ahead of the compute),
+// and the 576-FMA gather runs from registers.  Box starts are multiples of 4
+// floats (16 bytes) because of the one-element ghost layer: node i0-1 and
+// element i0-1 are both stored at x = i0.
+constexpr int kTmaStages = 4;
+constexpr int kBoxX = kStencilBX + 4;        // 36 >= 32 + 2 halo, 144 bytes
+constexpr int kBoxYN = kStencilBY + 2;       // node rows
+constexpr int kBoxYE = kStencilBY + 1;       // element rows
+constexpr int kNodeStage = kBoxX * kBoxYN * 3;  // floats
+constexpr int kElemStage = kBoxX * kBoxYE;      // floats
+constexpr uint32_t kStageTx = (uint32_t)(kNodeStage + kElemStage) * 4u;
+
+struct __align__(128) TmaStage {
+  float node[kNodeStage];
+  alignas(128) float elem[kElemStage];
+};
+
+template <class Epi>
+__global__ void __launch_bounds__(kStencilBX* kStencilBY)
+    k_stencil_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
+                  const Dims d, const __grid_constant__ K0<float> k0, const Epi epi, const Red red,
+                  const int zchunk, const int* __restrict__ done, int* __restrict__ errflag) {
+  if (done != nullptr && *done) return;  // uniform over the grid
+  __shared__ TmaStage st[kTmaStages];
+  __shared__ uint64_t bar[kTmaStages];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * kStencilBX + tx;
+  const int i0 = blockIdx.x * kStencilBX, j0 = blockIdx.y * kStencilBY;
+  const int i = i0 + tx, j = j0 + ty;
+  const int kb = blockIdx.z * zchunk;
+  const int ke = min(kb + zchunk, d.nz + 1);
+  const int nst = (ke - kb) + 2;  // stage s: node plane kb-1+s, element plane kb-2+s
+  const bool act = (i <= d.nx) && (j <= d.ny);
+  if (tid == 0) {
+    for (int q = 0; q < kTmaStages; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+    tma_prefetch_desc(&xmap);
+    tma_prefetch_desc(&emap);
+  }
+  __syncthreads();
+  auto issue = [&](int s) {
+    const int slot = s % kTmaStages;
+    mbar_arrive_expect_tx(&bar[slot], kStageTx);
+    // storage coordinates: +1 for the ghost layer in every direction
+    tma_load_4d(st[slot].node, &xmap, &bar[slot], i0, j0, kb + s, 0);
+    tma_load_3d(st[slot].elem, &emap, &bar[slot], i0, j0, kb - 1 + s);
+  };
+  if (tid == 0)
+    for (int s = 0; s < kTmaStages && s < nst; ++s) issue(s);
+  auto release = [&](int s) {
+    __syncthreads();  // every thread has copied stage s out of its slot
+    if (tid == 0 && s + kTmaStages < nst) {
+      // order the generic-proxy reads of the slot before the async-proxy refill
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(s + kTmaStages);
+    }
+  };
+  float w[3][3][3][3];
+  float e[2][2][2];
+  auto read_nodes = [&](int s, int zslot) {
+    const float* nd = st[s % kTmaStages].node;
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          w[zslot][yy][xx][c] = nd[c * (kBoxX * kBoxYN) + (ty + yy) * kBoxX + tx + xx];
+  };
+  auto read_elems = [&](int s, int zslot) {
+    const float* el = st[s % kTmaStages].elem;
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx) e[zslot][yy][xx] = el[(ty + yy) * kBoxX + tx + xx];
+  };
+  mbar_wait_bounded(&bar[0], 0, errflag);
+  read_nodes(0, 0);
+  release(0);
+  mbar_wait_bounded(&bar[1 % kTmaStages], (1 / kTmaStages) & 1, errflag);
+  read_nodes(1, 1);
+  read_elems(1, 0);
+  release(1);
+  double part = 0.0;
+  for (int k = kb; k < ke; ++k) {
+    const int s = k - kb + 2;
+    mbar_wait_bounded(&bar[s % kTmaStages], (uint32_t)((s / kTmaStages) & 1), errflag);
+    // plain shared-memory loads of the stage (the ordering of the TMA write
+    // before them is given by the mbarrier wait)
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          w[2][yy][xx][c] =
+              st[s % kTmaStages].node[c * (kBoxX * kBoxYN) + (ty + yy) * kBoxX + tx + xx];
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx)
+        e[1][yy][xx] = st[s % kTmaStages].elem[(ty + yy) * kBoxX + tx + xx];
+    release(s);
+    if (act) {
+      const float ctr[3] = {w[1][1][1][0], w[1][1][1][1], w[1][1][1][2]};
+      float t[3][3][3][3];  // shifted window (see k_stencil)
+#pragma unroll
+      for (int zz = 0; zz < 3; ++zz)
+#pragma unroll
+        for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+          for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[zz][yy][xx][c] = w[zz][yy][xx][c] - ctr[c];
+      float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const int ln = lidx(1 - a, 1 - b, 1 - c);
+            float sv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+              for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                  if (a + dx == 1 && b + dy == 1 && c + dz == 1) continue;
+                  const int lm = lidx(dx, dy, dz);
+#pragma unroll
+                  for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                      sv[r] = fmaf(k0.v[(3 * ln + r) * 24 + 3 * lm + q], t[c + dz][b + dy][a + dx][q],
+                                   sv[r]);
+                }
+            const float ee = e[c][b][a];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) acc[r] = fmaf(ee, sv[r], acc[r]);
+          }
+      part += epi(i, j, k, d.node(i, j, k), acc, ctr, d);
+    }
+#pragma unroll
+    for (int yy = 0; yy < 3; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 3; ++xx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          w[0][yy][xx][c] = w[1][yy][xx][c];
+          w[1][yy][xx][c] = w[2][yy][xx][c];
+        }
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx) e[0][yy][xx] = e[1][yy][xx];
+  }
+  if (Epi::kReduce) {
+    double v[1] = {part};
+    reduce_finalize<1>(v, red);
+  }
+}
+
+// host: tensor maps of a node vector (4-D: x, y, z, component) and of an
+// element array (3-D) in the ghosted layout, cached by base address
+bool stencil_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+                  CUtensorMap* emap);
+
 // z planes per thread: enough blocks for ~4 waves of 152 SMs at 2 resident
 // blocks each, a 2-plane halo reload below ~15%, and at most kMaxPartials blocks
 inline int stencil_zchunk(const Dims& d) {
@@ -206,14 +394,19 @@ inline int stencil_zchunk(const Dims& d) {
 
 template <typename T, class Epi>
 cudaError_t launch_stencil(const T* x, const T* E, const Dims& d, const K0<T>& k0, const Epi& epi,
-                           const Red& red, const int* done, cudaStream_t s) {
+                           const Red& red, const int* done, int* errflag, cudaStream_t s) {
   const int z = stencil_zchunk(d);
   dim3 block(kStencilBX, kStencilBY, 1);
   dim3 grid((d.nx + kStencilBX) / kStencilBX, (d.ny + kStencilBY) / kStencilBY, (d.nz + z) / z);
-  if constexpr (sizeof(T) == 8)
+  if constexpr (sizeof(T) == 8) {
     k_stencil_direct<T, Epi><<<grid, block, 0, s>>>(x, E, d, k0, epi, red, z, done);
-  else
-    k_stencil<T, Epi><<<grid, block, 0, s>>>(x, E, d, k0, epi, red, z, done);
+  } else {
+    CUtensorMap xm, em;
+    if (stencil_maps(x, E, d, &xm, &em))
+      k_stencil_tma<Epi><<<grid, block, 0, s>>>(xm, em, d, k0, epi, red, z, done, errflag);
+    else  // grids too small for the TMA boxes: same arithmetic from plain loads
+      k_stencil<T, Epi><<<grid, block, 0, s>>>(x, E, d, k0, epi, red, z, done);
+  }
   return cudaGetLastError();
 }
 

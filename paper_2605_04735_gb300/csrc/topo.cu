@@ -16,7 +16,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/topo.h"
@@ -81,9 +84,16 @@ struct Timer {
 
 }  // namespace
 
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels in one replay
+};
+
 struct topo_mesh {
   int dev = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the mesh's own non-blocking stream (all work runs here)
+  cudaStream_t user = nullptr;    // the caller's stream (NULL = legacy default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fences between the two
   bool own_stream = false;
   Dims d{};
   topo_params prm{};
@@ -108,6 +118,8 @@ struct topo_mesh {
   // scratch
   PcgScalars* sc = nullptr;
   PcgScalars* h_sc = nullptr;  // pinned mirror
+  int* h_flag = nullptr;       // pinned mirror of the timeout flag
+  cudaEvent_t ev_poll = nullptr;  // marks the arrival of h_sc / h_flag
   double* partials = nullptr;
   int* flags = nullptr;
   double* aos = nullptr;       // n_dof doubles (ABI transfers)
@@ -123,6 +135,9 @@ struct topo_mesh {
   double prof_ms = 0.0;
   long long prof_launches = 0;
   long long launches = 0;  // every kernel this mesh launched
+
+  // captured CG chunks, keyed by (kind, iterations, profiling)
+  std::map<long long, ChunkGraph> graphs;
 
   // multigrid hierarchy (built on the first GMG solve, set up per density)
   Gmg gmg;
@@ -193,6 +208,24 @@ topo_status sync_scalars(topo_mesh* m) {
   return TOPO_OK;
 }
 
+// Orders a call's work after everything the caller enqueued on its stream
+// before the call, and everything the caller enqueues afterwards after it.
+struct Fence {
+  topo_mesh* m;
+  topo_status st = TOPO_OK;
+  explicit Fence(topo_mesh* mm) : m(mm) {
+    if (cudaSetDevice(m->dev) != cudaSuccess || cudaEventRecord(m->ev_in, m->user) != cudaSuccess ||
+        cudaStreamWaitEvent(m->stream, m->ev_in, 0) != cudaSuccess)
+      st = TOPO_ERR_CUDA;
+  }
+  ~Fence() {
+    if (cudaEventRecord(m->ev_out, m->stream) == cudaSuccess)
+      cudaStreamWaitEvent(m->user, m->ev_out, 0);
+  }
+  Fence(const Fence&) = delete;
+  Fence& operator=(const Fence&) = delete;
+};
+
 topo_status ensure_fp64_inner(topo_mesh* m) {
   if (m->x64) return TOPO_OK;
   CKS(dalloc(m, &m->x64, m->nvec));
@@ -213,94 +246,88 @@ topo_status ensure_profile_events(topo_mesh* m, int n) {
   return TOPO_OK;
 }
 
-// Preconditioned CG on A x = b (A = masked stiffness operator in precision
-// T), from x = 0, to ||r|| <= rtol ||b||; returns iterations in *iters and
-// the device status (0 converged, 1 iteration cap, 2 breakdown).
-template <typename T>
-topo_status inner_pcg(topo_mesh* m, const T* b, T* x, T* r, T* z, T* p, T* q, const T* dinv,
-                      const T* E, const K0<T>& k0, double rtol, int max_iter, int check_every,
-                      bool profile, int* iters, int* dev_status) {
+enum InnerKind { IK_JAC32 = 0, IK_JAC64 = 1, IK_GMG32 = 2 };
+
+// Enqueue `count` CG iterations of the given kind.  Every kernel returns at
+// once when the device-side `done` flag is set, so iterations past
+// convergence are no-ops and a chunk can be replayed blindly.
+topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
   cudaStream_t s = m->stream;
-  LK(m, launch_set_max_iter(m->sc, max_iter, s));
-  LK(m, launch_pcg_init<T>(b, x, r, z, p, dinv, m->nvec, red_of(m, FIN_INIT, rtol * rtol), true, s));
   const int* done = &m->sc->done;
-  int it_before = 0;
-  if (profile) CKS(ensure_profile_events(m, check_every));
-  for (;;) {
-    for (int c = 0; c < check_every; ++c) {
-      if (profile) CK(cudaEventRecord(m->ev[2 * c], s));
-      LK(m, launch_apply<T>(p, q, E, nullptr, m->d, k0, red_of(m, FIN_ALPHA), APPLY_DOT, done, s));
-      if (profile) CK(cudaEventRecord(m->ev[2 * c + 1], s));
-      LK(m, launch_pcg_update<T>(x, r, z, p, q, dinv, m->nvec, red_of(m, FIN_UPDATE), true, s));
-      LK(m, launch_pcg_direction<T>(p, z, m->nvec, m->sc, s));
+  for (int c = 0; c < count; ++c) {
+    if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c], s, cudaEventRecordExternal));
+    if (kind == IK_JAC64) {
+      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
+                                 red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s));
+    } else {
+      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f,
+                                red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s));
     }
-    CKS(sync_scalars(m));
-    if (profile) {
-      const int worked = std::min(check_every, m->h_sc->iter - it_before);
-      for (int c = 0; c < worked; ++c) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
-        m->prof_ms += ms;
-        m->prof_launches += 1;
-      }
+    if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
+    switch (kind) {
+      case IK_JAC32:
+        LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32, m->nvec,
+                                       red_of(m, FIN_UPDATE), true, s));
+        LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
+        break;
+      case IK_JAC64:
+        LK(m, launch_pcg_update<double>(m->x64, m->s64, m->z64, m->p64, m->q64, m->dinv64,
+                                        m->nvec, red_of(m, FIN_UPDATE), true, s));
+        LK(m, launch_pcg_direction<double>(m->p64, m->z64, m->nvec, m->sc, s));
+        break;
+      default:
+        LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
+                                       red_of(m, FIN_RR_ONLY), false, s));
+        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, done, m->flags + 1, s, &m->launches));
+        LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_RZ_BETA), s));
+        LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
+        break;
     }
-    if (m->h_sc->done) break;
-    if (m->h_sc->iter == it_before) return TOPO_ERR_CUDA;  // no progress without a stop: bug
-    it_before = m->h_sc->iter;
   }
-  *iters = m->h_sc->iter;
-  *dev_status = m->h_sc->status;
   return TOPO_OK;
 }
 
-// Preconditioned CG with one V-cycle as the preconditioner (FP32).
-topo_status inner_pcg_gmg(topo_mesh* m, const float* b, float* x, float* r, float* z, float* p,
-                          float* q, double rtol, int max_iter, int check_every, bool profile,
-                          int* iters, int* dev_status) {
-  cudaStream_t s = m->stream;
-  const int* done = &m->sc->done;
-  LK(m, launch_set_max_iter(m->sc, max_iter, s));
-  LK(m, launch_pcg_init<float>(b, x, r, z, p, nullptr, m->nvec,
-                               red_of(m, FIN_INIT, rtol * rtol), false, s));
-  CK(gmg_vcycle(m->gmg, r, z, m->k0f, done, s, &m->launches));
-  LK(m, launch_dot<float>(r, z, m->nvec, red_of(m, FIN_SET_RZ), s));
-  LK(m, launch_pcg_direction<float>(p, z, m->nvec, m->sc, s));
-  int it_before = 0;
-  if (profile) CKS(ensure_profile_events(m, check_every));
-  for (;;) {
-    for (int c = 0; c < check_every; ++c) {
-      if (profile) CK(cudaEventRecord(m->ev[2 * c], s));
-      LK(m, launch_apply<float>(p, q, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_ALPHA),
-                                APPLY_DOT, done, s));
-      if (profile) CK(cudaEventRecord(m->ev[2 * c + 1], s));
-      LK(m, launch_pcg_update<float>(x, r, z, p, q, nullptr, m->nvec, red_of(m, FIN_RR_ONLY),
-                                     false, s));
-      CK(gmg_vcycle(m->gmg, r, z, m->k0f, done, s, &m->launches));
-      LK(m, launch_dot<float>(r, z, m->nvec, red_of(m, FIN_RZ_BETA), s));
-      LK(m, launch_pcg_direction<float>(p, z, m->nvec, m->sc, s));
+void clear_graphs(topo_mesh* m) {
+  for (auto& kv : m->graphs) cudaGraphExecDestroy(kv.second.exec);
+  m->graphs.clear();
+}
+
+// Run a chunk of iterations as one CUDA graph (captured on first use per
+// kind/size/profiling, then replayed): one launch instead of ~40 per
+// iteration for the multigrid path.
+topo_status run_iters(topo_mesh* m, int kind, int count, bool profile) {
+  const long long key = (long long)kind | ((long long)count << 4) | ((long long)profile << 24);
+  auto it = m->graphs.find(key);
+  if (it == m->graphs.end()) {
+    const long long l0 = m->launches;
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    const topo_status st = enqueue_iters(m, kind, count, profile);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+    if (st != TOPO_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != TOPO_OK ? st : cuda_status(e);
     }
-    CKS(sync_scalars(m));
-    if (profile) {
-      const int worked = std::min(check_every, m->h_sc->iter - it_before);
-      for (int c = 0; c < worked; ++c) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
-        m->prof_ms += ms;
-        m->prof_launches += 1;
-      }
-    }
-    if (m->h_sc->done) break;
-    if (m->h_sc->iter == it_before) return TOPO_ERR_CUDA;
-    it_before = m->h_sc->iter;
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    ChunkGraph cg;
+    cg.exec = ex;
+    cg.launches = m->launches - l0;
+    m->launches = l0;
+    it = m->graphs.emplace(key, cg).first;
   }
-  *iters = m->h_sc->iter;
-  *dev_status = m->h_sc->status;
+  CK(cudaGraphLaunch(it->second.exec, m->stream));
+  m->launches += it->second.launches;
   return TOPO_OK;
 }
 
 topo_status ensure_gmg(topo_mesh* m, const topo_solve_opts* o) {
   if (m->gmg_built && (m->gmg_levels_req != o->gmg_levels || m->gmg_degree != o->smooth_degree)) {
     CK(cudaStreamSynchronize(m->stream));
+    clear_graphs(m);
     m->bytes -= m->gmg.bytes;
     gmg_free(m->gmg);
     m->gmg = Gmg();
@@ -321,15 +348,79 @@ topo_status ensure_gmg(topo_mesh* m, const topo_solve_opts* o) {
   return TOPO_OK;
 }
 
-topo_status residual64(topo_mesh* m, double* rr) {
-  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
-                          APPLY_RESID, nullptr, m->stream));
-  CKS(sync_scalars(m));
-  *rr = m->h_sc->aux[0];
+// ---------------------------------------------------------------------------
+// Non-blocking solve driver.  A solve is a small state machine that only
+// ever enqueues work on its mesh's stream and asks for the device scalars
+// with an event; the host advances it when the event has completed.  One
+// host thread can thus drive many meshes at once (topo_solve_many), each on
+// its own stream, and a single solve simply waits on its event.
+// ---------------------------------------------------------------------------
+struct SolveTask {
+  topo_mesh* m = nullptr;
+  topo_solve_opts o{};
+  topo_solve_info* info = nullptr;
+  enum Phase { P_RESID, P_INNER, P_FINISHED } phase = P_FINISHED;
+  topo_status st = TOPO_OK;
+  int outer = 0, total = 0, it_before = 0, kind = IK_JAC32;
+  bool profile = false;
+  double fn = 0.0;
+  Timer timer;
+};
+
+topo_status request_scalars(topo_mesh* m) {
+  CK(cudaMemcpyAsync(m->h_sc, m->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaMemcpyAsync(m->h_flag, m->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaEventRecord(m->ev_poll, m->stream));
   return TOPO_OK;
 }
 
-topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* info) {
+void task_finish(SolveTask& t, topo_status st) {
+  t.st = st;
+  t.phase = SolveTask::P_FINISHED;
+  if (st == TOPO_OK) t.m->solved = true;
+  if (t.info) {
+    t.info->iters = t.total;
+    t.info->outer = t.outer;
+    t.info->status = st;
+    t.info->seconds = t.timer.seconds();
+  }
+}
+
+// FP64 residual r = f - K u (fixed DOFs 0), ||r||^2 -> aux[0]
+topo_status enqueue_residual64(topo_mesh* m) {
+  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
+                             APPLY_RESID, nullptr, m->flags + 1, m->stream));
+  return TOPO_OK;
+}
+
+// start of an inner CG from x = 0 on the current right-hand side
+topo_status enqueue_inner_start(SolveTask& t, double rtol, int max_iter) {
+  topo_mesh* m = t.m;
+  cudaStream_t s = m->stream;
+  const int* done = &m->sc->done;
+  LK(m, launch_set_max_iter(m->sc, max_iter, s));
+  if (t.kind == IK_JAC64) {
+    LK(m, launch_pcg_init<double>(m->r64, m->x64, m->s64, m->z64, m->p64, m->dinv64, m->nvec,
+                                  red_of(m, FIN_INIT, rtol * rtol), true, s));
+  } else {
+    LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s));  // b = r / ||r|| in FP32
+    if (t.kind == IK_JAC32) {
+      LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, m->dinv32, m->nvec,
+                                   red_of(m, FIN_INIT, rtol * rtol), true, s));
+    } else {
+      LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
+                                   red_of(m, FIN_INIT, rtol * rtol), false, s));
+      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, done, m->flags + 1, s, &m->launches));
+      LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s));
+      LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
+    }
+  }
+  return TOPO_OK;
+}
+
+topo_status task_start(SolveTask& t) {
+  topo_mesh* m = t.m;
+  const topo_solve_opts* o = &t.o;
   if (!m->has_density) return TOPO_ERR_NO_DENSITY;
   if (o->precision != TOPO_PREC_FP64 && o->precision != TOPO_PREC_FP32) return TOPO_ERR_INVALID;
   if (o->precond != TOPO_PRECOND_JACOBI && o->precond != TOPO_PRECOND_GMG) return TOPO_ERR_INVALID;
@@ -340,80 +431,117 @@ topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* in
       o->check_every > 1024)
     return TOPO_ERR_INVALID;
   cudaStream_t s = m->stream;
-  const bool fp64 = (o->precision == TOPO_PREC_FP64);
-  if (fp64) {
+  if (o->precision == TOPO_PREC_FP64) {
+    t.kind = IK_JAC64;
     CKS(ensure_fp64_inner(m));
     if (!m->diag64) {
       LK(m, launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, s));
       m->diag64 = true;
     }
-  } else if (!m->diag32) {
-    LK(m, launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s));
-    m->diag32 = true;
+  } else {
+    t.kind = (o->precond == TOPO_PRECOND_GMG) ? IK_GMG32 : IK_JAC32;
+    if (!m->diag32) {
+      LK(m, launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s));
+      m->diag32 = true;
+    }
   }
-  if (o->precond == TOPO_PRECOND_GMG) CKS(ensure_gmg(m, o));
+  if (t.kind == IK_GMG32) CKS(ensure_gmg(m, o));
+  t.profile = m->prof && t.kind != IK_JAC64;
+  if (t.profile) CKS(ensure_profile_events(m, o->check_every));
   m->solved = false;
-  double rr = 0.0;
+  t.fn = std::sqrt(m->fnorm2);
+  CK(cudaMemsetAsync(m->flags + 1, 0, sizeof(int), s));  // bounded-wait timeout flag
   if (o->warm_start) {
-    CKS(residual64(m, &rr));
+    CKS(enqueue_residual64(m));
   } else {
     CK(cudaMemsetAsync(m->u64, 0, sizeof(double) * m->nvec, s));
     CK(cudaMemcpyAsync(m->r64, m->f64, sizeof(double) * m->nvec, cudaMemcpyDeviceToDevice, s));
-    rr = m->fnorm2;
-    // aux[0] must hold ||r||^2 for the scaled narrowing below
     LK(m, launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s));
   }
-  int total_iters = 0, outer = 0;
-  topo_status st = TOPO_OK;
-  const double fn = std::sqrt(m->fnorm2);
-  for (;;) {
-    if (!std::isfinite(rr)) {
-      st = TOPO_ERR_NAN;
-      break;
+  CKS(request_scalars(m));
+  t.phase = SolveTask::P_RESID;
+  return TOPO_OK;
+}
+
+// Advance a task whose last scalar request has completed.
+topo_status task_step(SolveTask& t) {
+  topo_mesh* m = t.m;
+  const topo_solve_opts& o = t.o;
+  const PcgScalars& h = *m->h_sc;
+  if (*m->h_flag) return TOPO_ERR_TIMEOUT;
+  if (t.phase == SolveTask::P_RESID) {
+    const double rr = h.aux[0];
+    if (!std::isfinite(rr)) return TOPO_ERR_NAN;
+    const double rel = t.fn > 0 ? std::sqrt(rr) / t.fn : 0.0;
+    if (t.info) t.info->rel_residual = rel;
+    if (rel <= o.rtol) {
+      task_finish(t, TOPO_OK);
+      return TOPO_OK;
     }
-    const double rel = fn > 0 ? std::sqrt(rr) / fn : 0.0;
-    if (info) info->rel_residual = rel;
-    if (rel <= o->rtol) break;
-    if (outer >= o->max_outer || total_iters >= o->max_iter) {
-      st = TOPO_ERR_NOT_CONVERGED;
-      break;
-    }
-    int it = 0, dst = 0;
-    const int budget = o->max_iter - total_iters;
-    if (fp64) {
-      // target the final tolerance directly (relative to this rhs), with margin
-      double inner = 0.5 * o->rtol * fn / std::sqrt(rr);
-      inner = std::min(std::max(inner, 1e-15), 0.5);
-      CKS(inner_pcg<double>(m, m->r64, m->x64, m->s64, m->z64, m->p64, m->q64, m->dinv64, m->E64,
-                            m->k0d, inner, budget, o->check_every, false, &it, &dst));
-      LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, s));
-    } else {
-      LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s));
-      double inner = std::max(o->inner_rtol, 0.25 * o->rtol * fn / std::sqrt(rr));
-      inner = std::min(inner, 0.5);
-      if (o->precond == TOPO_PRECOND_GMG)
-        CKS(inner_pcg_gmg(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, inner, budget,
-                          o->check_every, m->prof, &it, &dst));
-      else
-        CKS(inner_pcg<float>(m, m->b32, m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32,
-                             m->E32, m->k0f, inner, budget, o->check_every, m->prof, &it, &dst));
-      // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
-      LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s));
-    }
-    total_iters += it;
-    ++outer;
-    if (dst == 2) {
-      st = TOPO_ERR_NAN;
-      break;
-    }
-    CKS(residual64(m, &rr));
+    if (t.outer >= o.max_outer || t.total >= o.max_iter) return TOPO_ERR_NOT_CONVERGED;
+    double inner;
+    if (t.kind == IK_JAC64)  // the final tolerance directly, with margin
+      inner = std::min(std::max(0.5 * o.rtol * t.fn / std::sqrt(rr), 1e-15), 0.5);
+    else
+      inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * t.fn / std::sqrt(rr)), 0.5);
+    CKS(enqueue_inner_start(t, inner, o.max_iter - t.total));
+    CKS(run_iters(m, t.kind, o.check_every, t.profile));
+    t.it_before = 0;
+    t.phase = SolveTask::P_INNER;
+    return request_scalars(m);
   }
-  if (info) {
-    info->iters = total_iters;
-    info->outer = outer;
+  // P_INNER: one chunk has run
+  if (t.profile) {
+    const int worked = std::min(o.check_every, h.iter - t.it_before);
+    for (int c = 0; c < worked; ++c) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
+      m->prof_ms += ms;
+      m->prof_launches += 1;
+    }
   }
-  if (st == TOPO_OK) m->solved = true;
-  return st;
+  if (!h.done) {
+    if (h.iter == t.it_before) return TOPO_ERR_CUDA;  // no progress without a stop: a bug
+    t.it_before = h.iter;
+    CKS(run_iters(m, t.kind, o.check_every, t.profile));
+    return request_scalars(m);
+  }
+  t.total += h.iter;
+  ++t.outer;
+  if (h.status == 2) return TOPO_ERR_NAN;
+  if (t.kind == IK_JAC64)
+    LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, m->stream));
+  else  // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
+    LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, m->stream));
+  CKS(enqueue_residual64(m));
+  t.phase = SolveTask::P_RESID;
+  return request_scalars(m);
+}
+
+void task_advance(SolveTask& t) {
+  const topo_status st = task_step(t);
+  if (st != TOPO_OK) task_finish(t, st);
+}
+
+topo_status do_solve(topo_mesh* m, const topo_solve_opts* o, topo_solve_info* info) {
+  SolveTask t;
+  t.m = m;
+  t.o = *o;
+  t.info = info;
+  topo_status st = task_start(t);
+  if (st != TOPO_OK) {
+    task_finish(t, st);
+    return st;
+  }
+  while (t.phase != SolveTask::P_FINISHED) {
+    const cudaError_t e = cudaEventSynchronize(m->ev_poll);
+    if (e != cudaSuccess) {
+      task_finish(t, cuda_status(e));
+      break;
+    }
+    task_advance(t);
+  }
+  return t.st;
 }
 
 topo_status upload_f64(topo_mesh* m, const double* src, double* dst_soa, size_t n_dof,
@@ -484,9 +612,14 @@ void topo_free(topo_mesh* m) {
                   m->rho_in};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  clear_graphs(m);
   if (m->gmg_built) gmg_free(m->gmg);
   if (m->h_sc) cudaFreeHost(m->h_sc);
+  if (m->h_flag) cudaFreeHost(m->h_flag);
+  if (m->ev_poll) cudaEventDestroy(m->ev_poll);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  if (m->ev_in) cudaEventDestroy(m->ev_in);
+  if (m->ev_out) cudaEventDestroy(m->ev_out);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
   delete m;
 }
@@ -494,12 +627,13 @@ void topo_free(topo_mesh* m) {
 static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
                                void* stream, topo_mesh* m) {
   CK(cudaGetDevice(&m->dev));
-  if (stream) {
-    m->stream = static_cast<cudaStream_t>(stream);
-  } else {
-    CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
-    m->own_stream = true;
-  }
+  m->user = static_cast<cudaStream_t>(stream);
+  CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
+  m->own_stream = true;
+  CK(cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming));
+  CK(cudaEventRecord(m->ev_in, m->user));
+  CK(cudaStreamWaitEvent(m->stream, m->ev_in, 0));
   m->d = make_dims(nx, ny, nz, bc, ny / 2);
   m->nvec = 3 * m->d.comp;
   if (prm)
@@ -534,10 +668,15 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
   CKS(dalloc(m, &m->aos, 3 * nn));
   CK(cudaMallocHost(&m->h_sc, sizeof(PcgScalars)));
   std::memset(m->h_sc, 0, sizeof(PcgScalars));
+  CK(cudaMallocHost(&m->h_flag, sizeof(int)));
+  *m->h_flag = 0;
+  CK(cudaEventCreateWithFlags(&m->ev_poll, cudaEventDisableTiming));
   LK(m, launch_build_load(m->f64, m->d, load, m->prm.load, m->prm.h, m->stream));
   LK(m, launch_dot<double>(m->f64, m->f64, m->nvec, red_of(m, FIN_AUX), m->stream));
   CKS(sync_scalars(m));
   m->fnorm2 = m->h_sc->aux[0];
+  CK(cudaEventRecord(m->ev_out, m->stream));
+  CK(cudaStreamWaitEvent(m->user, m->ev_out, 0));
   return TOPO_OK;
 }
 
@@ -566,7 +705,8 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
   if (!m || !rho) return TOPO_ERR_INVALID;
   const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
   if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   cudaStream_t s = m->stream;
   const float* src = rho;
   if (!on_device) {
@@ -600,10 +740,10 @@ topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_inf
   else
     topo_default_opts(&o);
   topo_status st;
-  if (cudaSetDevice(m->dev) != cudaSuccess)
-    st = TOPO_ERR_CUDA;
-  else
-    st = do_solve(m, &o, info);
+  {
+    Fence fence(m);
+    st = fence.st != TOPO_OK ? fence.st : do_solve(m, &o, info);
+  }
   if (info) {
     info->status = st;
     info->seconds = t.seconds();
@@ -611,10 +751,63 @@ topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_inf
   return st;
 }
 
+topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_opts* opts,
+                            topo_solve_info* infos) {
+  if (n < 0 || (n > 0 && !meshes)) return TOPO_ERR_INVALID;
+  for (int a = 0; a < n; ++a) {
+    if (!meshes[a]) return TOPO_ERR_INVALID;
+    for (int b = 0; b < a; ++b)
+      if (meshes[a] == meshes[b]) return TOPO_ERR_INVALID;  // one task per mesh
+  }
+  topo_solve_opts o;
+  if (opts)
+    o = *opts;
+  else
+    topo_default_opts(&o);
+  std::vector<SolveTask> tasks(n);
+  std::vector<std::unique_ptr<Fence>> fences;
+  fences.reserve(n);
+  for (int a = 0; a < n; ++a) {
+    if (infos) std::memset(&infos[a], 0, sizeof(topo_solve_info));
+    fences.emplace_back(new Fence(meshes[a]));
+    SolveTask& t = tasks[a];
+    t.m = meshes[a];
+    t.o = o;
+    t.info = infos ? &infos[a] : nullptr;
+    const topo_status st = fences.back()->st != TOPO_OK ? fences.back()->st : task_start(t);
+    if (st != TOPO_OK) task_finish(t, st);
+  }
+  // round-robin: advance every task whose scalars have arrived
+  for (;;) {
+    int active = 0, progressed = 0;
+    for (SolveTask& t : tasks) {
+      if (t.phase == SolveTask::P_FINISHED) continue;
+      ++active;
+      cudaSetDevice(t.m->dev);
+      const cudaError_t q = cudaEventQuery(t.m->ev_poll);
+      if (q == cudaSuccess) {
+        task_advance(t);
+        ++progressed;
+      } else if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+        task_finish(t, cuda_status(q));
+      }
+    }
+    if (!active) break;
+    if (!progressed) std::this_thread::yield();
+  }
+  fences.clear();  // make every caller stream wait for its mesh
+  topo_status first = TOPO_OK;
+  for (const SolveTask& t : tasks)
+    if (t.st != TOPO_OK && first == TOPO_OK) first = t.st;
+  return first;
+}
+
 topo_status topo_compliance(topo_mesh* m, double* c) {
   if (!m || !c) return TOPO_ERR_INVALID;
   if (!m->solved) return TOPO_ERR_NOT_SOLVED;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   LK(m, launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), m->stream));
   CKS(sync_scalars(m));
   *c = m->h_sc->aux[0];
@@ -632,7 +825,8 @@ static topo_status sens_impl(topo_mesh* m) {
 topo_status topo_compliance_energy(topo_mesh* m, double* c) {
   if (!m || !c) return TOPO_ERR_INVALID;
   if (!m->solved) return TOPO_ERR_NOT_SOLVED;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   CKS(sens_impl(m));
   CKS(sync_scalars(m));
   *c = m->h_sc->aux[0];
@@ -644,7 +838,8 @@ topo_status topo_sensitivity(topo_mesh* m, double* dc, size_t n_elem, int on_dev
   const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
   if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
   if (!m->solved) return TOPO_ERR_NOT_SOLVED;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   CKS(sens_impl(m));
   CK(cudaMemcpyAsync(dc, m->dc, ne * sizeof(double),
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
@@ -656,7 +851,8 @@ topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_
   if (!m || !u) return TOPO_ERR_INVALID;
   const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
   if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   double* dst = on_device ? u : m->aos;
   LK(m, launch_pack<double>(m->u64, dst, m->d, m->stream));
   if (!on_device) {
@@ -670,7 +866,8 @@ topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, i
   if (!m || !u) return TOPO_ERR_INVALID;
   const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
   if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   CKS(upload_f64(m, u, m->u64, n_dof, on_device));
   m->solved = false;
   if (!on_device) CK(cudaStreamSynchronize(m->stream));
@@ -684,7 +881,8 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
   const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
   if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
   if (!m->has_density) return TOPO_ERR_NO_DENSITY;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   cudaStream_t s = m->stream;
   const double* src = x;
   if (!on_device) {
@@ -695,12 +893,12 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
     CKS(ensure_fp64_inner(m));
     LK(m, launch_unpack<double>(src, m->p64, m->d, s));
     LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, red_of(m, FIN_NONE),
-                            APPLY_PLAIN, nullptr, s));
+                            APPLY_PLAIN, nullptr, m->flags + 1, s));
     LK(m, launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
   } else {
     LK(m, launch_unpack<float>(src, m->p32, m->d, s));
     LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
-                           APPLY_PLAIN, nullptr, s));
+                           APPLY_PLAIN, nullptr, m->flags + 1, s));
     LK(m, launch_pack<float>(m->q32, on_device ? y : m->aos, m->d, s));
   }
   if (!on_device) {
@@ -713,15 +911,16 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
 topo_status topo_apply_internal(topo_mesh* m, int precision, int reps) {
   if (!m || reps < 0) return TOPO_ERR_INVALID;
   if (!m->has_density) return TOPO_ERR_NO_DENSITY;
-  CK(cudaSetDevice(m->dev));
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
   for (int r = 0; r < reps; ++r) {
     if (precision == TOPO_PREC_FP64) {
       CKS(ensure_fp64_inner(m));
       LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
-                              red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->stream));
+                              red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->flags + 1, m->stream));
     } else if (precision == TOPO_PREC_FP32) {
       LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
-                             APPLY_PLAIN, nullptr, m->stream));
+                             APPLY_PLAIN, nullptr, m->flags + 1, m->stream));
     } else {
       return TOPO_ERR_INVALID;
     }
@@ -759,6 +958,12 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
   b += (long long)nx * ny * nz * (8 + 4);          // sensitivities + density staging
   if (opts && opts->precision == TOPO_PREC_FP64) b += nvec * 6 * 8;
   return b;
+}
+
+topo_status topo_set_stream(topo_mesh* m, void* stream) {
+  if (!m) return TOPO_ERR_INVALID;
+  m->user = static_cast<cudaStream_t>(stream);
+  return TOPO_OK;
 }
 
 topo_status topo_profile_enable(topo_mesh* m, int enable) {

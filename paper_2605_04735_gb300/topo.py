@@ -64,6 +64,7 @@ def lib():
             "topo_create_mesh": (i, [i, i, i, i, i, C.POINTER(Params), vp, C.POINTER(vp)]),
             "topo_set_density": (i, [vp, vp, sz, i]),
             "topo_solve": (i, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+            "topo_solve_many": (i, [C.POINTER(vp), i, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
             "topo_compliance": (i, [vp, C.POINTER(d)]),
             "topo_compliance_energy": (i, [vp, C.POINTER(d)]),
             "topo_sensitivity": (i, [vp, vp, sz, i]),
@@ -74,6 +75,7 @@ def lib():
             "topo_mesh_info": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                    C.POINTER(C.c_longlong)]),
             "topo_footprint_bytes": (C.c_longlong, [i, i, i, C.POINTER(SolveOpts)]),
+            "topo_set_stream": (i, [vp, vp]),
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
@@ -145,6 +147,17 @@ def _ptr(a, dtype):
     if str(a.dtype) != want:
         raise TypeError(f"expected {want}, got {a.dtype}")
     return a.data_ptr(), a.numel(), 1 if a.is_cuda else 0
+
+
+def solve_many(meshes, opts: SolveOpts | None = None, check: bool = True):
+    """Solve several meshes concurrently (one host thread, one stream each)."""
+    n = len(meshes)
+    arr = (C.c_void_p * n)(*[m._h for m in meshes])
+    infos = (SolveInfo * n)()
+    st = lib().topo_solve_many(arr, n, C.byref(opts) if opts else None, infos)
+    if check:
+        _check(st, "topo_solve_many")
+    return list(infos)
 
 
 class Mesh:
@@ -233,6 +246,11 @@ class Mesh:
 
     def apply_internal(self, precision=PREC_FP32, reps=1):
         _check(lib().topo_apply_internal(self._h, precision, reps), "topo_apply_internal")
+
+    def set_stream(self, stream):
+        """Order subsequent calls against `stream` (int handle or torch.cuda.Stream)."""
+        s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        _check(lib().topo_set_stream(self._h, s), "topo_set_stream")
 
     def info(self):
         a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()

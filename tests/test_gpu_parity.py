@@ -217,3 +217,90 @@ def test_errors_are_reported_not_raised_in_the_library(topo):
         assert info.status == topo.ERR_INVALID
         info = m.solve(topo.default_opts(precision=7), check=False)
         assert info.status == topo.ERR_INVALID
+
+
+def test_autograd_backward_matches_oracle_gradient_and_fd(topo):
+    """Compliance as a torch.autograd.Function: the backward (the adjoint
+    sensitivity kernel, no second solve) matches the oracle's gradient and
+    central finite differences of the oracle's compliance."""
+    import torch
+    from paper_2605_04735_gb300.autograd import compliance
+    nx, ny, nz = 6, 4, 4
+    rho_np = I.density_uniform(nx, ny, nz, 0.2, 1.0, 41)
+    rho = torch.from_numpy(rho_np).cuda().requires_grad_(True)
+    with topo.Mesh(nx, ny, nz, topo.BC_CANTILEVER, topo.LOAD_EDGE_XL_BOTTOM) as m:
+        c = compliance(rho, m, topo.default_opts(rtol=1e-11))
+        c.backward()
+    g = rho.grad.double().cpu().numpy()
+    P = fem.Problem(nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, rho_np)
+    u = P.solve()
+    assert abs(c.item() - P.compliance(u)) <= 1e-8 * P.compliance(u)
+    ref = P.sensitivity(u)
+    # rho.grad is float32: compare at float32 resolution
+    assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max()
+    for e in (0, 17, 50, 95):
+        cs = []
+        for s in (1, -1):
+            r2 = rho_np.astype(np.float64)
+            r2[e] += s * 1e-4
+            Q = fem.Problem(nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, r2)
+            cs.append(Q.compliance(Q.solve()))
+        fd = (cs[0] - cs[1]) / 2e-4
+        assert abs(fd - g[e]) <= 1e-5 * abs(fd) + 1e-6 * np.abs(ref).max()
+
+
+def test_stream_ordering_with_torch_default_stream(topo):
+    """Device outputs are ordered before later work on the caller's stream
+    (here torch's default stream), without a host synchronisation."""
+    import torch
+    w = I.WORKLOADS["cantilever_24x12x12"]
+    rho = torch.from_numpy(w.density()).cuda()
+    with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load) as m:
+        m.set_density(rho)
+        m.solve()
+        dc = torch.zeros(w.n_elem, dtype=torch.float64, device="cuda")
+        m.sensitivity(dc)
+        s1 = float(dc.sum().item())  # torch reads dc on the default stream
+        ref = m.sensitivity()
+    assert abs(s1 - ref.sum()) <= 1e-12 * abs(ref.sum())
+
+
+def test_solve_many_same_alone_and_in_the_mix(topo):
+    """Designs of different sizes and BCs solved concurrently (one stream
+    each, one host thread) give bitwise the same displacements, compliances
+    and sensitivities as when each is solved alone (all reductions are in a
+    fixed order), and each meets the FP64 residual target."""
+    specs = [(24, 12, 12, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, 1),
+             (32, 16, 16, I.BC_MBB, I.LOAD_EDGE_X0_TOP, 2),
+             (40, 20, 20, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, 3),
+             (16, 8, 8, I.BC_MBB, I.LOAD_EDGE_X0_TOP, 4)]
+    alone = []
+    for nx, ny, nz, bc, load, seed in specs:
+        rho = I.density_cone_smoothed(nx, ny, nz, seed)
+        with topo.Mesh(nx, ny, nz, bc, load) as m:
+            m.set_density(rho)
+            info = m.solve()
+            alone.append((info.iters, m.displacement(), m.compliance(), m.sensitivity()))
+    meshes = []
+    for nx, ny, nz, bc, load, seed in specs:
+        m = topo.Mesh(nx, ny, nz, bc, load)
+        m.set_density(I.density_cone_smoothed(nx, ny, nz, seed))
+        meshes.append(m)
+    try:
+        infos = topo.solve_many(meshes)
+        for (it, u, c, dc), m, info in zip(alone, meshes, infos):
+            assert info.status == 0 and info.rel_residual <= 1e-8
+            assert info.iters == it
+            assert np.array_equal(m.displacement(), u)
+            assert m.compliance() == c
+            assert np.array_equal(m.sensitivity(), dc)
+    finally:
+        for m in meshes:
+            m.close()
+    with pytest.raises(topo.TopoError):
+        m2 = topo.Mesh(4, 2, 2)
+        try:
+            m2.set_density(np.full(16, 0.5, np.float32))
+            topo.solve_many([m2, m2])
+        finally:
+            m2.close()
