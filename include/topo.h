@@ -84,6 +84,12 @@ enum {
   TOPO_PREC_FP32 = 1  /* FP32 PCG inside FP64 iterative refinement */
 };
 
+/* Operator kernels (both compute the same K x; results agree to rounding). */
+enum {
+  TOPO_OPERATOR_MODAL = 0, /* element-centric, k0 in the Walsh-Hadamard modal basis (default) */
+  TOPO_OPERATOR_GATHER = 1 /* node-centric 27-node gather with the dense 24x24 k0 */
+};
+
 enum {
   TOPO_PRECOND_JACOBI = 0, /* D^-1, D = diag K */
   TOPO_PRECOND_GMG = 1     /* one geometric multigrid V-cycle (2:1 vertex-nested grids) */
@@ -184,6 +190,10 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
  * timing.  Cites Eq. (2) (K u). */
 topo_status topo_apply_internal(topo_mesh* m, int precision, int reps);
 
+/* Select the operator kernel family for all later calls on this mesh
+ * (TOPO_OPERATOR_*); synchronises the mesh's stream.  Cites Eq. (2). */
+topo_status topo_set_operator(topo_mesh* m, int kind);
+
 /* Change the caller stream the mesh orders its calls against. */
 topo_status topo_set_stream(topo_mesh* m, void* stream);
 
@@ -229,6 +239,54 @@ topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launche
 topo_status topo_sensitivity_noalloc(int nx, int ny, int nz, const topo_params* prm,
                                      const double* u, const float* rho, double* dc, double* c,
                                      void* stream);
+
+/* ---------------------------------------------------------------------
+ * Continuous-batching solve server (no counterpart in the paper: the
+ * serving pattern of the hot path).  A design is opened once (grid, BC,
+ * load) and then receives solve jobs (densities).  Designs are admitted in
+ * arrival order, with backfill, while their estimated device footprint
+ * (topo_footprint_bytes) fits mem_budget_bytes and fewer than max_active are
+ * resident; an admitted design keeps its mesh, displacement (each new job
+ * warm-starts from the last solution) and multigrid hierarchy on the device
+ * until it is closed.  All admitted designs solve concurrently, each on its
+ * own stream; topo_server_poll advances them from the caller's thread.
+ * Every solve uses `opts` (NULL = defaults) and computes the compliance.
+ * --------------------------------------------------------------------- */
+typedef struct topo_server topo_server;
+
+typedef struct {
+  int job, design;       /* ids returned by topo_server_submit / topo_server_open */
+  int status;            /* topo_status of the solve */
+  int iters, outer;      /* as in topo_solve_info */
+  double rel_residual;   /* final true FP64 relative residual */
+  double compliance;     /* f^T u (valid when status == TOPO_OK) */
+  double submit_s, start_s, finish_s; /* seconds since topo_server_create */
+} topo_job_result;
+
+topo_status topo_server_create(long long mem_budget_bytes, int max_active, const topo_params* prm,
+                               const topo_solve_opts* opts, void* stream, topo_server** out);
+/* TOPO_ERR_OOM if the design alone exceeds the budget. */
+topo_status topo_server_open(topo_server* s, int nx, int ny, int nz, int bc, int load,
+                             int* design);
+/* Queue a solve of `design` with densities rho (host, n_elem floats, copied). */
+topo_status topo_server_submit(topo_server* s, int design, const float* rho, size_t n_elem,
+                               int* job);
+/* Advance all designs; return up to max_out finished jobs (in completion
+ * order).  wait != 0: block until at least one job finished or nothing is
+ * left to do. */
+topo_status topo_server_poll(topo_server* s, int wait, topo_job_result* out, int max_out,
+                             int* n_out);
+/* Results of the last finished job of a resident, idle design. */
+topo_status topo_server_sensitivity(topo_server* s, int design, double* dc, size_t n_elem,
+                                    int on_device);
+topo_status topo_server_displacement(topo_server* s, int design, double* u, size_t n_dof,
+                                     int on_device);
+/* Retire a design: its memory is released once its queued jobs are done
+ * (immediately, dropping its jobs, if it was never admitted). */
+topo_status topo_server_close(topo_server* s, int design);
+topo_status topo_server_stats(const topo_server* s, long long* bytes_in_use, long long* peak_bytes,
+                              int* active, int* waiting);
+void topo_server_free(topo_server* s);
 
 /* Release everything the mesh holds (NULL-safe). */
 void topo_free(topo_mesh* m);

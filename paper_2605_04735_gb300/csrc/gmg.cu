@@ -398,23 +398,45 @@ double k0_jacobi_bound(const double* k0) {
   return lam;
 }
 
+std::vector<Dims> gmg_plan(const Dims& fine, int max_levels) {
+  std::vector<Dims> out;
+  Dims d = fine;
+  for (;;) {
+    out.push_back(d);
+    const long long dof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    if (dof <= kCoarseMaxDof) break;
+    if (max_levels > 0 && (int)out.size() >= max_levels) break;
+    const int nx = (d.nx + 1) / 2, ny = (d.ny + 1) / 2, nz = (d.nz + 1) / 2;
+    if (nx == d.nx && ny == d.ny && nz == d.nz) break;
+    d = make_dims(nx, ny, nz, d.bc, d.pin_j / 2);
+    if ((int)out.size() >= 16) break;
+  }
+  return out;
+}
+
+long long gmg_footprint(const Dims& fine, int max_levels) {
+  const std::vector<Dims> lv = gmg_plan(fine, max_levels);
+  long long b = 0;
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const long long nvec = 3 * lv[l].comp;
+    b += nvec * 4 * 3;                                  // r, two Chebyshev directions
+    if (l > 0) b += lv[l].ecount * 4 + nvec * 4 * 3;    // E, dinv, b, x
+  }
+  const Dims& dc = lv.back();
+  const long long nc = 3LL * (dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
+  b += (nc * nc + 5 * nc) * 8;
+  return b;
+}
+
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max) {
   g.degree = std::max(1, degree);
   g.lam_max = lam_max;
-  Dims d = fine;
   g.lv.clear();
-  for (;;) {
+  for (const Dims& d : gmg_plan(fine, max_levels)) {
     GmgLevel L;
     L.d = d;
     L.nvec = 3 * d.comp;
     g.lv.push_back(L);
-    const long long dof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
-    if (dof <= kCoarseMaxDof) break;
-    if (max_levels > 0 && (int)g.lv.size() >= max_levels) break;
-    const int nx = (d.nx + 1) / 2, ny = (d.ny + 1) / 2, nz = (d.nz + 1) / 2;
-    if (nx == d.nx && ny == d.ny && nz == d.nz) break;
-    d = make_dims(nx, ny, nz, d.bc, d.pin_j / 2);
-    if ((int)g.lv.size() >= 16) break;
   }
   const Dims& dc = g.lv.back().d;
   g.nc = 3 * (dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
@@ -474,12 +496,21 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
   return cudaSuccess;
 }
 
-cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f, const int* done,
-                       int* errflag, cudaStream_t s, long long* launches) {
+template <class Epi>
+cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
+                     const ModalCoef<float>* mcf, const Epi& ep, const int* done, int* errflag,
+                     cudaStream_t s) {
+  Red nored{};
+  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, nored, done, errflag, s);
+  return launch_stencil<float>(x, L.E, L.d, k0f, ep, nored, done, errflag, s);
+}
+
+cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
+                       const ModalCoef<float>* mcf, const int* done, int* errflag,
+                       cudaStream_t s, long long* launches) {
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
-  Red nored{};
   auto B = [&](int l) { return l == 0 ? b0 : g.lv[l].b; };
   auto X = [&](int l) { return l == 0 ? x0 : g.lv[l].x; };
   // down
@@ -492,10 +523,10 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
-      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, errflag, s));
+      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s));
       ++*launches;
     }
-    GCK(launch_stencil<float>(L.dv[(m - 1) & 1], L.E, L.d, k0f, EpiChebLast{L.r}, nored, done, errflag, s));
+    GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s));
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     k_restrict<<<grid1d(nnc), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done);
@@ -522,11 +553,11 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     k_prolong_add<<<grid1d(nnf), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done);
     GCK(cudaGetLastError());
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
-    GCK(launch_stencil<float>(X(l), L.E, L.d, k0f, er, nored, done, errflag, s));
+    GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s));
     *launches += 2;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
-      GCK(launch_stencil<float>(L.dv[(k - 1) & 1], L.E, L.d, k0f, ep, nored, done, errflag, s));
+      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s));
       ++*launches;
     }
     if (m == 1) {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "modal.cuh"
 
 namespace topo {
 
@@ -40,6 +41,9 @@ struct Gmg {
   bool ready = false;        // set up for the current densities
 };
 
+// The level grids a fine grid coarsens to, and the bytes a hierarchy holds.
+std::vector<Dims> gmg_plan(const Dims& fine, int max_levels);
+long long gmg_footprint(const Dims& fine, int max_levels);
 // Choose levels for a fine grid and allocate them (fine-level E/dinv/b/x are
 // bound later, per call).  max_levels <= 0: automatic.
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max);
@@ -48,8 +52,10 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
                       const K0<double>& k0d, cudaStream_t s, long long* launches);
 // x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
 // when *done is set.
-cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f, const int* done,
-                       int* errflag, cudaStream_t s, long long* launches);
+// mcf != nullptr: smoother passes use the modal operator kernel
+cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f,
+                       const ModalCoef<float>* mcf, const int* done, int* errflag,
+                       cudaStream_t s, long long* launches);
 void gmg_free(Gmg& g);
 // lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
 double k0_jacobi_bound(const double* k0);

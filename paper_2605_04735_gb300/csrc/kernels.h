@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "modal.cuh"
 
 namespace topo {
 
@@ -18,10 +19,14 @@ enum ApplyMode {
   APPLY_DOT = 1,    // y = A x, reduce x . y
   APPLY_RESID = 2   // y = f - A x (0 on fixed DOFs), reduce y . y
 };
-// errflag: set to 1 by the kernel if a bounded device-side wait ran out
+// errflag: set to 1 by the kernel if a bounded device-side wait ran out.
+// mc != nullptr: element-centric modal kernel; nullptr: node-centric gather.
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
-                         const Red& red, int mode, const int* done, int* errflag, cudaStream_t s);
+                         const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
+                         int* errflag, cudaStream_t s);
+// modal coefficients of k0 (returns false if k0 does not have the expected pattern)
+bool build_modal_coef(const double* k0, ModalCoef<double>* out);
 template <typename T>
 cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s);
 
@@ -65,7 +70,7 @@ cudaError_t launch_pack(const T* soa, double* aos, const Dims& d, cudaStream_t s
 template <typename T>
 cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t s);
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
-                               const Dims& d, const K0<double>& k0, double penal, double dE,
+                               const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
                                const Red& red, cudaStream_t s);
 
 }  // namespace topo

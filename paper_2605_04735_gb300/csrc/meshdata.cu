@@ -6,14 +6,11 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "modal.cuh"
 
 namespace topo {
 
 namespace {
-
-__host__ __device__ constexpr int lidx(int dx, int dy, int dz) {
-  return 4 * dz + (dy ? (dx ? 2 : 3) : (dx ? 1 : 0));
-}
 
 // Eq. (1): E_e = Emin + rho_e^p (E0 - Emin), evaluated in FP64 and stored
 // both in FP64 and rounded to FP32; each scaled by the element size h
@@ -95,13 +92,17 @@ __global__ void k_unpack(const double* __restrict__ aos, T* __restrict__ soa, co
   }
 }
 
-// Eq. (3): dc_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e, FP64 throughout
-// (u_e^T k0 u_e as the symmetric quadratic form: 300 FMAs instead of 576);
-// also reduces sum_e E_e u_e^T k0 u_e (Eq. (2), element form) -> aux[0].
+// Eq. (3): dc_e = -p rho_e^(p-1) (E0 - Emin) u_e^T k0 u_e, FP64 throughout.
+// The quadratic form is evaluated in the modal basis of the brick (see
+// modal.cuh): with u^ = H^T (u_e - u_0), u_e^T k0 u_e = u^T K~ u^ =
+// sum_p,m D[p][m] u^_p[m]^2 + 2 sum_{p<q} couplings, about 105 FP64
+// operations instead of 300 FMAs for the dense symmetric form.  Also reduces
+// sum_e E_e u_e^T k0 u_e (Eq. (2), element form) -> aux[0].
 __global__ void __launch_bounds__(256)
     k_sensitivity(const double* __restrict__ u, const float* __restrict__ rho_g,
                   const double* __restrict__ E64, double* __restrict__ dc, const Dims d,
-                  const __grid_constant__ K0<double> k0, double penal, double dE, const Red red) {
+                  const __grid_constant__ ModalCoef<double> kc, double penal, double dE,
+                  const Red red) {
   const long long n = (long long)d.nx * d.ny * d.nz;
   double part = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -109,26 +110,30 @@ __global__ void __launch_bounds__(256)
     const int i = (int)(e % d.nx);
     const int j = (int)((e / d.nx) % d.ny);
     const int k = (int)(e / ((long long)d.nx * d.ny));
-    double ue[24];
+    double uh[3][8];
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
+    for (int c = 0; c < 3; ++c) {
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
+      for (int b = 0; b < 8; ++b)
+        uh[c][b] = __ldg(u + c * d.comp + d.node(i + (b & 1), j + ((b >> 1) & 1), k + (b >> 2)));
+      const double u0 = uh[c][0];
+      uh[c][0] = 0.0;
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const long long o = d.node(i + dx, j + dy, k + dz);
-          const int a = lidx(dx, dy, dz);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) ue[3 * a + c] = __ldg(u + c * d.comp + o);
-        }
+      for (int b = 1; b < 8; ++b) uh[c][b] -= u0;
+      fwht8(uh[c]);
+    }
     double s = 0.0;
 #pragma unroll
-    for (int a = 0; a < 24; ++a) {
-      double t = 0.5 * k0.v[a * 24 + a] * ue[a];
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int b = a + 1; b < 24; ++b) t = fma(k0.v[a * 24 + b], ue[b], t);
-      s = fma(2.0 * ue[a], t, s);
-    }
+      for (int m = 1; m < 8; ++m) {
+        s = fma(kc.D[p][m] * uh[p][m], uh[p][m], s);
+#pragma unroll
+        for (int q = p + 1; q < 3; ++q) {
+          if (((m >> p) & 1) == ((m >> q) & 1)) continue;
+          s = fma(2.0 * kc.C[p][q][m] * uh[p][m], uh[q][m ^ (1 << p) ^ (1 << q)], s);
+        }
+      }
     const long long og = d.elem(i, j, k);
     const double r = (double)rho_g[og];
     const double rp1 = (penal == 3.0) ? r * r : pow(r, penal - 1.0);
@@ -178,10 +183,10 @@ cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t
 }
 
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
-                               const Dims& d, const K0<double>& k0, double penal, double dE,
+                               const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
                                const Red& red, cudaStream_t s) {
   const long long n = (long long)d.nx * d.ny * d.nz;
-  k_sensitivity<<<grid_for(n, 256), 256, 0, s>>>(u, rho_g, E64, dc, d, k0, penal, dE, red);
+  k_sensitivity<<<grid_for(n, 256), 256, 0, s>>>(u, rho_g, E64, dc, d, kc, penal, dE, red);
   return cudaGetLastError();
 }
 

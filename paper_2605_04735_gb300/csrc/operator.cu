@@ -4,8 +4,11 @@
 // stencil.cuh; this file holds the epilogues.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "modal.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -80,8 +83,18 @@ __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const 
 
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
-                         const Red& red, int mode, const int* done, int* errflag,
-                         cudaStream_t s) {
+                         const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
+                         int* errflag, cudaStream_t s) {
+  if (mc) {
+    switch (mode) {
+      case APPLY_PLAIN:
+        return launch_modal<T>(x, E, d, *mc, EpiApply<T, false>{y}, red, done, errflag, s);
+      case APPLY_DOT:
+        return launch_modal<T>(x, E, d, *mc, EpiApply<T, true>{y}, red, done, errflag, s);
+      default:
+        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s);
+    }
+  }
   switch (mode) {
     case APPLY_PLAIN:
       return launch_stencil<T>(x, E, d, k0, EpiApply<T, false>{y}, red, done, errflag, s);
@@ -101,11 +114,49 @@ cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0,
 }
 
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,
-                                         const Dims&, const K0<float>&, const Red&, int,
-                                         const int*, int*, cudaStream_t);
+                                         const Dims&, const K0<float>&, const ModalCoef<float>*,
+                                         const Red&, int, const int*, int*, cudaStream_t);
 template cudaError_t launch_apply<double>(const double*, double*, const double*, const double*,
-                                          const Dims&, const K0<double>&, const Red&, int,
-                                          const int*, int*, cudaStream_t);
+                                          const Dims&, const K0<double>&,
+                                          const ModalCoef<double>*, const Red&, int, const int*,
+                                          int*, cudaStream_t);
+
+bool build_modal_coef(const double* k0, ModalCoef<double>* out) {
+  // corner a of the local numbering -> binary index b = ax + 2 ay + 4 az
+  static const int bin[8] = {0, 1, 3, 2, 4, 5, 7, 6};
+  auto H = [](int b, int m) { return (__builtin_popcount(b & m) & 1) ? -1.0 : 1.0; };
+  double Kt[24][24];  // [(p,m)][(q,n)] = (1/64) sum_ab H[b(a)][m] k0[3a+p][3b+q] H[b(b)][n]
+  for (int p = 0; p < 3; ++p)
+    for (int m = 0; m < 8; ++m)
+      for (int q = 0; q < 3; ++q)
+        for (int n = 0; n < 8; ++n) {
+          double acc = 0.0;
+          for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+              acc += H(bin[a], m) * k0[(3 * a + p) * 24 + 3 * b + q] * H(bin[b], n);
+          Kt[p * 8 + m][q * 8 + n] = acc / 64.0;
+        }
+  double scale = 0.0;
+  for (int r = 0; r < 24; ++r)
+    for (int c = 0; c < 24; ++c) scale = std::fmax(scale, std::fabs(Kt[r][c]));
+  *out = ModalCoef<double>{};
+  double used[24][24] = {};
+  for (int p = 0; p < 3; ++p)
+    for (int m = 1; m < 8; ++m) {
+      out->D[p][m] = Kt[p * 8 + m][p * 8 + m];
+      used[p * 8 + m][p * 8 + m] = 1;
+      for (int q = 0; q < 3; ++q) {
+        if (q == p || ((m >> p) & 1) == ((m >> q) & 1)) continue;
+        const int n = m ^ (1 << p) ^ (1 << q);
+        out->C[p][q][m] = Kt[p * 8 + m][q * 8 + n];
+        used[p * 8 + m][q * 8 + n] = 1;
+      }
+    }
+  for (int r = 0; r < 24; ++r)
+    for (int c = 0; c < 24; ++c)
+      if (!used[r][c] && std::fabs(Kt[r][c]) > 1e-12 * scale) return false;
+  return true;
+}
 template cudaError_t launch_diag_inv<float>(float*, const float*, const Dims&, const K0<float>&,
                                             cudaStream_t);
 template cudaError_t launch_diag_inv<double>(double*, const double*, const Dims&,

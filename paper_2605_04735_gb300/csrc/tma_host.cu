@@ -10,6 +10,7 @@
 #include <tuple>
 
 #include "common.cuh"
+#include "modal.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
 
@@ -36,12 +37,14 @@ EncodeFn encoder() {
   return fn;
 }
 
-using Key = std::tuple<const void*, int, int, int, int>;  // base, kind, px/ex, ny, nz
+// base, kind, pitch, ny, nz, box width, box rows
+using Key = std::tuple<const void*, int, int, int, int, int, int>;
 std::mutex g_mu;
 std::map<Key, CUtensorMap> g_cache;
 
-bool cached_map(const void* base, int kind, const Dims& d, CUtensorMap* out) {
-  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz};
+bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y,
+                CUtensorMap* out) {
+  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz, box_x, box_y};
   std::lock_guard<std::mutex> lock(g_mu);
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
@@ -54,13 +57,13 @@ bool cached_map(const void* base, int kind, const Dims& d, CUtensorMap* out) {
     const uint64_t dims[4] = {(uint64_t)d.px, (uint64_t)(d.ny + 3), (uint64_t)(d.nz + 3), 3};
     const uint64_t strides[3] = {(uint64_t)d.px * 4, (uint64_t)d.px * (d.ny + 3) * 4,
                                  (uint64_t)d.comp * 4};
-    const uint32_t box[4] = {(uint32_t)kBoxX, (uint32_t)kBoxYN, 1, 3};
+    const uint32_t box[4] = {(uint32_t)box_x, (uint32_t)box_y, 1, 3};
     ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims,
                           strides, box);
   } else {  // element array: (x, y, z)
     const uint64_t dims[3] = {(uint64_t)d.ex, (uint64_t)(d.ny + 2), (uint64_t)(d.nz + 2)};
     const uint64_t strides[2] = {(uint64_t)d.ex * 4, (uint64_t)d.ex * (d.ny + 2) * 4};
-    const uint32_t box[3] = {(uint32_t)kBoxX, (uint32_t)kBoxYE, 1};
+    const uint32_t box[3] = {(uint32_t)box_x, (uint32_t)box_y, 1};
     ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
                           strides, box);
   }
@@ -98,7 +101,12 @@ bool encode_tiled_map(CUtensorMap* map, CUtensorMapDataType dtype, int rank, voi
 
 bool stencil_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
                   CUtensorMap* emap) {
-  return cached_map(x, 0, d, xmap) && cached_map(E, 1, d, emap);
+  return cached_map(x, 0, d, kBoxX, kBoxYN, xmap) && cached_map(E, 1, d, kBoxX, kBoxYE, emap);
+}
+
+bool modal_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+                CUtensorMap* emap) {
+  return cached_map(x, 0, d, kMBoxX, kMBoxNY, xmap) && cached_map(E, 1, d, kMBoxX, kMBoxEY, emap);
 }
 
 }  // namespace topo

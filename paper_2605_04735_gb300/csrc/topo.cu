@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <new>
@@ -99,6 +100,9 @@ struct topo_mesh {
   topo_params prm{};
   K0<double> k0d{};
   K0<float> k0f{};
+  ModalCoef<double> mcd{};  // k0 in the modal basis (element-centric kernels)
+  ModalCoef<float> mcf{};
+  bool use_modal = true;    // false: node-centric gather kernels
   long long nvec = 0;  // entries of one 3-component vector (3 * comp)
 
   // element data (ghosted)
@@ -179,6 +183,9 @@ topo_status dalloc(topo_mesh* m, T** p, long long count) {
   return TOPO_OK;
 }
 
+#define MCD(m) ((m)->use_modal ? &(m)->mcd : nullptr)
+#define MCF(m) ((m)->use_modal ? &(m)->mcf : nullptr)
+
 // count one kernel launch of this mesh, then check the launch
 #define LK(mesh, call)          \
   do {                          \
@@ -257,10 +264,10 @@ topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
   for (int c = 0; c < count; ++c) {
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c], s, cudaEventRecordExternal));
     if (kind == IK_JAC64) {
-      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
+      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, MCD(m),
                                  red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s));
     } else {
-      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f,
+      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
                                 red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s));
     }
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
@@ -278,7 +285,7 @@ topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
       default:
         LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
                                        red_of(m, FIN_RR_ONLY), false, s));
-        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, done, m->flags + 1, s, &m->launches));
+        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches));
         LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_RZ_BETA), s));
         LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
         break;
@@ -388,7 +395,7 @@ void task_finish(SolveTask& t, topo_status st) {
 
 // FP64 residual r = f - K u (fixed DOFs 0), ||r||^2 -> aux[0]
 topo_status enqueue_residual64(topo_mesh* m) {
-  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, red_of(m, FIN_AUX),
+  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m), red_of(m, FIN_AUX),
                              APPLY_RESID, nullptr, m->flags + 1, m->stream));
   return TOPO_OK;
 }
@@ -410,7 +417,7 @@ topo_status enqueue_inner_start(SolveTask& t, double rtol, int max_iter) {
     } else {
       LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
                                    red_of(m, FIN_INIT, rtol * rtol), false, s));
-      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, done, m->flags + 1, s, &m->launches));
+      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches));
       LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s));
       LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
     }
@@ -558,6 +565,180 @@ topo_status upload_f64(topo_mesh* m, const double* src, double* dst_soa, size_t 
 
 }  // namespace
 
+
+// ===========================================================================
+// Continuous-batching solve server.
+//
+// A design (one grid, BC and load) is opened once and then receives a stream
+// of solve jobs (new densities), as an optimiser would send them.  The
+// server admits designs in arrival order while their estimated device
+// footprint fits the memory budget and fewer than max_active are resident
+// (later designs that fit may pass a blocked one: backfill); an admitted
+// design keeps its mesh, densities, displacement (warm start) and multigrid
+// hierarchy on the device until it is closed.  Every admitted design runs
+// its own solve state machine on its own stream, and topo_server_poll
+// advances all of them from the caller's thread, so jobs that arrive while
+// others are running start as soon as their design is resident and idle, and
+// their kernels overlap with the others' on the GPU.
+// ===========================================================================
+struct ServerJob {
+  int id = 0;
+  std::vector<float> rho;
+  double submit_s = 0.0, start_s = 0.0;
+};
+
+struct ServerDesign {
+  int id = 0;
+  int nx = 0, ny = 0, nz = 0, bc = 0, load = 0;
+  long long footprint = 0;
+  topo_mesh* mesh = nullptr;
+  std::deque<ServerJob> queue;
+  bool running = false, solved = false, closing = false, waiting = false;
+  SolveTask task;
+  ServerJob current;
+  topo_solve_info info{};
+};
+
+struct topo_server {
+  cudaStream_t user = nullptr;
+  topo_params prm{};
+  topo_solve_opts opts{};
+  long long budget = 0, in_use = 0, peak = 0;
+  int max_active = 0, active = 0;
+  int next_design = 1, next_job = 1;
+  std::map<int, ServerDesign> designs;
+  std::deque<int> admit;                   // designs waiting for admission, in arrival order
+  std::deque<topo_job_result> done;        // finished jobs not yet returned
+  Timer clock;
+};
+
+namespace {
+
+void server_release(topo_server* s, ServerDesign& d) {
+  if (d.mesh) {
+    topo_free(d.mesh);
+    d.mesh = nullptr;
+    s->in_use -= d.footprint;
+    --s->active;
+  }
+}
+
+// one pass over the server: admit, start, advance, retire; true if anything moved
+bool server_step(topo_server* s) {
+  bool moved = false;
+  // admission (arrival order with backfill)
+  for (auto it = s->admit.begin(); it != s->admit.end();) {
+    ServerDesign& d = s->designs[*it];
+    if (s->active < s->max_active && s->in_use + d.footprint <= s->budget) {
+      topo_mesh* m = nullptr;
+      const topo_status st = topo_create_mesh(d.nx, d.ny, d.nz, d.bc, d.load, &s->prm, s->user, &m);
+      if (st == TOPO_OK) {
+        d.mesh = m;
+        d.waiting = false;
+        s->in_use += d.footprint;
+        s->peak = std::max(s->peak, s->in_use);
+        ++s->active;
+        it = s->admit.erase(it);
+        moved = true;
+        continue;
+      }
+      if (st != TOPO_ERR_OOM) {  // a design that can never run: fail its jobs
+        for (ServerJob& j : d.queue) {
+          topo_job_result r{};
+          r.job = j.id;
+          r.design = d.id;
+          r.status = st;
+          r.submit_s = j.submit_s;
+          r.finish_s = s->clock.seconds();
+          s->done.push_back(r);
+        }
+        d.queue.clear();
+        d.waiting = false;
+        it = s->admit.erase(it);
+        moved = true;
+        continue;
+      }
+    }
+    ++it;
+  }
+  for (auto& kv : s->designs) {
+    ServerDesign& d = kv.second;
+    if (!d.mesh) continue;
+    // advance a running solve
+    if (d.running) {
+      cudaSetDevice(d.mesh->dev);
+      const cudaError_t q = cudaEventQuery(d.mesh->ev_poll);
+      if (q == cudaSuccess) {
+        task_advance(d.task);
+        moved = true;
+      } else if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+        task_finish(d.task, cuda_status(q));
+      }
+      if (d.task.phase == SolveTask::P_FINISHED) {
+        d.running = false;
+        moved = true;
+        topo_job_result r{};
+        r.job = d.current.id;
+        r.design = d.id;
+        r.status = d.task.st;
+        r.iters = d.info.iters;
+        r.outer = d.info.outer;
+        r.rel_residual = d.info.rel_residual;
+        r.submit_s = d.current.submit_s;
+        r.start_s = d.current.start_s;
+        if (r.status == TOPO_OK) {
+          topo_compliance(d.mesh, &r.compliance);
+          d.solved = true;
+        }
+        {
+          Fence fence(d.mesh);  // the caller's stream waits for this design's work
+        }
+        r.finish_s = s->clock.seconds();
+        s->done.push_back(r);
+        d.current.rho.clear();
+      }
+    }
+    // start the next job of an idle, resident design
+    if (!d.running && !d.queue.empty()) {
+      d.current = std::move(d.queue.front());
+      d.queue.pop_front();
+      d.current.start_s = s->clock.seconds();
+      d.info = topo_solve_info{};
+      topo_status st = topo_set_density(d.mesh, d.current.rho.data(), d.current.rho.size(), 0);
+      d.task = SolveTask();
+      d.task.m = d.mesh;
+      d.task.o = s->opts;
+      d.task.o.warm_start = d.solved ? 1 : 0;
+      d.task.info = &d.info;
+      if (st == TOPO_OK) st = task_start(d.task);
+      if (st != TOPO_OK) task_finish(d.task, st);
+      d.running = true;  // reported on the next pass (also when it failed to start)
+      moved = true;
+    }
+  }
+  // retire closed designs once idle
+  for (auto it = s->designs.begin(); it != s->designs.end();) {
+    ServerDesign& d = it->second;
+    if (d.closing && !d.running && d.queue.empty()) {
+      server_release(s, d);
+      it = s->designs.erase(it);
+      moved = true;
+    } else {
+      ++it;
+    }
+  }
+  return moved;
+}
+
+bool server_busy(const topo_server* s) {
+  for (const auto& kv : s->designs)
+    if (kv.second.running || !kv.second.queue.empty()) return true;
+  return false;
+}
+
+}  // namespace
+
 // =========================================================================
 // C ABI
 // =========================================================================
@@ -647,6 +828,12 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
     m->k0f.v[t] = (float)k[t];
   }
   m->lam_max = k0_jacobi_bound(k);
+  if (!build_modal_coef(k, &m->mcd)) return TOPO_ERR_INVALID;
+  {
+    const double* src = &m->mcd.D[0][0];
+    float* dst = &m->mcf.D[0][0];
+    for (size_t t = 0; t < sizeof(m->mcd) / sizeof(double); ++t) dst[t] = (float)src[t];
+  }
   const long long ne = m->d.ecount;
   CKS(dalloc(m, &m->rho_g, ne));
   CKS(dalloc(m, &m->E32, ne));
@@ -817,7 +1004,7 @@ topo_status topo_compliance(topo_mesh* m, double* c) {
 static topo_status sens_impl(topo_mesh* m) {
   const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
   if (!m->dc) CKS(dalloc(m, &m->dc, ne));
-  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->k0d, m->prm.penal,
+  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->mcd, m->prm.penal,
                         (m->prm.E0 - m->prm.Emin) * m->prm.h, red_of(m, FIN_AUX), m->stream));
   return TOPO_OK;
 }
@@ -892,12 +1079,12 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
   if (precision == TOPO_PREC_FP64) {
     CKS(ensure_fp64_inner(m));
     LK(m, launch_unpack<double>(src, m->p64, m->d, s));
-    LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, red_of(m, FIN_NONE),
+    LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, MCD(m), red_of(m, FIN_NONE),
                             APPLY_PLAIN, nullptr, m->flags + 1, s));
     LK(m, launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
   } else {
     LK(m, launch_unpack<float>(src, m->p32, m->d, s));
-    LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+    LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m), red_of(m, FIN_NONE),
                            APPLY_PLAIN, nullptr, m->flags + 1, s));
     LK(m, launch_pack<float>(m->q32, on_device ? y : m->aos, m->d, s));
   }
@@ -916,10 +1103,10 @@ topo_status topo_apply_internal(topo_mesh* m, int precision, int reps) {
   for (int r = 0; r < reps; ++r) {
     if (precision == TOPO_PREC_FP64) {
       CKS(ensure_fp64_inner(m));
-      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d,
+      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, MCD(m),
                               red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->flags + 1, m->stream));
     } else if (precision == TOPO_PREC_FP32) {
-      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, red_of(m, FIN_NONE),
+      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m), red_of(m, FIN_NONE),
                              APPLY_PLAIN, nullptr, m->flags + 1, m->stream));
     } else {
       return TOPO_ERR_INVALID;
@@ -957,7 +1144,20 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
   b += 3LL * (nx + 1) * (ny + 1) * (nz + 1) * 8;  // ABI staging
   b += (long long)nx * ny * nz * (8 + 4);          // sensitivities + density staging
   if (opts && opts->precision == TOPO_PREC_FP64) b += nvec * 6 * 8;
+  if (!opts || opts->precond == TOPO_PRECOND_GMG) b += gmg_footprint(d, opts ? opts->gmg_levels : 0);
   return b;
+}
+
+topo_status topo_set_operator(topo_mesh* m, int kind) {
+  if (!m || (kind != TOPO_OPERATOR_MODAL && kind != TOPO_OPERATOR_GATHER)) return TOPO_ERR_INVALID;
+  const bool modal = (kind == TOPO_OPERATOR_MODAL);
+  if (modal != m->use_modal) {
+    CK(cudaSetDevice(m->dev));
+    CK(cudaStreamSynchronize(m->stream));
+    clear_graphs(m);
+    m->use_modal = modal;
+  }
+  return TOPO_OK;
 }
 
 topo_status topo_set_stream(topo_mesh* m, void* stream) {
@@ -984,6 +1184,140 @@ topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launche
     m->launches = 0;
   }
   return TOPO_OK;
+}
+
+topo_status topo_server_create(long long mem_budget_bytes, int max_active, const topo_params* prm,
+                               const topo_solve_opts* opts, void* stream, topo_server** out) {
+  if (!out || mem_budget_bytes <= 0 || max_active < 1) return TOPO_ERR_INVALID;
+  topo_server* s = new (std::nothrow) topo_server();
+  if (!s) return TOPO_ERR_OOM;
+  s->budget = mem_budget_bytes;
+  s->max_active = max_active;
+  s->user = static_cast<cudaStream_t>(stream);
+  if (prm)
+    s->prm = *prm;
+  else
+    topo_default_params(&s->prm);
+  if (opts)
+    s->opts = *opts;
+  else
+    topo_default_opts(&s->opts);
+  *out = s;
+  return TOPO_OK;
+}
+
+topo_status topo_server_open(topo_server* s, int nx, int ny, int nz, int bc, int load,
+                             int* design) {
+  if (!s || !design) return TOPO_ERR_INVALID;
+  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 2 || load < 0 || load > 2) return TOPO_ERR_INVALID;
+  if (bc == TOPO_BC_MBB && (ny % 2)) return TOPO_ERR_INVALID;
+  const long long fp = topo_footprint_bytes(nx, ny, nz, &s->opts);
+  if (fp > s->budget) return TOPO_ERR_OOM;  // could never be admitted
+  ServerDesign d;
+  d.id = s->next_design++;
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.bc = bc;
+  d.load = load;
+  d.footprint = fp;
+  s->designs[d.id] = std::move(d);
+  *design = s->designs.rbegin()->first;
+  return TOPO_OK;
+}
+
+topo_status topo_server_submit(topo_server* s, int design, const float* rho, size_t n_elem,
+                               int* job) {
+  if (!s || !rho) return TOPO_ERR_INVALID;
+  auto it = s->designs.find(design);
+  if (it == s->designs.end() || it->second.closing) return TOPO_ERR_INVALID;
+  ServerDesign& d = it->second;
+  if ((long long)n_elem != (long long)d.nx * d.ny * d.nz) return TOPO_ERR_INVALID;
+  ServerJob j;
+  j.id = s->next_job++;
+  j.rho.assign(rho, rho + n_elem);
+  j.submit_s = s->clock.seconds();
+  d.queue.push_back(std::move(j));
+  if (!d.mesh && !d.waiting) {
+    d.waiting = true;
+    s->admit.push_back(d.id);
+  }
+  if (job) *job = s->next_job - 1;
+  return TOPO_OK;
+}
+
+topo_status topo_server_poll(topo_server* s, int wait, topo_job_result* out, int max_out,
+                             int* n_out) {
+  if (!s || (max_out > 0 && !out) || max_out < 0) return TOPO_ERR_INVALID;
+  for (;;) {
+    const bool moved = server_step(s);
+    if (!s->done.empty() || !wait || !server_busy(s)) break;
+    if (!moved) std::this_thread::yield();
+  }
+  int n = 0;
+  while (n < max_out && !s->done.empty()) {
+    out[n++] = s->done.front();
+    s->done.pop_front();
+  }
+  if (n_out) *n_out = n;
+  return TOPO_OK;
+}
+
+static ServerDesign* idle_design(topo_server* s, int design) {
+  auto it = s->designs.find(design);
+  if (it == s->designs.end() || !it->second.mesh || it->second.running) return nullptr;
+  return &it->second;
+}
+
+topo_status topo_server_sensitivity(topo_server* s, int design, double* dc, size_t n_elem,
+                                    int on_device) {
+  if (!s) return TOPO_ERR_INVALID;
+  ServerDesign* d = idle_design(s, design);
+  if (!d) return TOPO_ERR_INVALID;
+  return topo_sensitivity(d->mesh, dc, n_elem, on_device);
+}
+
+topo_status topo_server_displacement(topo_server* s, int design, double* u, size_t n_dof,
+                                     int on_device) {
+  if (!s) return TOPO_ERR_INVALID;
+  ServerDesign* d = idle_design(s, design);
+  if (!d) return TOPO_ERR_INVALID;
+  return topo_get_displacement(d->mesh, u, n_dof, on_device);
+}
+
+topo_status topo_server_close(topo_server* s, int design) {
+  if (!s) return TOPO_ERR_INVALID;
+  auto it = s->designs.find(design);
+  if (it == s->designs.end()) return TOPO_ERR_INVALID;
+  it->second.closing = true;
+  if (!it->second.mesh) {  // never admitted: drop it and its queued jobs
+    s->admit.erase(std::remove(s->admit.begin(), s->admit.end(), design), s->admit.end());
+    s->designs.erase(it);
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_server_stats(const topo_server* s, long long* bytes_in_use, long long* peak_bytes,
+                              int* active, int* waiting) {
+  if (!s) return TOPO_ERR_INVALID;
+  if (bytes_in_use) *bytes_in_use = s->in_use;
+  if (peak_bytes) *peak_bytes = s->peak;
+  if (active) *active = s->active;
+  if (waiting) *waiting = (int)s->admit.size();
+  return TOPO_OK;
+}
+
+void topo_server_free(topo_server* s) {
+  if (!s) return;
+  for (auto& kv : s->designs) {
+    ServerDesign& d = kv.second;
+    if (d.mesh) {
+      cudaSetDevice(d.mesh->dev);
+      cudaStreamSynchronize(d.mesh->stream);
+    }
+    server_release(s, d);
+  }
+  delete s;
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX = 0, 1, 2
 LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
+OPERATOR_MODAL, OPERATOR_GATHER = 0, 1
 
 
 class Params(C.Structure):
@@ -39,6 +40,12 @@ class SolveOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
                 ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("job", C.c_int), ("design", C.c_int), ("status", C.c_int), ("iters", C.c_int),
+                ("outer", C.c_int), ("rel_residual", C.c_double), ("compliance", C.c_double),
+                ("submit_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double)]
 
 
 class TopoError(RuntimeError):
@@ -76,10 +83,22 @@ def lib():
                                    C.POINTER(C.c_longlong)]),
             "topo_footprint_bytes": (C.c_longlong, [i, i, i, C.POINTER(SolveOpts)]),
             "topo_set_stream": (i, [vp, vp]),
+            "topo_set_operator": (i, [vp, i]),
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
             "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
+            "topo_server_create": (i, [C.c_longlong, i, C.POINTER(Params), C.POINTER(SolveOpts), vp,
+                                       C.POINTER(vp)]),
+            "topo_server_open": (i, [vp, i, i, i, i, i, C.POINTER(i)]),
+            "topo_server_submit": (i, [vp, i, vp, sz, C.POINTER(i)]),
+            "topo_server_poll": (i, [vp, i, C.POINTER(JobResult), i, C.POINTER(i)]),
+            "topo_server_sensitivity": (i, [vp, i, vp, sz, i]),
+            "topo_server_displacement": (i, [vp, i, vp, sz, i]),
+            "topo_server_close": (i, [vp, i]),
+            "topo_server_stats": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                      C.POINTER(i), C.POINTER(i)]),
+            "topo_server_free": (None, [vp]),
             "topo_free": (None, [vp]),
             "topo_status_string": (C.c_char_p, [i]),
         }
@@ -247,6 +266,10 @@ class Mesh:
     def apply_internal(self, precision=PREC_FP32, reps=1):
         _check(lib().topo_apply_internal(self._h, precision, reps), "topo_apply_internal")
 
+    def set_operator(self, kind):
+        """OPERATOR_MODAL (default) or OPERATOR_GATHER for all later calls."""
+        _check(lib().topo_set_operator(self._h, kind), "topo_set_operator")
+
     def set_stream(self, stream):
         """Order subsequent calls against `stream` (int handle or torch.cuda.Stream)."""
         s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
@@ -266,3 +289,84 @@ class Mesh:
         _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(a), int(reset)),
                "topo_profile_read")
         return ms.value, n.value, a.value
+
+
+class Server:
+    """Continuous-batching solve server (see topo_server_* in include/topo.h)."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int = 64, params: Params | None = None,
+                 opts: SolveOpts | None = None, stream=None):
+        h = C.c_void_p()
+        st = None if stream is None else C.c_void_p(stream if isinstance(stream, int)
+                                                     else stream.cuda_stream)
+        _check(lib().topo_server_create(int(mem_budget_bytes), int(max_active),
+                                        C.byref(params) if params else None,
+                                        C.byref(opts) if opts else None, st, C.byref(h)),
+               "topo_server_create")
+        self._h = h
+        self._dims = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().topo_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def open(self, nx, ny, nz, bc, load) -> int:
+        d = C.c_int()
+        _check(lib().topo_server_open(self._h, nx, ny, nz, bc, load, C.byref(d)), "topo_server_open")
+        self._dims[d.value] = (nx, ny, nz)
+        return d.value
+
+    def submit(self, design: int, rho: np.ndarray) -> int:
+        p, n, dev = _ptr(rho, np.float32)
+        if dev:
+            raise TypeError("topo_server_submit takes host densities")
+        j = C.c_int()
+        _check(lib().topo_server_submit(self._h, design, p, n, C.byref(j)), "topo_server_submit")
+        return j.value
+
+    def poll(self, wait: bool = False, max_out: int = 256):
+        out = (JobResult * max_out)()
+        n = C.c_int()
+        _check(lib().topo_server_poll(self._h, int(wait), out, max_out, C.byref(n)),
+               "topo_server_poll")
+        return [out[k] for k in range(n.value)]
+
+    def sensitivity(self, design: int, out=None):
+        nx, ny, nz = self._dims[design]
+        if out is None:
+            out = np.empty(nx * ny * nz, np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_server_sensitivity(self._h, design, p, n, dev), "topo_server_sensitivity")
+        return out
+
+    def displacement(self, design: int, out=None):
+        nx, ny, nz = self._dims[design]
+        if out is None:
+            out = np.empty(3 * (nx + 1) * (ny + 1) * (nz + 1), np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_server_displacement(self._h, design, p, n, dev),
+               "topo_server_displacement")
+        return out
+
+    def retire(self, design: int):
+        _check(lib().topo_server_close(self._h, design), "topo_server_close")
+
+    def stats(self):
+        a, b, c, d = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_int()
+        _check(lib().topo_server_stats(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)),
+               "topo_server_stats")
+        return {"bytes_in_use": a.value, "peak_bytes": b.value, "active": c.value,
+                "waiting": d.value}

@@ -1,0 +1,104 @@
+"""The continuous-batching solve server: every request gives the same result
+alone and in the mix (bitwise: all reductions are in a fixed order and each
+design's sequence of warm-started solves is the same), admission never
+exceeds the memory budget, and requests that arrive while others are on the
+GPU are admitted and finish."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_2605_04735_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def topo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_04735_gb300 import build
+    build.build()
+    from paper_2605_04735_gb300 import topo as t
+    t.lib()
+    return t
+
+
+def _alone(topo, r, steps):
+    """The request's solves on its own mesh, one after the other."""
+    out = []
+    with topo.Mesh(r.nx, r.ny, r.nz, r.bc, r.load) as m:
+        rho = r.rho0
+        for s in range(steps):
+            if s:
+                rho = I.perturb(rho, r.factor(s))
+            m.set_density(rho)
+            info = m.solve(topo.default_opts(warm_start=1 if s else 0))
+            out.append((info.iters, m.compliance()))
+        u = m.displacement()
+        dc = m.sensitivity()
+    return out, u, dc
+
+
+def test_server_same_alone_and_in_the_mix(topo):
+    steps = 3
+    reqs = I.serving_stream(n_requests=6, n_steps=steps, rate=0.0, max_ny=16, seed=77)
+    alone = {r.rid: _alone(topo, r, steps) for r in reqs}
+    fp = [topo.footprint_bytes(r.nx, r.ny, r.nz) for r in reqs]
+    budget = int(max(fp) * 2.5)  # not everyone fits at once: admission must queue
+    srv = topo.Server(budget, max_active=8)
+    try:
+        design, state, got = {}, {}, {r.rid: [] for r in reqs}
+        first, rest = reqs[:3], reqs[3:]
+        for r in first:
+            d = srv.open(r.nx, r.ny, r.nz, r.bc, r.load)
+            srv.submit(d, r.rho0)
+            design[d], state[d] = r, (0, r.rho0)
+        finished = 0
+        late_admitted = False
+        while finished < len(reqs):
+            for res in srv.poll(wait=True):
+                r = design[res.design]
+                step, rho = state[res.design]
+                assert res.status == 0 and res.rel_residual <= 1e-8
+                got[r.rid].append((res.iters, res.compliance))
+                if rest and not late_admitted:  # arrivals while others are on the GPU
+                    for r2 in rest:
+                        d2 = srv.open(r2.nx, r2.ny, r2.nz, r2.bc, r2.load)
+                        srv.submit(d2, r2.rho0)
+                        design[d2], state[d2] = r2, (0, r2.rho0)
+                    late_admitted = True
+                step += 1
+                if step < steps:
+                    rho = I.perturb(rho, r.factor(step))
+                    srv.submit(res.design, rho)
+                    state[res.design] = (step, rho)
+                else:
+                    a_steps, a_u, a_dc = alone[r.rid]
+                    assert np.array_equal(srv.displacement(res.design), a_u)
+                    assert np.array_equal(srv.sensitivity(res.design), a_dc)
+                    srv.retire(res.design)
+                    finished += 1
+            st = srv.stats()
+            assert st["bytes_in_use"] <= budget
+        assert srv.stats()["peak_bytes"] <= budget
+        for r in reqs:
+            assert got[r.rid] == alone[r.rid][0], r.rid
+    finally:
+        srv.close()
+
+
+def test_server_results_match_oracle_and_reject_oversize(topo):
+    r = I.serving_stream(n_requests=1, n_steps=1, rate=0.0, max_ny=12, seed=5)[0]
+    P = fem.Problem(r.nx, r.ny, r.nz, r.bc, r.load, r.rho0)
+    c_ref = P.compliance(P.solve())
+    with topo.Server(2**34, max_active=2) as srv:
+        d = srv.open(r.nx, r.ny, r.nz, r.bc, r.load)
+        srv.submit(d, r.rho0)
+        res = srv.poll(wait=True)
+        assert len(res) == 1 and res[0].status == 0
+        assert abs(res[0].compliance - c_ref) <= 1e-6 * c_ref
+    with topo.Server(1 << 20, max_active=2) as srv:  # 1 MiB: nothing fits
+        with pytest.raises(topo.TopoError) as e:
+            srv.open(24, 12, 12, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM)
+        assert e.value.status == topo.ERR_OOM
