@@ -42,6 +42,26 @@ def _dist():
     return ws, rank, local
 
 
+def design_seeds(base_seed: int, rank: int, batch: int):
+    """Seeds of the independent designs rank `rank` solves: disjoint across
+    ranks (weak scaling: every rank gets its own batch, no data exchange)."""
+    return [base_seed + 1000 * rank + b for b in range(batch)]
+
+
+def job_throughput(local_ms: float, units_per_rank: int, dist_mod=None, device=None):
+    """Whole-job throughput: units over all ranks / the slowest rank's time
+    (max-reduction across ranks; the only collective of the benchmark)."""
+    ws = 1
+    t = local_ms
+    if dist_mod is not None and dist_mod.is_initialized():
+        import torch
+        ws = dist_mod.get_world_size()
+        x = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist_mod.all_reduce(x, op=dist_mod.ReduceOp.MAX)
+        t = float(x.item())
+    return ws * units_per_rank / (t / 1e3), t
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -219,7 +239,7 @@ def main():
     w = workload
     B = max(1, args.batch)
     # independent designs: rank r, slot b gets seed + 1000 r + b (weak scaling)
-    rhos_np = [I.dataclasses.replace(w, seed=w.seed + 1000 * rank + b).density() for b in range(B)]
+    rhos_np = [I.dataclasses.replace(w, seed=sd).density() for sd in design_seeds(w.seed, rank, B)]
     rho_dev = [torch.from_numpy(r).cuda() for r in rhos_np]
     dc_dev = [torch.empty(w.n_elem, dtype=torch.float64, device="cuda") for _ in range(B)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -269,12 +289,7 @@ def main():
         dist.barrier()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     launches = sum(m.profile_read(reset=True)[2] for m in meshes)
-    total_ms = float(step_ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * B * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(float(step_ms.sum()), B * args.steps, dist, "cuda")
 
     # ---- single-design latency and the operator kernel's own timing ----
     m0 = meshes[0]

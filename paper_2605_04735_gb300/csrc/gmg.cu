@@ -76,9 +76,9 @@ struct EpiChebStep {
   const float* dinv;
   float c1, c2;
   int add_prev;
-  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
-                                               const float (&acc)[3], const float (&ctr)[3],
-                                               const Dims& d) const {
+  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
+                                              const float (&acc)[3], const float (&ctr)[3],
+                                              const Dims& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long oc = c * d.comp + o;
@@ -89,7 +89,7 @@ struct EpiChebStep {
       dn[oc] = dd;
       x[oc] += add_prev ? (dd + ctr[c]) : dd;
     }
-    return 0.0;
+    return 0.0f;
   }
 };
 
@@ -97,13 +97,13 @@ struct EpiChebStep {
 struct EpiChebLast {
   static constexpr bool kReduce = false;
   float* r;
-  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
-                                               const float (&acc)[3], const float (&)[3],
-                                               const Dims& d) const {
+  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
+                                              const float (&acc)[3], const float (&)[3],
+                                              const Dims& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (!d.fixed(c, i, j, k)) r[c * d.comp + o] -= acc[c];
-    return 0.0;
+    return 0.0f;
   }
 };
 
@@ -115,9 +115,9 @@ struct EpiChebResid {
   float* d0;
   const float* dinv;
   float inv_theta;
-  __device__ __forceinline__ double operator()(int i, int j, int k, long long o,
-                                               const float (&acc)[3], const float (&)[3],
-                                               const Dims& d) const {
+  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
+                                              const float (&acc)[3], const float (&)[3],
+                                              const Dims& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long oc = c * d.comp + o;
@@ -125,7 +125,7 @@ struct EpiChebResid {
       r[oc] = rr;
       d0[oc] = dinv[oc] * rr * inv_theta;
     }
-    return 0.0;
+    return 0.0f;
   }
 };
 

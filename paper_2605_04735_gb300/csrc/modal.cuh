@@ -103,10 +103,10 @@ struct __align__(128) ModalStage {
 // results (x by shuffle, y through smem, z by the register carry) and run
 // the epilogue for the completed node plane.
 template <typename T, class Epi>
-__device__ __forceinline__ double modal_combine(const T (&y)[3][8], T (&carry)[3],
-                                                T (*xch)[kModalTX][6], int tx, int ty, int ex,
-                                                int ey, int ez, bool emit, const T (&ctr)[3],
-                                                const Dims& d, const Epi& epi) {
+__device__ __forceinline__ T modal_combine(const T (&y)[3][8], T (&carry)[3],
+                                           T (*xch)[kModalTX][6], int tx, int ty, int ex, int ey,
+                                           int ez, bool emit, const T (&ctr)[3], const Dims& d,
+                                           const Epi& epi) {
   // x: the +x face (odd corners) moves to lane tx+1
   T s[2][2][3];  // [dy][dz][c] for node column x = ex
 #pragma unroll
@@ -125,7 +125,7 @@ __device__ __forceinline__ double modal_combine(const T (&y)[3][8], T (&carry)[3
 #pragma unroll
     for (int c = 0; c < 3; ++c) xch[ty][tx][3 * dz + c] = s[1][dz][c];
   __syncthreads();
-  double part = 0.0;
+  T part = T(0);
   T bot[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
   float bot[2][2][3], top[2][2][3];  // [dy][dx][c]
   float carry[3] = {0.f, 0.f, 0.f};
-  double part = 0.0;
+  float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   for (int t = 0; t < nst; ++t) {
     const int slot = t % kModalStages;
     mbar_wait_bounded(&bar[slot], (uint32_t)((t / kModalStages) & 1), errflag);
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
         for (int c = 0; c < 3; ++c) bot[dy][dx][c] = top[dy][dx][c];
   }
   if (Epi::kReduce) {
-    double v[1] = {part};
+    double v[1] = {(double)part};
     reduce_finalize<1>(v, red);
   }
 }
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
       for (int c = 0; c < 3; ++c) bot[dy][dx][c] = node_val(ex + dx, ey + dy, kb - 1, c);
   T carry[3] = {T(0), T(0), T(0)};
-  double part = 0.0;
+  T part = T(0);
   for (int ez = kb - 1; ez < ke; ++ez) {
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
         for (int c = 0; c < 3; ++c) bot[dy][dx][c] = top[dy][dx][c];
   }
   if (Epi::kReduce) {
-    double v[1] = {part};
+    double v[1] = {(double)part};
     reduce_finalize<1>(v, red);
   }
 }

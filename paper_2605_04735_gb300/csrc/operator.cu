@@ -20,14 +20,14 @@ template <typename T, bool DOT>
 struct EpiApply {
   static constexpr bool kReduce = DOT;
   T* y;
-  __device__ __forceinline__ double operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                               const T (&ctr)[3], const Dims& d) const {
-    double part = 0.0;
+  __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
+                                          const T (&ctr)[3], const Dims& d) const {
+    T part = T(0);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const T out = d.fixed(r, i, j, k) ? ctr[r] : acc[r];
       y[r * d.comp + o] = out;
-      if (DOT) part += (double)ctr[r] * (double)out;
+      if (DOT) part = fma(ctr[r], out, part);
     }
     return part;
   }
@@ -39,14 +39,14 @@ struct EpiResid {
   static constexpr bool kReduce = true;
   T* y;
   const T* f;
-  __device__ __forceinline__ double operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                               const T (&)[3], const Dims& d) const {
-    double part = 0.0;
+  __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
+                                          const T (&)[3], const Dims& d) const {
+    T part = T(0);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const T out = d.fixed(r, i, j, k) ? T(0) : (f[r * d.comp + o] - acc[r]);
       y[r * d.comp + o] = out;
-      part += (double)out * (double)out;
+      part = fma(out, out, part);
     }
     return part;
   }

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
   const int kb = blockIdx.z * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const bool act = (i <= d.nx) && (j <= d.ny);
-  double part = 0.0;
+  T part = T(0);
   if (act) {
     const long long ps = d.plane_stride();
     const long long eps = d.eplane();
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
     }
   }
   if (Epi::kReduce) {
-    double v[1] = {part};
+    double v[1] = {(double)part};
     reduce_finalize<1>(v, red);
   }
 }
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
   const int kb = blockIdx.z * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const bool act = (i <= d.nx) && (j <= d.ny);
-  double part = 0.0;
+  T part = T(0);
   for (int k = kb; act && k < ke; ++k) {
     const long long cs = d.comp;
     T acc[3] = {T(0), T(0), T(0)};
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
     part += epi(i, j, k, o, acc, ctr, d);
   }
   if (Epi::kReduce) {
-    double v[1] = {part};
+    double v[1] = {(double)part};
     reduce_finalize<1>(v, red);
   }
 }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
   read_nodes(1, 1);
   read_elems(1, 0);
   release(1);
-  double part = 0.0;
+  float part = 0.f;
   for (int k = kb; k < ke; ++k) {
     const int s = k - kb + 2;
     mbar_wait_bounded(&bar[s % kTmaStages], (uint32_t)((s / kTmaStages) & 1), errflag);
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
       for (int xx = 0; xx < 2; ++xx) e[0][yy][xx] = e[1][yy][xx];
   }
   if (Epi::kReduce) {
-    double v[1] = {part};
+    double v[1] = {(double)part};
     reduce_finalize<1>(v, red);
   }
 }

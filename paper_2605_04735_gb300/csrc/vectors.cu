@@ -1,5 +1,10 @@
 // Vector kernels of preconditioned CG and of the FP64 refinement loop.
 //
+// Dot products: the four products of one 16-byte group are summed in the
+// operand precision and only then widened, so FP32 vectors cost one FP64
+// add per four entries (GB300's FP64 rate is 1/64 of FP32; an FP64 FMA per
+// entry would make these streaming kernels FP64-bound).
+//
 // All vectors are whole padded arrays (ghost and pitch padding included,
 // always 0), 16-byte aligned with a length that is a multiple of 4, so the
 // kernels stream them with 16-byte vector loads.  Dots are accumulated in
@@ -65,11 +70,11 @@ __global__ void __launch_bounds__(kThreads)
       zv.w = dv.w * bv.w;
       st4(z, q, zv);
       st4(p, q, zv);
-      rz += (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z + (double)bv.w * zv.w;
+      rz += (double)(bv.x * zv.x + bv.y * zv.y + bv.z * zv.z + bv.w * zv.w);
     } else {
       st4(p, q, zero);  // the first direction is set after z = M r
     }
-    rr += (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z + (double)bv.w * bv.w;
+    rr += (double)(bv.x * bv.x + bv.y * bv.y + bv.z * bv.z + bv.w * bv.w);
   }
   double v[2] = {rz, rr};
   reduce_finalize<2>(v, red);
@@ -109,9 +114,9 @@ __global__ void __launch_bounds__(kThreads)
       zv.z = dv.z * rv.z;
       zv.w = dv.w * rv.w;
       st4(z, q, zv);
-      rz += (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z + (double)rv.w * zv.w;
+      rz += (double)(rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w);
     }
-    rr += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z + (double)rv.w * rv.w;
+    rr += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
   }
   if (JAC) {
     double v[2] = {rz, rr};
@@ -152,10 +157,10 @@ __global__ void __launch_bounds__(kThreads)
        q += (long long)gridDim.x * blockDim.x) {
     const auto av = ld4(a, q);
     const auto bv = ld4(b, q);
-    s0 += (double)av.x * bv.x + (double)av.y * bv.y + (double)av.z * bv.z + (double)av.w * bv.w;
+    s0 += (double)(av.x * bv.x + av.y * bv.y + av.z * bv.z + av.w * bv.w);
     if (TWO) {
       const auto cv = ld4(c, q);
-      s1 += (double)av.x * cv.x + (double)av.y * cv.y + (double)av.z * cv.z + (double)av.w * cv.w;
+      s1 += (double)(av.x * cv.x + av.y * cv.y + av.z * cv.z + av.w * cv.w);
     }
   }
   double v[2] = {s0, s1};
