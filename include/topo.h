@@ -117,10 +117,22 @@ typedef struct {
   int check_every;   /* inner iterations between host convergence checks (default 16) */
 } topo_solve_opts;
 
+/* Where a failed solve stopped (topo_solve_info.detail). */
+enum {
+  TOPO_FAIL_NONE = 0,
+  TOPO_FAIL_SETUP = 1,       /* options, allocation or setup before the first residual */
+  TOPO_FAIL_RESIDUAL = 2,    /* a true FP64 residual was not finite */
+  TOPO_FAIL_BREAKDOWN = 3,   /* inner CG breakdown (p.Ap <= 0 or r.z <= 0 or non-finite) */
+  TOPO_FAIL_LIMIT = 4,       /* iteration or refinement caps reached */
+  TOPO_FAIL_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  TOPO_FAIL_DEVICE = 6       /* a CUDA call failed */
+};
+
 typedef struct {
   int iters;           /* inner CG iterations (all refinement steps) */
   int outer;           /* FP64 refinement steps (residual evaluations after the first) */
   int status;          /* the topo_status the call returned */
+  int detail;          /* TOPO_FAIL_* */
   double rel_residual; /* final true FP64 relative residual */
   double seconds;      /* wall time of the call */
 } topo_solve_info;
@@ -257,6 +269,7 @@ typedef struct topo_server topo_server;
 typedef struct {
   int job, design;       /* ids returned by topo_server_submit / topo_server_open */
   int status;            /* topo_status of the solve */
+  int detail;            /* TOPO_FAIL_* (and 1 also when the density was rejected) */
   int iters, outer;      /* as in topo_solve_info */
   double rel_residual;   /* final true FP64 relative residual */
   double compliance;     /* f^T u (valid when status == TOPO_OK) */

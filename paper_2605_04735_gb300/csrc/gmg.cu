@@ -1,7 +1,6 @@
 // Geometric multigrid V-cycle (see gmg.h).  All grid transfers are gathers
 // (no atomics); the Chebyshev smoother's vector updates are fused into the
 // operator kernel's epilogue, so one smoothing step is one pass.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -256,46 +255,42 @@ __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const flo
 }
 
 // In-place Gauss-Jordan inversion of the SPD coarsest matrix (no pivoting
-// needed: every pivot is a Schur-complement diagonal, hence positive), as ONE
-// cooperative kernel with a grid-wide barrier between pivots.  The pivot row
-// and column as they were before step k are read from side buffers written
-// during step k-1 (ping-pong), so no entry is read after being overwritten
-// in the same step.
-__global__ void __launch_bounds__(256) k_gj_coop(double* __restrict__ A, int n,
-                                                 double* __restrict__ side) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
-  const long long nn = (long long)n * n;
-  const long long tid = grid.thread_rank();
-  const long long nthr = grid.size();
-  double* buf[2][2] = {{side, side + n}, {side + 2 * n, side + 3 * n}};
-  for (long long t = tid; t < n; t += nthr) {
-    buf[0][0][t] = A[t];
-    buf[0][1][t] = A[t * n];
+// needed: every pivot is a Schur-complement diagonal, hence positive), one
+// kernel per pivot k.  The pivot row and column as they were before step k
+// are read from side buffers that step k-1 wrote (ping-pong), so no entry is
+// read after being overwritten in the same step.  (Kernel boundaries are the
+// barriers: a single cooperative kernel with grid-wide barriers is not safe
+// when many meshes set up concurrently on their own streams.)  The chain of
+// n launches is captured once per hierarchy as a CUDA graph.
+__global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
+                          double* __restrict__ col) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    row[t] = A[t];
+    col[t] = A[(long long)t * n];
   }
-  grid.sync();
-  for (int k = 0; k < n; ++k) {
-    const double* rowk = buf[k & 1][0];
-    const double* colk = buf[k & 1][1];
-    double* rown = buf[(k + 1) & 1][0];
-    double* coln = buf[(k + 1) & 1][1];
-    const double p = 1.0 / rowk[k];
-    for (long long t = tid; t < nn; t += nthr) {
-      const int i = (int)(t / n), j = (int)(t % n);
-      double v;
-      if (i == k && j == k)
-        v = p;
-      else if (i == k)
-        v = rowk[j] * p;
-      else if (j == k)
-        v = -colk[i] * p;
-      else
-        v = A[t] - colk[i] * rowk[j] * p;
-      A[t] = v;
-      if (i == k + 1) rown[j] = v;
-      if (j == k + 1) coln[i] = v;
-    }
-    grid.sync();
+}
+
+__global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
+                          const double* __restrict__ colk, double* __restrict__ rown,
+                          double* __restrict__ coln) {
+  const long long nn = (long long)n * n;
+  const double p = 1.0 / rowk[k];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    double v;
+    if (i == k && j == k)
+      v = p;
+    else if (i == k)
+      v = rowk[j] * p;
+    else if (j == k)
+      v = -colk[i] * p;
+    else
+      v = A[t] - colk[i] * rowk[j] * p;
+    A[t] = v;
+    if (i == k + 1) rown[j] = v;
+    if (j == k + 1) coln[i] = v;
   }
 }
 
@@ -332,12 +327,15 @@ __global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __
   }
 }
 
+// Zero-filled allocation, ordered on the mesh's own stream (a plain
+// cudaMemset would go to the legacy default stream, which does not order
+// against the mesh's non-blocking stream).
 template <typename T>
-cudaError_t dmalloc(T** p, long long count, long long* bytes) {
+cudaError_t dmalloc(T** p, long long count, long long* bytes, cudaStream_t s) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
   if (e != cudaSuccess) return e;
   *bytes += count * (long long)sizeof(T);
-  return cudaMemset(*p, 0, (size_t)count * sizeof(T));
+  return cudaMemsetAsync(*p, 0, (size_t)count * sizeof(T), s);
 }
 
 #define GCK(call)                          \
@@ -428,7 +426,8 @@ long long gmg_footprint(const Dims& fine, int max_levels) {
   return b;
 }
 
-cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max) {
+cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
+                       cudaStream_t s) {
   g.degree = std::max(1, degree);
   g.lam_max = lam_max;
   g.lv.clear();
@@ -443,19 +442,19 @@ cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, dou
   if ((long long)g.nc * g.nc > (1LL << 27)) return cudaErrorInvalidValue;  // > 1 GB inverse
   for (size_t l = 0; l < g.lv.size(); ++l) {
     GmgLevel& L = g.lv[l];
-    GCK(dmalloc(&L.r, L.nvec, &g.bytes));
-    GCK(dmalloc(&L.dv[0], L.nvec, &g.bytes));
-    GCK(dmalloc(&L.dv[1], L.nvec, &g.bytes));
+    GCK(dmalloc(&L.r, L.nvec, &g.bytes, s));
+    GCK(dmalloc(&L.dv[0], L.nvec, &g.bytes, s));
+    GCK(dmalloc(&L.dv[1], L.nvec, &g.bytes, s));
     if (l > 0) {
-      GCK(dmalloc(&L.E, L.d.ecount, &g.bytes));
-      GCK(dmalloc(&L.dinv, L.nvec, &g.bytes));
-      GCK(dmalloc(&L.b, L.nvec, &g.bytes));
-      GCK(dmalloc(&L.x, L.nvec, &g.bytes));
+      GCK(dmalloc(&L.E, L.d.ecount, &g.bytes, s));
+      GCK(dmalloc(&L.dinv, L.nvec, &g.bytes, s));
+      GCK(dmalloc(&L.b, L.nvec, &g.bytes, s));
+      GCK(dmalloc(&L.x, L.nvec, &g.bytes, s));
     }
   }
-  GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes));
-  GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes));
-  GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes));
+  GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes, s));
+  GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes, s));
+  GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes, s));
   g.ready = false;
   return cudaSuccess;
 }
@@ -477,21 +476,29 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
   const long long nn = (long long)g.nc * g.nc;
   k_dense_assemble<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d);
   GCK(cudaGetLastError());
-  // one cooperative launch: as many co-resident blocks as the device holds,
-  // no more than the matrix needs
-  int per_sm = 0, sms = 0, dev = 0;
-  GCK(cudaGetDevice(&dev));
-  GCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  GCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, kPT, 0));
-  long long blocks = std::min<long long>((long long)per_sm * sms, (nn + kPT - 1) / kPT);
-  if (blocks < 1) blocks = 1;
-  int n = g.nc;
-  double* A = g.Ainv;
-  double* side = g.side;
-  void* args[] = {&A, &n, &side};
-  GCK(cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3((unsigned)blocks), dim3(kPT), args,
-                                  0, s));
-  *launches += 1;
+  // the pivot chain, captured once as a graph and replayed per density
+  if (!g.gj_exec) {
+    cudaStream_t cs = nullptr;
+    GCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
+      k_gj_seed<<<(g.nc + kPT - 1) / kPT, kPT, 0, cs>>>(g.Ainv, g.nc, buf[0][0], buf[0][1]);
+      for (int k = 0; k < g.nc; ++k) {
+        double** cur = buf[k & 1];
+        double** nxt = buf[(k + 1) & 1];
+        k_gj_step<<<grid1d(nn), kPT, 0, cs>>>(g.Ainv, g.nc, k, cur[0], cur[1], nxt[0], nxt[1]);
+      }
+      e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.gj_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    GCK(e);
+  }
+  GCK(cudaGraphLaunch(g.gj_exec, s));
+  *launches += 1 + g.nc;
   g.ready = true;
   return cudaSuccess;
 }
@@ -570,6 +577,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
 }
 
 void gmg_free(Gmg& g) {
+  if (g.gj_exec) cudaGraphExecDestroy(g.gj_exec);
+  g.gj_exec = nullptr;
   for (size_t l = 0; l < g.lv.size(); ++l) {
     GmgLevel& L = g.lv[l];
     cudaFree(L.r);

@@ -37,6 +37,7 @@ struct Gmg {
   double* Ainv = nullptr;    // nc * nc
   double* side = nullptr;    // 4 * nc (Gauss-Jordan pivot row/column, ping-pong)
   double* bd = nullptr;      // nc
+  cudaGraphExec_t gj_exec = nullptr;  // captured Gauss-Jordan pivot chain
   long long bytes = 0;
   bool ready = false;        // set up for the current densities
 };
@@ -46,7 +47,8 @@ std::vector<Dims> gmg_plan(const Dims& fine, int max_levels);
 long long gmg_footprint(const Dims& fine, int max_levels);
 // Choose levels for a fine grid and allocate them (fine-level E/dinv/b/x are
 // bound later, per call).  max_levels <= 0: automatic.
-cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max);
+cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
+                       cudaStream_t s);
 // Per-density setup: coarse moduli, Jacobi diagonals, coarsest inverse.
 cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
                       const K0<double>& k0d, cudaStream_t s, long long* launches);

@@ -15,13 +15,17 @@
 //
 // Work split (no atomics): a CTA is 32 x 8 threads; thread (tx, ty) owns the
 // element column (x0-1+tx, y0-1+ty, *) and marches up in z, one element
-// layer per step.  Its element's 8 nodal results are combined with its
-// neighbours' as follows: the +x face goes to lane tx+1 by warp shuffle, the
-// +y face to thread row ty+1 through a double-buffered shared-memory slot, and
-// the +z face is carried in registers to the next layer.  Thread (tx, ty) with
-// tx, ty >= 1 then holds the complete result of node (x0-1+tx, y0-1+ty, z)
-// after layer z: a CTA owns a 31 x 7 tile of node columns, recomputing one
-// halo element layer on its -x and -y sides.
+// layer per step.  The transform is split into its x-y part (per node plane)
+// and its z part (per element): the x-y transform of a node plane is computed
+// once and shared by the element below and the element above it, and on the
+// way back the two elements' contributions to a node plane are summed in the
+// x-y modal domain before one inverse x-y transform.  The plane's four
+// corner results are then combined with the neighbours': the +x corners go
+// to lane tx+1 by warp shuffle and the +y corner to thread row ty+1 through a
+// double-buffered shared-memory slot.  Thread (tx, ty) with tx, ty >= 1 then
+// holds the complete result of node (x0-1+tx, y0-1+ty, z): a CTA owns a
+// 31 x 7 tile of node columns, recomputing one halo element layer on its -x
+// and -y sides.
 #pragma once
 
 #include <cuda.h>
@@ -52,23 +56,67 @@ __device__ __forceinline__ void fwht8(T (&v)[8]) {
       }
 }
 
-// y = E k0 u for one element (u, y: [component][corner])
+// 4-point (x-y) Walsh-Hadamard transform, corner index dx + 2 dy
 template <typename T>
-__device__ __forceinline__ void modal_element(const T (&u)[3][8], T E, const ModalCoef<T>& kc,
-                                              T (&y)[3][8]) {
-  T uh[3][8];
+__device__ __forceinline__ void fwht4(T (&v)[4]) {
+  T a = v[0] + v[1], b = v[0] - v[1], c = v[2] + v[3], e = v[2] - v[3];
+  v[0] = a + c;
+  v[1] = b + e;
+  v[2] = a - c;
+  v[3] = b - e;
+}
+
+// Per-thread state of the z march (see the work split above).
+template <typename T>
+struct ModalColumn {
+  T bxy[3][4];   // x-y transform of the bottom node plane, shifted by ref
+  T ref[3];      // raw displacement of node (ex, ey, ez): the element's corner 0
+  T carry[3][4]; // z-upper half of the previous element's result (x-y modal)
+};
+
+// start of the march: node plane kb-1 (raw corner values [dy][dx][c])
+template <typename T>
+__device__ __forceinline__ void modal_seed(ModalColumn<T>& col, const T (&raw)[2][2][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    uh[c][0] = T(0);
+    col.ref[c] = raw[0][0][c];
+    T v[4] = {T(0), raw[0][1][c] - col.ref[c], raw[1][0][c] - col.ref[c],
+              raw[1][1][c] - col.ref[c]};
+    fwht4(v);
 #pragma unroll
-    for (int b = 1; b < 8; ++b) uh[c][b] = u[c][b] - u[c][0];
-    fwht8(uh[c]);
-#pragma unroll
-    for (int m = 1; m < 8; ++m) uh[c][m] *= E;
+    for (int q = 0; q < 4; ++q) {
+      col.bxy[c][q] = v[q];
+      col.carry[c][q] = T(0);
+    }
   }
+}
+
+// One element layer: top node plane raw values in, the finished result of
+// node plane ez (x-y corners [c][dx + 2 dy], before the neighbour exchange)
+// out.  ctr receives the raw displacement of node (ex, ey, ez).
+template <typename T>
+__device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[2][2][3], T E,
+                                           const ModalCoef<T>& kc, T (&plane)[3][4],
+                                           T (&ctr)[3]) {
+  T uh[3][8];
+  T txy[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    ctr[c] = col.ref[c];
+    T v[4] = {top[0][0][c] - col.ref[c], top[0][1][c] - col.ref[c], top[1][0][c] - col.ref[c],
+              top[1][1][c] - col.ref[c]};
+    fwht4(v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      txy[c][q] = v[q];
+      uh[c][q] = (col.bxy[c][q] + v[q]) * E;      // z mode 0
+      uh[c][q + 4] = (col.bxy[c][q] - v[q]) * E;  // z mode 1
+    }
+  }
+  T yh[3][8];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    y[p][0] = T(0);
+    yh[p][0] = T(0);
 #pragma unroll
     for (int m = 1; m < 8; ++m) {
       T acc = kc.D[p][m] * uh[p][m];
@@ -78,10 +126,49 @@ __device__ __forceinline__ void modal_element(const T (&u)[3][8], T E, const Mod
         if (((m >> p) & 1) == ((m >> q) & 1)) continue;
         acc = fma(kc.C[p][q][m], uh[q][m ^ (1 << p) ^ (1 << q)], acc);
       }
-      y[p][m] = acc;
+      yh[p][m] = acc;
     }
-    fwht8(y[p]);
   }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w[q] = yh[c][q] + yh[c][q + 4] + col.carry[c][q];  // bottom face + previous top face
+      col.carry[c][q] = yh[c][q] - yh[c][q + 4];         // this element's top face
+    }
+    fwht4(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) plane[c][q] = w[q];
+    // the top plane becomes the next bottom plane, re-referenced to its corner 0
+    const T nref = top[0][0][c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) col.bxy[c][q] = txy[c][q];
+    col.bxy[c][0] += T(4) * (col.ref[c] - nref);
+    col.ref[c] = nref;
+  }
+}
+
+// exchange a finished plane's corners with the neighbours and run the
+// epilogue on the owned node (ex, ey, ez)
+template <typename T, class Epi>
+__device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3], int tx, int ty,
+                                          int ex, int ey, int ez, bool emit, const T (&ctr)[3],
+                                          const Dims& d, const Epi& epi) {
+  T n0[3], n2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T r1 = __shfl_up_sync(0xffffffffu, plane[c][1], 1);
+    const T r3 = __shfl_up_sync(0xffffffffu, plane[c][3], 1);
+    n0[c] = plane[c][0] + (tx > 0 ? r1 : T(0));
+    n2[c] = plane[c][2] + (tx > 0 ? r3 : T(0));
+    xch[ty][tx][c] = n2[c];
+  }
+  __syncthreads();
+  T res[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) res[c] = n0[c] + (ty > 0 ? xch[ty - 1][tx][c] : T(0));
+  return emit ? epi(ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
 }
 
 constexpr int kModalTX = 32, kModalTY = 8;
@@ -99,45 +186,6 @@ struct __align__(128) ModalStage {
   alignas(128) float elem[kMElem];
 };
 
-// Shared by both variants: combine one element layer's results into node
-// results (x by shuffle, y through smem, z by the register carry) and run
-// the epilogue for the completed node plane.
-template <typename T, class Epi>
-__device__ __forceinline__ T modal_combine(const T (&y)[3][8], T (&carry)[3],
-                                           T (*xch)[kModalTX][6], int tx, int ty, int ex, int ey,
-                                           int ez, bool emit, const T (&ctr)[3], const Dims& d,
-                                           const Epi& epi) {
-  // x: the +x face (odd corners) moves to lane tx+1
-  T s[2][2][3];  // [dy][dz][c] for node column x = ex
-#pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T right = y[c][1 + 2 * dy + 4 * dz];
-        const T recv = __shfl_up_sync(0xffffffffu, right, 1);
-        s[dy][dz][c] = y[c][2 * dy + 4 * dz] + (tx > 0 ? recv : T(0));
-      }
-  // y: the +y face goes to thread row ty+1 (double-buffered slot, one barrier)
-#pragma unroll
-  for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) xch[ty][tx][3 * dz + c] = s[1][dz][c];
-  __syncthreads();
-  T part = T(0);
-  T bot[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const T r0 = ty > 0 ? xch[ty - 1][tx][c] : T(0);
-    const T r1 = ty > 0 ? xch[ty - 1][tx][3 + c] : T(0);
-    bot[c] = s[0][0][c] + r0 + carry[c];  // node (ex, ey, ez) is complete
-    carry[c] = s[0][1][c] + r1;           // node (ex, ey, ez+1) so far
-  }
-  if (emit) part = epi(ex, ey, ez, d.node(ex, ey, ez), bot, ctr, d);
-  return part;
-}
-
 template <class Epi>
 __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
@@ -147,7 +195,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   if (done != nullptr && *done) return;  // uniform over the grid
   __shared__ ModalStage st[kModalStages];
   __shared__ uint64_t bar[kModalStages];
-  __shared__ float xch[2][kModalTY][kModalTX][6];
+  __shared__ float xch[2][kModalTY][kModalTX][3];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kModalTX + tx;
   const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * kModalOwnY;
@@ -173,13 +221,13 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   if (tid == 0)
     for (int t = 0; t < kModalStages && t < nst; ++t) issue(t);
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
-  float bot[2][2][3], top[2][2][3];  // [dy][dx][c]
-  float carry[3] = {0.f, 0.f, 0.f};
+  ModalColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   for (int t = 0; t < nst; ++t) {
     const int slot = t % kModalStages;
     mbar_wait_bounded(&bar[slot], (uint32_t)((t / kModalStages) & 1), errflag);
     const float* nd = st[slot].node;
+    float top[2][2][3];  // [dy][dx][c]
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -188,46 +236,25 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
         for (int c = 0; c < 3; ++c)
           top[dy][dx][c] = nd[c * (kMBoxNY * kMBoxX) + (ty + dy) * kMBoxX + ox + tx + dx];
     const float E = st[slot].elem[ty * kMBoxX + ox + tx];
-    if (t == 0) {  // the first node plane only seeds the bottom face
+    if (t == 0) {  // the first node plane only seeds the march
       __syncthreads();
       if (tid == 0 && kModalStages < nst) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(kModalStages);
       }
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) bot[dy][dx][c] = top[dy][dx][c];
+      modal_seed<float>(col, top);
       continue;
     }
-    float u[3][8], y[3][8];
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            u[c][dx + 2 * dy + 4 * dz] = dz ? top[dy][dx][c] : bot[dy][dx][c];
-    modal_element<float>(u, E, kc, y);
+    float plane[3][4], ctr[3];
+    modal_layer<float>(col, top, E, kc, plane, ctr);
     const int ez = kb - 2 + t;
-    const float ctr[3] = {bot[0][0][0], bot[0][0][1], bot[0][0][2]};
-    // the barrier inside modal_combine also retires this stage's slot
-    part += modal_combine<float, Epi>(y, carry, xch[t & 1], tx, ty, ex, ey, ez,
-                                      own && t >= 2, ctr, d, epi);
+    // the barrier inside modal_finish also retires this stage's slot
+    part += modal_finish<float, Epi>(plane, xch[t & 1], tx, ty, ex, ey, ez, own && t >= 2, ctr, d,
+                                     epi);
     if (tid == 0 && t + kModalStages < nst) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(t + kModalStages);
     }
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) bot[dy][dx][c] = top[dy][dx][c];
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
@@ -243,7 +270,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
                   const __grid_constant__ ModalCoef<T> kc, const Epi epi, const Red red,
                   const int zchunk, const int* __restrict__ done) {
   if (done != nullptr && *done) return;
-  __shared__ T xch[2][kModalTY][kModalTX][6];
+  __shared__ T xch[2][kModalTY][kModalTX][3];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * kModalOwnY;
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
@@ -254,16 +281,20 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     if (i > d.nx + 1 || j > d.ny + 1 || k > d.nz + 1) return T(0);  // beyond the ghost ring
     return __ldg(x + c * d.comp + d.node(i, j, k));
   };
-  T bot[2][2][3], top[2][2][3];
+  ModalColumn<T> col;
+  {
+    T raw[2][2][3];
 #pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
+    for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx)
+      for (int dx = 0; dx < 2; ++dx)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) bot[dy][dx][c] = node_val(ex + dx, ey + dy, kb - 1, c);
-  T carry[3] = {T(0), T(0), T(0)};
+        for (int c = 0; c < 3; ++c) raw[dy][dx][c] = node_val(ex + dx, ey + dy, kb - 1, c);
+    modal_seed<T>(col, raw);
+  }
   T part = T(0);
   for (int ez = kb - 1; ez < ke; ++ez) {
+    T top[2][2][3];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -271,26 +302,10 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
         for (int c = 0; c < 3; ++c) top[dy][dx][c] = node_val(ex + dx, ey + dy, ez + 1, c);
     const T Ee = (ex <= d.nx && ey <= d.ny && ez <= d.nz) ? __ldg(E + d.elem(ex, ey, ez)) : T(0);
-    T u[3][8], y[3][8];
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            u[c][dx + 2 * dy + 4 * dz] = dz ? top[dy][dx][c] : bot[dy][dx][c];
-    modal_element<T>(u, Ee, kc, y);
-    const T ctr[3] = {bot[0][0][0], bot[0][0][1], bot[0][0][2]};
-    part += modal_combine<T, Epi>(y, carry, xch[(ez - kb + 1) & 1], tx, ty, ex, ey, ez,
-                                  own && ez >= kb, ctr, d, epi);
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) bot[dy][dx][c] = top[dy][dx][c];
+    T plane[3][4], ctr[3];
+    modal_layer<T>(col, top, Ee, kc, plane, ctr);
+    part += modal_finish<T, Epi>(plane, xch[(ez - kb + 1) & 1], tx, ty, ex, ey, ez,
+                                 own && ez >= kb, ctr, d, epi);
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};

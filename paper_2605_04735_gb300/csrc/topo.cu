@@ -341,7 +341,7 @@ topo_status ensure_gmg(topo_mesh* m, const topo_solve_opts* o) {
     m->gmg_built = false;
   }
   if (!m->gmg_built) {
-    cudaError_t e = gmg_create(m->gmg, m->d, o->gmg_levels, o->smooth_degree, m->lam_max);
+    cudaError_t e = gmg_create(m->gmg, m->d, o->gmg_levels, o->smooth_degree, m->lam_max, m->stream);
     m->bytes += m->gmg.bytes;
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -369,6 +369,7 @@ struct SolveTask {
   enum Phase { P_RESID, P_INNER, P_FINISHED } phase = P_FINISHED;
   topo_status st = TOPO_OK;
   int outer = 0, total = 0, it_before = 0, kind = IK_JAC32;
+  int detail = TOPO_FAIL_NONE;
   bool profile = false;
   double fn = 0.0;
   Timer timer;
@@ -384,11 +385,17 @@ topo_status request_scalars(topo_mesh* m) {
 void task_finish(SolveTask& t, topo_status st) {
   t.st = st;
   t.phase = SolveTask::P_FINISHED;
+  if (st != TOPO_OK && t.detail == TOPO_FAIL_NONE)
+    t.detail = (st == TOPO_ERR_NOT_CONVERGED) ? TOPO_FAIL_LIMIT
+               : (st == TOPO_ERR_TIMEOUT)     ? TOPO_FAIL_TIMEOUT
+               : (st == TOPO_ERR_CUDA || st == TOPO_ERR_OOM) ? TOPO_FAIL_DEVICE
+                                                               : TOPO_FAIL_SETUP;
   if (st == TOPO_OK) t.m->solved = true;
   if (t.info) {
     t.info->iters = t.total;
     t.info->outer = t.outer;
     t.info->status = st;
+    t.info->detail = t.detail;
     t.info->seconds = t.timer.seconds();
   }
 }
@@ -475,10 +482,16 @@ topo_status task_step(SolveTask& t) {
   topo_mesh* m = t.m;
   const topo_solve_opts& o = t.o;
   const PcgScalars& h = *m->h_sc;
-  if (*m->h_flag) return TOPO_ERR_TIMEOUT;
+  if (*m->h_flag) {
+    t.detail = TOPO_FAIL_TIMEOUT;
+    return TOPO_ERR_TIMEOUT;
+  }
   if (t.phase == SolveTask::P_RESID) {
     const double rr = h.aux[0];
-    if (!std::isfinite(rr)) return TOPO_ERR_NAN;
+    if (!std::isfinite(rr)) {
+      t.detail = TOPO_FAIL_RESIDUAL;
+      return TOPO_ERR_NAN;
+    }
     const double rel = t.fn > 0 ? std::sqrt(rr) / t.fn : 0.0;
     if (t.info) t.info->rel_residual = rel;
     if (rel <= o.rtol) {
@@ -515,7 +528,10 @@ topo_status task_step(SolveTask& t) {
   }
   t.total += h.iter;
   ++t.outer;
-  if (h.status == 2) return TOPO_ERR_NAN;
+  if (h.status == 2) {
+    t.detail = TOPO_FAIL_BREAKDOWN;
+    return TOPO_ERR_NAN;
+  }
   if (t.kind == IK_JAC64)
     LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, m->stream));
   else  // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
@@ -682,6 +698,7 @@ bool server_step(topo_server* s) {
         r.job = d.current.id;
         r.design = d.id;
         r.status = d.task.st;
+        r.detail = d.info.detail;
         r.iters = d.info.iters;
         r.outer = d.info.outer;
         r.rel_residual = d.info.rel_residual;
@@ -712,9 +729,22 @@ bool server_step(topo_server* s) {
       d.task.o.warm_start = d.solved ? 1 : 0;
       d.task.info = &d.info;
       if (st == TOPO_OK) st = task_start(d.task);
-      if (st != TOPO_OK) task_finish(d.task, st);
-      d.running = true;  // reported on the next pass (also when it failed to start)
       moved = true;
+      if (st != TOPO_OK) {  // report at once: the job never ran
+        task_finish(d.task, st);
+        topo_job_result r{};
+        r.job = d.current.id;
+        r.design = d.id;
+        r.status = st;
+        r.detail = TOPO_FAIL_SETUP;
+        r.submit_s = d.current.submit_s;
+        r.start_s = d.current.start_s;
+        r.finish_s = s->clock.seconds();
+        s->done.push_back(r);
+        d.current.rho.clear();
+      } else {
+        d.running = true;
+      }
     }
   }
   // retire closed designs once idle

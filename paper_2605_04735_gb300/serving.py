@@ -52,7 +52,8 @@ def run_stream(requests, budget_bytes: int, max_active: int = 64, opts=None,
                     clock0 = (time.perf_counter() - t0) - res.finish_s
                 r, step, rho, t_arr = state[res.design]
                 if res.status != 0:
-                    raise topo.TopoError(res.status, f"request {r.rid} step {step}")
+                    raise topo.TopoError(res.status, f"request {r.rid} step {step} "
+                                                     f"(failure detail {res.detail})")
                 solves.append({"rid": r.rid, "step": step, "latency_s": res.finish_s - res.submit_s,
                                "queue_s": res.start_s - res.submit_s, "iters": res.iters,
                                "rel_residual": res.rel_residual, "compliance": res.compliance,

@@ -38,12 +38,13 @@ class SolveOpts(C.Structure):
 
 
 class SolveInfo(C.Structure):
-    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int), ("detail", C.c_int),
                 ("rel_residual", C.c_double), ("seconds", C.c_double)]
 
 
 class JobResult(C.Structure):
-    _fields_ = [("job", C.c_int), ("design", C.c_int), ("status", C.c_int), ("iters", C.c_int),
+    _fields_ = [("job", C.c_int), ("design", C.c_int), ("status", C.c_int), ("detail", C.c_int),
+                ("iters", C.c_int),
                 ("outer", C.c_int), ("rel_residual", C.c_double), ("compliance", C.c_double),
                 ("submit_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double)]
 

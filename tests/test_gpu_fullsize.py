@@ -54,7 +54,8 @@ def _check_solution(topo, w, m, u, info):
     elems = I.fd_elements(rho, 60, 7)
     en = fem.element_energies_at(g, u, k0, elems)
     ref = -3.0 * rho[elems].astype(np.float64) ** 2 * (1 - 1e-9) * en
-    assert np.all(np.abs(dc[elems] - ref) <= 1e-8 * np.abs(ref) + 1e-12 * np.abs(ref).max())
+    # both FP64, different formulas: soft elements carry a cancellation floor ~1e-11 of max|dc|
+    assert np.all(np.abs(dc[elems] - ref) <= 1e-8 * np.abs(ref) + 1e-9 * np.abs(ref).max())
     assert np.all(dc <= 0.0)
 
 

@@ -102,3 +102,70 @@ def test_server_results_match_oracle_and_reject_oversize(topo):
         with pytest.raises(topo.TopoError) as e:
             srv.open(24, 12, 12, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM)
         assert e.value.status == topo.ERR_OOM
+
+
+def test_server_many_concurrent_setups_match_alone(topo):
+    """Two dozen designs admitted at once set up their multigrid hierarchies
+    and solve concurrently on their own streams; every compliance equals the
+    one computed alone (bitwise)."""
+    reqs = I.serving_stream(n_requests=24, n_steps=1, rate=0.0, max_ny=20, seed=123)
+    alone = {}
+    for r in reqs:
+        with topo.Mesh(r.nx, r.ny, r.nz, r.bc, r.load) as m:
+            m.set_density(r.rho0)
+            info = m.solve()
+            alone[r.rid] = (info.iters, m.compliance())
+    with topo.Server(1 << 36, max_active=64) as srv:
+        ds = {}
+        for r in reqs:
+            d = srv.open(r.nx, r.ny, r.nz, r.bc, r.load)
+            srv.submit(d, r.rho0)
+            ds[d] = r.rid
+        got = []
+        while len(got) < len(reqs):
+            got += srv.poll(wait=True)
+    for res in got:
+        assert res.status == 0, (ds[res.design], res.status)
+        assert (res.iters, res.compliance) == alone[ds[res.design]]
+
+
+def test_server_staggered_admission_matches_alone(topo):
+    """Designs admitted one by one while others are mid-solve (at most four
+    resident), over several re-solves each: every job succeeds and matches
+    the design's solves alone.  (A setup step ordered on the wrong stream
+    used to corrupt a newly admitted design in exactly this pattern.)"""
+    steps = 3
+    reqs = I.serving_stream(n_requests=16, n_steps=steps, rate=0.0, max_ny=24, seed=321)
+    alone = {r.rid: _alone(topo, r, steps)[0] for r in reqs}
+    with topo.Server(1 << 36, max_active=4) as srv:
+        design, state = {}, {}
+        queue = list(reqs)
+        got = {r.rid: [] for r in reqs}
+
+        def admit_one():
+            r = queue.pop(0)
+            d = srv.open(r.nx, r.ny, r.nz, r.bc, r.load)
+            srv.submit(d, r.rho0)
+            design[d], state[d] = r, (0, r.rho0)
+
+        for _ in range(4):
+            admit_one()
+        finished = 0
+        while finished < len(reqs):
+            for res in srv.poll(wait=True):
+                r = design[res.design]
+                step, rho = state[res.design]
+                assert res.status == 0, (r.rid, step, res.status, res.detail)
+                got[r.rid].append((res.iters, res.compliance))
+                if queue:
+                    admit_one()  # a new design arrives while the others keep solving
+                step += 1
+                if step < steps:
+                    rho = I.perturb(rho, r.factor(step))
+                    srv.submit(res.design, rho)
+                    state[res.design] = (step, rho)
+                else:
+                    srv.retire(res.design)
+                    finished += 1
+    for r in reqs:
+        assert got[r.rid] == alone[r.rid], r.rid
