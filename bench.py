@@ -32,7 +32,57 @@ from paper_2605_04735_gb300 import inputs as I  # noqa: E402
 
 METRIC = "PCG state solves/s at true FP64 rel. residual 1e-8 (solve + compliance + sensitivity)"
 UNIT = "solves/s"
-FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+# the operator kernel that dominates a step (by operator choice) and the
+# large-grid roofline case
+OPERATOR_KERNELS = {
+    0: "k_modal_tma (FP32 modal operator, one element column per thread; automatic form)",
+    1: "k_stencil_tma (FP32 node-centric 27-node gather)",
+    2: "k_modal_tma (FP32 modal operator, one element column per thread)",
+    3: "k_modal_pair (FP32 modal operator, two element columns per thread, packed f32x2)",
+}
+LARGE_WORKLOAD = "cantilever_voids_320x160x160"
+# DRAM bytes (read + write) per launch of the default operator kernel from one
+# ncu capture of the same kernel source, by workload; None until captured
+NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": None, LARGE_WORKLOAD: None}
+
+
+def operator_bytes(w: I.Workload) -> int:
+    """Algorithmic HBM bytes of one operator application y = K(rho) x in
+    FP32: x read and y written once per node (3 x 4 B each), E read once per
+    element (4 B)."""
+    return 24 * w.n_nodes + 4 * w.n_elem
+
+
+def roofline(w: I.Workload, avg_ms: float, peaks: dict, peaks_src: str, op: int = 0) -> dict:
+    achieved = operator_bytes(w) / (avg_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(w.name) if op == 0 else None,
+            "kernel": OPERATOR_KERNELS[op], "workload": w.name,
+            "bytes_per_launch": operator_bytes(w),
+            "avg_launch_us": avg_ms * 1e3,
+            "gdofs": 3.0 * w.n_nodes / (avg_ms * 1e-3) / 1e9,
+            "peak_source": f"{peaks_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth), "
+                           f"frac is of {peaks_src}"}
+
+
+def large_operator(topo, stream, flush, op: int = 0, reps: int = 20):
+    """The operator kernel alone on the 320x160x160 grid (inputs ~233 MB, above
+    L2): `reps` launches between CUDA events on the caller stream, L2 flushed
+    before; returns the average launch time in ms."""
+    import torch
+    w = I.WORKLOADS[LARGE_WORKLOAD]
+    with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) as m:
+        m.set_operator(op)
+        m.set_density(w.density())
+        m.apply_internal(1, 3)  # warm-up
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.apply_internal(1, reps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
 
 
 def _dist():
@@ -211,6 +261,8 @@ def main():
                     help="independent designs solved concurrently per step")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--precond", type=int, default=1)
+    ap.add_argument("--operator", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="operator kernel family (topo.OPERATOR_*)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -244,6 +296,8 @@ def main():
     dc_dev = [torch.empty(w.n_elem, dtype=torch.float64, device="cuda") for _ in range(B)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     meshes = [topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) for _ in range(B)]
+    for m in meshes:
+        m.set_operator(args.operator)
     opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
 
     def step_batch(rhos, dcs, opt):
@@ -347,12 +401,10 @@ def main():
         return
 
     peaks, peaks_src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     avg_ms = prof_ms / max(prof_n, 1)
-    flop_launch = 1152.0 * w.n_elem
-    achieved = flop_launch / (avg_ms * 1e-3) / 1e12
-    gdofs = 3.0 * w.n_nodes / (avg_ms * 1e-3) / 1e9
+    large = roofline(I.WORKLOADS[LARGE_WORKLOAD],
+                     large_operator(topo, stream, flush, args.operator), peaks, peaks_src,
+                     args.operator)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(w)
@@ -375,14 +427,13 @@ def main():
                   "outer_mean": float(np.mean([r[1] for r in recs])),
                   "rel_residual_max": float(max(r[2] for r in recs)),
                   "compliance_design0": recs[0][3]},
-        "matvec": {"kernel": "k_stencil_tma<EpiApply<float,true>> (FP32 27-node gather, CG apply)",
-                   "launches": prof_n, "avg_us": avg_ms * 1e3, "gdofs": gdofs},
         "fp64_jacobi_pcg": fp64,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_source": f"derived: {FP32_PEAK_NOTE} (FP32 SIMT is not in "
-                                    f"MEASURED_PEAKS.json); algorithmic 1152 flop/element; "
-                                    f"timed in the single-design loop"},
+        # the CG apply (operator fused with p.Ap) of the single-design loop,
+        # timed live with CUDA events on the mesh's stream around every launch
+        "roofline": dict(roofline(w, avg_ms, peaks, peaks_src, args.operator), launches=prof_n,
+                         timed="CG applies of the single-design loop (one design alone)"),
+        # the same kernel on the 320x160x160 grid, alone, inputs above L2
+        "roofline_large": dict(large, timed="20 back-to-back applies, CUDA events"),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem * B,
                 "d2h_bytes_per_step": (8 * w.n_elem + 8) * B},

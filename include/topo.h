@@ -68,14 +68,20 @@ typedef enum {
 enum {
   TOPO_BC_CANTILEVER = 0, /* every component of every node with i = 0 */
   TOPO_BC_MBB = 1,        /* u_x on i = 0; u_z on (i = nx, k = 0); u_y at (nx, ny/2, 0); ny even */
-  TOPO_BC_ROLLER_BOX = 2  /* u_x on i = 0, u_y on j = 0, u_z on k = 0 (test problem) */
+  TOPO_BC_ROLLER_BOX = 2, /* u_x on i = 0, u_y on j = 0, u_z on k = 0 (test problem) */
+  /* the paper's problems (Sec. 4.2, 4.3) on a 2:1:1 domain, sizes relative to
+   * the unit cross-section of ny x nz elements: */
+  TOPO_BC_CORNERS = 3,   /* i = 0 fixed on four corner squares j, k <= 0.3 n or >= 0.7 n */
+  TOPO_BC_MBB_STRIP = 4  /* u_x on i = 0; u_z on the bottom strip i >= nx-1; u_y pin; ny even */
 };
 
 /* Loads (consistent nodal forces; total magnitude params.load). */
 enum {
   TOPO_LOAD_EDGE_XL_BOTTOM = 0,  /* -z along the line i = nx, k = 0 */
   TOPO_LOAD_EDGE_X0_TOP = 1,     /* -z along the line i = 0, k = nz */
-  TOPO_LOAD_FACE_XL_TRACTION = 2 /* uniform +x traction (per unit area) on i = nx */
+  TOPO_LOAD_FACE_XL_TRACTION = 2, /* uniform +x traction (per unit area) on i = nx */
+  TOPO_LOAD_DISC_XL = 3,          /* -z on the x = L face quads within 0.1 ny of its centre */
+  TOPO_LOAD_HALFDISC_X0_TOP = 4   /* -z on the top face quads within 0.1 ny of (0, ny/2) */
 };
 
 /* Arithmetic of the inner (preconditioned CG) solve. */
@@ -86,8 +92,13 @@ enum {
 
 /* Operator kernels (both compute the same K x; results agree to rounding). */
 enum {
-  TOPO_OPERATOR_MODAL = 0, /* element-centric, k0 in the Walsh-Hadamard modal basis (default) */
-  TOPO_OPERATOR_GATHER = 1 /* node-centric 27-node gather with the dense 24x24 k0 */
+  TOPO_OPERATOR_MODAL = 0,  /* element-centric, k0 in the Walsh-Hadamard modal basis (default;
+                               the library picks the FP32 kernel form per grid) */
+  TOPO_OPERATOR_GATHER = 1, /* node-centric 27-node gather with the dense 24x24 k0 */
+  TOPO_OPERATOR_MODAL_SINGLE = 2, /* modal, one element column per thread */
+  TOPO_OPERATOR_MODAL_PAIR = 3    /* modal, two element columns per thread in packed two-wide
+                                     FP32 arithmetic, on FP32 grids with nx >= 65 (others fall
+                                     back to one column) */
 };
 
 enum {
@@ -201,6 +212,45 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
  * mesh's stream over the mesh's internal vectors (no copies, no sync), for
  * timing.  Cites Eq. (2) (K u). */
 topo_status topo_apply_internal(topo_mesh* m, int precision, int reps);
+
+/* ---------------------------------------------------------------------
+ * The rest of a SIMP iteration (Sec. 2.1.3 Eq. (4) filter, Optimality
+ * Criteria update named in Sec. 2.1.2 / Sec. 4.1).
+ * --------------------------------------------------------------------- */
+typedef struct {
+  double volfrac;       /* target mean density V_f (default 0.4, Sec. 4.1) */
+  double filter_radius; /* R in element edges (default 2: R = 2h, Sec. 4.1); <= 2.9 */
+  double move;          /* OC move limit per iteration (default 0.2; not in the paper) */
+  double eta;           /* OC damping exponent (default 0.5; not in the paper) */
+  double rho_min;       /* lower density bound (default 1e-3) */
+} topo_simp_opts;
+
+typedef struct {
+  double compliance; /* f^T u of the solved state the update used */
+  double volume;     /* mean of the new densities */
+  double change;     /* max_e |rho_new - rho| (the Delta rho_max of Sec. 4.1) */
+  double lambda;     /* the OC Lagrange multiplier found */
+} topo_simp_info;
+
+void topo_default_simp_opts(topo_simp_opts* o);
+
+/* One SIMP density update after a solve: sensitivities (Eq. (3)), filtered
+ * by Eq. (4) with H = max(0, R - |x_e - x_i|) and the denominator density
+ * guarded below by 1e-3, then the OC update rho_new = clip(rho (b/lambda)^eta,
+ * max(rho_min, rho - move), min(1, rho + move)), b = max(-filtered dc, 0),
+ * lambda bisected on the device so that mean(rho_new) = volfrac.  The new
+ * densities replace the mesh's (E by Eq. (1)); the displacement is kept as
+ * the warm start of the next solve.  Requires a solved state. */
+topo_status topo_simp_update(topo_mesh* m, const topo_simp_opts* opts, topo_simp_info* info);
+
+/* Filter an element field dc (n_elem doubles) by Eq. (4) with the mesh's
+ * current densities; result in dcf.  Invalidates the stored solution's
+ * sensitivities (call after compliance/sensitivity reads). */
+topo_status topo_filter(topo_mesh* m, double radius, const double* dc, double* dcf, size_t n_elem,
+                        int on_device);
+
+/* Copy the mesh's current densities out (n_elem floats). */
+topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_device);
 
 /* Select the operator kernel family for all later calls on this mesh
  * (TOPO_OPERATOR_*); synchronises the mesh's stream.  Cites Eq. (2). */

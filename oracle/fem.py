@@ -36,8 +36,14 @@ import scipy.sparse.linalg as spla
 LOCAL_NODES = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
                         [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], dtype=np.int64)
 
-BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX = 0, 1, 2
+BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX, BC_CORNERS, BC_MBB_STRIP = 0, 1, 2, 3, 4
 LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
+LOAD_DISC_XL, LOAD_HALFDISC_X0_TOP = 3, 4
+
+# The paper's test problems (Sec. 4.2, 4.3) on a 2 x 1 x 1 domain: supports and
+# load regions in units of the unit cross-section edge (ny elements).
+CORNER_FRACTION = 0.3   # corner support squares, 0.3 x 0.3 (Sec. 4.2)
+DISC_FRACTION = 0.1     # load disc / half-disc radius 0.1 (Sec. 4.2, 4.3)
 
 
 # --------------------------------------------------------------------------
@@ -194,6 +200,22 @@ def fixed_dofs(grid: Grid, bc: int) -> np.ndarray:
         m[i == 0, 0] = True
         m[j == 0, 1] = True
         m[k == 0, 2] = True
+    elif bc == BC_CORNERS:
+        # Sec. 4.2: x = 0 face fixed on four 0.3 x 0.3 corner squares (in units of
+        # the cross-section edge: ny and nz elements span 1.0)
+        cj = int(np.floor(CORNER_FRACTION * grid.ny + 1e-9))
+        ck = int(np.floor(CORNER_FRACTION * grid.nz + 1e-9))
+        in_j = (j <= cj) | (j >= grid.ny - cj)
+        in_k = (k <= ck) | (k >= grid.nz - ck)
+        m[(i == 0) & in_j & in_k, :] = True
+    elif bc == BC_MBB_STRIP:
+        # Sec. 4.3: u_x = 0 on x = 0; u_z = 0 on the bottom strip of one element at
+        # x = L; plus the same single u_y pin as BC_MBB (rigid y translation)
+        if grid.ny % 2:
+            raise ValueError("MBB needs an even ny for the y pin")
+        m[i == 0, 0] = True
+        m[(i >= grid.nx - 1) & (k == 0), 2] = True
+        m[(i == grid.nx) & (k == 0) & (j == grid.ny // 2), 1] = True
     else:
         raise ValueError(bc)
     return m.reshape(-1)
@@ -222,6 +244,31 @@ def load_vector(grid: Grid, load: int, magnitude: float = 1.0) -> np.ndarray:
                 fq = magnitude * h * h / 4.0
                 for dj, dk in ((0, 0), (1, 0), (1, 1), (0, 1)):
                     f[grid.node(nx, j + dj, k + dk), 0] += fq
+    elif load in (LOAD_DISC_XL, LOAD_HALFDISC_X0_TOP):
+        # total `magnitude` in -z as a uniform traction on the face quads whose
+        # centroids lie in the disc (Sec. 4.2: radius 0.1 about the centre of
+        # x = L) or half-disc (Sec. 4.3: radius 0.1 about (0, 0.5, 1) on the top
+        # face); each quad sends a quarter of its share to each corner
+        rad = DISC_FRACTION * ny
+        quads = []
+        if load == LOAD_DISC_XL:
+            for k in range(nz):
+                for j in range(ny):
+                    if (j + 0.5 - ny / 2.0) ** 2 + (k + 0.5 - nz / 2.0) ** 2 <= rad * rad:
+                        quads.append([grid.node(nx, j + a, k + b) for a, b in
+                                      ((0, 0), (1, 0), (1, 1), (0, 1))])
+        else:
+            for j in range(ny):
+                for i in range(nx):
+                    if (i + 0.5) ** 2 + (j + 0.5 - ny / 2.0) ** 2 <= rad * rad:
+                        quads.append([grid.node(i + a, j + b, nz) for a, b in
+                                      ((0, 0), (1, 0), (1, 1), (0, 1))])
+        if not quads:
+            raise ValueError("load region holds no face quad")
+        share = magnitude / len(quads) / 4.0
+        for q in quads:
+            for nd in q:
+                f[nd, 2] -= share
     else:
         raise ValueError(load)
     return f.reshape(-1)

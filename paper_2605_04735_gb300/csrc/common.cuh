@@ -19,7 +19,7 @@
 
 namespace topo {
 
-enum Bc { BC_CANTILEVER = 0, BC_MBB = 1, BC_ROLLER_BOX = 2 };
+enum Bc { BC_CANTILEVER = 0, BC_MBB = 1, BC_ROLLER_BOX = 2, BC_CORNERS = 3, BC_MBB_STRIP = 4 };
 
 // k0 as a kernel parameter: 24x24 row-major, unit Young's modulus.  Read
 // with compile-time indices only, so every access is a constant-bank
@@ -35,6 +35,8 @@ struct Dims {
   int ex;            // element row pitch, >= nx + 2, multiple of 4
   int bc;            // Bc
   int pin_j;         // MBB: j index of the single u_y pin (ny / 2)
+  int corner_j;      // BC_CORNERS: supported rows j <= corner_j or j >= ny - corner_j
+  int corner_k;      //             and layers k <= corner_k or k >= nz - corner_k
   long long comp;    // entries per vector component = px * (ny+3) * (nz+3)
   long long ecount;  // entries of an element array = ex * (ny+2) * (nz+2)
   __host__ __device__ long long node(int i, int j, int k) const {
@@ -47,6 +49,21 @@ struct Dims {
   __host__ __device__ long long plane_stride() const { return (long long)px * (ny + 3); }
   __host__ __device__ long long erow() const { return ex; }
   __host__ __device__ long long eplane() const { return (long long)ex * (ny + 2); }
+  // May a DOF of a node with i in [i0, i1], j >= j0, k >= k0 be fixed?
+  // (Conservative: false only when no such node is on a support.)
+  __host__ __device__ bool box_may_fix(int i0, int i1, int j0, int k0) const {
+    switch (bc) {
+      case BC_CANTILEVER:
+      case BC_CORNERS:
+        return i0 <= 0;
+      case BC_MBB:
+        return i0 <= 0 || (i1 >= nx && k0 <= 0);
+      case BC_MBB_STRIP:
+        return i0 <= 0 || (i1 >= nx - 1 && k0 <= 0);
+      default:
+        return i0 <= 0 || j0 <= 0 || k0 <= 0;
+    }
+  }
   // Is DOF c of node (i, j, k) held at zero?
   __host__ __device__ bool fixed(int c, int i, int j, int k) const {
     switch (bc) {
@@ -54,6 +71,12 @@ struct Dims {
         return i == 0;
       case BC_MBB:
         return (c == 0 && i == 0) || (c == 2 && i == nx && k == 0) ||
+               (c == 1 && i == nx && k == 0 && j == pin_j);
+      case BC_CORNERS:
+        return i == 0 && (j <= corner_j || j >= ny - corner_j) &&
+               (k <= corner_k || k >= nz - corner_k);
+      case BC_MBB_STRIP:
+        return (c == 0 && i == 0) || (c == 2 && i >= nx - 1 && k == 0) ||
                (c == 1 && i == nx && k == 0 && j == pin_j);
       default:
         return (c == 0 && i == 0) || (c == 1 && j == 0) || (c == 2 && k == 0);
@@ -71,6 +94,9 @@ inline Dims make_dims(int nx, int ny, int nz, int bc, int pin_j) {
   d.ex = ((nx + 2) + 3) / 4 * 4;
   d.bc = bc;
   d.pin_j = pin_j;
+  // paper Sec. 4.2: 0.3 x 0.3 corner squares of the unit cross-section
+  d.corner_j = (int)(0.3 * ny + 1e-9);
+  d.corner_k = (int)(0.3 * nz + 1e-9);
   d.comp = (long long)d.px * (ny + 3) * (nz + 3);
   d.ecount = (long long)d.ex * (ny + 2) * (nz + 2);
   return d;

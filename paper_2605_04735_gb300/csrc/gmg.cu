@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "gmg.h"
 #include "kernels.h"
+#include "modal2.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -75,9 +76,10 @@ struct EpiChebStep {
   const float* dinv;
   float c1, c2;
   int add_prev;
+  template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&ctr)[3],
-                                              const Dims& d) const {
+                                              const DD& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long oc = c * d.comp + o;
@@ -96,9 +98,10 @@ struct EpiChebStep {
 struct EpiChebLast {
   static constexpr bool kReduce = false;
   float* r;
+  template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&)[3],
-                                              const Dims& d) const {
+                                              const DD& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (!d.fixed(c, i, j, k)) r[c * d.comp + o] -= acc[c];
@@ -114,9 +117,10 @@ struct EpiChebResid {
   float* d0;
   const float* dinv;
   float inv_theta;
+  template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&)[3],
-                                              const Dims& d) const {
+                                              const DD& d) const {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long oc = c * d.comp + o;

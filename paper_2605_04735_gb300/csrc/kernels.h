@@ -73,4 +73,14 @@ cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double
                                const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
                                const Red& red, cudaStream_t s);
 
+// ---- SIMP update (simp.cu) -------------------------------------------------
+cudaError_t launch_filter(const double* dc, const float* rho_g, double* dcf, const Dims& d,
+                          double radius, double guard, cudaStream_t s);
+size_t oc_state_bytes();
+size_t oc_partials_count();
+cudaError_t launch_oc(const float* rho, const double* dcf, float* out, long long n, double volfrac,
+                      double move, double eta, double rho_min, int passes, void* state,
+                      double* partials, cudaStream_t s);
+void oc_results(const void* state_host, double* sum, double* change, double* lambda);
+
 }  // namespace topo

@@ -40,8 +40,23 @@ __global__ void k_simp(const float* __restrict__ rho, float* __restrict__ rho_g,
   if (nbad) atomicAdd(bad, nbad);
 }
 
+// Is face quad (a, b) in the load region?  Disc (paper Sec. 4.2): quads of
+// the x = L face, (a, b) = (j, k), centroid within 0.1 ny of the face centre.
+// Half-disc (Sec. 4.3): quads of the top face, (a, b) = (i, j), centroid
+// within 0.1 ny of (0, ny/2).
+__host__ __device__ inline bool in_load_region(int load, int a, int b, const Dims& d) {
+  const double rad = 0.1 * d.ny;
+  if (load == 3) {
+    const double y = a + 0.5 - d.ny / 2.0, z = b + 0.5 - d.nz / 2.0;
+    return a >= 0 && a < d.ny && b >= 0 && b < d.nz && y * y + z * z <= rad * rad;
+  }
+  const double x = a + 0.5, y = b + 0.5 - d.ny / 2.0;
+  return a >= 0 && a < d.nx && b >= 0 && b < d.ny && x * x + y * y <= rad * rad;
+}
+
 // Consistent nodal forces of the load cases (component-major ghosted layout).
-__global__ void k_build_load(double* __restrict__ f, const Dims d, int load, double mag, double h) {
+__global__ void k_build_load(double* __restrict__ f, const Dims d, int load, double mag, double h,
+                             int nquads) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (load == 0 || load == 1) {
     // total `mag` in -z along a line of ny segments: ends get half a share
@@ -51,7 +66,7 @@ __global__ void k_build_load(double* __restrict__ f, const Dims d, int load, dou
     const double share = mag / d.ny;
     const double v = (t == 0 || t == d.ny) ? 0.5 * share : share;
     f[2 * d.comp + d.node(i, t, k)] = -v;
-  } else {
+  } else if (load == 2) {
     // uniform +x traction `mag` per unit area on x = L: each face quad of
     // area h^2 sends a quarter of its force to each of its corners
     const int nyz = (d.ny + 1) * (d.nz + 1);
@@ -61,6 +76,19 @@ __global__ void k_build_load(double* __restrict__ f, const Dims d, int load, dou
     const int cj = (j == 0 || j == d.ny) ? 1 : 2;
     const int ck = (k == 0 || k == d.nz) ? 1 : 2;
     f[d.node(d.nx, j, k)] = mag * h * h * 0.25 * cj * ck;
+  } else {
+    // total `mag` in -z, uniform over the region's face quads; a face node
+    // collects a quarter share from each adjacent quad in the region
+    const int w = (load == 3) ? d.ny + 1 : d.nx + 1;
+    const int hgt = (load == 3) ? d.nz + 1 : d.ny + 1;
+    if (t >= w * hgt) return;
+    const int a = t % w, b = t / w;
+    int cnt = 0;
+    for (int da = -1; da <= 0; ++da)
+      for (int db = -1; db <= 0; ++db) cnt += in_load_region(load, a + da, b + db, d) ? 1 : 0;
+    if (!cnt) return;
+    const long long o = (load == 3) ? d.node(d.nx, a, b) : d.node(a, b, d.nz);
+    f[2 * d.comp + o] = -mag * 0.25 * cnt / nquads;
   }
 }
 
@@ -163,8 +191,17 @@ cudaError_t launch_simp(const float* rho, float* rho_g, float* E32, double* E64,
 
 cudaError_t launch_build_load(double* f, const Dims& d, int load, double magnitude, double h,
                               cudaStream_t s) {
-  const long long n = (load == 2) ? (long long)(d.ny + 1) * (d.nz + 1) : d.ny + 1;
-  k_build_load<<<(int)((n + 255) / 256), 256, 0, s>>>(f, d, load, magnitude, h);
+  long long n = d.ny + 1;
+  int nquads = 0;
+  if (load == 2) n = (long long)(d.ny + 1) * (d.nz + 1);
+  if (load == 3 || load == 4) {
+    const int A = (load == 3) ? d.ny : d.nx, B = (load == 3) ? d.nz : d.ny;
+    for (int b = 0; b < B; ++b)
+      for (int a = 0; a < A; ++a) nquads += in_load_region(load, a, b, d) ? 1 : 0;
+    if (!nquads) return cudaErrorInvalidValue;
+    n = (long long)(A + 1) * (B + 1);
+  }
+  k_build_load<<<(int)((n + 255) / 256), 256, 0, s>>>(f, d, load, magnitude, h, nquads);
   return cudaGetLastError();
 }
 

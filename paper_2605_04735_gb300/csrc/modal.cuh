@@ -40,6 +40,7 @@ template <typename T>
 struct ModalCoef {
   T D[3][8];     // diagonal of K~ per component and mode (mode 0 unused)
   T C[3][3][8];  // coupling of (p, m) with (q, m ^ (1<<p) ^ (1<<q)), bits p, q of m differ
+  int form;  // FP32 kernel form: 0 automatic, 1 one column per thread, 2 two columns (packed)
 };
 
 // in-place 8-point Walsh-Hadamard transform: v[m] <- sum_b (-1)^{b.m} v[b]
@@ -330,9 +331,9 @@ bool modal_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap
                 CUtensorMap* emap);
 
 template <typename T, class Epi>
-cudaError_t launch_modal(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
-                         const Epi& epi, const Red& red, const int* done, int* errflag,
-                         cudaStream_t s) {
+cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
+                                const Epi& epi, const Red& red, const int* done, int* errflag,
+                                cudaStream_t s) {
   const int z = modal_zchunk(d);
   dim3 block(kModalTX, kModalTY, 1);
   dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY,

@@ -1,0 +1,368 @@
+// Column-paired FP32 form of the modal (Walsh-Hadamard) element operator,
+// with packed two-wide FP32 arithmetic (add/sub/mul/fma .f32x2, sm_100+).
+//
+// The element arithmetic is the one in modal.cuh (k0 u = H K~ H^T u, 45
+// non-zeros of K~, x-y transform per node plane shared by the elements above
+// and below, modal-domain plane combine, corner-0 shift).  What changes is
+// the work split: thread (tx, ty) marches two element columns,
+// A = (x0 - 1 + tx, y0 - 1 + ty) and B = A + (32, 0), and keeps every
+// quantity as the pair (A, B) in one 64-bit register pair, so each
+// instruction of the element arithmetic does the work of two elements.
+// The two columns never share a node, so the pairs come straight out of
+// shared memory (two 32-bit loads into the halves of a pair).
+//
+// A CTA is 32 x 8 threads over element columns x0-1 .. x0+62 and rows
+// y0-1 .. y0+6 and owns the node columns x0 .. x0+62, y0 .. y0+6 (63 x 7):
+// the +x corners of column A of lane tx go to lane tx+1 (and those of lane
+// 31's A to lane 0's B) by one rotating warp shuffle, the +y corner through
+// a double-buffered shared-memory slot as in modal.cuh.  Node planes and
+// element layers stream through a 4-stage TMA ring (boxes of 68 x 9 x 3
+// nodes and 68 x 8 elements, x start rounded down to 16 bytes).
+//
+// Tiles without any fixed DOF run the epilogue without the per-DOF support
+// test (`FreeDims`).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "modal.cuh"
+#include "tma.cuh"
+
+namespace topo {
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
+
+// in-place 4-point (x-y) Walsh-Hadamard transform on pairs
+__device__ __forceinline__ void pfwht4(float2 (&v)[4]) {
+  const float2 a = padd(v[0], v[1]), b = psub(v[0], v[1]);
+  const float2 c = padd(v[2], v[3]), e = psub(v[2], v[3]);
+  v[0] = padd(a, c);
+  v[1] = padd(b, e);
+  v[2] = psub(a, c);
+  v[3] = psub(b, e);
+}
+
+// ModalCoef<float> with every coefficient duplicated into both halves
+struct ModalCoef2 {
+  float2 D[3][8];
+  float2 C[3][3][8];
+};
+
+inline ModalCoef2 pair_coef(const ModalCoef<float>& k) {
+  ModalCoef2 p{};
+  for (int a = 0; a < 3; ++a)
+    for (int m = 0; m < 8; ++m) {
+      p.D[a][m] = make_float2(k.D[a][m], k.D[a][m]);
+      for (int b = 0; b < 3; ++b) p.C[a][b][m] = make_float2(k.C[a][b][m], k.C[a][b][m]);
+    }
+  return p;
+}
+
+struct PairColumn {
+  float2 bxy[3][4];  // x-y transform of the bottom node plane, shifted by ref
+  float2 ref[3];     // raw displacement of the element's corner 0
+  float2 carry[3][4];  // previous element's top-face result; [c][0] holds its negative
+};
+
+__device__ __forceinline__ void pair_seed(PairColumn& col, const float2 (&raw)[2][2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    col.ref[c] = raw[0][0][c];
+    float2 v[4] = {make_float2(0.f, 0.f), psub(raw[0][1][c], col.ref[c]),
+                   psub(raw[1][0][c], col.ref[c]), psub(raw[1][1][c], col.ref[c])};
+    pfwht4(v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      col.bxy[c][q] = v[q];
+      col.carry[c][q] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// One element layer for the pair; see modal_layer in modal.cuh for the
+// meaning of every step.  plane[c][q]: x-y corner q of node plane ez.
+__device__ __forceinline__ void pair_layer(PairColumn& col, const float2 (&top)[2][2][3],
+                                           float2 E, float2 nE, const ModalCoef2& kc,
+                                           float2 (&plane)[3][4], float2 (&ctr)[3]) {
+  float2 uh[3][8];  // [c][0] (the rigid mode) is never formed
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 r = col.ref[c];
+    ctr[c] = r;
+    float2 v[4] = {psub(top[0][0][c], r), psub(top[0][1][c], r), psub(top[1][0][c], r),
+                   psub(top[1][1][c], r)};
+    pfwht4(v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 s = pmul(col.bxy[c][q], E);
+      if (q > 0) uh[c][q] = pfma(v[q], E, s);  // z mode 0: (bottom + top) E
+      uh[c][q + 4] = pfma(v[q], nE, s);        // z mode 1: (bottom - top) E
+    }
+    // the top plane becomes the next bottom plane, re-referenced to its corner 0
+    const float2 nref = top[0][0][c];
+    col.bxy[c][0] = pfma(psub(r, nref), make_float2(4.f, 4.f), v[0]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) col.bxy[c][q] = v[q];
+    col.ref[c] = nref;
+  }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    float2 yh[8];
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+      float2 acc = pmul(kc.D[p][m], uh[p][m]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q == p) continue;
+        if (((m >> p) & 1) == ((m >> q) & 1)) continue;
+        acc = pfma(kc.C[p][q][m], uh[q][m ^ (1 << p) ^ (1 << q)], acc);
+      }
+      yh[m] = acc;
+    }
+    float2 w[4];
+    w[0] = psub(yh[4], col.carry[p][0]);  // bottom face (mode 0 of yh is 0) + previous top
+    col.carry[p][0] = yh[4];              // stored negated
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      w[q] = padd(padd(yh[q], yh[q + 4]), col.carry[p][q]);
+      col.carry[p][q] = psub(yh[q], yh[q + 4]);
+    }
+    pfwht4(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) plane[p][q] = w[q];
+  }
+}
+
+// A view of Dims for a region that holds no fixed DOF: the epilogues skip
+// their support test.
+struct FreeDims {
+  long long comp;
+  __device__ __forceinline__ bool fixed(int, int, int, int) const { return false; }
+};
+
+constexpr int kPairTX = 32, kPairTY = 8;
+constexpr int kPairOwnX = 2 * kPairTX - 1, kPairOwnY = kPairTY - 1;
+constexpr int kPairStages = 4;
+constexpr int kPBoxX = 68;             // >= 3 (alignment slack) + 65 node columns
+constexpr int kPBoxNY = kPairTY + 1;   // node rows y0-1 .. y0+7
+constexpr int kPBoxEY = kPairTY;       // element rows y0-1 .. y0+6
+constexpr int kPNode = 3 * kPBoxNY * kPBoxX;
+constexpr int kPElem = kPBoxEY * kPBoxX;
+constexpr int kPNodeStride = (kPNode + 31) / 32 * 32;          // floats, 128-byte multiple
+constexpr int kPStageFloats = (kPNodeStride + kPElem + 31) / 32 * 32;
+constexpr uint32_t kPStageTx = (uint32_t)(kPNode + kPElem) * 4u;
+constexpr size_t kPairXchBytes = sizeof(float2) * 2 * kPairTY * kPairTX * 3;
+constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPairXchBytes +
+                             sizeof(uint64_t) * kPairStages + 128;  // + alignment slack
+
+template <class Epi>
+__global__ void __launch_bounds__(kPairTX* kPairTY, 2)
+    k_modal_pair(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
+                 const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi, const Red red,
+                 const int zchunk, const int* __restrict__ done, int* __restrict__ errflag) {
+  if (done != nullptr && *done) return;  // uniform over the grid
+  extern __shared__ __align__(128) unsigned char pair_dyn[];
+  // TMA destinations on 128-byte boundaries whatever the dynamic window's offset
+  unsigned char* pair_smem = pair_dyn + ((128u - (smem_u32(pair_dyn) & 127u)) & 127u);
+  float* stg = reinterpret_cast<float*>(pair_smem);
+  auto xch = reinterpret_cast<float2(*)[kPairTY][kPairTX][3]>(
+      pair_smem + sizeof(float) * kPStageFloats * kPairStages);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(pair_smem + sizeof(float) * kPStageFloats * kPairStages +
+                                              kPairXchBytes);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * kPairTX + tx;
+  const int x0 = blockIdx.x * kPairOwnX, y0 = blockIdx.y * kPairOwnY;
+  const int exA = x0 - 1 + tx, ey = y0 - 1 + ty;
+  const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
+  const int ox = x0 - bx;
+  const int kb = blockIdx.z * zchunk;
+  const int ke = min(kb + zchunk, d.nz + 1);
+  const int nst = (ke - kb) + 2;  // stage t: node plane kb-1+t, element layer kb-2+t
+  if (tid == 0) {
+    for (int q = 0; q < kPairStages; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+    tma_prefetch_desc(&xmap);
+    tma_prefetch_desc(&emap);
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int slot = t % kPairStages;
+    float* s = stg + slot * kPStageFloats;
+    mbar_arrive_expect_tx(&bar[slot], kPStageTx);
+    tma_load_4d(s, &xmap, &bar[slot], bx, y0, kb + t, 0);
+    tma_load_3d(s + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t);
+  };
+  if (tid == 0)
+    for (int t = 0; t < kPairStages && t < nst; ++t) issue(t);
+  const bool ownA = tx > 0 && ty > 0 && exA <= d.nx && ey <= d.ny;
+  const bool ownB = ty > 0 && exA + 32 <= d.nx && ey <= d.ny;
+  const bool clean = !d.box_may_fix(x0, x0 + kPairOwnX - 1, y0, kb);
+  const FreeDims fd{d.comp};
+  const int lx = ox + tx;  // this thread's column A inside a box row
+  const int src = (tx + kPairTX - 1) & (kPairTX - 1);
+  long long oA = d.node(exA, ey, kb);
+
+  PairColumn col;
+  {
+    mbar_wait_bounded(&bar[0], 0u, errflag);
+    const float* nd = stg;
+    float2 raw[2][2][3];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* p = nd + c * (kPBoxNY * kPBoxX) + (ty + dy) * kPBoxX + lx + dx;
+          raw[dy][dx][c] = make_float2(p[0], p[32]);
+        }
+    pair_seed(col, raw);
+    __syncthreads();
+    if (tid == 0 && kPairStages < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(kPairStages);
+    }
+  }
+  float part = 0.f;  // this thread's nodes only (at most 2 zchunk); widened to FP64 below
+#pragma unroll 2
+  for (int t = 1; t < nst; ++t) {
+    const int slot = t % kPairStages;
+    mbar_wait_bounded(&bar[slot], (uint32_t)((t / kPairStages) & 1), errflag);
+    const float* nd = stg + slot * kPStageFloats;
+    float2 top[2][2][3];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* p = nd + c * (kPBoxNY * kPBoxX) + (ty + dy) * kPBoxX + lx + dx;
+          top[dy][dx][c] = make_float2(p[0], p[32]);
+        }
+    const float* el = nd + kPNodeStride + ty * kPBoxX + lx;
+    const float2 E = make_float2(el[0], el[32]);
+    const float2 nE = make_float2(-E.x, -E.y);
+    float2 plane[3][4], ctr[3];
+    pair_layer(col, top, E, nE, kc, plane, ctr);
+    // +x corners from the column on the left: lane tx-1's A (B), lane 31's A for lane 0's B
+    float2 n0[3];
+    float2(*xb)[kPairTX][3] = xch[t & 1];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float r1a = __shfl_sync(0xffffffffu, plane[c][1].x, src);
+      const float r1b = __shfl_sync(0xffffffffu, plane[c][1].y, src);
+      const float r3a = __shfl_sync(0xffffffffu, plane[c][3].x, src);
+      const float r3b = __shfl_sync(0xffffffffu, plane[c][3].y, src);
+      n0[c] = padd(plane[c][0], make_float2(r1a, tx > 0 ? r1b : r1a));
+      xb[ty][tx][c] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
+    }
+    __syncthreads();  // also retires this stage's slot
+    if (tid == 0 && t + kPairStages < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + kPairStages);
+    }
+    const int ez = kb - 2 + t;
+    if (ty > 0 && t >= 2) {
+      float resA[3], resB[3], cA[3], cB[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 r = padd(n0[c], xb[ty - 1][tx][c]);
+        resA[c] = r.x;
+        resB[c] = r.y;
+        cA[c] = ctr[c].x;
+        cB[c] = ctr[c].y;
+      }
+      if (clean) {
+        if (ownA) part += epi(exA, ey, ez, oA, resA, cA, fd);
+        if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, fd);
+      } else {
+        if (ownA) part += epi(exA, ey, ez, oA, resA, cA, d);
+        if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, d);
+      }
+      oA += d.plane_stride();
+    }
+  }
+  if (Epi::kReduce) {
+    double v[1] = {(double)part};
+    reduce_finalize<1>(v, red);
+  }
+}
+
+bool pair_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+               CUtensorMap* emap);
+
+// z planes per CTA of the paired kernel: the chunk length that minimises
+// (waves of two CTAs per SM) x (planes per CTA + the two warm-up layers),
+// with no more CTAs than partial-sum slots
+inline int pair_zchunk(const Dims& d) {
+  const long long xy = (long long)((d.nx + kPairOwnX) / kPairOwnX) *
+                       ((d.ny + kPairOwnY) / kPairOwnY);
+  const int planes = d.nz + 1;
+  const long long slots = 152LL * 2;
+  int best = planes;
+  long long best_cost = -1;
+  for (int z = 4; z <= planes; ++z) {
+    const long long chunks = (planes + z - 1) / z;
+    if (xy * chunks > kMaxPartials) continue;
+    const long long cost = ((xy * chunks + slots - 1) / slots) * (z + 2);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = z;
+    }
+  }
+  return best;
+}
+
+template <class Epi>
+cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, const Dims& d,
+                              const ModalCoef<float>& kc, const Epi& epi, const Red& red,
+                              const int* done, int* errflag, cudaStream_t s) {
+  static bool attr = false;  // per instantiation; setting it twice is harmless
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_modal_pair<Epi>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kPairSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int z = pair_zchunk(d);
+  dim3 block(kPairTX, kPairTY, 1);
+  dim3 grid((d.nx + kPairOwnX) / kPairOwnX, (d.ny + kPairOwnY) / kPairOwnY, (d.nz + z) / z);
+  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, z, done,
+                                                   errflag);
+  return cudaGetLastError();
+}
+
+// Smallest nx for which the automatic form picks the paired kernel (it is
+// not faster than the one-column kernel on the grids measured so far).
+constexpr int kPairAutoMinNx = 1 << 30;
+
+// The operator launch of both modal forms: the paired kernel where it is
+// selected and the grid is wide enough for its boxes (px, ex >= 68), the
+// one-column kernels otherwise.
+template <typename T, class Epi>
+cudaError_t launch_modal(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
+                         const Epi& epi, const Red& red, const int* done, int* errflag,
+                         cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    CUtensorMap xm, em;
+    const bool want = kc.form == 2 || (kc.form == 0 && d.nx >= kPairAutoMinNx);
+    if (want && pair_maps(x, E, d, &xm, &em))
+      return launch_modal_pair<Epi>(xm, em, d, kc, epi, red, done, errflag, s);
+  }
+  return launch_modal_single<T, Epi>(x, E, d, kc, epi, red, done, errflag, s);
+}
+
+}  // namespace topo

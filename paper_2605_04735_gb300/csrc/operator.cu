@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "modal.cuh"
+#include "modal2.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -20,8 +21,9 @@ template <typename T, bool DOT>
 struct EpiApply {
   static constexpr bool kReduce = DOT;
   T* y;
+  template <class DD>
   __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                          const T (&ctr)[3], const Dims& d) const {
+                                          const T (&ctr)[3], const DD& d) const {
     T part = T(0);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -39,8 +41,9 @@ struct EpiResid {
   static constexpr bool kReduce = true;
   T* y;
   const T* f;
+  template <class DD>
   __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                          const T (&)[3], const Dims& d) const {
+                                          const T (&)[3], const DD& d) const {
     T part = T(0);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {

@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "modal.cuh"
+#include "modal2.cuh"
 #include "stencil.cuh"
 #include "tma.cuh"
 
@@ -107,6 +108,11 @@ bool stencil_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xm
 bool modal_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
                 CUtensorMap* emap) {
   return cached_map(x, 0, d, kMBoxX, kMBoxNY, xmap) && cached_map(E, 1, d, kMBoxX, kMBoxEY, emap);
+}
+
+bool pair_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+               CUtensorMap* emap) {
+  return cached_map(x, 0, d, kPBoxX, kPBoxNY, xmap) && cached_map(E, 1, d, kPBoxX, kPBoxEY, emap);
 }
 
 }  // namespace topo

@@ -128,7 +128,12 @@ struct topo_mesh {
   int* flags = nullptr;
   double* aos = nullptr;       // n_dof doubles (ABI transfers)
   double* dc = nullptr;        // n_elem doubles
-  float* rho_in = nullptr;     // n_elem floats (host-density staging)
+  float* rho_in = nullptr;     // n_elem floats: the current densities, dense element order
+  double* dcf = nullptr;       // n_elem doubles: filtered sensitivities
+  float* rho_next = nullptr;   // n_elem floats: densities after an OC update
+  void* oc_state = nullptr;    // device OC bracketing state
+  double* oc_part = nullptr;   // OC block partials
+  unsigned char* oc_host = nullptr;  // pinned copy of the OC state
 
   bool has_density = false, solved = false, diag32 = false, diag64 = false;
   double fnorm2 = 0.0;
@@ -820,13 +825,14 @@ void topo_free(topo_mesh* m) {
   void* ptrs[] = {m->rho_g, m->E32,  m->E64,  m->f64, m->u64,  m->r64, m->x32, m->r32,
                   m->z32,   m->p32,  m->q32,  m->b32, m->dinv32, m->x64, m->s64, m->z64,
                   m->p64,   m->q64,  m->dinv64, m->sc, m->partials, m->flags, m->aos, m->dc,
-                  m->rho_in};
+                  m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   clear_graphs(m);
   if (m->gmg_built) gmg_free(m->gmg);
   if (m->h_sc) cudaFreeHost(m->h_sc);
   if (m->h_flag) cudaFreeHost(m->h_flag);
+  if (m->oc_host) cudaFreeHost(m->oc_host);
   if (m->ev_poll) cudaEventDestroy(m->ev_poll);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   if (m->ev_in) cudaEventDestroy(m->ev_in);
@@ -902,8 +908,8 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
   if (!out) return TOPO_ERR_INVALID;
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
-  if (bc < 0 || bc > 2 || load < 0 || load > 2) return TOPO_ERR_INVALID;
-  if (bc == TOPO_BC_MBB && (ny % 2)) return TOPO_ERR_INVALID;
+  if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
               !(prm->E0 > 0.0) || !(prm->Emin >= 0.0) || !(prm->Emin < prm->E0)))
     return TOPO_ERR_INVALID;
@@ -918,22 +924,14 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
   return TOPO_OK;
 }
 
-topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int on_device) {
-  if (!m || !rho) return TOPO_ERR_INVALID;
-  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
-  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
-  Fence fence(m);
-  if (fence.st != TOPO_OK) return fence.st;
+static topo_status set_density_impl(topo_mesh* m, const float* src_dev) {
   cudaStream_t s = m->stream;
-  const float* src = rho;
-  if (!on_device) {
-    if (!m->rho_in) CKS(dalloc(m, &m->rho_in, ne));
-    CK(cudaMemcpyAsync(m->rho_in, rho, ne * sizeof(float), cudaMemcpyHostToDevice, s));
-    src = m->rho_in;
-  }
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if (src_dev != m->rho_in)
+    CK(cudaMemcpyAsync(m->rho_in, src_dev, ne * sizeof(float), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
-  LK(m, launch_simp(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin, m->prm.penal,
-                 m->prm.h, m->flags, s));
+  LK(m, launch_simp(m->rho_in, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin,
+                    m->prm.penal, m->prm.h, m->flags, s));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -942,6 +940,20 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
   m->solved = false;
   m->has_density = (bad == 0);
   return bad ? TOPO_ERR_NAN : TOPO_OK;
+}
+
+topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int on_device) {
+  if (!m || !rho) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  if (!m->rho_in) CKS(dalloc(m, &m->rho_in, ne));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(m->rho_in, rho, ne * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    return set_density_impl(m, m->rho_in);
+  }
+  return set_density_impl(m, rho);
 }
 
 topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_info* info) {
@@ -1156,6 +1168,11 @@ topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_
     fixed = 3 * face;
   else if (d.bc == BC_MBB)
     fixed = face + (d.ny + 1) + 1;
+  else if (d.bc == BC_MBB_STRIP)
+    fixed = face + 2 * (d.ny + 1) + 1;
+  else if (d.bc == BC_CORNERS)  // supported rows x supported layers on x = 0, all components
+    fixed = 3LL * std::min(2 * (d.corner_j + 1), d.ny + 1) *
+            (long long)std::min(2 * (d.corner_k + 1), d.nz + 1);
   else
     fixed = face + (long long)(d.nx + 1) * (d.nz + 1) + (long long)(d.nx + 1) * (d.ny + 1);
   if (n_nodes) *n_nodes = nn;
@@ -1178,14 +1195,117 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
   return b;
 }
 
+void topo_default_simp_opts(topo_simp_opts* o) {
+  if (!o) return;
+  o->volfrac = 0.4;
+  o->filter_radius = 2.0;
+  o->move = 0.2;
+  o->eta = 0.5;
+  o->rho_min = 1e-3;
+}
+
+static topo_status ensure_simp_buffers(topo_mesh* m) {
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if (!m->dc) CKS(dalloc(m, &m->dc, ne));
+  if (!m->dcf) CKS(dalloc(m, &m->dcf, ne));
+  if (!m->rho_next) CKS(dalloc(m, &m->rho_next, ne));
+  if (!m->oc_state) {
+    unsigned char* p = nullptr;
+    CKS(dalloc(m, &p, (long long)oc_state_bytes()));
+    m->oc_state = p;
+  }
+  if (!m->oc_part) CKS(dalloc(m, &m->oc_part, (long long)oc_partials_count()));
+  if (!m->oc_host) CK(cudaMallocHost(&m->oc_host, oc_state_bytes()));
+  return TOPO_OK;
+}
+
+topo_status topo_filter(topo_mesh* m, double radius, const double* dc, double* dcf, size_t n_elem,
+                        int on_device) {
+  if (!m || !dc || !dcf || !(radius > 0.0) || radius > 2.9) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CKS(ensure_simp_buffers(m));
+  cudaStream_t s = m->stream;
+  const cudaMemcpyKind in = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(m->dc, dc, ne * sizeof(double), in, s));
+  LK(m, launch_filter(m->dc, m->rho_g, m->dcf, m->d, radius, 1e-3, s));
+  CK(cudaMemcpyAsync(dcf, m->dcf, ne * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!on_device) CK(cudaStreamSynchronize(s));
+  m->solved = false;  // the stored sensitivities were overwritten
+  return TOPO_OK;
+}
+
+topo_status topo_simp_update(topo_mesh* m, const topo_simp_opts* opts, topo_simp_info* info) {
+  if (!m) return TOPO_ERR_INVALID;
+  topo_simp_opts o;
+  if (opts)
+    o = *opts;
+  else
+    topo_default_simp_opts(&o);
+  if (!(o.volfrac > 0.0 && o.volfrac <= 1.0) || !(o.filter_radius > 0.0) ||
+      o.filter_radius > 2.9 || !(o.move > 0.0) || !(o.eta > 0.0) || !(o.rho_min >= 0.0) ||
+      o.rho_min >= o.volfrac)
+    return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CKS(ensure_simp_buffers(m));
+  cudaStream_t s = m->stream;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  // J = f^T u of the solved state, then Eq. (3) -> Eq. (4) -> OC
+  LK(m, launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), s));
+  CKS(sync_scalars(m));
+  const double J = m->h_sc->aux[0];
+  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->mcd, m->prm.penal,
+                           (m->prm.E0 - m->prm.Emin) * m->prm.h, red_of(m, FIN_AUX), s));
+  LK(m, launch_filter(m->dc, m->rho_g, m->dcf, m->d, o.filter_radius, 1e-3, s));
+  const int passes = 8;
+  CK(launch_oc(m->rho_in, m->dcf, m->rho_next, ne, o.volfrac, o.move, o.eta, o.rho_min, passes,
+               m->oc_state, m->oc_part, s));
+  m->launches += 2 + passes;
+  CK(cudaMemcpyAsync(m->oc_host, m->oc_state, oc_state_bytes(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double sum = 0.0, change = 0.0, lam = 0.0;
+  oc_results(m->oc_host, &sum, &change, &lam);
+  // the new densities become the mesh's (E by Eq. (1)); u stays for a warm start
+  CKS(set_density_impl(m, m->rho_next));
+  if (info) {
+    info->compliance = J;
+    info->volume = sum / (double)ne;
+    info->change = change;
+    info->lambda = lam;
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_device) {
+  if (!m || !rho) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CK(cudaMemcpyAsync(rho, m->rho_in, ne * sizeof(float),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
 topo_status topo_set_operator(topo_mesh* m, int kind) {
-  if (!m || (kind != TOPO_OPERATOR_MODAL && kind != TOPO_OPERATOR_GATHER)) return TOPO_ERR_INVALID;
-  const bool modal = (kind == TOPO_OPERATOR_MODAL);
-  if (modal != m->use_modal) {
+  if (!m || kind < TOPO_OPERATOR_MODAL || kind > TOPO_OPERATOR_MODAL_PAIR)
+    return TOPO_ERR_INVALID;
+  const bool modal = (kind != TOPO_OPERATOR_GATHER);
+  const int form = kind == TOPO_OPERATOR_MODAL_SINGLE ? 1 : kind == TOPO_OPERATOR_MODAL_PAIR ? 2 : 0;
+  if (modal != m->use_modal || form != m->mcf.form) {
     CK(cudaSetDevice(m->dev));
     CK(cudaStreamSynchronize(m->stream));
-    clear_graphs(m);
+    clear_graphs(m);  // the captured chunks hold the old kernels
     m->use_modal = modal;
+    m->mcf.form = form;
   }
   return TOPO_OK;
 }
@@ -1239,8 +1359,8 @@ topo_status topo_server_create(long long mem_budget_bytes, int max_active, const
 topo_status topo_server_open(topo_server* s, int nx, int ny, int nz, int bc, int load,
                              int* design) {
   if (!s || !design) return TOPO_ERR_INVALID;
-  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 2 || load < 0 || load > 2) return TOPO_ERR_INVALID;
-  if (bc == TOPO_BC_MBB && (ny % 2)) return TOPO_ERR_INVALID;
+  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   const long long fp = topo_footprint_bytes(nx, ny, nz, &s->opts);
   if (fp > s->budget) return TOPO_ERR_OOM;  // could never be admitted
   ServerDesign d;

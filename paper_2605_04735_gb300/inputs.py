@@ -28,6 +28,10 @@ BC_ROLLER_BOX = 2          # normal rollers on the x = 0, y = 0, z = 0 planes
 LOAD_EDGE_XL_BOTTOM = 0    # unit -z load along the edge x = L, z = 0
 LOAD_EDGE_X0_TOP = 1       # unit -z load along the edge x = 0, z = H
 LOAD_FACE_XL_TRACTION = 2  # uniform unit +x traction on the face x = L
+BC_CORNERS = 3             # paper Sec. 4.2: four 0.3 x 0.3 corner supports on x = 0
+BC_MBB_STRIP = 4           # paper Sec. 4.3: symmetry x = 0, one-element strip support at x = L
+LOAD_DISC_XL = 3           # paper Sec. 4.2: -z on a disc of radius 0.1 at the centre of x = L
+LOAD_HALFDISC_X0_TOP = 4   # paper Sec. 4.3: -z on a half-disc of radius 0.1 at (0, 0.5, 1)
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -142,6 +146,13 @@ class Workload:
             return density_voids(self.nx, self.ny, self.nz, self.n_voids, self.seed)
         raise ValueError(self.recipe)
 
+
+# The paper's own test problems (Sec. 4.1: 40 x 20 x 20 on 2 x 1 x 1, SIMP from a
+# uniform 0.4, V_f = 0.4), run by the SIMP loop rather than the solve benchmark.
+PAPER_PROBLEMS = {
+    "paper_cantilever_40x20x20": (40, 20, 20, BC_CORNERS, LOAD_DISC_XL),
+    "paper_mbb_40x20x20": (40, 20, 20, BC_MBB_STRIP, LOAD_HALFDISC_X0_TOP),
+}
 
 # The five workloads (sizes, BCs, loads and density recipes).
 WORKLOADS = {

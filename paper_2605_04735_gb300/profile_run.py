@@ -1,0 +1,62 @@
+"""Small, self-contained drivers for profiler captures of the hot path.
+
+    python -m paper_2605_04735_gb300.profile_run apply <workload> [reps]
+        one mesh, density set, `reps` internal applications of the FP32
+        operator (the CG apply with its fused p.Ap reduction) on a
+        non-default stream: the capture target of the operator kernel.
+    python -m paper_2605_04735_gb300.profile_run solve <workload> [reps]
+        `reps` full steps (density, FP32 GMG-PCG + FP64 refinement to 1e-8,
+        compliance, sensitivities) on one mesh: the launch list of a step.
+    python -m paper_2605_04735_gb300.profile_run simp <workload> [iters]
+        `iters` SIMP iterations (solve, sensitivity, filter, OC update).
+
+Workloads are the seeded recipes of `inputs.WORKLOADS`; nothing is read
+from disk.  Each command prints one line starting with "ok".
+"""
+from __future__ import annotations
+
+import sys
+
+
+def main(argv):
+    import numpy as np
+    import torch
+
+    from . import inputs as I
+    from . import topo
+
+    mode = argv[0] if argv else "apply"
+    name = argv[1] if len(argv) > 1 else "cantilever_voids_320x160x160"
+    reps = int(argv[2]) if len(argv) > 2 else (1 if mode == "apply" else 3)
+    w = I.WORKLOADS[name]
+    torch.cuda.set_device(0)
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=s) as m:
+        rho = w.density()
+        if mode == "apply":
+            m.set_density(rho)
+            m.apply_internal(1, 3 * reps)
+            torch.cuda.synchronize()
+            print("ok", mode, name, reps)
+        elif mode == "solve":
+            info = None
+            for _ in range(reps):
+                m.set_density(rho)
+                info = m.solve()
+                m.compliance()
+                m.sensitivity()
+            torch.cuda.synchronize()
+            print("ok", mode, name, info.iters, info.outer, info.rel_residual)
+        elif mode == "simp":
+            r0 = np.full(w.n_elem, 0.4, np.float32)
+            hist = topo.simp_optimize(m, r0, topo.default_simp_opts(volfrac=0.4),
+                                      max_iter=reps, tol=0.0)
+            torch.cuda.synchronize()
+            print("ok", mode, name, len(hist), hist[-1][0])
+        else:
+            raise SystemExit(f"unknown mode {mode!r}")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -18,11 +18,12 @@ LIB_PATH = os.path.join(HERE, "libtopo.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NO_DENSITY, ERR_NOT_SOLVED, ERR_NOT_CONVERGED, \
     ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
-BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX = 0, 1, 2
+BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX, BC_CORNERS, BC_MBB_STRIP = 0, 1, 2, 3, 4
 LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
+LOAD_DISC_XL, LOAD_HALFDISC_X0_TOP = 3, 4
 PREC_FP64, PREC_FP32 = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
-OPERATOR_MODAL, OPERATOR_GATHER = 0, 1
+OPERATOR_MODAL, OPERATOR_GATHER, OPERATOR_MODAL_SINGLE, OPERATOR_MODAL_PAIR = 0, 1, 2, 3
 
 
 class Params(C.Structure):
@@ -40,6 +41,16 @@ class SolveOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int), ("detail", C.c_int),
                 ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+
+class SimpOpts(C.Structure):
+    _fields_ = [("volfrac", C.c_double), ("filter_radius", C.c_double), ("move", C.c_double),
+                ("eta", C.c_double), ("rho_min", C.c_double)]
+
+
+class SimpInfo(C.Structure):
+    _fields_ = [("compliance", C.c_double), ("volume", C.c_double), ("change", C.c_double),
+                ("lambda_", C.c_double)]
 
 
 class JobResult(C.Structure):
@@ -100,6 +111,10 @@ def lib():
             "topo_server_stats": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                       C.POINTER(i), C.POINTER(i)]),
             "topo_server_free": (None, [vp]),
+            "topo_default_simp_opts": (None, [C.POINTER(SimpOpts)]),
+            "topo_simp_update": (i, [vp, C.POINTER(SimpOpts), C.POINTER(SimpInfo)]),
+            "topo_filter": (i, [vp, d, vp, vp, sz, i]),
+            "topo_get_density": (i, [vp, vp, sz, i]),
             "topo_free": (None, [vp]),
             "topo_status_string": (C.c_char_p, [i]),
         }
@@ -131,6 +146,14 @@ def default_params(**kw) -> Params:
 def default_opts(**kw) -> SolveOpts:
     o = SolveOpts()
     lib().topo_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def default_simp_opts(**kw) -> SimpOpts:
+    o = SimpOpts()
+    lib().topo_default_simp_opts(C.byref(o))
     for k, v in kw.items():
         setattr(o, k, v)
     return o
@@ -267,8 +290,30 @@ class Mesh:
     def apply_internal(self, precision=PREC_FP32, reps=1):
         _check(lib().topo_apply_internal(self._h, precision, reps), "topo_apply_internal")
 
+    def simp_update(self, opts: SimpOpts | None = None) -> SimpInfo:
+        info = SimpInfo()
+        _check(lib().topo_simp_update(self._h, C.byref(opts) if opts else None, C.byref(info)),
+               "topo_simp_update")
+        return info
+
+    def filter(self, dc, radius=2.0, out=None):
+        if out is None:
+            out = np.empty(self.n_elem, np.float64)
+        p, n, dev = _ptr(dc, np.float64)
+        q, n2, dev2 = _ptr(out, np.float64)
+        _check(lib().topo_filter(self._h, radius, p, q, n, dev), "topo_filter")
+        return out
+
+    def density(self, out=None):
+        if out is None:
+            out = np.empty(self.n_elem, np.float32)
+        p, n, dev = _ptr(out, np.float32)
+        _check(lib().topo_get_density(self._h, p, n, dev), "topo_get_density")
+        return out
+
     def set_operator(self, kind):
-        """OPERATOR_MODAL (default) or OPERATOR_GATHER for all later calls."""
+        """OPERATOR_MODAL (default, automatic FP32 kernel form), OPERATOR_GATHER,
+        OPERATOR_MODAL_SINGLE or OPERATOR_MODAL_PAIR for all later calls."""
         _check(lib().topo_set_operator(self._h, kind), "topo_set_operator")
 
     def set_stream(self, stream):
@@ -371,3 +416,24 @@ class Server:
                "topo_server_stats")
         return {"bytes_in_use": a.value, "peak_bytes": b.value, "active": c.value,
                 "waiting": d.value}
+
+
+def simp_optimize(mesh: "Mesh", rho0, simp_opts: SimpOpts | None = None,
+                  solve_opts: SolveOpts | None = None, max_iter: int = 100, tol: float = 0.01,
+                  callback=None):
+    """SIMP loop on the device: solve (warm-started), then filter + OC update,
+    until max |Delta rho| <= tol (Sec. 4.1's stopping rule) or max_iter.
+    Returns the per-iteration (compliance, volume, change) history."""
+    mesh.set_density(rho0)
+    hist = []
+    for it in range(max_iter):
+        so = solve_opts or default_opts()
+        so.warm_start = 1 if it else 0
+        mesh.solve(so)
+        info = mesh.simp_update(simp_opts)
+        hist.append((info.compliance, info.volume, info.change))
+        if callback:
+            callback(it, info)
+        if info.change <= tol:
+            break
+    return hist

@@ -42,12 +42,28 @@ CASES = [
     (5, 17, 3, I.BC_ROLLER_BOX, I.LOAD_FACE_XL_TRACTION),
     (1, 1, 1, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM),
     (2, 2, 1, I.BC_MBB, I.LOAD_EDGE_X0_TOP),
+    # the paper's problems (Sec. 4.2 corner-supported cantilever, Sec. 4.3 MBB)
+    (40, 20, 20, I.BC_CORNERS, I.LOAD_DISC_XL),
+    (40, 20, 20, I.BC_MBB_STRIP, I.LOAD_HALFDISC_X0_TOP),
 ]
 
 
-@pytest.mark.parametrize("case", CASES + [(70, 12, 9, I.BC_MBB, I.LOAD_EDGE_X0_TOP)])
+# grids with nx >= 65 run the column-paired FP32 kernel (63 x 7 node tiles):
+# several x tiles with a ragged last one, every support type, tiles with and
+# without fixed DOFs
+PAIR_CASES = [
+    (70, 12, 9, I.BC_MBB, I.LOAD_EDGE_X0_TOP),
+    (130, 9, 7, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM),
+    (66, 17, 13, I.BC_ROLLER_BOX, I.LOAD_FACE_XL_TRACTION),
+    (80, 12, 12, I.BC_CORNERS, I.LOAD_DISC_XL),
+    (128, 16, 9, I.BC_MBB_STRIP, I.LOAD_HALFDISC_X0_TOP),
+]
+OPS = [0, 1, 2, 3]  # modal (automatic form), node-centric gather, modal one column, modal paired
+
+
+@pytest.mark.parametrize("case", CASES + PAIR_CASES)
 @pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 2e-6)])
-@pytest.mark.parametrize("op", [0, 1])  # modal element kernel, node-centric gather kernel
+@pytest.mark.parametrize("op", OPS)
 def test_operator_matches_assembled_K(topo, case, prec, tol, op):
     nx, ny, nz, bc, load = case
     rho = I.density_uniform(nx, ny, nz, 0.01, 1.0, 17)
@@ -65,11 +81,12 @@ def test_operator_matches_assembled_K(topo, case, prec, tol, op):
     assert np.all(y[P.fixed] == 0.0)
 
 
-@pytest.mark.parametrize("op", [0, 1])
-def test_operator_fp32_keeps_accuracy_under_rigid_translation(topo, op):
-    """Both FP32 kernels subtract a reference displacement before the element
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("nx", [40, 70])
+def test_operator_fp32_keeps_accuracy_under_rigid_translation(topo, op, nx):
+    """The FP32 kernels subtract a reference displacement before the element
     arithmetic, so a large rigid translation added to x does not swamp K x."""
-    nx, ny, nz = 40, 9, 7
+    ny, nz = 9, 7
     rho = I.density_uniform(nx, ny, nz, 0.01, 1.0, 19)
     P = fem.Problem(nx, ny, nz, I.BC_ROLLER_BOX, I.LOAD_FACE_XL_TRACTION, rho)
     g = P.grid

@@ -402,3 +402,25 @@ def test_pins_catch_planted_mistake(name):
     k = _mutants()[name]
     pins = [pin_symmetric(k), pin_rigid_nullspace(k), pin_constant_strain(k), pin_kronecker(k)]
     assert not all(pins), name
+
+
+def test_paper_supports_and_loads():
+    """Sec. 4.2/4.3 problems at the paper's 40x20x20: four 7x7-node corner
+    patches (0.3 of 20 elements = 6 -> nodes 0..6 and 14..20), a disc and a
+    half-disc load of total -1 that are symmetric about y = ny/2 (and z = nz/2)."""
+    g = fem.Grid(40, 20, 20)
+    m = fem.fixed_dofs(g, fem.BC_CORNERS).reshape(-1, 3)
+    ijk = g.node_ijk()[m.any(axis=1)]
+    assert m.sum() == 3 * 4 * 49 and (ijk[:, 0] == 0).all()
+    assert set(ijk[:, 1]) == set(range(7)) | set(range(14, 21))
+    m = fem.fixed_dofs(g, fem.BC_MBB_STRIP).reshape(-1, 3)
+    assert m[:, 0].sum() == 21 * 21 and m[:, 2].sum() == 2 * 21 and m[:, 1].sum() == 1
+    for load in (fem.LOAD_DISC_XL, fem.LOAD_HALFDISC_X0_TOP):
+        f = fem.load_vector(g, load).reshape(-1, 3)
+        assert abs(f[:, 2].sum() + 1.0) < 1e-14 and np.abs(f[:, :2]).max() == 0
+        F = f[:, 2].reshape(21, 21, 41)  # [k][j][i]
+        assert np.allclose(F, F[:, ::-1, :])  # mirror in y about ny/2
+        if load == fem.LOAD_DISC_XL:
+            assert np.allclose(F, F[::-1, :, :]) and np.count_nonzero(F[:, :, :40]) == 0
+        else:
+            assert np.count_nonzero(F[:20]) == 0 and np.count_nonzero(F[20, :, 4:]) == 0
