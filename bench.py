@@ -32,15 +32,18 @@ from paper_2605_04735_gb300 import inputs as I  # noqa: E402
 
 METRIC = "PCG state solves/s at true FP64 rel. residual 1e-8 (solve + compliance + sensitivity)"
 UNIT = "solves/s"
-# the operator kernel that dominates a step (by operator choice) and the
-# large-grid roofline case
-OPERATOR_KERNELS = {
-    0: "k_modal_tma (FP32 modal operator, one element column per thread; automatic form)",
-    1: "k_stencil_tma (FP32 node-centric 27-node gather)",
-    2: "k_modal_tma (FP32 modal operator, one element column per thread)",
-    3: "k_modal_pair (FP32 modal operator, two element columns per thread, packed f32x2)",
-}
 LARGE_WORKLOAD = "cantilever_voids_320x160x160"
+PAIR_AUTO_MIN_NX = 150  # the library's automatic modal form pairs columns from this nx on
+
+
+def operator_kernel(op: int, nx: int) -> str:
+    """The FP32 operator kernel that runs for operator choice `op` on a grid
+    of nx elements in x (topo.OPERATOR_*)."""
+    if op == 1:
+        return "k_stencil_tma (FP32 node-centric 27-node gather)"
+    if op == 3 or (op == 0 and nx >= PAIR_AUTO_MIN_NX):
+        return "k_modal_pair (FP32 modal operator, two element columns per thread, packed f32x2)"
+    return "k_modal_tma (FP32 modal operator, one element column per thread)"
 # DRAM bytes (read + write) per launch of the default operator kernel from one
 # ncu capture of the same kernel source, by workload; None until captured
 NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": None, LARGE_WORKLOAD: None}
@@ -58,7 +61,7 @@ def roofline(w: I.Workload, avg_ms: float, peaks: dict, peaks_src: str, op: int 
     peak = float(peaks["hbm_gbs"])
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(w.name) if op == 0 else None,
-            "kernel": OPERATOR_KERNELS[op], "workload": w.name,
+            "kernel": operator_kernel(op, w.nx), "workload": w.name,
             "bytes_per_launch": operator_bytes(w),
             "avg_launch_us": avg_ms * 1e3,
             "gdofs": 3.0 * w.n_nodes / (avg_ms * 1e-3) / 1e9,

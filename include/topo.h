@@ -252,6 +252,29 @@ topo_status topo_filter(topo_mesh* m, double radius, const double* dc, double* d
 /* Copy the mesh's current densities out (n_elem floats). */
 topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_device);
 
+/* ---- the level-set stage's state problem (ersatz material) ----------------- */
+
+/* Set the element moduli from a nodal level set instead of densities
+ * (Sec. 2.2.2, Eqs. (7)-(9)): phi_e = phi at the element centroid (the mean of
+ * the element's 8 nodal values), H_eta(phi_e) the regularised Heaviside of
+ * Eq. (8) (0 below -eta, 1 above eta), I = (1 - H) + eps0 H, and
+ * k_e(phi) = I(phi_e) k_e^0, i.e. E_e = E0 I(phi_e).  phi < 0 is material.
+ *   phi      n_nodes = (nx+1)(ny+1)(nz+1) doubles, node i + (nx+1)(j + (ny+1)k),
+ *            host or device (on_device); copied, not retained.
+ *   eta      band half-width (> 0, element units of h);  eps0 in [0, 1].
+ *   volume   if not NULL: V(phi) = sum_e V_e (1 - H(phi_e)) (Eq. (10)).
+ * Later solves, compliance and displacement use these moduli until the next
+ * topo_set_density / topo_set_levelset.  TOPO_ERR_NAN if phi holds a NaN. */
+topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, int on_device,
+                              double eta, double eps0, double* volume);
+
+/* Element strain energies for unit Young's modulus, w_e = u_e^T k^0 u_e
+ * (k^0 of edge h), of the last solve: the element factor of Eq. (3) and of
+ * the level-set derivative dJ/dphi_e = E0 (1 - eps0) H'(phi_e) w_e.
+ * n_elem doubles, element i + nx(j + ny k).  TOPO_ERR_NOT_SOLVED before a
+ * solve. */
+topo_status topo_element_energy(topo_mesh* m, double* w, size_t n_elem, int on_device);
+
 /* Select the operator kernel family for all later calls on this mesh
  * (TOPO_OPERATOR_*); synchronises the mesh's stream.  Cites Eq. (2). */
 topo_status topo_set_operator(topo_mesh* m, int kind);

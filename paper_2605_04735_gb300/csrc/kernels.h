@@ -69,6 +69,9 @@ template <typename T>
 cudaError_t launch_pack(const T* soa, double* aos, const Dims& d, cudaStream_t s);
 template <typename T>
 cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t s);
+cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
+                          double E0, double eta, double eps0, double hscale, const Red& red,
+                          int* bad, cudaStream_t s);
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
                                const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
                                const Red& red, cudaStream_t s);

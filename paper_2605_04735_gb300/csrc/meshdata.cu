@@ -4,6 +4,8 @@
 // the compliance (Eq. (2)) fused into the same pass.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "modal.cuh"
@@ -172,6 +174,54 @@ __global__ void __launch_bounds__(256)
   reduce_finalize<1>(v, red);
 }
 
+// Ersatz material of the level-set stage (Sec. 2.2.2): phi at the element
+// centroid (mean of the 8 corner values of the Q1 interpolant of the nodal
+// level set, node n = i + (nx+1)(j + (ny+1)k)), H_eta of Eq. (8),
+// I = (1 - H) + eps0 H of Eq. (7), E_e = E0 I(phi_e) (k_e(phi) = I k_e^0,
+// Eq. (9)); rho_g receives 1 - H (the material fraction).  Reduces the
+// volume sum_e (1 - H(phi_e)) of Eq. (10) (unit V_e) -> aux[0].
+__global__ void __launch_bounds__(256)
+    k_ersatz(const double* __restrict__ phi, float* __restrict__ rho_g, float* __restrict__ E32,
+             double* __restrict__ E64, const Dims d, double E0, double eta, double eps0,
+             double hscale, const Red red, int* __restrict__ bad) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  const long long sx = d.nx + 1, sxy = (long long)(d.nx + 1) * (d.ny + 1);
+  double part = 0.0;
+  int nbad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % d.nx);
+    const int j = (int)((e / d.nx) % d.ny);
+    const int k = (int)(e / ((long long)d.nx * d.ny));
+    const long long n0 = i + sx * j + sxy * k;
+    double pe = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      pe += __ldg(phi + n0 + (b & 1) + sx * ((b >> 1) & 1) + sxy * (b >> 2));
+    pe *= 0.125;
+    if (!(pe == pe)) {  // NaN
+      ++nbad;
+      pe = 0.0;
+    }
+    double H;
+    if (pe < -eta)
+      H = 0.0;
+    else if (pe > eta)
+      H = 1.0;
+    else
+      H = 0.5 + pe / (2.0 * eta) + sin(M_PI * pe / eta) / (2.0 * M_PI);
+    const double Ee = E0 * ((1.0 - H) + eps0 * H) * hscale;
+    const long long o = d.elem(i, j, k);
+    rho_g[o] = (float)(1.0 - H);
+    E64[o] = Ee;
+    E32[o] = (float)Ee;
+    part += 1.0 - H;
+  }
+  if (nbad) atomicAdd(bad, nbad);
+  double v[1] = {part};
+  reduce_finalize<1>(v, red);
+}
+
 inline int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152 * 8) b = 152 * 8;
@@ -224,6 +274,15 @@ cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double
                                const Red& red, cudaStream_t s) {
   const long long n = (long long)d.nx * d.ny * d.nz;
   k_sensitivity<<<grid_for(n, 256), 256, 0, s>>>(u, rho_g, E64, dc, d, kc, penal, dE, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
+                          double E0, double eta, double eps0, double hscale, const Red& red,
+                          int* bad, cudaStream_t s) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  k_ersatz<<<grid_for(n, 256), 256, 0, s>>>(phi, rho_g, E32, E64, d, E0, eta, eps0, hscale, red,
+                                            bad);
   return cudaGetLastError();
 }
 

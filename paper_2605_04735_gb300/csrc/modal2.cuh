@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
   // TMA destinations on 128-byte boundaries whatever the dynamic window's offset
   unsigned char* pair_smem = pair_dyn + ((128u - (smem_u32(pair_dyn) & 127u)) & 127u);
   float* stg = reinterpret_cast<float*>(pair_smem);
-  auto xch = reinterpret_cast<float2(*)[kPairTY][kPairTX][3]>(
+  auto xch = reinterpret_cast<float2(*)[3][kPairTY][kPairTX]>(
       pair_smem + sizeof(float) * kPStageFloats * kPairStages);
   uint64_t* bar = reinterpret_cast<uint64_t*>(pair_smem + sizeof(float) * kPStageFloats * kPairStages +
                                               kPairXchBytes);
@@ -214,34 +214,11 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
   const int src = (tx + kPairTX - 1) & (kPairTX - 1);
   long long oA = d.node(exA, ey, kb);
 
-  PairColumn col;
-  {
-    mbar_wait_bounded(&bar[0], 0u, errflag);
-    const float* nd = stg;
-    float2 raw[2][2][3];
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float* p = nd + c * (kPBoxNY * kPBoxX) + (ty + dy) * kPBoxX + lx + dx;
-          raw[dy][dx][c] = make_float2(p[0], p[32]);
-        }
-    pair_seed(col, raw);
-    __syncthreads();
-    if (tid == 0 && kPairStages < nst) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(kPairStages);
-    }
-  }
-  float part = 0.f;  // this thread's nodes only (at most 2 zchunk); widened to FP64 below
-#pragma unroll 2
-  for (int t = 1; t < nst; ++t) {
+  // stage t -> registers: the top node plane (pairs A, B) and the element moduli
+  auto load_stage = [&](int t, float2(&top)[2][2][3], float2& E) {
     const int slot = t % kPairStages;
     mbar_wait_bounded(&bar[slot], (uint32_t)((t / kPairStages) & 1), errflag);
     const float* nd = stg + slot * kPStageFloats;
-    float2 top[2][2][3];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -252,13 +229,29 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
           top[dy][dx][c] = make_float2(p[0], p[32]);
         }
     const float* el = nd + kPNodeStride + ty * kPBoxX + lx;
-    const float2 E = make_float2(el[0], el[32]);
+    E = make_float2(el[0], el[32]);
+  };
+  // one stage per layer: wait, read, compute, exchange, barrier, refill,
+  // epilogue.  (Reading stage t+1 before the barrier, to overlap its latency
+  // with the exchange, measured slower: it spills at the 128-register cap.)
+  PairColumn col;
+  float2 top[2][2][3], E;
+  load_stage(0, top, E);
+  pair_seed(col, top);
+  __syncthreads();
+  if (tid == 0 && kPairStages < nst) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue(kPairStages);
+  }
+  float part = 0.f;
+#pragma unroll 2
+  for (int t = 1; t < nst; ++t) {
+    load_stage(t, top, E);
     const float2 nE = make_float2(-E.x, -E.y);
     float2 plane[3][4], ctr[3];
     pair_layer(col, top, E, nE, kc, plane, ctr);
-    // +x corners from the column on the left: lane tx-1's A (B), lane 31's A for lane 0's B
     float2 n0[3];
-    float2(*xb)[kPairTX][3] = xch[t & 1];
+    float2(*xb)[kPairTY][kPairTX] = xch[t & 1];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float r1a = __shfl_sync(0xffffffffu, plane[c][1].x, src);
@@ -266,9 +259,9 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
       const float r3a = __shfl_sync(0xffffffffu, plane[c][3].x, src);
       const float r3b = __shfl_sync(0xffffffffu, plane[c][3].y, src);
       n0[c] = padd(plane[c][0], make_float2(r1a, tx > 0 ? r1b : r1a));
-      xb[ty][tx][c] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
+      xb[c][ty][tx] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
     }
-    __syncthreads();  // also retires this stage's slot
+    __syncthreads();
     if (tid == 0 && t + kPairStages < nst) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(t + kPairStages);
@@ -278,7 +271,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
       float resA[3], resB[3], cA[3], cB[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float2 r = padd(n0[c], xb[ty - 1][tx][c]);
+        const float2 r = padd(n0[c], xb[c][ty - 1][tx]);
         resA[c] = r.x;
         resB[c] = r.y;
         cA[c] = ctr[c].x;
@@ -345,9 +338,11 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
   return cudaGetLastError();
 }
 
-// Smallest nx for which the automatic form picks the paired kernel (it is
-// not faster than the one-column kernel on the grids measured so far).
-constexpr int kPairAutoMinNx = 1 << 30;
+// Smallest nx for which the automatic form picks the paired kernel.  Measured
+// on GB300 (one plain FP32 application, inputs above L2): 96x32x32 10.3 us
+// either form; 192x96x96 37.1 us paired vs 41.1 us one-column; 320x160x160
+// 133 us vs 143 us.
+constexpr int kPairAutoMinNx = 150;
 
 // The operator launch of both modal forms: the paired kernel where it is
 // selected and the grid is wide enough for its boxes (px, ex >= 68), the

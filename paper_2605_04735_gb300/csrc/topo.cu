@@ -129,6 +129,7 @@ struct topo_mesh {
   double* aos = nullptr;       // n_dof doubles (ABI transfers)
   double* dc = nullptr;        // n_elem doubles
   float* rho_in = nullptr;     // n_elem floats: the current densities, dense element order
+  double* phi_in = nullptr;    // n_node doubles: the nodal level set (ersatz material)
   double* dcf = nullptr;       // n_elem doubles: filtered sensitivities
   float* rho_next = nullptr;   // n_elem floats: densities after an OC update
   void* oc_state = nullptr;    // device OC bracketing state
@@ -825,7 +826,7 @@ void topo_free(topo_mesh* m) {
   void* ptrs[] = {m->rho_g, m->E32,  m->E64,  m->f64, m->u64,  m->r64, m->x32, m->r32,
                   m->z32,   m->p32,  m->q32,  m->b32, m->dinv32, m->x64, m->s64, m->z64,
                   m->p64,   m->q64,  m->dinv64, m->sc, m->partials, m->flags, m->aos, m->dc,
-                  m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part};
+                  m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part, m->phi_in};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   clear_graphs(m);
@@ -954,6 +955,51 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
     return set_density_impl(m, m->rho_in);
   }
   return set_density_impl(m, rho);
+}
+
+topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, int on_device,
+                              double eta, double eps0, double* volume) {
+  if (!m || !phi || !(eta > 0.0) || !(eps0 >= 0.0 && eps0 <= 1.0)) return TOPO_ERR_INVALID;
+  const long long nn = (long long)(m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  if ((long long)n_nodes != nn) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  cudaStream_t s = m->stream;
+  const double* src = phi;
+  if (!on_device) {
+    if (!m->phi_in) CKS(dalloc(m, &m->phi_in, nn));
+    CK(cudaMemcpyAsync(m->phi_in, phi, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = m->phi_in;
+  }
+  CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
+  LK(m, launch_ersatz(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, eta, eps0, m->prm.h,
+                      red_of(m, FIN_AUX), m->flags, s));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKS(sync_scalars(m));
+  m->diag32 = m->diag64 = false;
+  m->gmg.ready = false;
+  m->solved = false;
+  m->has_density = (bad == 0);
+  if (volume) *volume = m->h_sc->aux[0] * m->prm.h * m->prm.h * m->prm.h;
+  return bad ? TOPO_ERR_NAN : TOPO_OK;
+}
+
+topo_status topo_element_energy(topo_mesh* m, double* w, size_t n_elem, int on_device) {
+  if (!m || !w) return TOPO_ERR_INVALID;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_elem != ne) return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  if (!m->dc) CKS(dalloc(m, &m->dc, ne));
+  // the Eq. (3) kernel with p = 1 and -(E0 - Emin) h replaced by h: w_e = u_e^T k0(h) u_e
+  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->mcd, 1.0, -m->prm.h,
+                           red_of(m, FIN_AUX), m->stream));
+  CK(cudaMemcpyAsync(w, m->dc, ne * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
 }
 
 topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_info* info) {

@@ -117,6 +117,22 @@ def density_voids(nx: int, ny: int, nz: int, n_voids: int, seed: int, slope: flo
     return rho.reshape(-1).astype(np.float32)
 
 
+def levelset_voids(nx: int, ny: int, nz: int, n_voids: int, seed: int, rmin: float = 2.0,
+                   rmax: float = 6.0) -> np.ndarray:
+    """Nodal level set of a block with spherical voids (phi < 0 is material):
+    phi_n = max_k (r_k - |x_n - c_k|) at the nodes x_n = (i, j, k), i.e. the
+    signed distance to the union of the void balls outside overlaps, with the
+    seeded centres and radii of `void_spheres`.  Node order i + (nx+1)(j + (ny+1)k),
+    float64."""
+    centres, radii = void_spheres(nx, ny, nz, n_voids, seed, rmin, rmax)
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    X = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    phi = np.full(X.shape[0], -np.inf)
+    for c, r in zip(centres, radii):
+        np.maximum(phi, r - np.linalg.norm(X - np.asarray(c), axis=1), out=phi)
+    return phi
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     name: str

@@ -95,6 +95,8 @@ def lib():
                                    C.POINTER(C.c_longlong)]),
             "topo_footprint_bytes": (C.c_longlong, [i, i, i, C.POINTER(SolveOpts)]),
             "topo_set_stream": (i, [vp, vp]),
+            "topo_set_levelset": (i, [vp, vp, sz, i, d, d, C.POINTER(d)]),
+            "topo_element_energy": (i, [vp, vp, sz, i]),
             "topo_set_operator": (i, [vp, i]),
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
@@ -285,6 +287,23 @@ class Mesh:
         if dev != dev2:
             raise TypeError("x and out must both be host or both be device arrays")
         _check(lib().topo_apply(self._h, precision, px, py, n, dev), "topo_apply")
+        return out
+
+    def set_levelset(self, phi, eta=1.0, eps0=1e-3) -> float:
+        """Ersatz material from the nodal level set phi (Eqs. (7)-(9)); returns
+        the material volume V(phi) of Eq. (10)."""
+        p, n, dev = _ptr(phi, np.float64)
+        vol = C.c_double()
+        _check(lib().topo_set_levelset(self._h, p, n, dev, eta, eps0, C.byref(vol)),
+               "topo_set_levelset")
+        return vol.value
+
+    def element_energy(self, out=None):
+        """w_e = u_e^T k^0 u_e (unit E) of the last solve."""
+        if out is None:
+            out = np.empty(self.n_elem, np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_element_energy(self._h, p, n, dev), "topo_element_energy")
         return out
 
     def apply_internal(self, precision=PREC_FP32, reps=1):
