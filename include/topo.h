@@ -267,6 +267,51 @@ topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_dev
  * topo_set_density / topo_set_levelset.  TOPO_ERR_NAN if phi holds a NaN. */
 topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, int on_device,
                               double eta, double eps0, double* volume);
+/* (phi may be NULL: the mesh's current level set, e.g. after topo_hj_evolve
+ * or topo_reinit, is used.  The mesh keeps its own copy of phi.) */
+
+/* Copy the mesh's current level set out (n_nodes doubles). */
+topo_status topo_get_levelset(topo_mesh* m, double* phi, size_t n_nodes, int on_device);
+
+/* Nodal right-hand sides of the relaxed shape derivatives (Sec. 2.2.5,
+ * Eqs. (14), (15)) for the last solve and the level set of the last
+ * topo_set_levelset, by 2x2x2 Gauss quadrature per element with phi and
+ * grad(phi) of the Q1 interpolant:
+ *   bJ[n] = int sigma(u):eps(u) N_n H'_eta(phi) |grad phi| dx
+ *           (sigma:eps = eps^T D(E0, nu) eps, the solid's strain energy density)
+ *   bV[n] = int N_n H'_eta(phi) |grad phi| dx   (C' of Eq. (15) is -bV / V_D)
+ * The augmented-Lagrangian right-hand side (Eqs. (16)-(18)) is
+ * bJ + ((lambda - Lambda C) / V_D) bV.  Either output may be NULL.
+ * TOPO_ERR_NOT_SOLVED before a solve; TOPO_ERR_INVALID if the level set has
+ * changed since the moduli were set. */
+topo_status topo_shape_rhs(topo_mesh* m, double* bJ, double* bV, size_t n_nodes, int on_device);
+
+/* Hilbertian extension-regularisation (Sec. 2.2.6, Eqs. (19), (20)): solve
+ * A_H v = b, A_H the Q1 discretisation of int (ell^2 grad v . grad w + v w),
+ * with v = 0 on the loaded nodes (the traction boundary Gamma_N), by
+ * Jacobi-PCG in FP64 on the device from v = 0 to the relative residual rtol
+ * (b, v: n_nodes doubles, host or device).  *iters: CG iterations.
+ * TOPO_ERR_NOT_CONVERGED when max_iter is reached (v holds the last iterate). */
+topo_status topo_hilbertian_solve(topo_mesh* m, double ell, const double* b, double* v,
+                                  size_t n_nodes, int on_device, double rtol, int max_iter,
+                                  int* iters);
+
+/* Hamilton-Jacobi evolution (Sec. 2.2.7, Eqs. (21), (22)) of the mesh's level
+ * set under the nodal speed v (phi decreases where v > 0: material grows):
+ * `steps` forward-Euler steps of the first-order Godunov upwind scheme with
+ * dt = gamma h / max|v| (*dt, if not NULL, receives it; 0 when v = 0).
+ * Differences that would reach outside the grid are 0.  The moduli are not
+ * updated: call topo_set_levelset(m, NULL, ...) for the next state solve. */
+topo_status topo_hj_evolve(topo_mesh* m, const double* v, size_t n_nodes, int on_device,
+                           double gamma, int steps, double* dt);
+
+/* Reinitialisation (Sec. 2.2.8, Eqs. (23), (24)): pseudo-time steps of
+ * phi_t + S(phi)(|grad phi| - 1) = 0, S(phi) = phi / sqrt(phi^2 + h^2 |grad phi|^2)
+ * recomputed from the current phi each step (central differences, one-sided on
+ * the boundary), the same upwind scheme, dt = gamma h (0 < gamma <= 1), until
+ * a step changes no node by more than tol h or after max_steps steps (the test
+ * runs every 8 steps); *steps receives the count. */
+topo_status topo_reinit(topo_mesh* m, double gamma, double tol, int max_steps, int* steps);
 
 /* Element strain energies for unit Young's modulus, w_e = u_e^T k^0 u_e
  * (k^0 of edge h), of the last solve: the element factor of Eq. (3) and of

@@ -2,6 +2,8 @@
 // family; definitions live in the .cu file of that family).
 #pragma once
 
+#include <cstdint>
+
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -69,6 +71,22 @@ template <typename T>
 cudaError_t launch_pack(const T* soa, double* aos, const Dims& d, cudaStream_t s);
 template <typename T>
 cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t s);
+// level-set stage (levelset.cu)
+cudaError_t launch_shape_rhs(const double* u, const double* phi, double* part, double* bJ,
+                             double* bV, const Dims& d, double eta, double E0, double nu,
+                             double h, cudaStream_t s);
+cudaError_t launch_hilb_setup(const double* f, uint8_t* dir, double* dinv, const Dims& d,
+                              double ell2, double h, long long npad, cudaStream_t s);
+cudaError_t launch_hilb_rhs(const double* src, double* b, const uint8_t* dir, const Dims& d,
+                            long long npad, cudaStream_t s);
+cudaError_t launch_hilb_apply(const double* x, double* y, const uint8_t* dir, const Dims& d,
+                              double ell2, double h, const Red& red, bool dot, const int* done,
+                              cudaStream_t s);
+cudaError_t launch_hj_steps(double* phi, double* tmp, const double* v, const Dims& d,
+                            double gamma, double h, int steps, unsigned long long* scratch,
+                            double* dt_dev, cudaStream_t s);
+cudaError_t launch_reinit_step(const double* phi, double* out, const Dims& d, double dt, double h,
+                               unsigned long long* maxchange, cudaStream_t s);
 cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
                           double E0, double eta, double eps0, double hscale, const Red& red,
                           int* bad, cudaStream_t s);

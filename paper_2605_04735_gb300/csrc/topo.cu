@@ -130,6 +130,20 @@ struct topo_mesh {
   double* dc = nullptr;        // n_elem doubles
   float* rho_in = nullptr;     // n_elem floats: the current densities, dense element order
   double* phi_in = nullptr;    // n_node doubles: the nodal level set (ersatz material)
+  // level-set stage (lazily allocated): second level-set buffer, shape
+  // right-hand sides, the extension solve's CG vectors and Dirichlet mask
+  double* phi_tmp = nullptr;
+  double ls_eta = 1.0, ls_eps0 = 1e-3;
+  bool ls_ready = false;       // phi_in holds the level set the moduli came from
+  double* ls_part = nullptr;   // 16 n_elem doubles: element shares of bJ, bV
+  double* ls_bJ = nullptr;     // n_node doubles each
+  double* ls_bV = nullptr;
+  double *hx = nullptr, *hr = nullptr, *hz = nullptr, *hp = nullptr, *hq = nullptr,
+         *hdinv = nullptr, *hb = nullptr;  // padded to a multiple of 4 nodes
+  uint8_t* hdir = nullptr;
+  double h_ell2 = -1.0;        // ell^2 the Jacobi diagonal was built for
+  unsigned long long* ls_scratch = nullptr;
+  double* ls_dt = nullptr;
   double* dcf = nullptr;       // n_elem doubles: filtered sensitivities
   float* rho_next = nullptr;   // n_elem floats: densities after an OC update
   void* oc_state = nullptr;    // device OC bracketing state
@@ -826,7 +840,9 @@ void topo_free(topo_mesh* m) {
   void* ptrs[] = {m->rho_g, m->E32,  m->E64,  m->f64, m->u64,  m->r64, m->x32, m->r32,
                   m->z32,   m->p32,  m->q32,  m->b32, m->dinv32, m->x64, m->s64, m->z64,
                   m->p64,   m->q64,  m->dinv64, m->sc, m->partials, m->flags, m->aos, m->dc,
-                  m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part, m->phi_in};
+                  m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part, m->phi_in,
+                  m->phi_tmp, m->ls_part, m->ls_bJ, m->ls_bV, m->hx, m->hr, m->hz, m->hp,
+                  m->hq, m->hdinv, m->hb, m->hdir, m->ls_scratch, m->ls_dt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   clear_graphs(m);
@@ -959,20 +975,21 @@ topo_status topo_set_density(topo_mesh* m, const float* rho, size_t n_elem, int 
 
 topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, int on_device,
                               double eta, double eps0, double* volume) {
-  if (!m || !phi || !(eta > 0.0) || !(eps0 >= 0.0 && eps0 <= 1.0)) return TOPO_ERR_INVALID;
+  if (!m || !(eta > 0.0) || !(eps0 >= 0.0 && eps0 <= 1.0)) return TOPO_ERR_INVALID;
   const long long nn = (long long)(m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
   if ((long long)n_nodes != nn) return TOPO_ERR_INVALID;
+  if (!phi && !m->phi_in) return TOPO_ERR_INVALID;  // no current level set to reuse
   Fence fence(m);
   if (fence.st != TOPO_OK) return fence.st;
   cudaStream_t s = m->stream;
-  const double* src = phi;
-  if (!on_device) {
-    if (!m->phi_in) CKS(dalloc(m, &m->phi_in, nn));
-    CK(cudaMemcpyAsync(m->phi_in, phi, nn * sizeof(double), cudaMemcpyHostToDevice, s));
-    src = m->phi_in;
-  }
+  if (!m->phi_in) CKS(dalloc(m, &m->phi_in, nn));
+  if (phi && phi != m->phi_in)
+    CK(cudaMemcpyAsync(m->phi_in, phi, nn * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  m->ls_eta = eta;
+  m->ls_eps0 = eps0;
   CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
-  LK(m, launch_ersatz(src, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, eta, eps0, m->prm.h,
+  LK(m, launch_ersatz(m->phi_in, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, eta, eps0, m->prm.h,
                       red_of(m, FIN_AUX), m->flags, s));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -981,8 +998,163 @@ topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, i
   m->gmg.ready = false;
   m->solved = false;
   m->has_density = (bad == 0);
+  m->ls_ready = (bad == 0);
   if (volume) *volume = m->h_sc->aux[0] * m->prm.h * m->prm.h * m->prm.h;
   return bad ? TOPO_ERR_NAN : TOPO_OK;
+}
+
+static long long node_count(const topo_mesh* m) {
+  return (long long)(m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+}
+
+topo_status topo_get_levelset(topo_mesh* m, double* phi, size_t n_nodes, int on_device) {
+  if (!m || !phi) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m);
+  if ((long long)n_nodes != nn || !m->phi_in) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CK(cudaMemcpyAsync(phi, m->phi_in, nn * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_shape_rhs(topo_mesh* m, double* bJ, double* bV, size_t n_nodes, int on_device) {
+  if (!m || (!bJ && !bV)) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m), ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if ((long long)n_nodes != nn || !m->ls_ready) return TOPO_ERR_INVALID;
+  if (!m->solved) return TOPO_ERR_NOT_SOLVED;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  cudaStream_t s = m->stream;
+  if (!m->ls_part) CKS(dalloc(m, &m->ls_part, 16 * ne));
+  if (!m->ls_bJ) CKS(dalloc(m, &m->ls_bJ, nn));
+  if (!m->ls_bV) CKS(dalloc(m, &m->ls_bV, nn));
+  LK(m, launch_shape_rhs(m->u64, m->phi_in, m->ls_part, m->ls_bJ, m->ls_bV, m->d, m->ls_eta,
+                         m->prm.E0, m->prm.nu, m->prm.h, s));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (bJ) CK(cudaMemcpyAsync(bJ, m->ls_bJ, nn * sizeof(double), kind, s));
+  if (bV) CK(cudaMemcpyAsync(bV, m->ls_bV, nn * sizeof(double), kind, s));
+  if (!on_device) CK(cudaStreamSynchronize(s));
+  return TOPO_OK;
+}
+
+topo_status topo_hilbertian_solve(topo_mesh* m, double ell, const double* b, double* v,
+                                  size_t n_nodes, int on_device, double rtol, int max_iter,
+                                  int* iters) {
+  if (iters) *iters = 0;
+  if (!m || !b || !v || !(ell >= 0.0) || !(rtol > 0.0) || max_iter < 1) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m);
+  if ((long long)n_nodes != nn) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  cudaStream_t s = m->stream;
+  const long long npad = (nn + 3) / 4 * 4;
+  double** vecs[] = {&m->hx, &m->hr, &m->hz, &m->hp, &m->hq, &m->hdinv, &m->hb};
+  for (double** q : vecs)
+    if (!*q) CKS(dalloc(m, q, npad));
+  if (!m->hdir) CKS(dalloc(m, &m->hdir, npad));
+  const double ell2 = ell * ell;
+  if (ell2 != m->h_ell2) {
+    LK(m, launch_hilb_setup(m->f64, m->hdir, m->hdinv, m->d, ell2, m->prm.h, npad, s));
+    m->h_ell2 = ell2;
+  }
+  const double* src = b;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(m->hq, b, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = m->hq;
+  }
+  LK(m, launch_hilb_rhs(src, m->hb, m->hdir, m->d, npad, s));  // b = 0 on Gamma_N
+  // Jacobi-PCG (Eq. (20) is SPD and well conditioned): x0 = 0
+  LK(m, launch_set_max_iter(m->sc, max_iter, s));
+  LK(m, launch_pcg_init<double>(m->hb, m->hx, m->hr, m->hz, m->hp, m->hdinv, npad,
+                                red_of(m, FIN_INIT, rtol * rtol), true, s));
+  const int* done = &m->sc->done;
+  for (int chunk = 0;; ++chunk) {
+    for (int c = 0; c < 8; ++c) {
+      LK(m, launch_hilb_apply(m->hp, m->hq, m->hdir, m->d, ell2, m->prm.h, red_of(m, FIN_ALPHA),
+                              true, done, s));
+      LK(m, launch_pcg_update<double>(m->hx, m->hr, m->hz, m->hp, m->hq, m->hdinv, npad,
+                                      red_of(m, FIN_UPDATE), true, s));
+      LK(m, launch_pcg_direction<double>(m->hp, m->hz, npad, m->sc, s));
+    }
+    CKS(sync_scalars(m));
+    if (m->h_sc->done) break;
+    if (chunk > max_iter) return TOPO_ERR_CUDA;  // the device never stopped: a bug
+  }
+  if (iters) *iters = m->h_sc->iter;
+  CK(cudaMemcpyAsync(v, m->hx, nn * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (m->h_sc->status == 1) return TOPO_ERR_NOT_CONVERGED;
+  if (m->h_sc->status != 0) return TOPO_ERR_NAN;
+  return TOPO_OK;
+}
+
+topo_status topo_hj_evolve(topo_mesh* m, const double* v, size_t n_nodes, int on_device,
+                           double gamma, int steps, double* dt) {
+  if (dt) *dt = 0.0;
+  if (!m || !v || !(gamma > 0.0) || steps < 0) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m);
+  if ((long long)n_nodes != nn || !m->phi_in) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  cudaStream_t s = m->stream;
+  if (!m->phi_tmp) CKS(dalloc(m, &m->phi_tmp, nn));
+  if (!m->hq) CKS(dalloc(m, &m->hq, (nn + 3) / 4 * 4));
+  if (!m->ls_scratch) CKS(dalloc(m, &m->ls_scratch, 1));
+  if (!m->ls_dt) CKS(dalloc(m, &m->ls_dt, 1));
+  const double* vd = v;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(m->hq, v, nn * sizeof(double), cudaMemcpyHostToDevice, s));
+    vd = m->hq;
+  }
+  LK(m, launch_hj_steps(m->phi_in, m->phi_tmp, vd, m->d, gamma, m->prm.h, steps, m->ls_scratch,
+                        m->ls_dt, s));
+  m->ls_ready = false;  // the moduli no longer match phi until topo_set_levelset
+  if (dt) {
+    CK(cudaMemcpyAsync(dt, m->ls_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return TOPO_OK;
+}
+
+topo_status topo_reinit(topo_mesh* m, double gamma, double tol, int max_steps, int* steps) {
+  if (steps) *steps = 0;
+  if (!m || !(gamma > 0.0 && gamma <= 1.0) || !(tol >= 0.0) || max_steps < 1)
+    return TOPO_ERR_INVALID;
+  if (!m->phi_in) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m);
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  cudaStream_t s = m->stream;
+  if (!m->phi_tmp) CKS(dalloc(m, &m->phi_tmp, nn));
+  if (!m->ls_scratch) CKS(dalloc(m, &m->ls_scratch, 1));
+  const double h = m->prm.h, dt = gamma * h;
+  double* a = m->phi_in;
+  double* b = m->phi_tmp;
+  int done = 0;
+  unsigned long long bits = 0;
+  while (done < max_steps) {
+    const int chunk = std::min(8, max_steps - done);
+    for (int c = 0; c < chunk; ++c) {
+      if (c == chunk - 1) CK(cudaMemsetAsync(m->ls_scratch, 0, sizeof(unsigned long long), s));
+      LK(m, launch_reinit_step(a, b, m->d, dt, h, m->ls_scratch, s));
+      std::swap(a, b);
+    }
+    done += chunk;
+    CK(cudaMemcpyAsync(&bits, m->ls_scratch, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double change;
+    std::memcpy(&change, &bits, sizeof(change));
+    if (change <= tol * h) break;
+  }
+  if (a != m->phi_in) CK(cudaMemcpyAsync(m->phi_in, a, nn * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  m->ls_ready = false;
+  if (steps) *steps = done;
+  return TOPO_OK;
 }
 
 topo_status topo_element_energy(topo_mesh* m, double* w, size_t n_elem, int on_device) {

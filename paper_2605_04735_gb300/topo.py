@@ -97,6 +97,11 @@ def lib():
             "topo_set_stream": (i, [vp, vp]),
             "topo_set_levelset": (i, [vp, vp, sz, i, d, d, C.POINTER(d)]),
             "topo_element_energy": (i, [vp, vp, sz, i]),
+            "topo_get_levelset": (i, [vp, vp, sz, i]),
+            "topo_shape_rhs": (i, [vp, vp, vp, sz, i]),
+            "topo_hilbertian_solve": (i, [vp, d, vp, vp, sz, i, d, i, C.POINTER(i)]),
+            "topo_hj_evolve": (i, [vp, vp, sz, i, d, i, C.POINTER(d)]),
+            "topo_reinit": (i, [vp, d, d, i, C.POINTER(i)]),
             "topo_set_operator": (i, [vp, i]),
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
@@ -289,14 +294,60 @@ class Mesh:
         _check(lib().topo_apply(self._h, precision, px, py, n, dev), "topo_apply")
         return out
 
-    def set_levelset(self, phi, eta=1.0, eps0=1e-3) -> float:
-        """Ersatz material from the nodal level set phi (Eqs. (7)-(9)); returns
-        the material volume V(phi) of Eq. (10)."""
-        p, n, dev = _ptr(phi, np.float64)
+    def set_levelset(self, phi=None, eta=1.0, eps0=1e-3) -> float:
+        """Ersatz material from the nodal level set phi (Eqs. (7)-(9)), or from
+        the mesh's current level set if phi is None; returns the material
+        volume V(phi) of Eq. (10)."""
+        if phi is None:
+            p, n, dev = None, self.n_nodes, 0
+        else:
+            p, n, dev = _ptr(phi, np.float64)
         vol = C.c_double()
         _check(lib().topo_set_levelset(self._h, p, n, dev, eta, eps0, C.byref(vol)),
                "topo_set_levelset")
         return vol.value
+
+    def levelset(self, out=None):
+        if out is None:
+            out = np.empty(self.n_nodes, np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_get_levelset(self._h, p, n, dev), "topo_get_levelset")
+        return out
+
+    def shape_rhs(self):
+        """(bJ, bV): nodal right-hand sides of Eqs. (14), (15) for the last solve."""
+        bJ = np.empty(self.n_nodes, np.float64)
+        bV = np.empty(self.n_nodes, np.float64)
+        _check(lib().topo_shape_rhs(self._h, bJ.ctypes.data, bV.ctypes.data, self.n_nodes, 0),
+               "topo_shape_rhs")
+        return bJ, bV
+
+    def hilbertian_solve(self, b, ell, rtol=1e-10, max_iter=2000, out=None):
+        """v with A_H v = b, v = 0 on the loaded nodes (Eqs. (19), (20)); returns (v, iters)."""
+        if out is None:
+            out = np.empty(self.n_nodes, np.float64)
+        pb, n, dev = _ptr(b, np.float64)
+        pv, n2, dev2 = _ptr(out, np.float64)
+        if n != n2 or dev != dev2:
+            raise TypeError("b and out must be alike")
+        it = C.c_int()
+        _check(lib().topo_hilbertian_solve(self._h, ell, pb, pv, n, dev, rtol, max_iter,
+                                           C.byref(it)), "topo_hilbertian_solve")
+        return out, it.value
+
+    def hj_evolve(self, v, gamma=0.5, steps=1) -> float:
+        """Evolve the mesh's level set under speed v (Eqs. (21), (22)); returns dt."""
+        p, n, dev = _ptr(v, np.float64)
+        dt = C.c_double()
+        _check(lib().topo_hj_evolve(self._h, p, n, dev, gamma, steps, C.byref(dt)),
+               "topo_hj_evolve")
+        return dt.value
+
+    def reinit(self, gamma=0.5, tol=1e-4, max_steps=500) -> int:
+        """Reinitialise the mesh's level set (Eqs. (23), (24)); returns the steps taken."""
+        st = C.c_int()
+        _check(lib().topo_reinit(self._h, gamma, tol, max_steps, C.byref(st)), "topo_reinit")
+        return st.value
 
     def element_energy(self, out=None):
         """w_e = u_e^T k^0 u_e (unit E) of the last solve."""

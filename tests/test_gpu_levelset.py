@@ -95,3 +95,80 @@ def test_levelset_rejects_bad_input(topo):
             m.set_levelset(phi)
         with pytest.raises(RuntimeError):
             m.element_energy()  # no solve yet
+
+
+# ---- shape derivatives, extension, evolution, reinitialisation -----------
+
+def _ls_case(topo, nx=24, ny=10, nz=10, bc=I.BC_CANTILEVER, load=I.LOAD_EDGE_XL_BOTTOM,
+             eta=1.5):
+    phi = I.levelset_voids(nx, ny, nz, 5, seed=77)
+    m = topo.Mesh(nx, ny, nz, bc, load)
+    m.set_levelset(phi, eta=eta, eps0=1e-3)
+    m.solve(topo.default_opts(precision=0, precond=topo.PRECOND_JACOBI, rtol=1e-11))
+    return m, phi
+
+
+def test_shape_rhs_matches_oracle(topo):
+    from oracle import fem
+    nx, ny, nz, eta = 24, 10, 10, 1.5
+    m, phi = _ls_case(topo, nx, ny, nz, eta=eta)
+    with m:
+        u = m.displacement()
+        bJ, bV = m.shape_rhs()
+    rJ, rV = L.shape_rhs(fem.Grid(nx, ny, nz), u, phi, eta)  # the same u on both sides
+    assert np.abs(bJ - rJ).max() <= 1e-12 * np.abs(rJ).max()
+    assert np.abs(bV - rV).max() <= 1e-12 * np.abs(rV).max()
+    assert np.count_nonzero(rV) > 0
+
+
+@pytest.mark.parametrize("ell", [0.0, 1.0, 3.0])
+def test_hilbertian_solve_matches_oracle(topo, ell):
+    from oracle import fem
+    nx, ny, nz = 24, 10, 10
+    m, phi = _ls_case(topo, nx, ny, nz)
+    g = fem.Grid(nx, ny, nz)
+    with m:
+        u = m.displacement()
+        rJ, rV = L.shape_rhs(g, u, phi, 1.5)
+        b = rJ - 0.3 * rV                      # an augmented-Lagrangian style right-hand side
+        v, iters = m.hilbertian_solve(b, ell, rtol=1e-12)
+    dirichlet = L.loaded_nodes(g, I.LOAD_EDGE_XL_BOTTOM)
+    ref = L.hilbertian_solve(g, ell, b, dirichlet)
+    assert iters > 0
+    assert np.all(v[dirichlet] == 0.0)
+    assert np.linalg.norm(v - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_hj_evolution_and_reinit_match_oracle(topo):
+    from oracle import fem
+    nx, ny, nz = 20, 9, 8
+    g = fem.Grid(nx, ny, nz)
+    phi = I.levelset_voids(nx, ny, nz, 4, seed=3)
+    v = np.sin(0.3 * np.arange(g.n_nodes)) * 0.7      # any smooth-ish speed of both signs
+    with topo.Mesh(nx, ny, nz) as m:
+        m.set_levelset(phi)
+        dt = m.hj_evolve(v, gamma=0.5, steps=5)
+        evolved = m.levelset()
+        steps = m.reinit(gamma=0.5, tol=0.0, max_steps=24)
+        reinit = m.levelset()
+        vol = m.set_levelset(None, eta=1.0)           # moduli from the evolved level set
+    assert dt == pytest.approx(L.cfl_dt(g, v, 0.5), rel=1e-15)
+    ref = L.hj_evolve(g, phi, v, 0.5, 5)
+    assert np.abs(evolved - ref).max() <= 1e-12 * np.abs(ref).max()
+    ref2, s2 = L.reinit(g, ref, gamma=0.5, tol=0.0, max_steps=24)
+    assert steps == s2 == 24
+    assert np.abs(reinit - ref2).max() <= 1e-11 * np.abs(ref2).max()
+    assert vol == pytest.approx(L.volume(reinit, nx, ny, nz, 1.0), rel=1e-12)
+
+
+def test_reinit_stops_on_tolerance(topo):
+    nx, ny, nz = 16, 6, 6
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    sdf = (i - 7.4).astype(np.float64).ravel()
+    with topo.Mesh(nx, ny, nz) as m:
+        m.set_levelset(sdf)
+        steps = m.reinit(gamma=0.5, tol=1e-9, max_steps=200)
+        out = m.levelset()
+    assert steps <= 16                                # an exact distance is already steady
+    inner = (i.ravel() > 0) & (i.ravel() < nx)
+    assert np.abs(out[inner] - sdf[inner]).max() < 1e-9

@@ -109,3 +109,90 @@ def test_ersatz_compliance_energy_identity_and_element_derivative():
             Js.append(fem.compliance(P.f, us))
         fd = (Js[0] - Js[1]) / (2 * d)
         assert g[e] == pytest.approx(fd, rel=1e-5, abs=1e-10 * abs(P.compliance(u)))
+
+
+# ---- shape derivatives, Hilbertian extension, HJ, reinitialisation --------
+
+def test_hilbertian_matrix_pins():
+    g = fem.Grid(6, 4, 3)
+    Klap = L.hilbertian_matrix(g, 1.0) - L.hilbertian_matrix(g, 0.0)
+    M = L.hilbertian_matrix(g, 0.0)
+    one = np.ones(g.n_nodes)
+    assert np.abs(Klap @ one).max() < 1e-13          # constants are in the kernel
+    assert one @ (M @ one) == pytest.approx(6 * 4 * 3, rel=1e-13)  # total volume
+    X = g.node_ijk().astype(float)
+    a = np.array([0.4, -1.3, 0.9])
+    v = X @ a                                         # linear field: exact energy
+    assert v @ (Klap @ v) == pytest.approx(a @ a * 6 * 4 * 3, rel=1e-12)
+    # constant data extends to the same constant (natural boundary, no Dirichlet)
+    b = 2.5 * (L.hilbertian_matrix(g, 0.0) @ one)
+    vs = L.hilbertian_solve(g, 2.0, b, np.zeros(g.n_nodes, bool))
+    assert np.allclose(vs, 2.5, atol=1e-12)
+
+
+def test_hilbertian_solve_matches_the_1d_modal_solution():
+    """-ell^2 v'' + v = cos(pi x / Lx) with natural boundaries has
+    v = cos(pi x / Lx) / (1 + (ell pi / Lx)^2); the Q1 solution converges to it."""
+    nx, ny, nz, ell = 32, 2, 2, 3.0
+    g = fem.Grid(nx, ny, nz)
+    X = g.node_ijk().astype(float)
+    gx = np.cos(np.pi * X[:, 0] / nx)
+    b = L.hilbertian_matrix(g, 0.0) @ gx              # int g N_n with g interpolated
+    v = L.hilbertian_solve(g, ell, b, np.zeros(g.n_nodes, bool))
+    exact = gx / (1.0 + (ell * np.pi / nx) ** 2)
+    assert np.abs(v - exact).max() < 5e-3
+
+
+@pytest.mark.parametrize("eta", [1.5, 2.0])
+def test_shape_rhs_measures_the_interface_and_scales_with_uniform_energy(eta):
+    nx, ny, nz = 16, 6, 5
+    g = fem.Grid(nx, ny, nz)
+    X = g.node_ijk().astype(float)
+    phi = X[:, 0] - 7.3                              # plane x = 7.3, |grad phi| = 1
+    t = 1e-3                                         # uniform strain eps_xx = t
+    u = np.zeros(g.n_dof)
+    u[0::3] = t * X[:, 0]
+    bJ, bV = L.shape_rhs(g, u, phi, eta)
+    # coarea: int H'(phi) |grad phi| = area of the zero level set = ny * nz
+    assert bV.sum() == pytest.approx(ny * nz, rel=2e-3)
+    lam, mu = fem.lame(1.0, 0.3)
+    assert np.allclose(bJ, (lam + 2 * mu) * t * t * bV, rtol=1e-12, atol=1e-20)
+
+
+def test_shape_rhs_measures_a_sphere():
+    n, r = 24, 7.0
+    g = fem.Grid(n, n, n)
+    X = g.node_ijk().astype(float)
+    phi = np.linalg.norm(X - n / 2, axis=1) - r
+    _, bV = L.shape_rhs(g, np.zeros(g.n_dof), phi, 1.5)
+    assert bV.sum() == pytest.approx(4 * np.pi * r * r, rel=0.03)
+
+
+def test_hj_step_moves_a_plane_by_v_dt_and_follows_hopf_lax_at_a_kink():
+    g = fem.Grid(12, 3, 3)
+    X = g.node_ijk().astype(float)
+    dt = 0.3
+    for v in (1.0, -1.0):
+        phi = X[:, 0] - 5.5
+        out = L.hj_step(g, phi, v * np.ones(g.n_nodes), dt)
+        inner = (X[:, 0] > 0) & (X[:, 0] < g.nx)
+        assert np.allclose(out[inner], phi[inner] - v * dt, atol=1e-14)
+    # phi0 = |x - 6|: phi(x, t) = min over |y - x| <= t of phi0 = max(|x - 6| - t, 0)
+    phi = np.abs(X[:, 0] - 6.0)
+    out = L.hj_step(g, phi, np.ones(g.n_nodes), dt)
+    inner = (X[:, 0] > 0) & (X[:, 0] < g.nx)
+    assert np.allclose(out[inner], np.maximum(phi[inner] - dt, 0.0), atol=1e-14)
+    assert L.cfl_dt(g, np.array([0.5, -2.0]), 0.5) == 0.25
+
+
+def test_reinit_keeps_a_distance_and_restores_one_from_a_scaled_field():
+    g = fem.Grid(20, 4, 4)
+    X = g.node_ijk().astype(float)
+    sdf = X[:, 0] - 9.4
+    out, steps = L.reinit(g, sdf, tol=1e-10, max_steps=5)
+    inner = (X[:, 0] > 0) & (X[:, 0] < g.nx)
+    assert np.allclose(out[inner], sdf[inner], atol=1e-12)
+    out, steps = L.reinit(g, 3.0 * sdf, tol=1e-6, max_steps=400)
+    near = inner & (np.abs(sdf) < 3.0)
+    assert np.abs(out[near] - sdf[near]).max() < 0.1
+    assert np.sign(out[np.abs(sdf) > 0.5]).tolist() == np.sign(sdf[np.abs(sdf) > 0.5]).tolist()
