@@ -305,6 +305,36 @@ topo_status topo_hilbertian_solve(topo_mesh* m, double ell, const double* b, dou
 topo_status topo_hj_evolve(topo_mesh* m, const double* v, size_t n_nodes, int on_device,
                            double gamma, int steps, double* dt);
 
+/* ---- SIMP -> level-set geometry transfer (Sec. 3.2-3.4) ------------------- */
+
+/* Nodal densities from the mesh's current element densities (Eqs. (25)-(27)):
+ * per node, the linear polynomial fitted by least squares (normal equations
+ * X^T X a = X^T rho over the m elements sharing the node, X rows [1 x_e^T],
+ * x_e the centroids) evaluated at the node when m >= 4 and the centroids are
+ * not coplanar; otherwise the average weighted by 1 / |x_n - x_e| (m > 1) or
+ * the single element's density.  rho_n: n_nodes doubles. */
+topo_status topo_nodal_density(topo_mesh* m, double* rho_n, size_t n_nodes, int on_device);
+
+/* The whole transfer: nodal densities, the iso-surface at rho_t (0 < rho_t < 1)
+ * as a triangle soup, and the signed distance to it at every node (Eqs.
+ * (28)-(30): exact closest points; phi = -d where rho_n >= rho_t), stored as
+ * the mesh's level set (moduli unchanged until topo_set_levelset(m, NULL, ...)).
+ * The surface is made by marching tetrahedra: linear interpolation on the
+ * edges of the 6 tetrahedra of the Kuhn split of each hexahedron (a closed
+ * surface).  *n_triangles: its size (topo_get_surface copies it).
+ * TOPO_ERR_INVALID if no boundary exists at rho_t (nothing to measure from). */
+topo_status topo_levelset_from_density(topo_mesh* m, double rho_t, long long* n_triangles);
+
+/* Triangulate the zero level set of the mesh's current level set (material
+ * phi <= 0) the same way: the discretisation of the final design (Sec. 3.6). */
+topo_status topo_extract_levelset_surface(topo_mesh* m, long long* n_triangles);
+
+/* Copy the last extracted surface: 9 doubles per triangle (x, y, z of its three
+ * vertices), triangles grouped by cell in element order.  max_triangles must be
+ * at least *n_triangles (which is always set). */
+topo_status topo_get_surface(topo_mesh* m, double* tri, size_t max_triangles, int on_device,
+                             long long* n_triangles);
+
 /* Reinitialisation (Sec. 2.2.8, Eqs. (23), (24)): pseudo-time steps of
  * phi_t + S(phi)(|grad phi| - 1) = 0, S(phi) = phi / sqrt(phi^2 + h^2 |grad phi|^2)
  * recomputed from the current phi each step (central differences, one-sided on

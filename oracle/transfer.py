@@ -160,12 +160,43 @@ def closest_point_distance(p, tri):
     return np.where(inside, np.abs(s) * np.sqrt(nn), d_edges)
 
 
-def surface_distance(points, tris) -> np.ndarray:
-    """Eq. (29): d(x) = min over the triangles of the closest-point distance."""
+def _closest_many(p, T):
+    """closest_point_distance for points p (P, 3) and triangles T (M, 3, 3) at
+    once, (P, M): the same projection / clamped-edge rule, broadcast."""
+    a, b, c = T[:, 0], T[:, 1], T[:, 2]
+
+    def seg(a, b):
+        ab = b - a                                          # (M, 3)
+        L2 = np.einsum("mk,mk->m", ab, ab)
+        ap = p[:, None, :] - a[None]                        # (P, M, 3)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            t = np.clip(np.einsum("pmk,mk->pm", ap, ab) / L2, 0.0, 1.0)
+        t = np.where(L2 > 0.0, t, 0.0)
+        q = ap - t[..., None] * ab[None]
+        return np.sqrt(np.einsum("pmk,pmk->pm", q, q))
+
+    de = np.minimum(np.minimum(seg(a, b), seg(b, c)), seg(c, a))
+    n = np.cross(b - a, c - a)
+    nn = np.einsum("mk,mk->m", n, n)
+    ok = nn > 0.0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        s = np.einsum("pmk,mk->pm", p[:, None, :] - a[None], n) / nn
+        q = p[:, None, :] - s[..., None] * n[None]
+        l1 = np.einsum("pmk,mk->pm", np.cross(c - b, q - b[None]), n) / nn
+        l2 = np.einsum("pmk,mk->pm", np.cross(a - c, q - c[None]), n) / nn
+    l3 = 1.0 - l1 - l2
+    inside = ok & (l1 >= 0.0) & (l2 >= 0.0) & (l3 >= 0.0)
+    return np.where(inside, np.abs(s) * np.sqrt(nn), de)
+
+
+def surface_distance(points, tris, chunk: int = 256) -> np.ndarray:
+    """Eq. (29): d(x) = min over the triangles of the closest-point distance
+    (every point against every triangle, in chunks of triangles)."""
     points = np.asarray(points, dtype=np.float64)
+    tris = np.asarray(tris, dtype=np.float64).reshape(-1, 3, 3)
     d = np.full(points.shape[0], np.inf)
-    for t in np.asarray(tris):
-        np.minimum(d, closest_point_distance(points, t), out=d)
+    for s in range(0, len(tris), chunk):
+        np.minimum(d, _closest_many(points, tris[s:s + chunk]).min(axis=1), out=d)
     return d
 
 

@@ -87,6 +87,17 @@ cudaError_t launch_hj_steps(double* phi, double* tmp, const double* v, const Dim
                             double* dt_dev, cudaStream_t s);
 cudaError_t launch_reinit_step(const double* phi, double* out, const Dims& d, double dt, double h,
                                unsigned long long* maxchange, cudaStream_t s);
+// geometry transfer (transfer.cu)
+cudaError_t launch_nodal_density(const float* rho, double* out, const Dims& d, double h,
+                                 cudaStream_t s);
+long long scan_scratch_count(long long n);
+cudaError_t launch_mt_count(const double* f, long long* counts, long long* offsets,
+                            long long* scratch, const Dims& d, double level, bool above, double h,
+                            cudaStream_t s);
+cudaError_t launch_mt_emit(const double* f, const long long* offsets, double* tris, const Dims& d,
+                           double level, bool above, double h, cudaStream_t s);
+cudaError_t launch_sdf(const double* tris, const long long* offsets, const double* rho_n,
+                       double rho_t, double* phi, const Dims& d, double h, cudaStream_t s);
 cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
                           double E0, double eta, double eps0, double hscale, const Red& red,
                           int* bad, cudaStream_t s);

@@ -144,6 +144,14 @@ struct topo_mesh {
   double h_ell2 = -1.0;        // ell^2 the Jacobi diagonal was built for
   unsigned long long* ls_scratch = nullptr;
   double* ls_dt = nullptr;
+  // geometry transfer: nodal densities, the last extracted triangle soup
+  // (9 doubles per triangle, grouped by cell) and its per-cell offsets
+  double* tr_rho_n = nullptr;
+  long long* tr_counts = nullptr;
+  long long* tr_off = nullptr;
+  long long* tr_scratch = nullptr;
+  double* tr_tris = nullptr;
+  long long tr_cap = 0, tr_n = 0;
   double* dcf = nullptr;       // n_elem doubles: filtered sensitivities
   float* rho_next = nullptr;   // n_elem floats: densities after an OC update
   void* oc_state = nullptr;    // device OC bracketing state
@@ -842,7 +850,8 @@ void topo_free(topo_mesh* m) {
                   m->p64,   m->q64,  m->dinv64, m->sc, m->partials, m->flags, m->aos, m->dc,
                   m->rho_in, m->dcf, m->rho_next, m->oc_state, m->oc_part, m->phi_in,
                   m->phi_tmp, m->ls_part, m->ls_bJ, m->ls_bV, m->hx, m->hr, m->hz, m->hp,
-                  m->hq, m->hdinv, m->hb, m->hdir, m->ls_scratch, m->ls_dt};
+                  m->hq, m->hdinv, m->hb, m->hdir, m->ls_scratch, m->ls_dt, m->tr_rho_n,
+                  m->tr_counts, m->tr_off, m->tr_scratch, m->tr_tris};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   clear_graphs(m);
@@ -1116,6 +1125,96 @@ topo_status topo_hj_evolve(topo_mesh* m, const double* v, size_t n_nodes, int on
     CK(cudaMemcpyAsync(dt, m->ls_dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
+  return TOPO_OK;
+}
+
+// nodal densities from the mesh's current element densities (Eqs. (25)-(27))
+static topo_status nodal_density_impl(topo_mesh* m) {
+  const long long nn = node_count(m);
+  if (!m->rho_in) return TOPO_ERR_NO_DENSITY;
+  if (!m->tr_rho_n) CKS(dalloc(m, &m->tr_rho_n, nn));
+  LK(m, launch_nodal_density(m->rho_in, m->tr_rho_n, m->d, m->prm.h, m->stream));
+  return TOPO_OK;
+}
+
+// iso-surface of a nodal field into tr_tris / tr_off / tr_n
+static topo_status extract_impl(topo_mesh* m, const double* f, double level, bool above) {
+  cudaStream_t s = m->stream;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  if (!m->tr_counts) CKS(dalloc(m, &m->tr_counts, ne));
+  if (!m->tr_off) CKS(dalloc(m, &m->tr_off, ne + 1));
+  if (!m->tr_scratch) CKS(dalloc(m, &m->tr_scratch, scan_scratch_count(ne)));
+  LK(m, launch_mt_count(f, m->tr_counts, m->tr_off, m->tr_scratch, m->d, level, above, m->prm.h,
+                        s));
+  long long n = 0;
+  CK(cudaMemcpyAsync(&n, m->tr_off + ne, sizeof(n), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (n > m->tr_cap) {
+    if (m->tr_tris) CK(cudaFree(m->tr_tris));
+    m->tr_tris = nullptr;
+    m->tr_cap = 0;
+    const long long cap = n + n / 4 + 64;
+    CKS(dalloc(m, &m->tr_tris, 9 * cap));
+    m->tr_cap = cap;
+  }
+  if (n > 0)
+    LK(m, launch_mt_emit(f, m->tr_off, m->tr_tris, m->d, level, above, m->prm.h, s));
+  m->tr_n = n;
+  return TOPO_OK;
+}
+
+topo_status topo_nodal_density(topo_mesh* m, double* rho_n, size_t n_nodes, int on_device) {
+  if (!m || !rho_n) return TOPO_ERR_INVALID;
+  const long long nn = node_count(m);
+  if ((long long)n_nodes != nn) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CKS(nodal_density_impl(m));
+  CK(cudaMemcpyAsync(rho_n, m->tr_rho_n, nn * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_levelset_from_density(topo_mesh* m, double rho_t, long long* n_triangles) {
+  if (n_triangles) *n_triangles = 0;
+  if (!m || !(rho_t > 0.0 && rho_t < 1.0)) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  const long long nn = node_count(m);
+  CKS(nodal_density_impl(m));
+  CKS(extract_impl(m, m->tr_rho_n, rho_t, true));
+  if (n_triangles) *n_triangles = m->tr_n;
+  if (m->tr_n == 0) return TOPO_ERR_INVALID;  // no boundary at rho_t: no distance to it
+  if (!m->phi_in) CKS(dalloc(m, &m->phi_in, nn));
+  LK(m, launch_sdf(m->tr_tris, m->tr_off, m->tr_rho_n, rho_t, m->phi_in, m->d, m->prm.h,
+                   m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  m->ls_ready = false;  // moduli still come from the densities until topo_set_levelset
+  return TOPO_OK;
+}
+
+topo_status topo_extract_levelset_surface(topo_mesh* m, long long* n_triangles) {
+  if (n_triangles) *n_triangles = 0;
+  if (!m || !m->phi_in) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CKS(extract_impl(m, m->phi_in, 0.0, false));
+  if (n_triangles) *n_triangles = m->tr_n;
+  return TOPO_OK;
+}
+
+topo_status topo_get_surface(topo_mesh* m, double* tri, size_t max_triangles, int on_device,
+                             long long* n_triangles) {
+  if (!m || (!tri && max_triangles)) return TOPO_ERR_INVALID;
+  if (n_triangles) *n_triangles = m->tr_n;
+  if ((long long)max_triangles < m->tr_n) return TOPO_ERR_INVALID;
+  if (m->tr_n == 0) return TOPO_OK;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CK(cudaMemcpyAsync(tri, m->tr_tris, 9 * m->tr_n * sizeof(double),
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  if (!on_device) CK(cudaStreamSynchronize(m->stream));
   return TOPO_OK;
 }
 

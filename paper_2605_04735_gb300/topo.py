@@ -102,6 +102,10 @@ def lib():
             "topo_hilbertian_solve": (i, [vp, d, vp, vp, sz, i, d, i, C.POINTER(i)]),
             "topo_hj_evolve": (i, [vp, vp, sz, i, d, i, C.POINTER(d)]),
             "topo_reinit": (i, [vp, d, d, i, C.POINTER(i)]),
+            "topo_nodal_density": (i, [vp, vp, sz, i]),
+            "topo_levelset_from_density": (i, [vp, d, C.POINTER(C.c_longlong)]),
+            "topo_extract_levelset_surface": (i, [vp, C.POINTER(C.c_longlong)]),
+            "topo_get_surface": (i, [vp, vp, sz, i, C.POINTER(C.c_longlong)]),
             "topo_set_operator": (i, [vp, i]),
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
@@ -342,6 +346,37 @@ class Mesh:
         _check(lib().topo_hj_evolve(self._h, p, n, dev, gamma, steps, C.byref(dt)),
                "topo_hj_evolve")
         return dt.value
+
+    def nodal_density(self, out=None):
+        """Nodal densities of the current element densities (Eqs. (25)-(27))."""
+        if out is None:
+            out = np.empty(self.n_nodes, np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_nodal_density(self._h, p, n, dev), "topo_nodal_density")
+        return out
+
+    def levelset_from_density(self, rho_t=0.5) -> int:
+        """SIMP -> level set: nodal densities, iso-surface, signed distance
+        (Eqs. (25)-(30)) into the mesh's level set; returns the triangle count."""
+        n = C.c_longlong()
+        _check(lib().topo_levelset_from_density(self._h, rho_t, C.byref(n)),
+               "topo_levelset_from_density")
+        return n.value
+
+    def extract_levelset_surface(self) -> int:
+        n = C.c_longlong()
+        _check(lib().topo_extract_levelset_surface(self._h, C.byref(n)),
+               "topo_extract_levelset_surface")
+        return n.value
+
+    def surface(self):
+        """The last extracted triangle soup, (n, 3, 3) float64."""
+        n = C.c_longlong()
+        lib().topo_get_surface(self._h, None, 0, 0, C.byref(n))
+        out = np.empty((n.value, 3, 3), np.float64)
+        _check(lib().topo_get_surface(self._h, out.ctypes.data if n.value else None, n.value, 0,
+                                      C.byref(n)), "topo_get_surface")
+        return out
 
     def reinit(self, gamma=0.5, tol=1e-4, max_steps=500) -> int:
         """Reinitialise the mesh's level set (Eqs. (23), (24)); returns the steps taken."""
