@@ -272,6 +272,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="one mesh group solved as a batch instead of independent meshes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -301,10 +303,15 @@ def main():
     rho_dev = [torch.from_numpy(r).cuda() for r in rhos_np]
     dc_dev = [torch.empty(w.n_elem, dtype=torch.float64, device="cuda") for _ in range(B)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
-    meshes = [topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) for _ in range(B)]
+    opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
+    # independent meshes on their own streams, or (--batched) one mesh group
+    # that solve_many runs as one batch (one launch per step for all designs)
+    if not args.batched:
+        meshes = [topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) for _ in range(B)]
+    else:
+        meshes = topo.create_batch(B, w.nx, w.ny, w.nz, w.bc, w.load, stream=stream, opts=opts)
     for m in meshes:
         m.set_operator(args.operator)
-    opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
 
     def step_batch(rhos, dcs, opt):
         for m, r in zip(meshes, rhos):

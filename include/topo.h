@@ -160,6 +160,20 @@ void topo_default_opts(topo_solve_opts* o);
 topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
                              void* stream, topo_mesh** out);
 
+/* Create a group of n_designs (1..1024) meshes of one grid, BC, load and
+ * material whose solve state (vectors, scalars and a multigrid hierarchy built
+ * now with gmg_levels / smooth_degree as in topo_solve_opts) shares one device
+ * arena, design b at a fixed stride from design 0.  Each out[b] is an ordinary
+ * mesh (every call works on it, topo_free frees it; the arena goes with the
+ * last one).  topo_solve_many on exactly the group's meshes (any order), with
+ * FP32 precision, the multigrid preconditioner and the group's gmg_levels and
+ * smooth_degree, solves them as one batch: one kernel launch per step for all
+ * designs, FP64 refinement in lockstep (a design that has converged sits out).
+ * Results equal the one-at-a-time solves up to FP rounding order. */
+topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
+                              void* stream, int n_designs, int gmg_levels, int smooth_degree,
+                              topo_mesh** out);
+
 /* Set element densities rho (n_elem float32 values in [0, 1], element
  * order) and derive E_e by Eq. (1).  NaN/Inf or values outside [0, 1] give
  * TOPO_ERR_NAN (checked on the device; the call synchronises).  Invalidates
@@ -175,7 +189,8 @@ topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_inf
 
 /* Solve n distinct meshes at once (same options; NULL = defaults): each
  * mesh runs on its own stream and one host thread advances all of them, so
- * their kernels overlap on the GPU (batched / continuous solving).  infos:
+ * their kernels overlap on the GPU (batched / continuous solving); the meshes
+ * of one group (topo_create_batch) run as one batch instead.  infos:
  * NULL or n entries, each filled as by topo_solve.  Returns TOPO_OK if every
  * solve succeeded, else the first failing status (see infos for each);
  * TOPO_ERR_INVALID if a mesh appears twice.  Blocks until all are done. */

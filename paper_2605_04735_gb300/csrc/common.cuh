@@ -118,7 +118,28 @@ struct PcgScalars {
   int done;       // 1: converged or stopped; every loop kernel returns at once
   int status;     // 0 ok, 1 hit max_iter, 2 breakdown / non-finite
   unsigned counter[8];  // last-block counters of the reductions (reset by the last block)
+  // per-design settings of the next inner solve, written by the host for
+  // batched solves (FIN_INIT with a negative launch tolerance reads rtol2_next;
+  // rtol2_next >= 1 finishes the inner solve at once: the design sits out)
+  double rtol2_next;
+  int max_iter_next;
+  int pad_;
 };
+
+// A batch of designs with identical grids whose buffers sit at a fixed byte
+// stride S from design 0's (the designs of a mesh group share one arena):
+// a kernel launched for nb designs offsets every pointer by design * S.
+struct Bat {
+  int nb = 1;
+  long long S = 0;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ T* bshift(T* p, long long off) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<char*>(const_cast<void*>(
+                 static_cast<const void*>(p))) + off)
+           : p;
+}
 
 enum FinalizeOp {
   FIN_NONE = 0,
@@ -138,7 +159,13 @@ struct Red {
   PcgScalars* sc;
   int slot;           // which counter
   int op;             // FinalizeOp
-  double rtol2;       // FIN_INIT: relative tolerance squared
+  double rtol2;       // FIN_INIT: relative tolerance squared (< 0: sc->rtol2_next)
+  __host__ __device__ Red shifted(long long off) const {
+    Red r = *this;
+    r.partials = bshift(partials, off);
+    r.sc = bshift(sc, off);
+    return r;
+  }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -180,13 +207,14 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
       break;
     }
     case FIN_INIT: {
+      const double rt2 = (red.rtol2 >= 0.0) ? red.rtol2 : s->rtol2_next;
       s->rz = tot[0];
       s->rr = tot[nv - 1];
       s->rr0 = tot[nv - 1];
-      s->tol2 = red.rtol2 * tot[nv - 1];
+      s->tol2 = rt2 * tot[nv - 1];
       s->iter = 0;
       s->status = 0;
-      s->done = (tot[nv - 1] <= 0.0) ? 1 : 0;
+      s->done = (tot[nv - 1] <= 0.0 || rt2 >= 1.0) ? 1 : 0;
       break;
     }
     case FIN_AUX:
@@ -219,16 +247,17 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
 // finalisation: every block writes its partials, the last block to arrive
 // sums them in block order (fixed order => bitwise reproducible) and calls
 // finalize().  Must be called by every thread of every block.
+// Block reduction over the blocks of one design: `bid` in [0, nblocks) is the
+// block's number among the design's blocks (the whole grid for one design).
 template <int NV>
-__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const Red& red) {
+__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const Red& red, int bid,
+                                                int nblocks) {
   __shared__ double sh[NV][32];
   __shared__ bool last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int warp = tid >> 5;
   const int nthreads = blockDim.x * blockDim.y * blockDim.z;
   const int nwarps = (nthreads + 31) >> 5;
-  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     double w = warp_sum(v[q]);
@@ -276,6 +305,12 @@ __device__ __forceinline__ void reduce_finalize(double (&v)[NV], const Red& red)
     red.sc->counter[red.slot] = 0u;
     __threadfence();
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void reduce_finalize(double (&v)[NV], const Red& red) {
+  reduce_finalize<NV>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                      gridDim.x * gridDim.y * gridDim.z);
 }
 
 }  // namespace topo

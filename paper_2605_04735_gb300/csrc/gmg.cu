@@ -31,11 +31,19 @@ inline int grid1d(long long n) {
 // d_k = c1_k d_{k-1} + c2_k D^-1 r_k, r_k = r_{k-1} - A d_{k-1}, x += d_k.
 
 // pre-smoothing start from x = 0: r = b, d0 = D^-1 b / theta, x = d0
+// (all kernels below: blockIdx.y = design, buffers at design * S bytes)
 __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
                             float* __restrict__ d0, float* __restrict__ x,
                             const float* __restrict__ dinv, long long n4, float inv_theta,
-                            const int* __restrict__ done) {
+                            const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  b = bshift(b, off);
+  r = bshift(r, off);
+  d0 = bshift(d0, off);
+  x = bshift(x, off);
+  dinv = bshift(dinv, off);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
     const float4 bv = reinterpret_cast<const float4*>(b)[q];
@@ -52,8 +60,12 @@ __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
 }
 
 __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long long n4,
-                        const int* __restrict__ done) {
+                        const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  x = bshift(x, off);
+  d = bshift(d, off);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
     float4 xv = reinterpret_cast<float4*>(x)[q];
@@ -76,6 +88,10 @@ struct EpiChebStep {
   const float* dinv;
   float c1, c2;
   int add_prev;
+  __device__ EpiChebStep shifted(long long off) const {
+    return EpiChebStep{bshift(r, off), bshift(dn, off), bshift(x, off), bshift(dinv, off),
+                       c1, c2, add_prev};
+  }
   template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&ctr)[3],
@@ -98,6 +114,7 @@ struct EpiChebStep {
 struct EpiChebLast {
   static constexpr bool kReduce = false;
   float* r;
+  __device__ EpiChebLast shifted(long long off) const { return EpiChebLast{bshift(r, off)}; }
   template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&)[3],
@@ -117,6 +134,10 @@ struct EpiChebResid {
   float* d0;
   const float* dinv;
   float inv_theta;
+  __device__ EpiChebResid shifted(long long off) const {
+    return EpiChebResid{bshift(b, off), bshift(r, off), bshift(d0, off), bshift(dinv, off),
+                        inv_theta};
+  }
   template <class DD>
   __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
                                               const float (&acc)[3], const float (&)[3],
@@ -137,7 +158,9 @@ struct EpiChebResid {
 // doubled edge (k0 of an element of edge 2h is 2h times the unit k0);
 // children beyond an odd fine grid are ghosts with E = 0
 __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* __restrict__ Ec,
-                            const Dims dc) {
+                            const Dims dc, long long S) {
+  Ef = bshift(Ef, blockIdx.y * S);
+  Ec = bshift(Ec, blockIdx.y * S);
   const long long n = (long long)dc.nx * dc.ny * dc.nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -161,8 +184,12 @@ __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* 
 // b_c = P^T r_f for trilinear P: coarse node (I,J,K) sits on fine node
 // (2I,2J,2K) and collects fine neighbours with weights 1, 1/2 per axis offset
 __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* __restrict__ bc,
-                           const Dims dc, const int* __restrict__ done) {
+                           const Dims dc, const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  rf = bshift(rf, off);
+  bc = bshift(bc, off);
   const long long nn = (long long)(dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
@@ -197,8 +224,12 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
 // x_f += P x_c (trilinear interpolation from the coarse nodes around each
 // fine node), fixed fine DOFs untouched
 __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float* __restrict__ xf,
-                              const Dims df, const int* __restrict__ done) {
+                              const Dims df, const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  xc = bshift(xc, off);
+  xf = bshift(xf, off);
   const long long nn = (long long)(df.nx + 1) * (df.ny + 1) * (df.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
@@ -230,7 +261,9 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
 // per thread, summed over the elements shared by the two nodes (a gather:
 // deterministic, no atomics)
 __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const float* __restrict__ E,
-                                 const __grid_constant__ K0<double> k0) {
+                                 const __grid_constant__ K0<double> k0, long long S) {
+  A = bshift(A, blockIdx.y * S);
+  E = bshift(E, blockIdx.y * S);
   const int n = 3 * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -267,7 +300,10 @@ __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const flo
 // when many meshes set up concurrently on their own streams.)  The chain of
 // n launches is captured once per hierarchy as a CUDA graph.
 __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
-                          double* __restrict__ col) {
+                          double* __restrict__ col, long long S) {
+  A = bshift(A, blockIdx.y * S);
+  row = bshift(row, blockIdx.y * S);
+  col = bshift(col, blockIdx.y * S);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     row[t] = A[t];
@@ -277,7 +313,13 @@ __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restric
 
 __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
                           const double* __restrict__ colk, double* __restrict__ rown,
-                          double* __restrict__ coln) {
+                          double* __restrict__ coln, long long S) {
+  const long long off = blockIdx.y * S;
+  A = bshift(A, off);
+  rowk = bshift(rowk, off);
+  colk = bshift(colk, off);
+  rown = bshift(rown, off);
+  coln = bshift(coln, off);
   const long long nn = (long long)n * n;
   const double p = 1.0 / rowk[k];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -299,8 +341,12 @@ __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __
 }
 
 __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, double* __restrict__ bd,
-                                const int* __restrict__ done) {
+                                const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  b = bshift(b, off);
+  bd = bshift(bd, off);
   const int nn = (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
     const int i = n % (d.nx + 1), j = (n / (d.nx + 1)) % (d.ny + 1),
@@ -314,8 +360,13 @@ __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, doubl
 // x = A^-1 b, one warp per row (A^-1 symmetric, rows read coalesced), FP64
 __global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __restrict__ bd,
                                int n, float* __restrict__ x, const Dims d,
-                               const int* __restrict__ done) {
+                               const int* __restrict__ done, long long S) {
+  const long long off = blockIdx.y * S;
+  done = bshift(done, off);
   if (*done) return;
+  Ainv = bshift(Ainv, off);
+  bd = bshift(bd, off);
+  x = bshift(x, off);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= n) return;
@@ -335,8 +386,11 @@ __global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __
 // cudaMemset would go to the legacy default stream, which does not order
 // against the mesh's non-blocking stream).
 template <typename T>
-cudaError_t dmalloc(T** p, long long count, long long* bytes, cudaStream_t s) {
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
+cudaError_t dmalloc(T** p, long long count, long long* bytes, cudaStream_t s,
+                    const GmgAlloc* alloc) {
+  cudaError_t e = alloc ? alloc->fn(alloc->ctx, reinterpret_cast<void**>(p),
+                                    (size_t)count * sizeof(T))
+                        : cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
   if (e != cudaSuccess) return e;
   *bytes += count * (long long)sizeof(T);
   return cudaMemsetAsync(*p, 0, (size_t)count * sizeof(T), s);
@@ -431,7 +485,8 @@ long long gmg_footprint(const Dims& fine, int max_levels) {
 }
 
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
-                       cudaStream_t s) {
+                       cudaStream_t s, const GmgAlloc* alloc) {
+  g.arena = (alloc != nullptr);
   g.degree = std::max(1, degree);
   g.lam_max = lam_max;
   g.lv.clear();
@@ -446,41 +501,45 @@ cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, dou
   if ((long long)g.nc * g.nc > (1LL << 27)) return cudaErrorInvalidValue;  // > 1 GB inverse
   for (size_t l = 0; l < g.lv.size(); ++l) {
     GmgLevel& L = g.lv[l];
-    GCK(dmalloc(&L.r, L.nvec, &g.bytes, s));
-    GCK(dmalloc(&L.dv[0], L.nvec, &g.bytes, s));
-    GCK(dmalloc(&L.dv[1], L.nvec, &g.bytes, s));
+    GCK(dmalloc(&L.r, L.nvec, &g.bytes, s, alloc));
+    GCK(dmalloc(&L.dv[0], L.nvec, &g.bytes, s, alloc));
+    GCK(dmalloc(&L.dv[1], L.nvec, &g.bytes, s, alloc));
     if (l > 0) {
-      GCK(dmalloc(&L.E, L.d.ecount, &g.bytes, s));
-      GCK(dmalloc(&L.dinv, L.nvec, &g.bytes, s));
-      GCK(dmalloc(&L.b, L.nvec, &g.bytes, s));
-      GCK(dmalloc(&L.x, L.nvec, &g.bytes, s));
+      GCK(dmalloc(&L.E, L.d.ecount, &g.bytes, s, alloc));
+      GCK(dmalloc(&L.dinv, L.nvec, &g.bytes, s, alloc));
+      GCK(dmalloc(&L.b, L.nvec, &g.bytes, s, alloc));
+      GCK(dmalloc(&L.x, L.nvec, &g.bytes, s, alloc));
     }
   }
-  GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes, s));
-  GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes, s));
-  GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes, s));
+  GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes, s, alloc));
+  GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes, s, alloc));
+  GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes, s, alloc));
   g.ready = false;
   return cudaSuccess;
 }
 
 cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
-                      const K0<double>& k0d, cudaStream_t s, long long* launches) {
+                      const K0<double>& k0d, cudaStream_t s, long long* launches, const Bat& bt) {
   g.lv[0].E = const_cast<float*>(E0);
   g.lv[0].dinv = const_cast<float*>(dinv0);
   for (size_t l = 1; l < g.lv.size(); ++l) {
     const GmgLevel& F = g.lv[l - 1];
     GmgLevel& C = g.lv[l];
     const long long ne = (long long)C.d.nx * C.d.ny * C.d.nz;
-    k_coarsen_E<<<grid1d(ne), kPT, 0, s>>>(F.E, F.d, C.E, C.d);
+    k_coarsen_E<<<dim3(grid1d(ne), bt.nb), kPT, 0, s>>>(F.E, F.d, C.E, C.d, bt.S);
     GCK(cudaGetLastError());
-    GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s));
+    GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s, bt));
     *launches += 2;
   }
   const GmgLevel& Lc = g.lv.back();
   const long long nn = (long long)g.nc * g.nc;
-  k_dense_assemble<<<grid1d(nn), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d);
+  k_dense_assemble<<<dim3(grid1d(nn), bt.nb), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d, bt.S);
   GCK(cudaGetLastError());
-  // the pivot chain, captured once as a graph and replayed per density
+  // the pivot chain, captured once per batch shape as a graph and replayed per density
+  if (g.gj_exec && (g.gj_nb != bt.nb || g.gj_S != bt.S)) {
+    cudaGraphExecDestroy(g.gj_exec);
+    g.gj_exec = nullptr;
+  }
   if (!g.gj_exec) {
     cudaStream_t cs = nullptr;
     GCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -488,15 +547,19 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
-      k_gj_seed<<<(g.nc + kPT - 1) / kPT, kPT, 0, cs>>>(g.Ainv, g.nc, buf[0][0], buf[0][1]);
+      k_gj_seed<<<dim3((g.nc + kPT - 1) / kPT, bt.nb), kPT, 0, cs>>>(g.Ainv, g.nc, buf[0][0],
+                                                                      buf[0][1], bt.S);
       for (int k = 0; k < g.nc; ++k) {
         double** cur = buf[k & 1];
         double** nxt = buf[(k + 1) & 1];
-        k_gj_step<<<grid1d(nn), kPT, 0, cs>>>(g.Ainv, g.nc, k, cur[0], cur[1], nxt[0], nxt[1]);
+        k_gj_step<<<dim3(grid1d(nn), bt.nb), kPT, 0, cs>>>(g.Ainv, g.nc, k, cur[0], cur[1],
+                                                           nxt[0], nxt[1], bt.S);
       }
       e = cudaStreamEndCapture(cs, &graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g.gj_exec, graph, 0);
+    g.gj_nb = bt.nb;
+    g.gj_S = bt.S;
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cs);
     GCK(e);
@@ -510,15 +573,16 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 template <class Epi>
 cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
                      const ModalCoef<float>* mcf, const Epi& ep, const int* done, int* errflag,
-                     cudaStream_t s) {
+                     cudaStream_t s, const Bat& bt) {
   Red nored{};
-  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, nored, done, errflag, s);
+  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, nored, done, errflag, s, bt);
+  if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
   return launch_stencil<float>(x, L.E, L.d, k0f, ep, nored, done, errflag, s);
 }
 
 cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
-                       cudaStream_t s, long long* launches) {
+                       cudaStream_t s, long long* launches, const Bat& bt) {
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
@@ -528,19 +592,19 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   for (int l = 0; l < nl - 1; ++l) {
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
-    k_cheb_init<<<grid1d(n4), kPT, 0, s>>>(B(l), L.r, L.dv[0], X(l), L.dinv, n4, cc.inv_theta,
-                                          done);
+    k_cheb_init<<<dim3(grid1d(n4), bt.nb), kPT, 0, s>>>(B(l), L.r, L.dv[0], X(l), L.dinv, n4,
+                                                        cc.inv_theta, done, bt.S);
     GCK(cudaGetLastError());
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
-      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s));
+      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
       ++*launches;
     }
-    GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s));
+    GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s, bt));
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
-    k_restrict<<<grid1d(nnc), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done);
+    k_restrict<<<dim3(grid1d(nnc), bt.nb), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done, bt.S);
     GCK(cudaGetLastError());
     *launches += 2;
   }
@@ -548,11 +612,12 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   {
     const GmgLevel& C = g.lv[nl - 1];
     const int nnc = (C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
-    k_coarse_gather<<<(nnc + kPT - 1) / kPT, kPT, 0, s>>>(B(nl - 1), C.d, g.bd, done);
+    k_coarse_gather<<<dim3((nnc + kPT - 1) / kPT, bt.nb), kPT, 0, s>>>(B(nl - 1), C.d, g.bd, done,
+                                                                      bt.S);
     GCK(cudaGetLastError());
     const long long thr = 32LL * g.nc;
-    k_coarse_apply<<<(int)((thr + kPT - 1) / kPT), kPT, 0, s>>>(g.Ainv, g.bd, g.nc, X(nl - 1),
-                                                              C.d, done);
+    k_coarse_apply<<<dim3((int)((thr + kPT - 1) / kPT), bt.nb), kPT, 0, s>>>(
+        g.Ainv, g.bd, g.nc, X(nl - 1), C.d, done, bt.S);
     GCK(cudaGetLastError());
     *launches += 2;
   }
@@ -561,18 +626,19 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
-    k_prolong_add<<<grid1d(nnf), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done);
+    k_prolong_add<<<dim3(grid1d(nnf), bt.nb), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done, bt.S);
     GCK(cudaGetLastError());
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
-    GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s));
+    GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
-      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s));
+      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
       ++*launches;
     }
     if (m == 1) {
-      k_axpy1<<<grid1d(L.nvec / 4), kPT, 0, s>>>(X(l), L.dv[0], L.nvec / 4, done);
+      k_axpy1<<<dim3(grid1d(L.nvec / 4), bt.nb), kPT, 0, s>>>(X(l), L.dv[0], L.nvec / 4, done,
+                                                              bt.S);
       GCK(cudaGetLastError());
       ++*launches;
     }
@@ -583,6 +649,10 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
 void gmg_free(Gmg& g) {
   if (g.gj_exec) cudaGraphExecDestroy(g.gj_exec);
   g.gj_exec = nullptr;
+  if (g.arena) {  // the buffers belong to the mesh group's arena
+    g.lv.clear();
+    return;
+  }
   for (size_t l = 0; l < g.lv.size(); ++l) {
     GmgLevel& L = g.lv[l];
     cudaFree(L.r);

@@ -38,8 +38,17 @@ struct Gmg {
   double* side = nullptr;    // 4 * nc (Gauss-Jordan pivot row/column, ping-pong)
   double* bd = nullptr;      // nc
   cudaGraphExec_t gj_exec = nullptr;  // captured Gauss-Jordan pivot chain
+  int gj_nb = 0;             // ... for this many designs
+  long long gj_S = 0;        // ... at this design stride
   long long bytes = 0;
   bool ready = false;        // set up for the current densities
+  bool arena = false;        // buffers come from a mesh group's arena (not freed here)
+};
+
+// Optional allocator for the hierarchy's buffers (a mesh group's arena).
+struct GmgAlloc {
+  void* ctx;
+  cudaError_t (*fn)(void* ctx, void** p, size_t bytes);
 };
 
 // The level grids a fine grid coarsens to, and the bytes a hierarchy holds.
@@ -48,16 +57,19 @@ long long gmg_footprint(const Dims& fine, int max_levels);
 // Choose levels for a fine grid and allocate them (fine-level E/dinv/b/x are
 // bound later, per call).  max_levels <= 0: automatic.
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
-                       cudaStream_t s);
+                       cudaStream_t s, const GmgAlloc* alloc = nullptr);
 // Per-density setup: coarse moduli, Jacobi diagonals, coarsest inverse.
+// bt: the designs of a mesh group (pointers are design 0's; each design's
+// hierarchy sits at the group's design stride from design 0's).
 cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
-                      const K0<double>& k0d, cudaStream_t s, long long* launches);
+                      const K0<double>& k0d, cudaStream_t s, long long* launches,
+                      const Bat& bt = Bat{});
 // x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
 // when *done is set.
 // mcf != nullptr: smoother passes use the modal operator kernel
 cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
-                       cudaStream_t s, long long* launches);
+                       cudaStream_t s, long long* launches, const Bat& bt = Bat{});
 void gmg_free(Gmg& g);
 // lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
 double k0_jacobi_bound(const double* k0);

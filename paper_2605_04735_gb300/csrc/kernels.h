@@ -22,42 +22,49 @@ enum ApplyMode {
   APPLY_RESID = 2   // y = f - A x (0 on fixed DOFs), reduce y . y
 };
 // errflag: set to 1 by the kernel if a bounded device-side wait ran out.
-// mc != nullptr: element-centric modal kernel; nullptr: node-centric gather.
+// mc != nullptr: element-centric modal kernel; nullptr: node-centric gather
+// (one design only).  bt: designs of a mesh group (all pointers are design 0's).
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
                          const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
-                         int* errflag, cudaStream_t s);
+                         int* errflag, cudaStream_t s, const Bat& bt = Bat{});
 // modal coefficients of k0 (returns false if k0 does not have the expected pattern)
 bool build_modal_coef(const double* k0, ModalCoef<double>* out);
 template <typename T>
-cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s);
+cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s,
+                            const Bat& bt = Bat{});
 
 // ---- vectors (vectors.cu) -----------------------------------------------
-cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s);
+// Every launcher takes the designs of a mesh group (default: one design).
+// max_iter < 0: each design's max_iter_next
+cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s,
+                                const Bat& bt = Bat{});
 // n = total entries of one vector (3 * comp); all arrays 16-byte aligned
 template <typename T>
 cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, long long n,
-                            const Red& red, bool jacobi, cudaStream_t s);
+                            const Red& red, bool jacobi, cudaStream_t s, const Bat& bt = Bat{});
 template <typename T>
 cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
-                              const Red& red, bool jacobi, cudaStream_t s);
+                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt = Bat{});
 template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const Bat& bt = Bat{});
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s);
+cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s,
+                       const Bat& bt = Bat{});
 template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
-                        cudaStream_t s);
+                        cudaStream_t s, const Bat& bt = Bat{});
 // b32 = float(r64 * scale), scale = 1 / sqrt(sc->aux[0]) read on the device
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const Bat& bt = Bat{});
 // u64 += scale * x, scale = sqrt(sc->aux[0]) read on the device (T = float or double)
 template <typename T>
 cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgScalars* sc,
-                              bool scaled, cudaStream_t s);
+                              bool scaled, cudaStream_t s, const Bat& bt = Bat{});
 template <typename T>
-cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s);
+cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
+                             const Bat& bt = Bat{});
 
 // ---- mesh data (meshdata.cu) -------------------------------------------
 // rho (dense element order) -> ghosted rho32, E32, E64; counts bad values into *bad

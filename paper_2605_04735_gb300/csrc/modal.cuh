@@ -187,13 +187,22 @@ struct __align__(128) ModalStage {
   alignas(128) float elem[kMElem];
 };
 
+// Grid: (x tiles, y tiles, zc z-chunks x designs); design b reads and writes
+// its own buffers at b * S bytes from design 0's (the TMA maps carry the
+// design as their outermost dimension).
 template <class Epi>
 __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
-                const Dims d, const __grid_constant__ ModalCoef<float> kc, const Epi epi,
-                const Red red, const int zchunk, const int* __restrict__ done,
-                int* __restrict__ errflag) {
-  if (done != nullptr && *done) return;  // uniform over the grid
+                const Dims d, const __grid_constant__ ModalCoef<float> kc, const Epi epi0,
+                const Red red0, const int zchunk, const int zc, const long long S,
+                const int* __restrict__ done, int* __restrict__ errflag) {
+  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
+  const long long off = design * S;
+  done = bshift(done, off);
+  errflag = bshift(errflag, off);
+  if (done != nullptr && *done) return;  // uniform over the design's blocks
+  const Epi epi = epi0.shifted(off);
+  const Red red = red0.shifted(off);
   __shared__ ModalStage st[kModalStages];
   __shared__ uint64_t bar[kModalStages];
   __shared__ float xch[2][kModalTY][kModalTX][3];
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
   const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
   const int ox = x0 - bx;
-  const int kb = blockIdx.z * zchunk;
+  const int kb = chunk * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const int nst = (ke - kb) + 2;  // stage t: node plane kb-2+t+1, element layer kb-2+t
   if (tid == 0) {
@@ -216,8 +225,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   auto issue = [&](int t) {
     const int slot = t % kModalStages;
     mbar_arrive_expect_tx(&bar[slot], kMStageTx);
-    tma_load_4d(st[slot].node, &xmap, &bar[slot], bx, y0, kb + t, 0);
-    tma_load_3d(st[slot].elem, &emap, &bar[slot], bx, y0, kb - 1 + t);
+    tma_load_5d(st[slot].node, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
+    tma_load_4d(st[slot].elem, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
   };
   if (tid == 0)
     for (int t = 0; t < kModalStages && t < nst; ++t) issue(t);
@@ -259,7 +268,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
-    reduce_finalize<1>(v, red);
+    reduce_finalize<1>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * chunk),
+                       gridDim.x * gridDim.y * zc);
   }
 }
 
@@ -268,14 +278,22 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 template <typename T, class Epi>
 __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_plain(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
-                  const __grid_constant__ ModalCoef<T> kc, const Epi epi, const Red red,
-                  const int zchunk, const int* __restrict__ done) {
+                  const __grid_constant__ ModalCoef<T> kc, const Epi epi0, const Red red0,
+                  const int zchunk, const int zc, const long long S,
+                  const int* __restrict__ done) {
+  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
+  const long long off = design * S;
+  done = bshift(done, off);
   if (done != nullptr && *done) return;
+  x = bshift(x, off);
+  E = bshift(E, off);
+  const Epi epi = epi0.shifted(off);
+  const Red red = red0.shifted(off);
   __shared__ T xch[2][kModalTY][kModalTX][3];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * kModalOwnY;
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
-  const int kb = blockIdx.z * zchunk;
+  const int kb = chunk * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
   auto node_val = [&](int i, int j, int k, int c) -> T {
@@ -310,7 +328,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
-    reduce_finalize<1>(v, red);
+    reduce_finalize<1>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * chunk),
+                       gridDim.x * gridDim.y * zc);
   }
 }
 
@@ -327,25 +346,26 @@ inline int modal_zchunk(const Dims& d) {
   return z;
 }
 
-bool modal_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                 CUtensorMap* emap);
 
 template <typename T, class Epi>
 cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                                 const Epi& epi, const Red& red, const int* done, int* errflag,
-                                cudaStream_t s) {
+                                cudaStream_t s, const Bat& bt) {
   const int z = modal_zchunk(d);
+  const int zc = (d.nz + z) / z;
   dim3 block(kModalTX, kModalTY, 1);
-  dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY,
-            (d.nz + z) / z);
+  dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY, zc * bt.nb);
   if constexpr (sizeof(T) == 4) {
     CUtensorMap xm, em;
-    if (modal_maps(x, E, d, &xm, &em)) {
-      k_modal_tma<Epi><<<grid, block, 0, s>>>(xm, em, d, kc, epi, red, z, done, errflag);
+    if (modal_maps(x, E, d, bt, &xm, &em)) {
+      k_modal_tma<Epi><<<grid, block, 0, s>>>(xm, em, d, kc, epi, red, z, zc, bt.S, done,
+                                              errflag);
       return cudaGetLastError();
     }
   }
-  k_modal_plain<T, Epi><<<grid, block, 0, s>>>(x, E, d, kc, epi, red, z, done);
+  k_modal_plain<T, Epi><<<grid, block, 0, s>>>(x, E, d, kc, epi, red, z, zc, bt.S, done);
   return cudaGetLastError();
 }
 

@@ -170,9 +170,17 @@ constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPair
 template <class Epi>
 __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     k_modal_pair(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
-                 const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi, const Red red,
-                 const int zchunk, const int* __restrict__ done, int* __restrict__ errflag) {
-  if (done != nullptr && *done) return;  // uniform over the grid
+                 const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi0,
+                 const Red red0, const int zchunk, const int zc, const long long S,
+                 const int* __restrict__ done, int* __restrict__ errflag) {
+  // grid z: zc z-chunks x designs (see k_modal_tma)
+  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
+  const long long off = design * S;
+  done = bshift(done, off);
+  errflag = bshift(errflag, off);
+  if (done != nullptr && *done) return;  // uniform over the design's blocks
+  const Epi epi = epi0.shifted(off);
+  const Red red = red0.shifted(off);
   extern __shared__ __align__(128) unsigned char pair_dyn[];
   // TMA destinations on 128-byte boundaries whatever the dynamic window's offset
   unsigned char* pair_smem = pair_dyn + ((128u - (smem_u32(pair_dyn) & 127u)) & 127u);
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
   const int exA = x0 - 1 + tx, ey = y0 - 1 + ty;
   const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
   const int ox = x0 - bx;
-  const int kb = blockIdx.z * zchunk;
+  const int kb = chunk * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const int nst = (ke - kb) + 2;  // stage t: node plane kb-1+t, element layer kb-2+t
   if (tid == 0) {
@@ -201,8 +209,8 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     const int slot = t % kPairStages;
     float* s = stg + slot * kPStageFloats;
     mbar_arrive_expect_tx(&bar[slot], kPStageTx);
-    tma_load_4d(s, &xmap, &bar[slot], bx, y0, kb + t, 0);
-    tma_load_3d(s + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t);
+    tma_load_5d(s, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
+    tma_load_4d(s + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
   };
   if (tid == 0)
     for (int t = 0; t < kPairStages && t < nst; ++t) issue(t);
@@ -289,11 +297,12 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
-    reduce_finalize<1>(v, red);
+    reduce_finalize<1>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * chunk),
+                       gridDim.x * gridDim.y * zc);
   }
 }
 
-bool pair_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                CUtensorMap* emap);
 
 // z planes per CTA of the paired kernel: the chunk length that minimises
@@ -321,7 +330,7 @@ inline int pair_zchunk(const Dims& d) {
 template <class Epi>
 cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, const Dims& d,
                               const ModalCoef<float>& kc, const Epi& epi, const Red& red,
-                              const int* done, int* errflag, cudaStream_t s) {
+                              const int* done, int* errflag, cudaStream_t s, const Bat& bt) {
   static bool attr = false;  // per instantiation; setting it twice is harmless
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(k_modal_pair<Epi>,
@@ -331,10 +340,11 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
     attr = true;
   }
   const int z = pair_zchunk(d);
+  const int zc = (d.nz + z) / z;
   dim3 block(kPairTX, kPairTY, 1);
-  dim3 grid((d.nx + kPairOwnX) / kPairOwnX, (d.ny + kPairOwnY) / kPairOwnY, (d.nz + z) / z);
-  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, z, done,
-                                                   errflag);
+  dim3 grid((d.nx + kPairOwnX) / kPairOwnX, (d.ny + kPairOwnY) / kPairOwnY, zc * bt.nb);
+  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, z, zc, bt.S,
+                                                   done, errflag);
   return cudaGetLastError();
 }
 
@@ -350,14 +360,14 @@ constexpr int kPairAutoMinNx = 150;
 template <typename T, class Epi>
 cudaError_t launch_modal(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                          const Epi& epi, const Red& red, const int* done, int* errflag,
-                         cudaStream_t s) {
+                         cudaStream_t s, const Bat& bt = Bat{}) {
   if constexpr (sizeof(T) == 4) {
     CUtensorMap xm, em;
     const bool want = kc.form == 2 || (kc.form == 0 && d.nx >= kPairAutoMinNx);
-    if (want && pair_maps(x, E, d, &xm, &em))
-      return launch_modal_pair<Epi>(xm, em, d, kc, epi, red, done, errflag, s);
+    if (want && pair_maps(x, E, d, bt, &xm, &em))
+      return launch_modal_pair<Epi>(xm, em, d, kc, epi, red, done, errflag, s, bt);
   }
-  return launch_modal_single<T, Epi>(x, E, d, kc, epi, red, done, errflag, s);
+  return launch_modal_single<T, Epi>(x, E, d, kc, epi, red, done, errflag, s, bt);
 }
 
 }  // namespace topo

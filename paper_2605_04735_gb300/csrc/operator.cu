@@ -21,6 +21,7 @@ template <typename T, bool DOT>
 struct EpiApply {
   static constexpr bool kReduce = DOT;
   T* y;
+  __device__ EpiApply shifted(long long off) const { return EpiApply{bshift(y, off)}; }
   template <class DD>
   __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
                                           const T (&ctr)[3], const DD& d) const {
@@ -41,6 +42,9 @@ struct EpiResid {
   static constexpr bool kReduce = true;
   T* y;
   const T* f;
+  __device__ EpiResid shifted(long long off) const {
+    return EpiResid{bshift(y, off), bshift(f, off)};
+  }
   template <class DD>
   __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
                                           const T (&)[3], const DD& d) const {
@@ -59,10 +63,13 @@ struct EpiResid {
 // and 1 on fixed DOFs (and on nodes that touch no stiffness at all).
 template <typename T>
 __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const Dims d,
-                           const __grid_constant__ K0<T> k0) {
+                           const __grid_constant__ K0<T> k0, long long S) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+  const int design = blockIdx.z / (d.nz + 1);
+  const int k = blockIdx.z - design * (d.nz + 1);
+  dinv = bshift(dinv, design * S);
+  E = bshift(E, design * S);
   if (i > d.nx || j > d.ny) return;
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -87,17 +94,18 @@ __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const 
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
                          const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
-                         int* errflag, cudaStream_t s) {
+                         int* errflag, cudaStream_t s, const Bat& bt) {
   if (mc) {
     switch (mode) {
       case APPLY_PLAIN:
-        return launch_modal<T>(x, E, d, *mc, EpiApply<T, false>{y}, red, done, errflag, s);
+        return launch_modal<T>(x, E, d, *mc, EpiApply<T, false>{y}, red, done, errflag, s, bt);
       case APPLY_DOT:
-        return launch_modal<T>(x, E, d, *mc, EpiApply<T, true>{y}, red, done, errflag, s);
+        return launch_modal<T>(x, E, d, *mc, EpiApply<T, true>{y}, red, done, errflag, s, bt);
       default:
-        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s);
+        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s, bt);
     }
   }
+  if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
   switch (mode) {
     case APPLY_PLAIN:
       return launch_stencil<T>(x, E, d, k0, EpiApply<T, false>{y}, red, done, errflag, s);
@@ -109,20 +117,22 @@ cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d
 }
 
 template <typename T>
-cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s) {
+cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0, cudaStream_t s,
+                            const Bat& bt) {
   dim3 block(32, 4, 1);
-  dim3 grid((d.nx + 32) / 32, (d.ny + 4) / 4, d.nz + 1);
-  k_diag_inv<T><<<grid, block, 0, s>>>(dinv, E, d, k0);
+  dim3 grid((d.nx + 32) / 32, (d.ny + 4) / 4, (d.nz + 1) * bt.nb);
+  k_diag_inv<T><<<grid, block, 0, s>>>(dinv, E, d, k0, bt.S);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,
                                          const Dims&, const K0<float>&, const ModalCoef<float>*,
-                                         const Red&, int, const int*, int*, cudaStream_t);
+                                         const Red&, int, const int*, int*, cudaStream_t,
+                                         const Bat&);
 template cudaError_t launch_apply<double>(const double*, double*, const double*, const double*,
                                           const Dims&, const K0<double>&,
                                           const ModalCoef<double>*, const Red&, int, const int*,
-                                          int*, cudaStream_t);
+                                          int*, cudaStream_t, const Bat&);
 
 bool build_modal_coef(const double* k0, ModalCoef<double>* out) {
   // corner a of the local numbering -> binary index b = ax + 2 ay + 4 az
@@ -161,8 +171,8 @@ bool build_modal_coef(const double* k0, ModalCoef<double>* out) {
   return true;
 }
 template cudaError_t launch_diag_inv<float>(float*, const float*, const Dims&, const K0<float>&,
-                                            cudaStream_t);
+                                            cudaStream_t, const Bat&);
 template cudaError_t launch_diag_inv<double>(double*, const double*, const Dims&,
-                                             const K0<double>&, cudaStream_t);
+                                             const K0<double>&, cudaStream_t, const Bat&);
 
 }  // namespace topo

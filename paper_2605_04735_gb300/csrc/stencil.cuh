@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
     const int slot = s % kTmaStages;
     mbar_arrive_expect_tx(&bar[slot], kStageTx);
     // storage coordinates: +1 for the ghost layer in every direction
-    tma_load_4d(st[slot].node, &xmap, &bar[slot], i0, j0, kb + s, 0);
-    tma_load_3d(st[slot].elem, &emap, &bar[slot], i0, j0, kb - 1 + s);
+    tma_load_5d(st[slot].node, &xmap, &bar[slot], i0, j0, kb + s, 0, 0);
+    tma_load_4d(st[slot].elem, &emap, &bar[slot], i0, j0, kb - 1 + s, 0);
   };
   if (tid == 0)
     for (int s = 0; s < kTmaStages && s < nst; ++s) issue(s);

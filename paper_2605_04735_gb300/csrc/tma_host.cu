@@ -38,14 +38,21 @@ EncodeFn encoder() {
   return fn;
 }
 
-// base, kind, pitch, ny, nz, box width, box rows
-using Key = std::tuple<const void*, int, int, int, int, int, int>;
+// base, kind, pitch, ny, nz, box width, box rows, designs, design stride
+using Key = std::tuple<const void*, int, int, int, int, int, int, int, long long>;
 std::mutex g_mu;
 std::map<Key, CUtensorMap> g_cache;
 
-bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y,
+// kind 0: node vector (x, y, z, component, design); kind 1: element array
+// (x, y, z, design).  The design dimension has bt.nb entries bt.S bytes apart
+// (stride 16 bytes when there is one design: unused).
+bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y, const Bat& bt,
                 CUtensorMap* out) {
-  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz, box_x, box_y};
+  // one design: the natural size of the array (the dimension has one entry)
+  const long long natural = kind ? d.ecount * 4 : 3 * d.comp * 4;
+  const long long dstride = (bt.nb > 1) ? bt.S : natural;
+  if (bt.nb > 1 && (bt.S < natural || bt.S % 16 != 0)) return false;
+  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz, box_x, box_y, bt.nb, dstride};
   std::lock_guard<std::mutex> lock(g_mu);
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
@@ -54,18 +61,21 @@ bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y,
   }
   CUtensorMap m;
   bool ok;
-  if (kind == 0) {  // node vector: (x, y, z, component)
-    const uint64_t dims[4] = {(uint64_t)d.px, (uint64_t)(d.ny + 3), (uint64_t)(d.nz + 3), 3};
-    const uint64_t strides[3] = {(uint64_t)d.px * 4, (uint64_t)d.px * (d.ny + 3) * 4,
-                                 (uint64_t)d.comp * 4};
-    const uint32_t box[4] = {(uint32_t)box_x, (uint32_t)box_y, 1, 3};
-    ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims,
+  if (kind == 0) {  // node vector: (x, y, z, component, design)
+    const uint64_t dims[5] = {(uint64_t)d.px, (uint64_t)(d.ny + 3), (uint64_t)(d.nz + 3), 3,
+                              (uint64_t)bt.nb};
+    const uint64_t strides[4] = {(uint64_t)d.px * 4, (uint64_t)d.px * (d.ny + 3) * 4,
+                                 (uint64_t)d.comp * 4, (uint64_t)dstride};
+    const uint32_t box[5] = {(uint32_t)box_x, (uint32_t)box_y, 1, 3, 1};
+    ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(base), dims,
                           strides, box);
-  } else {  // element array: (x, y, z)
-    const uint64_t dims[3] = {(uint64_t)d.ex, (uint64_t)(d.ny + 2), (uint64_t)(d.nz + 2)};
-    const uint64_t strides[2] = {(uint64_t)d.ex * 4, (uint64_t)d.ex * (d.ny + 2) * 4};
-    const uint32_t box[3] = {(uint32_t)box_x, (uint32_t)box_y, 1};
-    ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims,
+  } else {  // element array: (x, y, z, design)
+    const uint64_t dims[4] = {(uint64_t)d.ex, (uint64_t)(d.ny + 2), (uint64_t)(d.nz + 2),
+                              (uint64_t)bt.nb};
+    const uint64_t strides[3] = {(uint64_t)d.ex * 4, (uint64_t)d.ex * (d.ny + 2) * 4,
+                                 (uint64_t)dstride};
+    const uint32_t box[4] = {(uint32_t)box_x, (uint32_t)box_y, 1, 1};
+    ok = encode_tiled_map(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims,
                           strides, box);
   }
   if (!ok) return false;
@@ -102,17 +112,20 @@ bool encode_tiled_map(CUtensorMap* map, CUtensorMapDataType dtype, int rank, voi
 
 bool stencil_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
                   CUtensorMap* emap) {
-  return cached_map(x, 0, d, kBoxX, kBoxYN, xmap) && cached_map(E, 1, d, kBoxX, kBoxYE, emap);
+  return cached_map(x, 0, d, kBoxX, kBoxYN, Bat{}, xmap) &&
+         cached_map(E, 1, d, kBoxX, kBoxYE, Bat{}, emap);
 }
 
-bool modal_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                 CUtensorMap* emap) {
-  return cached_map(x, 0, d, kMBoxX, kMBoxNY, xmap) && cached_map(E, 1, d, kMBoxX, kMBoxEY, emap);
+  return cached_map(x, 0, d, kMBoxX, kMBoxNY, bt, xmap) &&
+         cached_map(E, 1, d, kMBoxX, kMBoxEY, bt, emap);
 }
 
-bool pair_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xmap,
+bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                CUtensorMap* emap) {
-  return cached_map(x, 0, d, kPBoxX, kPBoxNY, xmap) && cached_map(E, 1, d, kPBoxX, kPBoxEY, emap);
+  return cached_map(x, 0, d, kPBoxX, kPBoxNY, bt, xmap) &&
+         cached_map(E, 1, d, kPBoxX, kPBoxEY, bt, emap);
 }
 
 }  // namespace topo

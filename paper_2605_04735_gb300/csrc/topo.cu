@@ -90,8 +90,18 @@ struct ChunkGraph {
   long long launches = 0;  // kernels in one replay
 };
 
+struct MeshGroup;
+
 struct topo_mesh {
   int dev = 0;
+  // mesh groups (topo_create_batch): this design's region of the group arena;
+  // while region_open, allocations come from the region (fixed order and sizes,
+  // so every design's buffer sits at gidx * S bytes from design 0's)
+  MeshGroup* group = nullptr;
+  int gidx = 0;
+  char* region = nullptr;
+  long long region_size = 0, region_used = 0;
+  bool region_open = false;
   cudaStream_t stream = nullptr;  // the mesh's own non-blocking stream (all work runs here)
   cudaStream_t user = nullptr;    // the caller's stream (NULL = legacy default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // fences between the two
@@ -178,6 +188,29 @@ struct topo_mesh {
   double lam_max = 0.0;
 };
 
+// A mesh group: designs of one grid, BC, load and material whose solve
+// buffers live in one arena, design b's region at b * S bytes from design
+// 0's, so one launch with a design index can serve all of them (batched
+// solves, topo_solve_many).
+struct MeshGroup {
+  int nb = 0;
+  long long S = 0;
+  char* arena = nullptr;
+  int refs = 0;
+  std::vector<topo_mesh*> meshes;
+  std::map<long long, ChunkGraph> graphs;  // batched CG chunks
+  PcgScalars* h_sc = nullptr;              // nb pinned host copies
+  int* h_flag = nullptr;                   // nb
+  struct Next {
+    double rtol2;
+    int max_iter;
+    int pad;
+  };
+  Next* h_next = nullptr;  // nb: per-design settings of the next inner solve
+  int gmg_levels = -1, gmg_degree = -1;
+  topo_params prm{};
+};
+
 namespace {
 
 topo_status cuda_status(cudaError_t e) {
@@ -195,6 +228,14 @@ topo_status cuda_status(cudaError_t e) {
 template <typename T>
 topo_status dalloc(topo_mesh* m, T** p, long long count) {
   const size_t bytes = (size_t)count * sizeof(T);
+  if (m->region_open) {  // bump allocation in the group arena (zero-filled at creation)
+    const long long off = (m->region_used + 255) / 256 * 256;
+    if (off + (long long)bytes > m->region_size) return TOPO_ERR_OOM;
+    *p = reinterpret_cast<T*>(m->region + off);
+    m->region_used = off + (long long)bytes;
+    m->bytes += (long long)bytes;
+    return TOPO_OK;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
@@ -260,6 +301,15 @@ struct Fence {
   Fence(const Fence&) = delete;
   Fence& operator=(const Fence&) = delete;
 };
+
+cudaError_t region_alloc(void* ctx, void** p, size_t bytes) {
+  topo_mesh* m = static_cast<topo_mesh*>(ctx);
+  const long long off = (m->region_used + 255) / 256 * 256;
+  if (off + (long long)bytes > m->region_size) return cudaErrorMemoryAllocation;
+  *p = m->region + off;
+  m->region_used = off + (long long)bytes;
+  return cudaSuccess;
+}
 
 topo_status ensure_fp64_inner(topo_mesh* m) {
   if (m->x64) return TOPO_OK;
@@ -852,10 +902,27 @@ void topo_free(topo_mesh* m) {
                   m->phi_tmp, m->ls_part, m->ls_bJ, m->ls_bV, m->hx, m->hr, m->hz, m->hp,
                   m->hq, m->hdinv, m->hb, m->hdir, m->ls_scratch, m->ls_dt, m->tr_rho_n,
                   m->tr_counts, m->tr_off, m->tr_scratch, m->tr_tris};
+  MeshGroup* G = m->group;
+  auto in_arena = [&](void* p) {
+    return G && static_cast<char*>(p) >= G->arena &&
+           static_cast<char*>(p) < G->arena + (long long)G->nb * G->S;
+  };
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p && !in_arena(p)) cudaFree(p);
   clear_graphs(m);
   if (m->gmg_built) gmg_free(m->gmg);
+  if (G) {
+    for (auto& q : G->meshes)
+      if (q == m) q = nullptr;
+    if (--G->refs == 0) {
+      for (auto& kv : G->graphs) cudaGraphExecDestroy(kv.second.exec);
+      if (G->arena) cudaFree(G->arena);
+      if (G->h_sc) cudaFreeHost(G->h_sc);
+      if (G->h_flag) cudaFreeHost(G->h_flag);
+      if (G->h_next) cudaFreeHost(G->h_next);
+      delete G;
+    }
+  }
   if (m->h_sc) cudaFreeHost(m->h_sc);
   if (m->h_flag) cudaFreeHost(m->h_flag);
   if (m->oc_host) cudaFreeHost(m->oc_host);
@@ -947,6 +1014,117 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
     return st;
   }
   *out = m;
+  return TOPO_OK;
+}
+
+// Bytes of one design's region: create_impl's buffers and the multigrid
+// hierarchy, in their order, each rounded up to 256 bytes (the region
+// allocator checks every allocation against this bound).
+static long long group_region_bytes(const Dims& d, int levels) {
+  const long long nvec = 3 * d.comp, ne = d.ecount;
+  const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+  long long b = 0;
+  auto add = [&](long long bytes) { b += (bytes + 255) / 256 * 256 + 256; };
+  add(ne * 4);
+  add(ne * 4);
+  add(ne * 8);
+  for (int q = 0; q < 3; ++q) add(nvec * 8);
+  for (int q = 0; q < 7; ++q) add(nvec * 4);
+  add(sizeof(PcgScalars));
+  add(4LL * kMaxPartials * 8);
+  add(4 * 4);
+  add(3 * nn * 8);
+  const std::vector<Dims> lv = gmg_plan(d, levels);
+  for (size_t l = 0; l < lv.size(); ++l) {
+    const long long n = 3 * lv[l].comp;
+    for (int q = 0; q < 3; ++q) add(n * 4);
+    if (l > 0) {
+      add(lv[l].ecount * 4);
+      for (int q = 0; q < 3; ++q) add(n * 4);
+    }
+  }
+  const Dims& dc = lv.back();
+  const long long nc = 3LL * (dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
+  add(nc * nc * 8);
+  add(4 * nc * 8);
+  add(nc * 8);
+  return (b + 4095) / 4096 * 4096;
+}
+
+topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
+                              void* stream, int n_designs, int gmg_levels, int smooth_degree,
+                              topo_mesh** out) {
+  if (!out || n_designs < 1 || n_designs > 1024 || smooth_degree < 1 || smooth_degree > 8)
+    return TOPO_ERR_INVALID;
+  for (int b = 0; b < n_designs; ++b) out[b] = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
+  if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
+  if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
+              !(prm->E0 > 0.0) || !(prm->Emin >= 0.0) || !(prm->Emin < prm->E0)))
+    return TOPO_ERR_INVALID;
+  const Dims d = make_dims(nx, ny, nz, bc, ny / 2);
+  MeshGroup* G = new (std::nothrow) MeshGroup();
+  if (!G) return TOPO_ERR_OOM;
+  G->nb = n_designs;
+  G->S = group_region_bytes(d, gmg_levels);
+  G->gmg_levels = gmg_levels;
+  G->gmg_degree = smooth_degree;
+  if (prm)
+    G->prm = *prm;
+  else
+    topo_default_params(&G->prm);
+  auto fail = [&](topo_status st) {
+    for (int b = 0; b < n_designs; ++b) out[b] = nullptr;
+    const std::vector<topo_mesh*> made = G->meshes;
+    if (made.empty()) {
+      if (G->arena) cudaFree(G->arena);
+      if (G->h_sc) cudaFreeHost(G->h_sc);
+      if (G->h_flag) cudaFreeHost(G->h_flag);
+      if (G->h_next) cudaFreeHost(G->h_next);
+      delete G;
+    } else {
+      for (topo_mesh* m : made) topo_free(m);  // the last one frees the group
+    }
+    return st;
+  };
+  if (cudaMalloc(&G->arena, (size_t)(G->nb * G->S)) != cudaSuccess) {
+    cudaGetLastError();
+    G->arena = nullptr;
+    return fail(TOPO_ERR_OOM);
+  }
+  if (cudaMemset(G->arena, 0, (size_t)(G->nb * G->S)) != cudaSuccess) return fail(TOPO_ERR_CUDA);
+  if (cudaMallocHost(&G->h_sc, sizeof(PcgScalars) * G->nb) != cudaSuccess ||
+      cudaMallocHost(&G->h_flag, sizeof(int) * G->nb) != cudaSuccess ||
+      cudaMallocHost(&G->h_next, sizeof(MeshGroup::Next) * G->nb) != cudaSuccess)
+    return fail(TOPO_ERR_OOM);
+  for (int b = 0; b < n_designs; ++b) {
+    topo_mesh* m = new (std::nothrow) topo_mesh();
+    if (!m) return fail(TOPO_ERR_OOM);
+    m->group = G;
+    m->gidx = b;
+    m->region = G->arena + b * G->S;
+    m->region_size = G->S;
+    m->region_open = true;
+    G->meshes.push_back(m);
+    ++G->refs;
+    topo_status st = create_impl(nx, ny, nz, bc, load, &G->prm, stream, m);
+    if (st != TOPO_OK) return fail(st);
+    GmgAlloc alloc{m, region_alloc};
+    const cudaError_t e = gmg_create(m->gmg, m->d, gmg_levels, smooth_degree, m->lam_max,
+                                     m->stream, &alloc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? TOPO_ERR_OOM : TOPO_ERR_INVALID);
+    }
+    m->bytes += m->gmg.bytes;
+    m->gmg_built = true;
+    m->gmg_levels_req = gmg_levels;
+    m->gmg_degree = smooth_degree;
+    m->region_open = false;  // later (optional) buffers are ordinary allocations
+    if (m->region_used != G->meshes[0]->region_used) return fail(TOPO_ERR_INVALID);
+  }
+  for (int b = 0; b < n_designs; ++b) out[b] = G->meshes[b];
   return TOPO_OK;
 }
 
@@ -1297,6 +1475,244 @@ topo_status topo_solve(topo_mesh* m, const topo_solve_opts* opts, topo_solve_inf
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// Batched solve of a whole mesh group: the FP32 GMG-PCG inner solves and the
+// FP64 refinement steps of all designs run in lockstep, one launch per
+// kernel for all designs (the design is a grid dimension).  A design whose
+// true residual already meets rtol, or that has stopped, sits out later outer
+// steps (its inner tolerance is 1: its inner solve ends at once, x = 0 adds
+// nothing); inner CG chunks run until every design's inner solve is done,
+// finished designs' kernels returning at once.
+// ---------------------------------------------------------------------------
+namespace {
+
+topo_status group_read_scalars(MeshGroup* G) {
+  topo_mesh* m = G->meshes[0];
+  CK(cudaMemcpy2DAsync(G->h_sc, sizeof(PcgScalars), m->sc, (size_t)G->S, sizeof(PcgScalars),
+                       G->nb, cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaMemcpy2DAsync(G->h_flag, sizeof(int), m->flags + 1, (size_t)G->S, sizeof(int), G->nb,
+                       cudaMemcpyDeviceToHost, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status group_enqueue_iters(MeshGroup* G, int count) {
+  topo_mesh* m = G->meshes[0];
+  cudaStream_t s = m->stream;
+  const Bat bt{G->nb, G->S};
+  const int* done = &m->sc->done;
+  for (int c = 0; c < count; ++c) {
+    LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
+                              red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
+    LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
+                                   red_of(m, FIN_RR_ONLY), false, s, bt));
+    CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
+    LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_RZ_BETA), s, bt));
+    LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
+  }
+  return TOPO_OK;
+}
+
+topo_status group_run_iters(MeshGroup* G, int count) {
+  topo_mesh* m = G->meshes[0];
+  auto it = G->graphs.find(count);
+  if (it == G->graphs.end()) {
+    const long long l0 = m->launches;
+    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    const topo_status st = group_enqueue_iters(G, count);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+    if (st != TOPO_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != TOPO_OK ? st : cuda_status(e);
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(ei);
+    ChunkGraph cg;
+    cg.exec = ex;
+    cg.launches = m->launches - l0;
+    m->launches = l0;
+    it = G->graphs.emplace(count, cg).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, m->stream));
+  m->launches += it->second.launches;
+  return TOPO_OK;
+}
+
+// Can these meshes (in any order) be solved as their group, with these options?
+MeshGroup* batchable(topo_mesh* const* meshes, int n, const topo_solve_opts& o) {
+  if (n < 2) return nullptr;
+  MeshGroup* G = meshes[0]->group;
+  if (!G || G->nb != n) return nullptr;
+  if (o.precision != TOPO_PREC_FP32 || o.precond != TOPO_PRECOND_GMG) return nullptr;
+  if (o.gmg_levels != G->gmg_levels || o.smooth_degree != G->gmg_degree) return nullptr;
+  if (!(o.rtol > 0.0) || o.max_iter < 1 || o.max_outer < 1 || o.check_every < 1 ||
+      o.check_every > 1024)
+    return nullptr;
+  for (int a = 0; a < n; ++a) {
+    topo_mesh* m = meshes[a];
+    if (m->group != G || !m->use_modal || m->mcf.form != G->meshes[0]->mcf.form || m->prof ||
+        !m->gmg.arena || !m->gmg_built || m->gmg_levels_req != G->gmg_levels ||
+        m->gmg_degree != G->gmg_degree)
+      return nullptr;
+  }
+  for (topo_mesh* m : G->meshes)
+    if (!m) return nullptr;
+  return G;
+}
+
+// infos[b]: design b of the group
+topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info* infos) {
+  Timer timer;
+  const int nb = G->nb;
+  topo_mesh* m = G->meshes[0];
+  cudaStream_t s = m->stream;
+  const Bat bt{nb, G->S};
+  for (topo_mesh* q : G->meshes)
+    if (!q->has_density) return TOPO_ERR_NO_DENSITY;
+  // design 0's stream (which runs the batch) after every design's earlier work
+  for (int b = 1; b < nb; ++b) {
+    CK(cudaEventRecord(G->meshes[b]->ev_in, G->meshes[b]->stream));
+    CK(cudaStreamWaitEvent(s, G->meshes[b]->ev_in, 0));
+  }
+  // setup for the current moduli (all designs at once)
+  bool need_diag = false, need_gmg = false;
+  for (topo_mesh* q : G->meshes) {
+    need_diag |= !q->diag32;
+    need_gmg |= !q->gmg.ready;
+  }
+  if (need_diag || need_gmg) {
+    LK(m, launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s, bt));
+    CK(gmg_setup(m->gmg, m->E32, m->dinv32, m->k0f, m->k0d, s, &m->launches, bt));
+    for (topo_mesh* q : G->meshes) {
+      q->diag32 = true;
+      q->gmg.ready = true;
+      q->gmg.lv[0].E = q->E32;  // each design's own hierarchy now describes its moduli
+      q->gmg.lv[0].dinv = q->dinv32;
+    }
+  }
+  for (topo_mesh* q : G->meshes) q->solved = false;
+  CK(cudaMemset2DAsync(m->flags + 1, (size_t)G->S, 0, sizeof(int), nb, s));
+  if (o.warm_start) {
+    LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
+                               red_of(m, FIN_AUX), APPLY_RESID, nullptr, m->flags + 1, s, bt));
+  } else {
+    CK(cudaMemset2DAsync(m->u64, (size_t)G->S, 0, sizeof(double) * m->nvec, nb, s));
+    CK(cudaMemcpy2DAsync(m->r64, (size_t)G->S, m->f64, (size_t)G->S, sizeof(double) * m->nvec,
+                         nb, cudaMemcpyDeviceToDevice, s));
+    LK(m, launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s, bt));
+  }
+  CKS(group_read_scalars(G));
+  std::vector<int> outer(nb, 0), total(nb, 0), detail(nb, TOPO_FAIL_NONE);
+  std::vector<topo_status> st(nb, TOPO_OK);
+  std::vector<char> running(nb, 1);
+  std::vector<double> rel(nb, 0.0);
+  for (;;) {
+    // decisions on the fresh FP64 residuals
+    int live = 0;
+    for (int b = 0; b < nb; ++b) {
+      MeshGroup::Next& nx = G->h_next[b];
+      nx.rtol2 = 4.0;  // sit out
+      nx.max_iter = 1;
+      if (!running[b]) continue;
+      const PcgScalars& h = G->h_sc[b];
+      const double fn = std::sqrt(G->meshes[b]->fnorm2), rr = h.aux[0];
+      if (G->h_flag[b]) {
+        st[b] = TOPO_ERR_TIMEOUT;
+        detail[b] = TOPO_FAIL_TIMEOUT;
+        running[b] = 0;
+        continue;
+      }
+      if (!std::isfinite(rr)) {
+        st[b] = TOPO_ERR_NAN;
+        detail[b] = TOPO_FAIL_RESIDUAL;
+        running[b] = 0;
+        continue;
+      }
+      rel[b] = fn > 0 ? std::sqrt(rr) / fn : 0.0;
+      if (rel[b] <= o.rtol) {
+        running[b] = 0;
+        continue;
+      }
+      if (outer[b] >= o.max_outer || total[b] >= o.max_iter) {
+        st[b] = TOPO_ERR_NOT_CONVERGED;
+        detail[b] = TOPO_FAIL_LIMIT;
+        running[b] = 0;
+        continue;
+      }
+      const double inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * fn / std::sqrt(rr)), 0.5);
+      nx.rtol2 = inner * inner;
+      nx.max_iter = o.max_iter - total[b];
+      ++live;
+    }
+    if (!live) break;
+    CK(cudaMemcpy2DAsync(&m->sc->rtol2_next, (size_t)G->S, G->h_next, sizeof(MeshGroup::Next),
+                         sizeof(double) + sizeof(int), nb, cudaMemcpyHostToDevice, s));
+    // inner start: b = r / ||r|| in FP32, x = 0, z = V(r), p = z
+    const int* done = &m->sc->done;
+    LK(m, launch_set_max_iter(m->sc, -1, s, bt));
+    LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s, bt));
+    LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
+                                 red_of(m, FIN_INIT, -1.0), false, s, bt));
+    CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
+    LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s, bt));
+    LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
+    std::vector<int> before(nb, -1);
+    for (int chunk = 0;; ++chunk) {
+      CKS(group_run_iters(G, o.check_every));
+      CKS(group_read_scalars(G));
+      bool all_done = true, progress = false;
+      for (int b = 0; b < nb; ++b) {
+        const PcgScalars& h = G->h_sc[b];
+        if (!h.done) all_done = false;
+        if (h.iter != before[b]) progress = true;
+        before[b] = h.iter;
+      }
+      if (all_done) break;
+      if (!progress) return TOPO_ERR_CUDA;  // no design moved without stopping: a bug
+    }
+    for (int b = 0; b < nb; ++b) {
+      if (!running[b]) continue;
+      const PcgScalars& h = G->h_sc[b];
+      total[b] += h.iter;
+      ++outer[b];
+      if (h.status == 2) {
+        st[b] = TOPO_ERR_NAN;
+        detail[b] = TOPO_FAIL_BREAKDOWN;
+        running[b] = 0;
+      }
+    }
+    // u += ||r|| x (designs that sat out have x = 0), then the FP64 residual
+    LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s, bt));
+    LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
+                               red_of(m, FIN_AUX), APPLY_RESID, nullptr, m->flags + 1, s, bt));
+    CKS(group_read_scalars(G));
+  }
+  // every design's stream after the batch
+  CK(cudaEventRecord(m->ev_in, s));
+  for (int b = 1; b < nb; ++b) CK(cudaStreamWaitEvent(G->meshes[b]->stream, m->ev_in, 0));
+  topo_status first = TOPO_OK;
+  for (int b = 0; b < nb; ++b) {
+    topo_mesh* q = G->meshes[b];
+    q->solved = (st[b] == TOPO_OK);
+    if (infos) {
+      infos[b].iters = total[b];
+      infos[b].outer = outer[b];
+      infos[b].status = st[b];
+      infos[b].detail = detail[b];
+      infos[b].rel_residual = rel[b];
+      infos[b].seconds = timer.seconds();
+    }
+    if (st[b] != TOPO_OK && first == TOPO_OK) first = st[b];
+  }
+  return first;
+}
+
+}  // namespace
+
 topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_opts* opts,
                             topo_solve_info* infos) {
   if (n < 0 || (n > 0 && !meshes)) return TOPO_ERR_INVALID;
@@ -1310,6 +1726,25 @@ topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_op
     o = *opts;
   else
     topo_default_opts(&o);
+  if (MeshGroup* G = batchable(meshes, n, o)) {
+    std::vector<std::unique_ptr<Fence>> fences;
+    topo_status fst = TOPO_OK;
+    for (int a = 0; a < n; ++a) {
+      if (infos) std::memset(&infos[a], 0, sizeof(topo_solve_info));
+      fences.emplace_back(new Fence(meshes[a]));
+      if (fences.back()->st != TOPO_OK) fst = fences.back()->st;
+    }
+    if (fst != TOPO_OK) return fst;
+    std::vector<topo_solve_info> by_design(G->nb);
+    const topo_status st = group_solve(G, o, by_design.data());
+    if (infos)
+      for (int a = 0; a < n; ++a) {
+        infos[a] = by_design[meshes[a]->gidx];
+        if (st != TOPO_OK && infos[a].status == TOPO_OK && !meshes[a]->solved)
+          infos[a].status = st;
+      }
+    return st;  // the fences order every caller stream after its design
+  }
   std::vector<SolveTask> tasks(n);
   std::vector<std::unique_ptr<Fence>> fences;
   fences.reserve(n);

@@ -53,7 +53,16 @@ __device__ __forceinline__ void st4(T* p, long long q, const typename Vec4<T>::t
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_init(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-               T* __restrict__ p, const T* __restrict__ dinv, long long n4, const Red red) {
+               T* __restrict__ p, const T* __restrict__ dinv, long long n4, const Red red0,
+               long long S) {
+  const long long off = blockIdx.y * S;
+  b = bshift(b, off);
+  x = bshift(x, off);
+  r = bshift(r, off);
+  z = bshift(z, off);
+  p = bshift(p, off);
+  dinv = bshift(dinv, off);
+  const Red red = red0.shifted(off);
   double rz = 0.0, rr = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
@@ -77,7 +86,7 @@ __global__ void __launch_bounds__(kThreads)
     rr += (double)(bv.x * bv.x + bv.y * bv.y + bv.z * bv.z + bv.w * bv.w);
   }
   double v[2] = {rz, rr};
-  reduce_finalize<2>(v, red);
+  reduce_finalize<2>(v, red, blockIdx.x, gridDim.x);
 }
 
 // x += alpha p, r -= alpha q; Jacobi: z = D^-1 r, reduce (r.z, r.r) -> FIN_UPDATE;
@@ -85,7 +94,16 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
-                 const T* __restrict__ qv, const T* __restrict__ dinv, long long n4, const Red red) {
+                 const T* __restrict__ qv, const T* __restrict__ dinv, long long n4,
+                 const Red red0, long long S) {
+  const long long off = blockIdx.y * S;
+  x = bshift(x, off);
+  r = bshift(r, off);
+  z = bshift(z, off);
+  p = bshift(p, off);
+  qv = bshift(qv, off);
+  dinv = bshift(dinv, off);
+  const Red red = red0.shifted(off);
   const PcgScalars* sc = red.sc;
   if (sc->done) return;
   const T a = (T)sc->alpha;
@@ -120,10 +138,10 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (JAC) {
     double v[2] = {rz, rr};
-    reduce_finalize<2>(v, red);
+    reduce_finalize<2>(v, red, blockIdx.x, gridDim.x);
   } else {
     double v[1] = {rr};
-    reduce_finalize<1>(v, red);
+    reduce_finalize<1>(v, red, blockIdx.x, gridDim.x);
   }
 }
 
@@ -131,7 +149,11 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, long long n4,
-                    const PcgScalars* __restrict__ sc) {
+                    const PcgScalars* __restrict__ sc, long long S) {
+  const long long off = blockIdx.y * S;
+  p = bshift(p, off);
+  z = bshift(z, off);
+  sc = bshift(sc, off);
   if (sc->done) return;
   const T b = (T)sc->beta;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
@@ -150,8 +172,15 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(kThreads)
     k_dot(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c, long long n4,
-          const Red red) {
-  if (red.op == FIN_RZ_BETA && red.sc->done) return;
+          const Red red0, long long S) {
+  const long long off = blockIdx.y * S;
+  a = bshift(a, off);
+  b = bshift(b, off);
+  c = bshift(c, off);
+  const Red red = red0.shifted(off);
+  // a finished inner solve (converged, or a design sitting out a batched
+  // step) takes no further scalar decisions
+  if ((red.op == FIN_RZ_BETA || red.op == FIN_SET_RZ) && red.sc->done) return;
   double s0 = 0.0, s1 = 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
@@ -164,12 +193,16 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   double v[2] = {s0, s1};
-  reduce_finalize<2>(v, red);
+  reduce_finalize<2>(v, red, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kThreads)
     k_narrow_scaled(float* __restrict__ b32, const double* __restrict__ r64, long long n4,
-                    const PcgScalars* __restrict__ sc) {
+                    const PcgScalars* __restrict__ sc, long long S) {
+  const long long off = blockIdx.y * S;
+  b32 = bshift(b32, off);
+  r64 = bshift(r64, off);
+  sc = bshift(sc, off);
   const double nrm2 = sc->aux[0];
   const double s = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
@@ -187,7 +220,11 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_accumulate(double* __restrict__ u, const T* __restrict__ x, long long n4,
-                 const PcgScalars* __restrict__ sc, int scaled) {
+                 const PcgScalars* __restrict__ sc, int scaled, long long S) {
+  const long long off = blockIdx.y * S;
+  u = bshift(u, off);
+  x = bshift(x, off);
+  sc = bshift(sc, off);
   const double s = scaled ? sqrt(sc->aux[0]) : 1.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
@@ -203,7 +240,10 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_copy_cast(T* __restrict__ dst, const double* __restrict__ src, long long n4) {
+    k_copy_cast(T* __restrict__ dst, const double* __restrict__ src, long long n4, long long S) {
+  const long long off = blockIdx.y * S;
+  dst = bshift(dst, off);
+  src = bshift(src, off);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
     const double4_32a v = ld4(src, q);
@@ -216,102 +256,112 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void k_set_max_iter(PcgScalars* sc, int max_iter) {
-  sc->max_iter = max_iter;
-  sc->done = 0;
-  sc->status = 0;
+// thread b: design b; max_iter < 0 takes each design's max_iter_next
+__global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, long long S) {
+  const int b = threadIdx.x + blockIdx.x * blockDim.x;
+  if (b >= nb) return;
+  PcgScalars* t = bshift(sc, b * S);
+  t->max_iter = (max_iter >= 0) ? max_iter : t->max_iter_next;
+  t->done = 0;
+  t->status = 0;
 }
 
 }  // namespace
 
-cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s) {
-  k_set_max_iter<<<1, 1, 0, s>>>(sc, max_iter);
+cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s, const Bat& bt) {
+  k_set_max_iter<<<(bt.nb + 127) / 128, 128, 0, s>>>(sc, max_iter, bt.nb, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, long long n,
-                            const Red& red, bool jacobi, cudaStream_t s) {
+                            const Red& red, bool jacobi, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  const int g = reduce_blocks(n4);
+  const dim3 g(reduce_blocks(n4), bt.nb);
   if (jacobi)
-    k_pcg_init<T, true><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red);
+    k_pcg_init<T, true><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red, bt.S);
   else
-    k_pcg_init<T, false><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red);
+    k_pcg_init<T, false><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
-                              const Red& red, bool jacobi, cudaStream_t s) {
+                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  const int g = reduce_blocks(n4);
+  const dim3 g(reduce_blocks(n4), bt.nb);
   if (jacobi)
-    k_pcg_update<T, true><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red);
+    k_pcg_update<T, true><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red, bt.S);
   else
-    k_pcg_update<T, false><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red);
+    k_pcg_update<T, false><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  const int g = reduce_blocks(n4);
-  k_pcg_direction<T><<<g, kThreads, 0, s>>>(p, z, n4, sc);
+  k_pcg_direction<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(p, z, n4, sc, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s) {
+cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s,
+                       const Bat& bt) {
   const long long n4 = n / 4;
-  k_dot<T, false><<<reduce_blocks(n4), kThreads, 0, s>>>(a, b, nullptr, n4, red);
+  k_dot<T, false><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(a, b, nullptr, n4, red,
+                                                                       bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
-                        cudaStream_t s) {
+                        cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_dot<T, true><<<reduce_blocks(n4), kThreads, 0, s>>>(a, b, c, n4, red);
+  k_dot<T, true><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(a, b, c, n4, red, bt.S);
   return cudaGetLastError();
 }
 
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_narrow_scaled<<<reduce_blocks(n4), kThreads, 0, s>>>(b32, r64, n4, sc);
+  k_narrow_scaled<<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(b32, r64, n4, sc, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgScalars* sc,
-                              bool scaled, cudaStream_t s) {
+                              bool scaled, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_accumulate<T><<<reduce_blocks(n4), kThreads, 0, s>>>(u64, x, n4, sc, scaled ? 1 : 0);
+  k_accumulate<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(u64, x, n4, sc,
+                                                                       scaled ? 1 : 0, bt.S);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s) {
+cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
+                             const Bat& bt) {
   const long long n4 = n / 4;
-  k_copy_cast<T><<<reduce_blocks(n4), kThreads, 0, s>>>(dst, src, n4);
+  k_copy_cast<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(dst, src, n4, bt.S);
   return cudaGetLastError();
 }
 
 #define TOPO_INST(T)                                                                           \
   template cudaError_t launch_pcg_init<T>(const T*, T*, T*, T*, T*, const T*, long long,       \
-                                          const Red&, bool, cudaStream_t);                     \
+                                          const Red&, bool, cudaStream_t, const Bat&);         \
   template cudaError_t launch_pcg_update<T>(T*, T*, T*, const T*, const T*, const T*,          \
-                                            long long, const Red&, bool, cudaStream_t);        \
+                                            long long, const Red&, bool, cudaStream_t,         \
+                                            const Bat&);                                       \
   template cudaError_t launch_pcg_direction<T>(T*, const T*, long long, const PcgScalars*,     \
-                                               cudaStream_t);                                  \
-  template cudaError_t launch_dot<T>(const T*, const T*, long long, const Red&, cudaStream_t); \
+                                               cudaStream_t, const Bat&);                      \
+  template cudaError_t launch_dot<T>(const T*, const T*, long long, const Red&, cudaStream_t,  \
+                                     const Bat&);                                              \
   template cudaError_t launch_dot2<T>(const T*, const T*, const T*, long long, const Red&,     \
-                                      cudaStream_t);                                           \
+                                      cudaStream_t, const Bat&);                               \
   template cudaError_t launch_accumulate<T>(double*, const T*, long long, const PcgScalars*,   \
-                                            bool, cudaStream_t);                               \
-  template cudaError_t launch_copy_cast<T>(T*, const double*, long long, cudaStream_t);
+                                            bool, cudaStream_t, const Bat&);                   \
+  template cudaError_t launch_copy_cast<T>(T*, const double*, long long, cudaStream_t,         \
+                                           const Bat&);
 TOPO_INST(float)
 TOPO_INST(double)
 

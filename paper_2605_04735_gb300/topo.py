@@ -81,6 +81,8 @@ def lib():
             "topo_default_params": (None, [C.POINTER(Params)]),
             "topo_default_opts": (None, [C.POINTER(SolveOpts)]),
             "topo_create_mesh": (i, [i, i, i, i, i, C.POINTER(Params), vp, C.POINTER(vp)]),
+            "topo_create_batch": (i, [i, i, i, i, i, C.POINTER(Params), vp, i, i, i,
+                                      C.POINTER(vp)]),
             "topo_set_density": (i, [vp, vp, sz, i]),
             "topo_solve": (i, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
             "topo_solve_many": (i, [C.POINTER(vp), i, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
@@ -214,18 +216,38 @@ def solve_many(meshes, opts: SolveOpts | None = None, check: bool = True):
     return list(infos)
 
 
+def _stream_arg(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def create_batch(n, nx, ny, nz, bc=None, load=None, params: "Params | None" = None,
+                 stream=None, opts: "SolveOpts | None" = None):
+    """n meshes of one grid that solve_many runs as one batch (topo_create_batch);
+    `opts` fixes the multigrid settings (default: default_opts())."""
+    bc = BC_CANTILEVER if bc is None else bc
+    load = LOAD_EDGE_XL_BOTTOM if load is None else load
+    o = opts or default_opts()
+    hs = (C.c_void_p * n)()
+    _check(lib().topo_create_batch(nx, ny, nz, bc, load, C.byref(params) if params else None,
+                                   _stream_arg(stream), n, o.gmg_levels, o.smooth_degree, hs),
+           "topo_create_batch")
+    return [Mesh(nx, ny, nz, bc, load, _handle=C.c_void_p(h)) for h in hs]
+
+
 class Mesh:
     """One structured hex8 design domain held on the current CUDA device."""
 
     def __init__(self, nx, ny, nz, bc=BC_CANTILEVER, load=LOAD_EDGE_XL_BOTTOM,
-                 params: Params | None = None, stream=None):
-        L = lib()
-        h = C.c_void_p()
-        s = None
-        if stream is not None:
-            s = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
-        _check(L.topo_create_mesh(nx, ny, nz, bc, load, C.byref(params) if params else None, s,
-                                  C.byref(h)), "topo_create_mesh")
+                 params: Params | None = None, stream=None, _handle=None):
+        if _handle is not None:
+            h = _handle
+        else:
+            h = C.c_void_p()
+            _check(lib().topo_create_mesh(nx, ny, nz, bc, load,
+                                          C.byref(params) if params else None,
+                                          _stream_arg(stream), C.byref(h)), "topo_create_mesh")
         self._h = h
         self.nx, self.ny, self.nz, self.bc, self.load = nx, ny, nz, bc, load
         self.n_elem = nx * ny * nz

@@ -1,0 +1,154 @@
+"""Batched solves of a mesh group (topo_create_batch + topo_solve_many): every
+design's result against the same design solved alone and against the FP64
+oracle.
+
+Both paths stop on the true FP64 relative residual (1e-10 here), so their
+displacements agree with the direct solution to ~1e-8 and with each other to
+the same order; compliances to 1e-8 relative."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_2605_04735_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def topo():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_04735_gb300 import build
+    build.build()
+    from paper_2605_04735_gb300 import topo as t
+    t.lib()
+    return t
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _alone(topo, nx, ny, nz, bc, load, rho, opts):
+    with topo.Mesh(nx, ny, nz, bc, load) as m:
+        m.set_density(rho)
+        info = m.solve(opts)
+        return m.displacement(), m.compliance(), m.sensitivity(), info
+
+
+@pytest.mark.parametrize("nx,ny,nz,bc,load,nb", [
+    (40, 12, 10, I.BC_MBB, I.LOAD_EDGE_X0_TOP, 5),
+    (33, 9, 7, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, 3),
+    (160, 8, 8, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM, 3),   # the paired operator kernel
+    (40, 20, 20, I.BC_CORNERS, I.LOAD_DISC_XL, 4),
+])
+def test_batch_matches_single_solves(topo, nx, ny, nz, bc, load, nb):
+    opts = topo.default_opts(rtol=1e-10)
+    rhos = [I.density_cone_smoothed(nx, ny, nz, 40 + b) for b in range(nb)]
+    meshes = topo.create_batch(nb, nx, ny, nz, bc, load, opts=opts)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_density(r)
+        infos = topo.solve_many(meshes, opts)
+        res = [(m.displacement(), m.compliance(), m.sensitivity()) for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    for b in range(nb):
+        u, c, dc = res[b]
+        u1, c1, dc1, info1 = _alone(topo, nx, ny, nz, bc, load, rhos[b], opts)
+        assert infos[b].status == 0 and infos[b].rel_residual <= 1e-10
+        assert _rel(u, u1) <= 1e-8
+        assert c == pytest.approx(c1, rel=1e-8)
+        assert np.abs(dc - dc1).max() <= 1e-7 * np.abs(dc1).max()
+    if nx * ny * nz <= 6000:  # one design against the direct solution
+        P = fem.Problem(nx, ny, nz, bc, load, rhos[0])
+        ref = P.solve()
+        assert _rel(res[0][0], ref) <= 1e-8
+
+
+def test_batch_designs_converge_at_different_outer_steps(topo):
+    """A solid design converges in fewer outer steps than near-binary void
+    designs; it sits out the later steps and its result is unchanged."""
+    nx, ny, nz, nb = 48, 12, 12, 4
+    opts = topo.default_opts(rtol=1e-10)
+    rhos = [np.ones(nx * ny * nz, np.float32)] + \
+           [I.density_voids(nx, ny, nz, 8, seed=s, rmin=2.0, rmax=4.0) for s in range(nb - 1)]
+    meshes = topo.create_batch(nb, nx, ny, nz, opts=opts)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_density(r)
+        infos = topo.solve_many(meshes, opts)
+        us = [m.displacement() for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    for b in range(nb):
+        u1, _, _, info1 = _alone(topo, nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM,
+                                 rhos[b], opts)
+        assert infos[b].status == 0
+        assert infos[b].outer == info1.outer
+        assert _rel(us[b], u1) <= 1e-8
+
+
+def test_batch_warm_start_and_repeated_solves(topo):
+    nx, ny, nz, nb = 36, 10, 10, 3
+    opts = topo.default_opts(rtol=1e-9)
+    warm = topo.default_opts(rtol=1e-9, warm_start=1)
+    meshes = topo.create_batch(nb, nx, ny, nz, I.BC_MBB, I.LOAD_EDGE_X0_TOP, opts=opts)
+    try:
+        base = [I.density_cone_smoothed(nx, ny, nz, 70 + b) for b in range(nb)]
+        for m, r in zip(meshes, base):
+            m.set_density(r)
+        topo.solve_many(meshes, opts)
+        g = np.random.default_rng(3)
+        new = [I.perturb(r, g.uniform(0.95, 1.05, r.size)) for r in base]
+        for m, r in zip(meshes, new):
+            m.set_density(r)
+        infos = topo.solve_many(meshes, warm)
+        us = [m.displacement() for m in meshes]
+        cs = [m.compliance() for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    for b in range(nb):
+        u1, c1, _, _ = _alone(topo, nx, ny, nz, I.BC_MBB, I.LOAD_EDGE_X0_TOP, new[b], opts)
+        assert infos[b].status == 0
+        assert _rel(us[b], u1) <= 1e-7
+        assert cs[b] == pytest.approx(c1, rel=1e-8)
+
+
+def test_batch_falls_back_when_not_a_whole_group(topo):
+    """Part of a group, a different operator, or freed designs: the designs are
+    solved one by one, with the same results."""
+    nx, ny, nz, nb = 30, 8, 8, 4
+    opts = topo.default_opts(rtol=1e-10)
+    rhos = [I.density_uniform(nx, ny, nz, 0.1, 1.0, 90 + b) for b in range(nb)]
+    meshes = topo.create_batch(nb, nx, ny, nz, opts=opts)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_density(r)
+        part = topo.solve_many(meshes[1:3], opts)            # a subset
+        meshes[3].set_operator(topo.OPERATOR_GATHER)
+        whole = topo.solve_many(meshes, opts)                 # one design differs
+        meshes[3].set_operator(topo.OPERATOR_MODAL)
+        meshes[0].close()                                     # design 0 freed first
+        rest = topo.solve_many(meshes[1:], opts)
+        us = [m.displacement() for m in meshes[1:]]
+        single = meshes[2].solve(opts)
+    finally:
+        for m in meshes:
+            m.close()
+    assert all(i.status == 0 for i in part + whole + rest) and single.status == 0
+    for b in range(1, nb):
+        u1, _, _, _ = _alone(topo, nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM,
+                             rhos[b], opts)
+        assert _rel(us[b - 1], u1) <= 1e-8
+
+
+def test_batch_rejects_bad_arguments(topo):
+    with pytest.raises(RuntimeError):
+        topo.create_batch(0, 8, 4, 4)
+    with pytest.raises(RuntimeError):
+        topo.create_batch(2, 8, 5, 4, I.BC_MBB, I.LOAD_EDGE_X0_TOP)  # MBB needs an even ny
