@@ -333,13 +333,16 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   }
 }
 
-// z planes per CTA for the modal kernels: a few waves over 152 SMs, a one-
-// layer warm-up below ~10%, and no more CTAs than partial-sum slots
-inline int modal_zchunk(const Dims& d) {
+// z planes per CTA for the modal kernels: a few waves over 152 SMs counting
+// all `nb` designs of a launch, a one-layer warm-up below ~10%, and no more
+// CTAs per design than partial-sum slots
+// (a floor of 8 or 16 planes measured 1-5 % more solves/s with 64 designs in
+// flight on 96x32x32 but 57-147 % more latency for one design: 4 it is)
+inline int modal_zchunk(const Dims& d, int nb = 1) {
   const long long xy = (long long)((d.nx + kModalOwnX) / kModalOwnX) *
                        ((d.ny + kModalOwnY) / kModalOwnY);
   const int planes = d.nz + 1;
-  int z = (int)((xy * planes) / (152 * 2 * 4));
+  int z = (int)((xy * planes * nb) / (152 * 2 * 4));
   if (z < 4) z = 4;
   if (z > 32) z = 32;
   while (xy * ((planes + z - 1) / z) > kMaxPartials) ++z;
@@ -353,7 +356,7 @@ template <typename T, class Epi>
 cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                                 const Epi& epi, const Red& red, const int* done, int* errflag,
                                 cudaStream_t s, const Bat& bt) {
-  const int z = modal_zchunk(d);
+  const int z = modal_zchunk(d, bt.nb);
   const int zc = (d.nz + z) / z;
   dim3 block(kModalTX, kModalTY, 1);
   dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY, zc * bt.nb);

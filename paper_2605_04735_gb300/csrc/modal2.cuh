@@ -164,6 +164,9 @@ constexpr int kPNodeStride = (kPNode + 31) / 32 * 32;          // floats, 128-by
 constexpr int kPStageFloats = (kPNodeStride + kPElem + 31) / 32 * 32;
 constexpr uint32_t kPStageTx = (uint32_t)(kPNode + kPElem) * 4u;
 constexpr size_t kPairXchBytes = sizeof(float2) * 2 * kPairTY * kPairTX * 3;
+// CTAs resident per SM (the register budget).  Holding the kernel to one CTA
+// per SM (one wave) measured 49% slower at 320x160x160: two CTAs per SM it is.
+constexpr int kPairCtasPerSm = 2;
 constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPairXchBytes +
                              sizeof(uint64_t) * kPairStages + 128;  // + alignment slack
 
@@ -308,11 +311,11 @@ bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUt
 // z planes per CTA of the paired kernel: the chunk length that minimises
 // (waves of two CTAs per SM) x (planes per CTA + the two warm-up layers),
 // with no more CTAs than partial-sum slots
-inline int pair_zchunk(const Dims& d) {
+inline int pair_zchunk(const Dims& d, int nb = 1) {
   const long long xy = (long long)((d.nx + kPairOwnX) / kPairOwnX) *
-                       ((d.ny + kPairOwnY) / kPairOwnY);
+                       ((d.ny + kPairOwnY) / kPairOwnY) * nb;
   const int planes = d.nz + 1;
-  const long long slots = 152LL * 2;
+  const long long slots = 152LL * kPairCtasPerSm;
   int best = planes;
   long long best_cost = -1;
   for (int z = 4; z <= planes; ++z) {
@@ -339,7 +342,7 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int z = pair_zchunk(d);
+  const int z = pair_zchunk(d, bt.nb);
   const int zc = (d.nz + z) / z;
   dim3 block(kPairTX, kPairTY, 1);
   dim3 grid((d.nx + kPairOwnX) / kPairOwnX, (d.ny + kPairOwnY) / kPairOwnY, zc * bt.nb);
