@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -170,14 +171,19 @@ constexpr int kPairCtasPerSm = 2;
 constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPairXchBytes +
                              sizeof(uint64_t) * kPairStages + 128;  // + alignment slack
 
+// Grid: (G CTAs per design, 1, designs).  The work of a design is the list of
+// (x-y tile, node plane) pairs in tile-major order; CTA b takes the equal
+// share [b W / G, (b + 1) W / G) of its W entries and marches it as one or
+// two z segments (a segment that starts inside a tile's march pays the
+// two-layer warm-up again).  G is one resident wave, so no SM idles while
+// others finish a second CTA.
 template <class Epi>
 __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     k_modal_pair(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
                  const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi0,
-                 const Red red0, const int zchunk, const int zc, const long long S,
+                 const Red red0, const int gx, const int gy, const long long S,
                  const int* __restrict__ done, int* __restrict__ errflag) {
-  // grid z: zc z-chunks x designs (see k_modal_tma)
-  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
+  const int design = blockIdx.z;
   const long long off = design * S;
   done = bshift(done, off);
   errflag = bshift(errflag, off);
@@ -194,13 +200,10 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
                                               kPairXchBytes);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kPairTX + tx;
-  const int x0 = blockIdx.x * kPairOwnX, y0 = blockIdx.y * kPairOwnY;
-  const int exA = x0 - 1 + tx, ey = y0 - 1 + ty;
-  const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
-  const int ox = x0 - bx;
-  const int kb = chunk * zchunk;
-  const int ke = min(kb + zchunk, d.nz + 1);
-  const int nst = (ke - kb) + 2;  // stage t: node plane kb-1+t, element layer kb-2+t
+  const int planes = d.nz + 1;
+  const long long W = (long long)gx * gy * planes;
+  const long long L0 = (long long)blockIdx.x * W / gridDim.x;
+  const long long L1 = (long long)(blockIdx.x + 1) * W / gridDim.x;
   if (tid == 0) {
     for (int q = 0; q < kPairStages; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
@@ -208,126 +211,132 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     tma_prefetch_desc(&emap);
   }
   __syncthreads();
-  auto issue = [&](int t) {
-    const int slot = t % kPairStages;
-    float* s = stg + slot * kPStageFloats;
-    mbar_arrive_expect_tx(&bar[slot], kPStageTx);
-    tma_load_5d(s, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
-    tma_load_4d(s + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
-  };
-  if (tid == 0)
-    for (int t = 0; t < kPairStages && t < nst; ++t) issue(t);
-  const bool ownA = tx > 0 && ty > 0 && exA <= d.nx && ey <= d.ny;
-  const bool ownB = ty > 0 && exA + 32 <= d.nx && ey <= d.ny;
-  const bool clean = !d.box_may_fix(x0, x0 + kPairOwnX - 1, y0, kb);
   const FreeDims fd{d.comp};
-  const int lx = ox + tx;  // this thread's column A inside a box row
   const int src = (tx + kPairTX - 1) & (kPairTX - 1);
-  long long oA = d.node(exA, ey, kb);
-
-  // stage t -> registers: the top node plane (pairs A, B) and the element moduli
-  auto load_stage = [&](int t, float2(&top)[2][2][3], float2& E) {
-    const int slot = t % kPairStages;
-    mbar_wait_bounded(&bar[slot], (uint32_t)((t / kPairStages) & 1), errflag);
-    const float* nd = stg + slot * kPStageFloats;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float* p = nd + c * (kPBoxNY * kPBoxX) + (ty + dy) * kPBoxX + lx + dx;
-          top[dy][dx][c] = make_float2(p[0], p[32]);
-        }
-    const float* el = nd + kPNodeStride + ty * kPBoxX + lx;
-    E = make_float2(el[0], el[32]);
-  };
-  // one stage per layer: wait, read, compute, exchange, barrier, refill,
-  // epilogue.  (Reading stage t+1 before the barrier, to overlap its latency
-  // with the exchange, measured slower: it spills at the 128-register cap.)
-  PairColumn col;
-  float2 top[2][2][3], E;
-  load_stage(0, top, E);
-  pair_seed(col, top);
-  __syncthreads();
-  if (tid == 0 && kPairStages < nst) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue(kPairStages);
-  }
   float part = 0.f;
-#pragma unroll 2
-  for (int t = 1; t < nst; ++t) {
-    load_stage(t, top, E);
-    const float2 nE = make_float2(-E.x, -E.y);
-    float2 plane[3][4], ctr[3];
-    pair_layer(col, top, E, nE, kc, plane, ctr);
-    float2 n0[3];
-    float2(*xb)[kPairTY][kPairTX] = xch[t & 1];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float r1a = __shfl_sync(0xffffffffu, plane[c][1].x, src);
-      const float r1b = __shfl_sync(0xffffffffu, plane[c][1].y, src);
-      const float r3a = __shfl_sync(0xffffffffu, plane[c][3].x, src);
-      const float r3b = __shfl_sync(0xffffffffu, plane[c][3].y, src);
-      n0[c] = padd(plane[c][0], make_float2(r1a, tx > 0 ? r1b : r1a));
-      xb[c][ty][tx] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
-    }
-    __syncthreads();
-    if (tid == 0 && t + kPairStages < nst) {
+  int gs = 0;  // stages consumed so far over all segments (mbarrier phases)
+  for (long long L = L0; L < L1;) {
+    const long long T = L / planes;
+    const int kb = (int)(L - T * planes);
+    const int ke = (int)min((long long)planes, kb + (L1 - L));
+    L += ke - kb;
+    const int x0 = (int)(T % gx) * kPairOwnX, y0 = (int)(T / gx) * kPairOwnY;
+    const int exA = x0 - 1 + tx, ey = y0 - 1 + ty;
+    const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
+    const int ox = x0 - bx;
+    const int nst = (ke - kb) + 2;  // stage t: node plane kb-1+t, element layer kb-2+t
+    auto issue = [&](int t) {
+      const int slot = (gs + t) % kPairStages;
+      float* sp = stg + slot * kPStageFloats;
+      mbar_arrive_expect_tx(&bar[slot], kPStageTx);
+      tma_load_5d(sp, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
+      tma_load_4d(sp + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
+    };
+    if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + kPairStages);
+      for (int t = 0; t < kPairStages && t < nst; ++t) issue(t);
     }
-    const int ez = kb - 2 + t;
-    if (ty > 0 && t >= 2) {
-      float resA[3], resB[3], cA[3], cB[3];
+    const bool ownA = tx > 0 && ty > 0 && exA <= d.nx && ey <= d.ny;
+    const bool ownB = ty > 0 && exA + 32 <= d.nx && ey <= d.ny;
+    const bool clean = !d.box_may_fix(x0, x0 + kPairOwnX - 1, y0, kb);
+    const int lx = ox + tx;  // this thread's column A inside a box row
+    long long oA = d.node(exA, ey, kb);
+
+    // stage t -> registers: the top node plane (pairs A, B) and the element moduli
+    auto load_stage = [&](int t, float2(&top)[2][2][3], float2& E) {
+      const int g = gs + t;
+      const int slot = g % kPairStages;
+      mbar_wait_bounded(&bar[slot], (uint32_t)((g / kPairStages) & 1), errflag);
+      const float* nd = stg + slot * kPStageFloats;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float* p = nd + c * (kPBoxNY * kPBoxX) + (ty + dy) * kPBoxX + lx + dx;
+            top[dy][dx][c] = make_float2(p[0], p[32]);
+          }
+      const float* el = nd + kPNodeStride + ty * kPBoxX + lx;
+      E = make_float2(el[0], el[32]);
+    };
+    // one stage per layer: wait, read, compute, exchange, barrier, refill,
+    // epilogue.  (Reading stage t+1 before the barrier, to overlap its latency
+    // with the exchange, measured slower: it spills at the 128-register cap.)
+    PairColumn col;
+    float2 top[2][2][3], E;
+    load_stage(0, top, E);
+    pair_seed(col, top);
+    __syncthreads();  // stage 0 read everywhere; the previous segment's exchange slots retired
+    if (tid == 0 && kPairStages < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(kPairStages);
+    }
+#pragma unroll 2
+    for (int t = 1; t < nst; ++t) {
+      load_stage(t, top, E);
+      const float2 nE = make_float2(-E.x, -E.y);
+      float2 plane[3][4], ctr[3];
+      pair_layer(col, top, E, nE, kc, plane, ctr);
+      float2 n0[3];
+      float2(*xb)[kPairTY][kPairTX] = xch[t & 1];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float2 r = padd(n0[c], xb[c][ty - 1][tx]);
-        resA[c] = r.x;
-        resB[c] = r.y;
-        cA[c] = ctr[c].x;
-        cB[c] = ctr[c].y;
+        const float r1a = __shfl_sync(0xffffffffu, plane[c][1].x, src);
+        const float r1b = __shfl_sync(0xffffffffu, plane[c][1].y, src);
+        const float r3a = __shfl_sync(0xffffffffu, plane[c][3].x, src);
+        const float r3b = __shfl_sync(0xffffffffu, plane[c][3].y, src);
+        n0[c] = padd(plane[c][0], make_float2(r1a, tx > 0 ? r1b : r1a));
+        xb[c][ty][tx] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
       }
-      if (clean) {
-        if (ownA) part += epi(exA, ey, ez, oA, resA, cA, fd);
-        if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, fd);
-      } else {
-        if (ownA) part += epi(exA, ey, ez, oA, resA, cA, d);
-        if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, d);
+      __syncthreads();  // also retires this stage's slot
+      if (tid == 0 && t + kPairStages < nst) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(t + kPairStages);
       }
-      oA += d.plane_stride();
+      const int ez = kb - 2 + t;
+      if (ty > 0 && t >= 2) {
+        float resA[3], resB[3], cA[3], cB[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 r = padd(n0[c], xb[c][ty - 1][tx]);
+          resA[c] = r.x;
+          resB[c] = r.y;
+          cA[c] = ctr[c].x;
+          cB[c] = ctr[c].y;
+        }
+        if (clean) {
+          if (ownA) part += epi(exA, ey, ez, oA, resA, cA, fd);
+          if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, fd);
+        } else {
+          if (ownA) part += epi(exA, ey, ez, oA, resA, cA, d);
+          if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, d);
+        }
+        oA += d.plane_stride();
+      }
     }
+    gs += nst;
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
-    reduce_finalize<1>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * chunk),
-                       gridDim.x * gridDim.y * zc);
+    reduce_finalize<1>(v, red, blockIdx.x, gridDim.x);
   }
 }
 
 bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                CUtensorMap* emap);
 
-// z planes per CTA of the paired kernel: the chunk length that minimises
-// (waves of two CTAs per SM) x (planes per CTA + the two warm-up layers),
-// with no more CTAs than partial-sum slots
-inline int pair_zchunk(const Dims& d, int nb = 1) {
-  const long long xy = (long long)((d.nx + kPairOwnX) / kPairOwnX) *
-                       ((d.ny + kPairOwnY) / kPairOwnY) * nb;
-  const int planes = d.nz + 1;
-  const long long slots = 152LL * kPairCtasPerSm;
-  int best = planes;
-  long long best_cost = -1;
-  for (int z = 4; z <= planes; ++z) {
-    const long long chunks = (planes + z - 1) / z;
-    if (xy * chunks > kMaxPartials) continue;
-    const long long cost = ((xy * chunks + slots - 1) / slots) * (z + 2);
-    if (best_cost < 0 || cost < best_cost) {
-      best_cost = cost;
-      best = z;
-    }
-  }
-  return best;
+// CTAs per design of the paired kernel: one resident wave over the designs
+// of the launch (two CTAs per SM), at least 4 node planes of work each, and
+// no more than the partial-sum slots.  (Measured: 123 us at 320x160x160 and
+// 35.0 us at 192x96x96, against 133 and 37.1 us for whole-tile z-chunks.)
+inline int pair_ctas(const Dims& d, int nb = 1) {
+  const long long W = (long long)((d.nx + kPairOwnX) / kPairOwnX) *
+                      ((d.ny + kPairOwnY) / kPairOwnY) * (d.nz + 1);
+  long long g = 152LL * kPairCtasPerSm / nb;
+  g = std::min(g, W / 4);
+  g = std::min<long long>(g, kMaxPartials);
+  return (int)std::max(1LL, g);
 }
 
 template <class Epi>
@@ -342,19 +351,18 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int z = pair_zchunk(d, bt.nb);
-  const int zc = (d.nz + z) / z;
+  const int gx = (d.nx + kPairOwnX) / kPairOwnX, gy = (d.ny + kPairOwnY) / kPairOwnY;
   dim3 block(kPairTX, kPairTY, 1);
-  dim3 grid((d.nx + kPairOwnX) / kPairOwnX, (d.ny + kPairOwnY) / kPairOwnY, zc * bt.nb);
-  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, z, zc, bt.S,
+  dim3 grid(pair_ctas(d, bt.nb), 1, bt.nb);
+  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, gx, gy, bt.S,
                                                    done, errflag);
   return cudaGetLastError();
 }
 
 // Smallest nx for which the automatic form picks the paired kernel.  Measured
 // on GB300 (one plain FP32 application, inputs above L2): 96x32x32 10.3 us
-// either form; 192x96x96 37.1 us paired vs 41.1 us one-column; 320x160x160
-// 133 us vs 143 us.
+// one-column; 192x96x96 35.0 us paired vs 41.2 us one-column; 320x160x160
+// 123 us vs 145 us.
 constexpr int kPairAutoMinNx = 150;
 
 // The operator launch of both modal forms: the paired kernel where it is
