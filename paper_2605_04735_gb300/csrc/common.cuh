@@ -243,6 +243,58 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
   }
 }
 
+// *p += v as a fire-and-forget reduction performed at L2 (no load round trip
+// and no register kept for the old value).  Used where one thread owns the
+// entry, so the result is the same sum in the same order as a load-add-store
+// (round to nearest; subnormal inputs and results flush to zero).
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// Operator epilogues implement run<N>() over N owned nodes of one plane:
+// every operand of the N nodes is loaded before the first store, so the
+// group costs one memory round trip (the compiler must otherwise assume a
+// store may alias the next load and serialises them).  epi_one() runs the
+// epilogue on one node.
+template <class Epi, typename T, class DD>
+__device__ __forceinline__ T epi_one(const Epi& e, int i, int j, int k, long long o,
+                                     const T (&acc)[3], const T (&ctr)[3], const DD& d) {
+  const int ii[1] = {i};
+  const long long oo[1] = {o};
+  const bool own[1] = {true};
+  const T a[1][3] = {{acc[0], acc[1], acc[2]}};
+  const T c[1][3] = {{ctr[0], ctr[1], ctr[2]}};
+  return e.template run<1>(ii, j, k, oo, own, a, c, d);
+}
+
+// Programmatic dependent launch.  Kernels of the solve path start with
+// pdl_start(): wait until the kernel launched before them on the stream has
+// completed and its writes are visible (a no-op when there is no programmatic
+// dependency), then allow the next kernel to be launched, so its CTAs are
+// resident and waiting when this one ends.  launch_pdl() launches a kernel
+// with that dependency (stream order otherwise unchanged; kept by graph
+// capture).  Every kernel launched with launch_pdl must begin with pdl_start.
+__device__ __forceinline__ void pdl_start() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Deterministic block-partial reduction of NV doubles with a last-block
 // finalisation: every block writes its partials, the last block to arrive
 // sums them in block order (fixed order => bitwise reproducible) and calls

@@ -36,6 +36,7 @@ __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
                             float* __restrict__ d0, float* __restrict__ x,
                             const float* __restrict__ dinv, long long n4, float inv_theta,
                             const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -61,6 +62,7 @@ __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
 
 __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long long n4,
                         const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -92,20 +94,33 @@ struct EpiChebStep {
     return EpiChebStep{bshift(r, off), bshift(dn, off), bshift(x, off), bshift(dinv, off),
                        c1, c2, add_prev};
   }
-  template <class DD>
-  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
-                                              const float (&acc)[3], const float (&ctr)[3],
-                                              const DD& d) const {
+  template <int N, class DD>
+  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                       const bool (&own)[N], const float (&acc)[N][3],
+                                       const float (&ctr)[N][3], const DD& d) const {
+    float rv[N][3], dv[N][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long oc = c * d.comp + o;
-      const float Ad = d.fixed(c, i, j, k) ? 0.0f : acc[c];
-      const float rn = r[oc] - Ad;
-      const float dd = fmaf(c1, ctr[c], c2 * dinv[oc] * rn);
-      r[oc] = rn;
-      dn[oc] = dd;
-      x[oc] += add_prev ? (dd + ctr[c]) : dd;
-    }
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long oc = c * d.comp + o[n];
+          rv[n][c] = r[oc];
+          dv[n][c] = dinv[oc];
+        }
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long oc = c * d.comp + o[n];
+          const float Ad = d.fixed(c, i[n], j, k) ? 0.0f : acc[n][c];
+          const float rn = rv[n][c] - Ad;
+          const float dd = fmaf(c1, ctr[n][c], c2 * dv[n][c] * rn);
+          r[oc] = rn;
+          dn[oc] = dd;
+          red_add(x + oc, add_prev ? (dd + ctr[n][c]) : dd);
+        }
     return 0.0f;
   }
 };
@@ -115,13 +130,16 @@ struct EpiChebLast {
   static constexpr bool kReduce = false;
   float* r;
   __device__ EpiChebLast shifted(long long off) const { return EpiChebLast{bshift(r, off)}; }
-  template <class DD>
-  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
-                                              const float (&acc)[3], const float (&)[3],
-                                              const DD& d) const {
+  template <int N, class DD>
+  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                       const bool (&own)[N], const float (&acc)[N][3],
+                                       const float (&)[N][3], const DD& d) const {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (!d.fixed(c, i, j, k)) r[c * d.comp + o] -= acc[c];
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (!d.fixed(c, i[n], j, k)) red_add(r + c * d.comp + o[n], -acc[n][c]);
     return 0.0f;
   }
 };
@@ -138,17 +156,30 @@ struct EpiChebResid {
     return EpiChebResid{bshift(b, off), bshift(r, off), bshift(d0, off), bshift(dinv, off),
                         inv_theta};
   }
-  template <class DD>
-  __device__ __forceinline__ float operator()(int i, int j, int k, long long o,
-                                              const float (&acc)[3], const float (&)[3],
-                                              const DD& d) const {
+  template <int N, class DD>
+  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                       const bool (&own)[N], const float (&acc)[N][3],
+                                       const float (&)[N][3], const DD& d) const {
+    float bv[N][3], dv[N][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const long long oc = c * d.comp + o;
-      const float rr = d.fixed(c, i, j, k) ? 0.0f : (b[oc] - acc[c]);
-      r[oc] = rr;
-      d0[oc] = dinv[oc] * rr * inv_theta;
-    }
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long oc = c * d.comp + o[n];
+          bv[n][c] = b[oc];
+          dv[n][c] = dinv[oc];
+        }
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long oc = c * d.comp + o[n];
+          const float rr = d.fixed(c, i[n], j, k) ? 0.0f : (bv[n][c] - acc[n][c]);
+          r[oc] = rr;
+          d0[oc] = dv[n][c] * rr * inv_theta;
+        }
     return 0.0f;
   }
 };
@@ -159,6 +190,7 @@ struct EpiChebResid {
 // children beyond an odd fine grid are ghosts with E = 0
 __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* __restrict__ Ec,
                             const Dims dc, long long S) {
+  pdl_start();
   Ef = bshift(Ef, blockIdx.y * S);
   Ec = bshift(Ec, blockIdx.y * S);
   const long long n = (long long)dc.nx * dc.ny * dc.nz;
@@ -185,6 +217,7 @@ __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* 
 // (2I,2J,2K) and collects fine neighbours with weights 1, 1/2 per axis offset
 __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* __restrict__ bc,
                            const Dims dc, const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -225,6 +258,7 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
 // fine node), fixed fine DOFs untouched
 __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float* __restrict__ xf,
                               const Dims df, const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -262,6 +296,7 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
 // deterministic, no atomics)
 __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const float* __restrict__ E,
                                  const __grid_constant__ K0<double> k0, long long S) {
+  pdl_start();
   A = bshift(A, blockIdx.y * S);
   E = bshift(E, blockIdx.y * S);
   const int n = 3 * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
@@ -301,6 +336,7 @@ __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const flo
 // n launches is captured once per hierarchy as a CUDA graph.
 __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
                           double* __restrict__ col, long long S) {
+  pdl_start();
   A = bshift(A, blockIdx.y * S);
   row = bshift(row, blockIdx.y * S);
   col = bshift(col, blockIdx.y * S);
@@ -314,6 +350,7 @@ __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restric
 __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
                           const double* __restrict__ colk, double* __restrict__ rown,
                           double* __restrict__ coln, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   A = bshift(A, off);
   rowk = bshift(rowk, off);
@@ -342,6 +379,7 @@ __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __
 
 __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, double* __restrict__ bd,
                                 const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -361,6 +399,7 @@ __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, doubl
 __global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __restrict__ bd,
                                int n, float* __restrict__ x, const Dims d,
                                const int* __restrict__ done, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   done = bshift(done, off);
   if (*done) return;
@@ -526,15 +565,15 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     const GmgLevel& F = g.lv[l - 1];
     GmgLevel& C = g.lv[l];
     const long long ne = (long long)C.d.nx * C.d.ny * C.d.nz;
-    k_coarsen_E<<<dim3(grid1d(ne), bt.nb), kPT, 0, s>>>(F.E, F.d, C.E, C.d, bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_coarsen_E, dim3(grid1d(ne), bt.nb), dim3(kPT), 0, s, F.E, F.d, C.E, C.d,
+                   bt.S));
     GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s, bt));
     *launches += 2;
   }
   const GmgLevel& Lc = g.lv.back();
   const long long nn = (long long)g.nc * g.nc;
-  k_dense_assemble<<<dim3(grid1d(nn), bt.nb), kPT, 0, s>>>(g.Ainv, Lc.d, Lc.E, k0d, bt.S);
-  GCK(cudaGetLastError());
+  GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d, Lc.E,
+                 k0d, bt.S));
   // the pivot chain, captured once per batch shape as a graph and replayed per density
   if (g.gj_exec && (g.gj_nb != bt.nb || g.gj_S != bt.S)) {
     cudaGraphExecDestroy(g.gj_exec);
@@ -547,15 +586,16 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
-      k_gj_seed<<<dim3((g.nc + kPT - 1) / kPT, bt.nb), kPT, 0, cs>>>(g.Ainv, g.nc, buf[0][0],
-                                                                      buf[0][1], bt.S);
-      for (int k = 0; k < g.nc; ++k) {
+      e = launch_pdl(k_gj_seed, dim3((g.nc + kPT - 1) / kPT, bt.nb), dim3(kPT), 0, cs, g.Ainv,
+                     g.nc, buf[0][0], buf[0][1], bt.S);
+      for (int k = 0; k < g.nc && e == cudaSuccess; ++k) {
         double** cur = buf[k & 1];
         double** nxt = buf[(k + 1) & 1];
-        k_gj_step<<<dim3(grid1d(nn), bt.nb), kPT, 0, cs>>>(g.Ainv, g.nc, k, cur[0], cur[1],
-                                                           nxt[0], nxt[1], bt.S);
+        e = launch_pdl(k_gj_step, dim3(grid1d(nn), bt.nb), dim3(kPT), 0, cs, g.Ainv, g.nc, k,
+                       cur[0], cur[1], nxt[0], nxt[1], bt.S);
       }
-      e = cudaStreamEndCapture(cs, &graph);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = ec;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&g.gj_exec, graph, 0);
     g.gj_nb = bt.nb;
@@ -592,9 +632,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   for (int l = 0; l < nl - 1; ++l) {
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
-    k_cheb_init<<<dim3(grid1d(n4), bt.nb), kPT, 0, s>>>(B(l), L.r, L.dv[0], X(l), L.dinv, n4,
-                                                        cc.inv_theta, done, bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4), bt.nb), dim3(kPT), 0, s, B(l), L.r, L.dv[0],
+                   X(l), L.dinv, n4, cc.inv_theta, done, bt.S));
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
@@ -604,21 +643,19 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s, bt));
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
-    k_restrict<<<dim3(grid1d(nnc), bt.nb), kPT, 0, s>>>(L.r, L.d, C.b, C.d, done, bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_restrict, dim3(grid1d(nnc), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b, C.d,
+                   done, bt.S));
     *launches += 2;
   }
   // coarsest
   {
     const GmgLevel& C = g.lv[nl - 1];
     const int nnc = (C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
-    k_coarse_gather<<<dim3((nnc + kPT - 1) / kPT, bt.nb), kPT, 0, s>>>(B(nl - 1), C.d, g.bd, done,
-                                                                      bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_coarse_gather, dim3((nnc + kPT - 1) / kPT, bt.nb), dim3(kPT), 0, s,
+                   B(nl - 1), C.d, g.bd, done, bt.S));
     const long long thr = 32LL * g.nc;
-    k_coarse_apply<<<dim3((int)((thr + kPT - 1) / kPT), bt.nb), kPT, 0, s>>>(
-        g.Ainv, g.bd, g.nc, X(nl - 1), C.d, done, bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_coarse_apply, dim3((int)((thr + kPT - 1) / kPT), bt.nb), dim3(kPT), 0, s,
+                   g.Ainv, g.bd, g.nc, X(nl - 1), C.d, done, bt.S));
     *launches += 2;
   }
   // up
@@ -626,8 +663,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
-    k_prolong_add<<<dim3(grid1d(nnf), bt.nb), kPT, 0, s>>>(X(l + 1), C.d, X(l), L.d, done, bt.S);
-    GCK(cudaGetLastError());
+    GCK(launch_pdl(k_prolong_add, dim3(grid1d(nnf), bt.nb), dim3(kPT), 0, s, X(l + 1), C.d, X(l),
+                   L.d, done, bt.S));
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
@@ -637,9 +674,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
       ++*launches;
     }
     if (m == 1) {
-      k_axpy1<<<dim3(grid1d(L.nvec / 4), bt.nb), kPT, 0, s>>>(X(l), L.dv[0], L.nvec / 4, done,
-                                                              bt.S);
-      GCK(cudaGetLastError());
+      GCK(launch_pdl(k_axpy1, dim3(grid1d(L.nvec / 4), bt.nb), dim3(kPT), 0, s, X(l), L.dv[0],
+                     L.nvec / 4, done, bt.S));
       ++*launches;
     }
   }

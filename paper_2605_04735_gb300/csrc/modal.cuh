@@ -169,7 +169,7 @@ __device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3
   T res[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) res[c] = n0[c] + (ty > 0 ? xch[ty - 1][tx][c] : T(0));
-  return emit ? epi(ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
+  return emit ? epi_one(epi, ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
 }
 
 constexpr int kModalTX = 32, kModalTY = 8;
@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
                 const Dims d, const __grid_constant__ ModalCoef<float> kc, const Epi epi0,
                 const Red red0, const int zchunk, const int zc, const long long S,
                 const int* __restrict__ done, int* __restrict__ errflag) {
+  pdl_start();
   const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
   const long long off = design * S;
   done = bshift(done, off);
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
                   const __grid_constant__ ModalCoef<T> kc, const Epi epi0, const Red red0,
                   const int zchunk, const int zc, const long long S,
                   const int* __restrict__ done) {
+  pdl_start();
   const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
   const long long off = design * S;
   done = bshift(done, off);
@@ -363,13 +365,12 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
   if constexpr (sizeof(T) == 4) {
     CUtensorMap xm, em;
     if (modal_maps(x, E, d, bt, &xm, &em)) {
-      k_modal_tma<Epi><<<grid, block, 0, s>>>(xm, em, d, kc, epi, red, z, zc, bt.S, done,
-                                              errflag);
-      return cudaGetLastError();
+      return launch_pdl(k_modal_tma<Epi>, grid, block, 0, s, xm, em, d, kc, epi, red, z, zc,
+                        bt.S, done, errflag);
     }
   }
-  k_modal_plain<T, Epi><<<grid, block, 0, s>>>(x, E, d, kc, epi, red, z, zc, bt.S, done);
-  return cudaGetLastError();
+  return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.S,
+                    done);
 }
 
 }  // namespace topo

@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
                  const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi0,
                  const Red red0, const int gx, const int gy, const long long S,
                  const int* __restrict__ done, int* __restrict__ errflag) {
+  pdl_start();
   const int design = blockIdx.z;
   const long long off = design * S;
   done = bshift(done, off);
@@ -296,22 +297,22 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
       }
       const int ez = kb - 2 + t;
       if (ty > 0 && t >= 2) {
-        float resA[3], resB[3], cA[3], cB[3];
+        float res[2][3], cc[2][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float2 r = padd(n0[c], xb[c][ty - 1][tx]);
-          resA[c] = r.x;
-          resB[c] = r.y;
-          cA[c] = ctr[c].x;
-          cB[c] = ctr[c].y;
+          res[0][c] = r.x;
+          res[1][c] = r.y;
+          cc[0][c] = ctr[c].x;
+          cc[1][c] = ctr[c].y;
         }
-        if (clean) {
-          if (ownA) part += epi(exA, ey, ez, oA, resA, cA, fd);
-          if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, fd);
-        } else {
-          if (ownA) part += epi(exA, ey, ez, oA, resA, cA, d);
-          if (ownB) part += epi(exA + 32, ey, ez, oA + 32, resB, cB, d);
-        }
+        const int ii[2] = {exA, exA + 32};
+        const long long oo[2] = {oA, oA + 32};
+        const bool own[2] = {ownA, ownB};
+        if (clean)
+          part += epi.template run<2>(ii, ey, ez, oo, own, res, cc, fd);
+        else
+          part += epi.template run<2>(ii, ey, ez, oo, own, res, cc, d);
         oA += d.plane_stride();
       }
     }
@@ -354,9 +355,8 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
   const int gx = (d.nx + kPairOwnX) / kPairOwnX, gy = (d.ny + kPairOwnY) / kPairOwnY;
   dim3 block(kPairTX, kPairTY, 1);
   dim3 grid(pair_ctas(d, bt.nb), 1, bt.nb);
-  k_modal_pair<Epi><<<grid, block, kPairSmem, s>>>(xm, em, d, pair_coef(kc), epi, red, gx, gy, bt.S,
-                                                   done, errflag);
-  return cudaGetLastError();
+  return launch_pdl(k_modal_pair<Epi>, grid, block, kPairSmem, s, xm, em, d, pair_coef(kc), epi,
+                    red, gx, gy, bt.S, done, errflag);
 }
 
 // Smallest nx for which the automatic form picks the paired kernel.  Measured

@@ -22,16 +22,20 @@ struct EpiApply {
   static constexpr bool kReduce = DOT;
   T* y;
   __device__ EpiApply shifted(long long off) const { return EpiApply{bshift(y, off)}; }
-  template <class DD>
-  __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                          const T (&ctr)[3], const DD& d) const {
+  template <int N, class DD>
+  __device__ __forceinline__ T run(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                   const bool (&own)[N], const T (&acc)[N][3],
+                                   const T (&ctr)[N][3], const DD& d) const {
     T part = T(0);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const T out = d.fixed(r, i, j, k) ? ctr[r] : acc[r];
-      y[r * d.comp + o] = out;
-      if (DOT) part = fma(ctr[r], out, part);
-    }
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const T out = d.fixed(r, i[n], j, k) ? ctr[n][r] : acc[n][r];
+          y[r * d.comp + o[n]] = out;
+          if (DOT) part = fma(ctr[n][r], out, part);
+        }
     return part;
   }
 };
@@ -45,16 +49,26 @@ struct EpiResid {
   __device__ EpiResid shifted(long long off) const {
     return EpiResid{bshift(y, off), bshift(f, off)};
   }
-  template <class DD>
-  __device__ __forceinline__ T operator()(int i, int j, int k, long long o, const T (&acc)[3],
-                                          const T (&)[3], const DD& d) const {
+  template <int N, class DD>
+  __device__ __forceinline__ T run(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                   const bool (&own)[N], const T (&acc)[N][3],
+                                   const T (&)[N][3], const DD& d) const {
+    T fv[N][3];
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int r = 0; r < 3; ++r) fv[n][r] = f[r * d.comp + o[n]];
     T part = T(0);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const T out = d.fixed(r, i, j, k) ? T(0) : (f[r * d.comp + o] - acc[r]);
-      y[r * d.comp + o] = out;
-      part = fma(out, out, part);
-    }
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const T out = d.fixed(r, i[n], j, k) ? T(0) : (fv[n][r] - acc[n][r]);
+          y[r * d.comp + o[n]] = out;
+          part = fma(out, out, part);
+        }
     return part;
   }
 };
@@ -64,6 +78,7 @@ struct EpiResid {
 template <typename T>
 __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const Dims d,
                            const __grid_constant__ K0<T> k0, long long S) {
+  pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int design = blockIdx.z / (d.nz + 1);
@@ -121,8 +136,7 @@ cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0,
                             const Bat& bt) {
   dim3 block(32, 4, 1);
   dim3 grid((d.nx + 32) / 32, (d.ny + 4) / 4, (d.nz + 1) * bt.nb);
-  k_diag_inv<T><<<grid, block, 0, s>>>(dinv, E, d, k0, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_diag_inv<T>, grid, block, 0, s, dinv, E, d, k0, bt.S);
 }
 
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,

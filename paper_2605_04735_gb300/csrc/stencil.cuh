@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
 #pragma unroll
             for (int r = 0; r < 3; ++r) acc[r] = fma(ee, s[r], acc[r]);
           }
-      part += epi(i, j, k, d.node(i, j, k), acc, ctr, d);
+      part += epi_one(epi, i, j, k, d.node(i, j, k), acc, ctr, d);
       // slide the window up one plane
 #pragma unroll
       for (int yy = 0; yy < 3; ++yy)
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
         }
     const long long o = d.node(i, j, k);
     const T ctr[3] = {x[o], x[cs + o], x[2 * cs + o]};
-    part += epi(i, j, k, o, acc, ctr, d);
+    part += epi_one(epi, i, j, k, o, acc, ctr, d);
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kStencilBX* kStencilBY)
 #pragma unroll
             for (int r = 0; r < 3; ++r) acc[r] = fmaf(ee, sv[r], acc[r]);
           }
-      part += epi(i, j, k, d.node(i, j, k), acc, ctr, d);
+      part += epi_one(epi, i, j, k, d.node(i, j, k), acc, ctr, d);
     }
 #pragma unroll
     for (int yy = 0; yy < 3; ++yy)

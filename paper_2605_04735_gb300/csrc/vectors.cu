@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kThreads)
     k_pcg_init(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                T* __restrict__ p, const T* __restrict__ dinv, long long n4, const Red red0,
                long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   b = bshift(b, off);
   x = bshift(x, off);
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(kThreads)
     k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
                  const T* __restrict__ qv, const T* __restrict__ dinv, long long n4,
                  const Red red0, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   x = bshift(x, off);
   r = bshift(r, off);
@@ -150,6 +152,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, long long n4,
                     const PcgScalars* __restrict__ sc, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   p = bshift(p, off);
   z = bshift(z, off);
@@ -173,6 +176,7 @@ template <typename T, bool TWO>
 __global__ void __launch_bounds__(kThreads)
     k_dot(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c, long long n4,
           const Red red0, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   a = bshift(a, off);
   b = bshift(b, off);
@@ -199,6 +203,7 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_narrow_scaled(float* __restrict__ b32, const double* __restrict__ r64, long long n4,
                     const PcgScalars* __restrict__ sc, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   b32 = bshift(b32, off);
   r64 = bshift(r64, off);
@@ -221,6 +226,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_accumulate(double* __restrict__ u, const T* __restrict__ x, long long n4,
                  const PcgScalars* __restrict__ sc, int scaled, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   u = bshift(u, off);
   x = bshift(x, off);
@@ -241,6 +247,7 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_copy_cast(T* __restrict__ dst, const double* __restrict__ src, long long n4, long long S) {
+  pdl_start();
   const long long off = blockIdx.y * S;
   dst = bshift(dst, off);
   src = bshift(src, off);
@@ -269,8 +276,8 @@ __global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, long long S
 }  // namespace
 
 cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s, const Bat& bt) {
-  k_set_max_iter<<<(bt.nb + 127) / 128, 128, 0, s>>>(sc, max_iter, bt.nb, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_set_max_iter, dim3((bt.nb + 127) / 128), dim3(128), 0, s, sc, max_iter,
+                    bt.nb, bt.S);
 }
 
 template <typename T>
@@ -279,10 +286,10 @@ cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, l
   const long long n4 = n / 4;
   const dim3 g(reduce_blocks(n4), bt.nb);
   if (jacobi)
-    k_pcg_init<T, true><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red, bt.S);
-  else
-    k_pcg_init<T, false><<<g, kThreads, 0, s>>>(b, x, r, z, p, dinv, n4, red, bt.S);
-  return cudaGetLastError();
+    return launch_pdl(k_pcg_init<T, true>, g, dim3(kThreads), 0, s, b, x, r, z, p, dinv, n4, red,
+                      bt.S);
+  return launch_pdl(k_pcg_init<T, false>, g, dim3(kThreads), 0, s, b, x, r, z, p, dinv, n4, red,
+                    bt.S);
 }
 
 template <typename T>
@@ -291,59 +298,57 @@ cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T*
   const long long n4 = n / 4;
   const dim3 g(reduce_blocks(n4), bt.nb);
   if (jacobi)
-    k_pcg_update<T, true><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red, bt.S);
-  else
-    k_pcg_update<T, false><<<g, kThreads, 0, s>>>(x, r, z, p, q, dinv, n4, red, bt.S);
-  return cudaGetLastError();
+    return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4,
+                      red, bt.S);
+  return launch_pdl(k_pcg_update<T, false>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
+                    bt.S);
 }
 
 template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_pcg_direction<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(p, z, n4, sc, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_pcg_direction<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, p,
+                    z, n4, sc, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s,
                        const Bat& bt) {
   const long long n4 = n / 4;
-  k_dot<T, false><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(a, b, nullptr, n4, red,
-                                                                       bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_dot<T, false>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, a, b,
+                    nullptr, n4, red, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
                         cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_dot<T, true><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(a, b, c, n4, red, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_dot<T, true>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, a, b,
+                    c, n4, red, bt.S);
 }
 
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_narrow_scaled<<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(b32, r64, n4, sc, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_narrow_scaled, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, b32,
+                    r64, n4, sc, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgScalars* sc,
                               bool scaled, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  k_accumulate<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(u64, x, n4, sc,
-                                                                       scaled ? 1 : 0, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_accumulate<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, u64, x,
+                    n4, sc, scaled ? 1 : 0, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
                              const Bat& bt) {
   const long long n4 = n / 4;
-  k_copy_cast<T><<<dim3(reduce_blocks(n4), bt.nb), kThreads, 0, s>>>(dst, src, n4, bt.S);
-  return cudaGetLastError();
+  return launch_pdl(k_copy_cast<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, dst,
+                    src, n4, bt.S);
 }
 
 #define TOPO_INST(T)                                                                           \

@@ -9,6 +9,10 @@
         compliance, sensitivities) on one mesh: the launch list of a step.
     python -m paper_2605_04735_gb300.profile_run simp <workload> [iters]
         `iters` SIMP iterations (solve, sensitivity, filter, OC update).
+    python -m paper_2605_04735_gb300.profile_run batch <workload> [designs]
+        one mesh group of `designs` seeded designs (default 16) solved in
+        lockstep twice (a warm-up and the captured step), compliance and
+        sensitivities included: the launch list of a batched step.
 
 Workloads are the seeded recipes of `inputs.WORKLOADS`; nothing is read
 from disk.  Each command prints one line starting with "ok".
@@ -32,6 +36,25 @@ def main(argv):
     torch.cuda.set_device(0)
     s = torch.cuda.Stream()
     torch.cuda.set_stream(s)
+    if mode == "batch":
+        n = int(argv[2]) if len(argv) > 2 else 16
+        rhos = [I.dataclasses.replace(w, seed=w.seed + b).density() for b in range(n)]
+        opts = topo.default_opts(rtol=1e-8)
+        meshes = topo.create_batch(n, w.nx, w.ny, w.nz, w.bc, w.load, stream=s, opts=opts)
+        try:
+            for _ in range(2):
+                for m, r in zip(meshes, rhos):
+                    m.set_density(r)
+                infos = topo.solve_many(meshes, opts)
+                for m in meshes:
+                    m.compliance()
+                    m.sensitivity()
+            torch.cuda.synchronize()
+        finally:
+            for m in meshes:
+                m.close()
+        print("ok", mode, name, n, max(i.iters for i in infos), max(i.outer for i in infos))
+        return
     with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=s) as m:
         rho = w.density()
         if mode == "apply":
