@@ -251,11 +251,33 @@ __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-// Operator epilogues implement run<N>() over N owned nodes of one plane:
-// every operand of the N nodes is loaded before the first store, so the
-// group costs one memory round trip (the compiler must otherwise assume a
-// store may alias the next load and serialises them).  epi_one() runs the
-// epilogue on one node.
+// Operator epilogues.  An epilogue names kAux operand vectors (aux(q), read
+// at the node) and implements finish<N>() over N owned nodes of one plane,
+// given the operands in av[q][n][c]; it only stores.  epi_run() loads every
+// operand of the N nodes before the first store, so the group costs one
+// memory round trip (the compiler must otherwise assume a store may alias
+// the next load and serialises them); kernels that stage the operand planes
+// in shared memory call finish() directly.  epi_one() runs one node.
+template <class Epi>
+__host__ __device__ constexpr int epi_slots() {
+  return Epi::kAux > 0 ? Epi::kAux : 1;
+}
+
+template <class Epi, int N, typename T, class DD>
+__device__ __forceinline__ T epi_run(const Epi& e, const int (&i)[N], int j, int k,
+                                     const long long (&o)[N], const bool (&own)[N],
+                                     const T (&acc)[N][3], const T (&ctr)[N][3], const DD& d) {
+  T av[epi_slots<Epi>()][N][3];
+#pragma unroll
+  for (int q = 0; q < Epi::kAux; ++q)
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      if (own[n])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) av[q][n][c] = e.aux(q)[c * d.comp + o[n]];
+  return e.template finish<N>(i, j, k, o, own, acc, ctr, av, d);
+}
+
 template <class Epi, typename T, class DD>
 __device__ __forceinline__ T epi_one(const Epi& e, int i, int j, int k, long long o,
                                      const T (&acc)[3], const T (&ctr)[3], const DD& d) {
@@ -264,7 +286,7 @@ __device__ __forceinline__ T epi_one(const Epi& e, int i, int j, int k, long lon
   const bool own[1] = {true};
   const T a[1][3] = {{acc[0], acc[1], acc[2]}};
   const T c[1][3] = {{ctr[0], ctr[1], ctr[2]}};
-  return e.template run<1>(ii, j, k, oo, own, a, c, d);
+  return epi_run<Epi, 1>(e, ii, j, k, oo, own, a, c, d);
 }
 
 // Programmatic dependent launch.  Kernels of the solve path start with

@@ -84,6 +84,7 @@ __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long
 // d_k = c1 d_{k-1} + c2 D^-1 r; x += d_k (+ d_{k-1} when it was not yet added)
 struct EpiChebStep {
   static constexpr bool kReduce = false;
+  static constexpr int kAux = 2;  // r, D^-1
   float* r;
   float* dn;
   float* x;
@@ -94,20 +95,12 @@ struct EpiChebStep {
     return EpiChebStep{bshift(r, off), bshift(dn, off), bshift(x, off), bshift(dinv, off),
                        c1, c2, add_prev};
   }
+  __host__ __device__ const float* aux(int q) const { return q == 0 ? r : dinv; }
   template <int N, class DD>
-  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
-                                       const bool (&own)[N], const float (&acc)[N][3],
-                                       const float (&ctr)[N][3], const DD& d) const {
-    float rv[N][3], dv[N][3];
-#pragma unroll
-    for (int n = 0; n < N; ++n)
-      if (own[n])
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const long long oc = c * d.comp + o[n];
-          rv[n][c] = r[oc];
-          dv[n][c] = dinv[oc];
-        }
+  __device__ __forceinline__ float finish(const int (&i)[N], int j, int k,
+                                          const long long (&o)[N], const bool (&own)[N],
+                                          const float (&acc)[N][3], const float (&ctr)[N][3],
+                                          const float (&av)[2][N][3], const DD& d) const {
 #pragma unroll
     for (int n = 0; n < N; ++n)
       if (own[n])
@@ -115,8 +108,8 @@ struct EpiChebStep {
         for (int c = 0; c < 3; ++c) {
           const long long oc = c * d.comp + o[n];
           const float Ad = d.fixed(c, i[n], j, k) ? 0.0f : acc[n][c];
-          const float rn = rv[n][c] - Ad;
-          const float dd = fmaf(c1, ctr[n][c], c2 * dv[n][c] * rn);
+          const float rn = av[0][n][c] - Ad;
+          const float dd = fmaf(c1, ctr[n][c], c2 * av[1][n][c] * rn);
           r[oc] = rn;
           dn[oc] = dd;
           red_add(x + oc, add_prev ? (dd + ctr[n][c]) : dd);
@@ -128,12 +121,15 @@ struct EpiChebStep {
 // r -= A d (the residual after pre-smoothing)
 struct EpiChebLast {
   static constexpr bool kReduce = false;
+  static constexpr int kAux = 0;
   float* r;
   __device__ EpiChebLast shifted(long long off) const { return EpiChebLast{bshift(r, off)}; }
+  __host__ __device__ const float* aux(int) const { return nullptr; }
   template <int N, class DD>
-  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
-                                       const bool (&own)[N], const float (&acc)[N][3],
-                                       const float (&)[N][3], const DD& d) const {
+  __device__ __forceinline__ float finish(const int (&i)[N], int j, int k,
+                                          const long long (&o)[N], const bool (&own)[N],
+                                          const float (&acc)[N][3], const float (&)[N][3],
+                                          const float (&)[1][N][3], const DD& d) const {
 #pragma unroll
     for (int n = 0; n < N; ++n)
       if (own[n])
@@ -147,6 +143,7 @@ struct EpiChebLast {
 // post-smoothing start: r = b - A x (gathering x), d0 = D^-1 r / theta
 struct EpiChebResid {
   static constexpr bool kReduce = false;
+  static constexpr int kAux = 2;  // b, D^-1
   const float* b;
   float* r;
   float* d0;
@@ -156,29 +153,21 @@ struct EpiChebResid {
     return EpiChebResid{bshift(b, off), bshift(r, off), bshift(d0, off), bshift(dinv, off),
                         inv_theta};
   }
+  __host__ __device__ const float* aux(int q) const { return q == 0 ? b : dinv; }
   template <int N, class DD>
-  __device__ __forceinline__ float run(const int (&i)[N], int j, int k, const long long (&o)[N],
-                                       const bool (&own)[N], const float (&acc)[N][3],
-                                       const float (&)[N][3], const DD& d) const {
-    float bv[N][3], dv[N][3];
+  __device__ __forceinline__ float finish(const int (&i)[N], int j, int k,
+                                          const long long (&o)[N], const bool (&own)[N],
+                                          const float (&acc)[N][3], const float (&)[N][3],
+                                          const float (&av)[2][N][3], const DD& d) const {
 #pragma unroll
     for (int n = 0; n < N; ++n)
       if (own[n])
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const long long oc = c * d.comp + o[n];
-          bv[n][c] = b[oc];
-          dv[n][c] = dinv[oc];
-        }
-#pragma unroll
-    for (int n = 0; n < N; ++n)
-      if (own[n])
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const long long oc = c * d.comp + o[n];
-          const float rr = d.fixed(c, i[n], j, k) ? 0.0f : (bv[n][c] - acc[n][c]);
+          const float rr = d.fixed(c, i[n], j, k) ? 0.0f : (av[0][n][c] - acc[n][c]);
           r[oc] = rr;
-          d0[oc] = dv[n][c] * rr * inv_theta;
+          d0[oc] = av[1][n][c] * rr * inv_theta;
         }
     return 0.0f;
   }

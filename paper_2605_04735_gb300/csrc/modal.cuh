@@ -31,6 +31,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -150,25 +152,32 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
   }
 }
 
-// exchange a finished plane's corners with the neighbours and run the
-// epilogue on the owned node (ex, ey, ez)
-template <typename T, class Epi>
-__device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3], int tx, int ty,
-                                          int ex, int ey, int ez, bool emit, const T (&ctr)[3],
-                                          const Dims& d, const Epi& epi) {
-  T n0[3], n2[3];
+// exchange a finished plane's corners with the neighbours: res = the sums at
+// the node (ex, ey) of the plane (includes the CTA barrier)
+template <typename T>
+__device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[32][3], int tx,
+                                               int ty, T (&res)[3]) {
+  T n0[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T r1 = __shfl_up_sync(0xffffffffu, plane[c][1], 1);
     const T r3 = __shfl_up_sync(0xffffffffu, plane[c][3], 1);
     n0[c] = plane[c][0] + (tx > 0 ? r1 : T(0));
-    n2[c] = plane[c][2] + (tx > 0 ? r3 : T(0));
-    xch[ty][tx][c] = n2[c];
+    xch[ty][tx][c] = plane[c][2] + (tx > 0 ? r3 : T(0));
   }
   __syncthreads();
-  T res[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) res[c] = n0[c] + (ty > 0 ? xch[ty - 1][tx][c] : T(0));
+}
+
+// the exchange, then the epilogue on the owned node (ex, ey, ez), operands
+// read from global memory
+template <typename T, class Epi>
+__device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3], int tx, int ty,
+                                          int ex, int ey, int ez, bool emit, const T (&ctr)[3],
+                                          const Dims& d, const Epi& epi) {
+  T res[3];
+  modal_exchange<T>(plane, xch, tx, ty, res);
   return emit ? epi_one(epi, ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
 }
 
@@ -181,11 +190,24 @@ constexpr int kMBoxEY = kModalTY;        // element rows y0-1 .. y0+6
 constexpr int kMNode = 3 * kMBoxNY * kMBoxX;
 constexpr int kMElem = kMBoxEY * kMBoxX;
 constexpr uint32_t kMStageTx = (uint32_t)(kMNode + kMElem) * 4u;
-
-struct __align__(128) ModalStage {
-  float node[kMNode];
-  alignas(128) float elem[kMElem];
-};
+// stage layout (floats): node box, element box at a 128-byte boundary, then
+// the epilogue's operand planes (Epi::kAux boxes of 36 x 7 x 3 nodes: the
+// owned rows y0 .. y0+6 of the node plane the stage's epilogue writes)
+constexpr int kMElemOff = (kMNode + 31) / 32 * 32;
+constexpr int kMStageBase = (kMElemOff + kMElem + 31) / 32 * 32;
+constexpr int kMAuxX = 36;  // >= 3 (alignment slack) + 32 columns
+constexpr int kMAuxY = kModalOwnY;
+constexpr int kMAux = 3 * kMAuxY * kMAuxX;
+constexpr int kMAuxStride = (kMAux + 31) / 32 * 32;
+constexpr uint32_t kMAuxTx = (uint32_t)kMAux * 4u;
+__host__ __device__ constexpr int modal_stage_floats(int naux) {
+  return kMStageBase + naux * kMAuxStride;
+}
+constexpr size_t kModalXchBytes = sizeof(float) * 2 * kModalTY * kModalTX * 3;
+__host__ __device__ constexpr size_t modal_smem(int naux) {
+  return sizeof(float) * modal_stage_floats(naux) * kModalStages + kModalXchBytes +
+         sizeof(uint64_t) * kModalStages + 128;  // + alignment slack
+}
 
 // Grid: (x tiles, y tiles, zc z-chunks x designs); design b reads and writes
 // its own buffers at b * S bytes from design 0's (the TMA maps carry the
@@ -193,9 +215,14 @@ struct __align__(128) ModalStage {
 template <class Epi>
 __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
-                const Dims d, const __grid_constant__ ModalCoef<float> kc, const Epi epi0,
-                const Red red0, const int zchunk, const int zc, const long long S,
-                const int* __restrict__ done, int* __restrict__ errflag) {
+                const __grid_constant__ CUtensorMap amap0,
+                const __grid_constant__ CUtensorMap amap1, const Dims d,
+                const __grid_constant__ ModalCoef<float> kc, const Epi epi0, const Red red0,
+                const int zchunk, const int zc, const long long S, const int* __restrict__ done,
+                int* __restrict__ errflag) {
+  constexpr int NA = Epi::kAux;
+  static_assert(NA <= 2, "at most two staged operand vectors");
+  constexpr int SF = modal_stage_floats(NA);
   pdl_start();
   const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
   const long long off = design * S;
@@ -204,9 +231,14 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   if (done != nullptr && *done) return;  // uniform over the design's blocks
   const Epi epi = epi0.shifted(off);
   const Red red = red0.shifted(off);
-  __shared__ ModalStage st[kModalStages];
-  __shared__ uint64_t bar[kModalStages];
-  __shared__ float xch[2][kModalTY][kModalTX][3];
+  extern __shared__ __align__(128) unsigned char modal_dyn[];
+  // TMA destinations on 128-byte boundaries whatever the dynamic window's offset
+  unsigned char* base = modal_dyn + ((128u - (smem_u32(modal_dyn) & 127u)) & 127u);
+  float* stg = reinterpret_cast<float*>(base);
+  auto xch = reinterpret_cast<float(*)[kModalTY][kModalTX][3]>(
+      base + sizeof(float) * SF * kModalStages);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(base + sizeof(float) * SF * kModalStages + kModalXchBytes);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kModalTX + tx;
   const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * kModalOwnY;
@@ -221,13 +253,25 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     fence_mbar_init();
     tma_prefetch_desc(&xmap);
     tma_prefetch_desc(&emap);
+    if (NA > 0) tma_prefetch_desc(&amap0);
+    if (NA > 1) tma_prefetch_desc(&amap1);
   }
   __syncthreads();
+  // stage t: node plane kb-1+t, element layer kb-2+t and, once that plane
+  // has an epilogue (t >= 2), the operand planes of node plane kb-2+t
   auto issue = [&](int t) {
     const int slot = t % kModalStages;
-    mbar_arrive_expect_tx(&bar[slot], kMStageTx);
-    tma_load_5d(st[slot].node, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
-    tma_load_4d(st[slot].elem, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
+    float* sp = stg + slot * SF;
+    const bool ax = NA > 0 && t >= 2;
+    mbar_arrive_expect_tx(&bar[slot], kMStageTx + (ax ? NA * kMAuxTx : 0u));
+    tma_load_5d(sp, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
+    tma_load_4d(sp + kMElemOff, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
+    if (ax) {
+      tma_load_5d(sp + kMStageBase, &amap0, &bar[slot], bx, y0 + 1, kb - 1 + t, 0, design);
+      if (NA > 1)
+        tma_load_5d(sp + kMStageBase + kMAuxStride, &amap1, &bar[slot], bx, y0 + 1, kb - 1 + t,
+                    0, design);
+    }
   };
   if (tid == 0)
     for (int t = 0; t < kModalStages && t < nst; ++t) issue(t);
@@ -237,7 +281,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   for (int t = 0; t < nst; ++t) {
     const int slot = t % kModalStages;
     mbar_wait_bounded(&bar[slot], (uint32_t)((t / kModalStages) & 1), errflag);
-    const float* nd = st[slot].node;
+    const float* nd = stg + slot * SF;
     float top[2][2][3];  // [dy][dx][c]
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
@@ -246,7 +290,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           top[dy][dx][c] = nd[c * (kMBoxNY * kMBoxX) + (ty + dy) * kMBoxX + ox + tx + dx];
-    const float E = st[slot].elem[ty * kMBoxX + ox + tx];
+    const float E = nd[kMElemOff + ty * kMBoxX + ox + tx];
     if (t == 0) {  // the first node plane only seeds the march
       __syncthreads();
       if (tid == 0 && kModalStages < nst) {
@@ -259,12 +303,29 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     float plane[3][4], ctr[3];
     modal_layer<float>(col, top, E, kc, plane, ctr);
     const int ez = kb - 2 + t;
-    // the barrier inside modal_finish also retires this stage's slot
-    part += modal_finish<float, Epi>(plane, xch[t & 1], tx, ty, ex, ey, ez, own && t >= 2, ctr, d,
-                                     epi);
-    if (tid == 0 && t + kModalStages < nst) {
+    float res[3];
+    modal_exchange<float>(plane, xch[t & 1], tx, ty, res);
+    // the slot the exchange barrier retires: stage t's (its node data is
+    // read), or with staged operands stage t-1's (its epilogue, before this
+    // barrier, was the last reader; stage 0's slot was refilled after the seed)
+    const int freed = NA > 0 ? t - 1 : t;
+    if (tid == 0 && freed >= 1 && freed + kModalStages < nst) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + kModalStages);
+      issue(freed + kModalStages);
+    }
+    if (own && t >= 2) {
+      const int ii[1] = {ex};
+      const long long oo[1] = {d.node(ex, ey, ez)};
+      const bool ow[1] = {true};
+      const float rr[1][3] = {{res[0], res[1], res[2]}};
+      const float cc[1][3] = {{ctr[0], ctr[1], ctr[2]}};
+      float av[epi_slots<Epi>()][1][3];
+      const float* ap = nd + kMStageBase + (ty - 1) * kMAuxX + ox + tx;
+#pragma unroll
+      for (int q = 0; q < NA; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) av[q][0][c] = ap[q * kMAuxStride + c * (kMAuxY * kMAuxX)];
+      part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
     }
   }
   if (Epi::kReduce) {
@@ -353,6 +414,7 @@ inline int modal_zchunk(const Dims& d, int nb = 1) {
 
 bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                 CUtensorMap* emap);
+bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map);
 
 template <typename T, class Epi>
 cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
@@ -363,10 +425,21 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
   dim3 block(kModalTX, kModalTY, 1);
   dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY, zc * bt.nb);
   if constexpr (sizeof(T) == 4) {
-    CUtensorMap xm, em;
-    if (modal_maps(x, E, d, bt, &xm, &em)) {
-      return launch_pdl(k_modal_tma<Epi>, grid, block, 0, s, xm, em, d, kc, epi, red, z, zc,
-                        bt.S, done, errflag);
+    CUtensorMap xm, em, am[2];
+    std::memset(am, 0, sizeof(am));
+    bool ok = modal_maps(x, E, d, bt, &xm, &em);
+    for (int q = 0; q < Epi::kAux && ok; ++q) ok = modal_aux_map(epi.aux(q), d, bt, &am[q]);
+    if (ok) {
+      constexpr size_t smem = modal_smem(Epi::kAux);
+      static bool attr = false;  // per instantiation; setting it twice is harmless
+      if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_modal_tma<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      return launch_pdl(k_modal_tma<Epi>, grid, block, smem, s, xm, em, am[0], am[1], d, kc, epi,
+                        red, z, zc, bt.S, done, errflag);
     }
   }
   return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.S,

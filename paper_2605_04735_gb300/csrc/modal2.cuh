@@ -25,6 +25,7 @@
 
 #include <cuda.h>
 #include <algorithm>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -164,12 +165,24 @@ constexpr int kPElem = kPBoxEY * kPBoxX;
 constexpr int kPNodeStride = (kPNode + 31) / 32 * 32;          // floats, 128-byte multiple
 constexpr int kPStageFloats = (kPNodeStride + kPElem + 31) / 32 * 32;
 constexpr uint32_t kPStageTx = (uint32_t)(kPNode + kPElem) * 4u;
+// The epilogue's operand vectors (Epi::kAux of them) ride in the same ring:
+// for the node plane the stage's epilogue writes, a box of 68 x 7 x 3 nodes
+// (the owned rows y0 .. y0+6) per vector.
+constexpr int kPAuxY = kPairOwnY;
+constexpr int kPAux = 3 * kPAuxY * kPBoxX;
+constexpr int kPAuxStride = (kPAux + 31) / 32 * 32;  // floats, 128-byte multiple
+constexpr uint32_t kPAuxTx = (uint32_t)kPAux * 4u;
+__host__ __device__ constexpr int pair_stage_floats(int naux) {
+  return kPStageFloats + naux * kPAuxStride;
+}
 constexpr size_t kPairXchBytes = sizeof(float2) * 2 * kPairTY * kPairTX * 3;
 // CTAs resident per SM (the register budget).  Holding the kernel to one CTA
 // per SM (one wave) measured 49% slower at 320x160x160: two CTAs per SM it is.
 constexpr int kPairCtasPerSm = 2;
-constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPairXchBytes +
-                             sizeof(uint64_t) * kPairStages + 128;  // + alignment slack
+__host__ __device__ constexpr size_t pair_smem(int naux) {
+  return sizeof(float) * pair_stage_floats(naux) * kPairStages + kPairXchBytes +
+         sizeof(uint64_t) * kPairStages + 128;  // + alignment slack
+}
 
 // Grid: (G CTAs per design, 1, designs).  The work of a design is the list of
 // (x-y tile, node plane) pairs in tile-major order; CTA b takes the equal
@@ -180,9 +193,14 @@ constexpr size_t kPairSmem = sizeof(float) * kPStageFloats * kPairStages + kPair
 template <class Epi>
 __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     k_modal_pair(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
-                 const Dims d, const __grid_constant__ ModalCoef2 kc, const Epi epi0,
-                 const Red red0, const int gx, const int gy, const long long S,
-                 const int* __restrict__ done, int* __restrict__ errflag) {
+                 const __grid_constant__ CUtensorMap amap0,
+                 const __grid_constant__ CUtensorMap amap1, const Dims d,
+                 const __grid_constant__ ModalCoef2 kc, const Epi epi0, const Red red0,
+                 const int gx, const int gy, const long long S, const int* __restrict__ done,
+                 int* __restrict__ errflag) {
+  constexpr int NA = Epi::kAux;
+  static_assert(NA <= 2, "at most two staged operand vectors");
+  constexpr int SF = pair_stage_floats(NA);
   pdl_start();
   const int design = blockIdx.z;
   const long long off = design * S;
@@ -196,9 +214,9 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
   unsigned char* pair_smem = pair_dyn + ((128u - (smem_u32(pair_dyn) & 127u)) & 127u);
   float* stg = reinterpret_cast<float*>(pair_smem);
   auto xch = reinterpret_cast<float2(*)[3][kPairTY][kPairTX]>(
-      pair_smem + sizeof(float) * kPStageFloats * kPairStages);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(pair_smem + sizeof(float) * kPStageFloats * kPairStages +
-                                              kPairXchBytes);
+      pair_smem + sizeof(float) * SF * kPairStages);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(pair_smem + sizeof(float) * SF * kPairStages + kPairXchBytes);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kPairTX + tx;
   const int planes = d.nz + 1;
@@ -210,6 +228,8 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     fence_mbar_init();
     tma_prefetch_desc(&xmap);
     tma_prefetch_desc(&emap);
+    if (NA > 0) tma_prefetch_desc(&amap0);
+    if (NA > 1) tma_prefetch_desc(&amap1);
   }
   __syncthreads();
   const FreeDims fd{d.comp};
@@ -226,12 +246,21 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
     const int ox = x0 - bx;
     const int nst = (ke - kb) + 2;  // stage t: node plane kb-1+t, element layer kb-2+t
+    // stage t also carries the operand planes of node plane kb-2+t (storage
+    // plane kb-1+t, rows y0 .. y0+6) once that plane has an epilogue (t >= 2)
     auto issue = [&](int t) {
       const int slot = (gs + t) % kPairStages;
-      float* sp = stg + slot * kPStageFloats;
-      mbar_arrive_expect_tx(&bar[slot], kPStageTx);
+      float* sp = stg + slot * SF;
+      const bool ax = NA > 0 && t >= 2;
+      mbar_arrive_expect_tx(&bar[slot], kPStageTx + (ax ? NA * kPAuxTx : 0u));
       tma_load_5d(sp, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
       tma_load_4d(sp + kPNodeStride, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
+      if (ax) {
+        tma_load_5d(sp + kPStageFloats, &amap0, &bar[slot], bx, y0 + 1, kb - 1 + t, 0, design);
+        if (NA > 1)
+          tma_load_5d(sp + kPStageFloats + kPAuxStride, &amap1, &bar[slot], bx, y0 + 1,
+                      kb - 1 + t, 0, design);
+      }
     };
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -248,7 +277,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
       const int g = gs + t;
       const int slot = g % kPairStages;
       mbar_wait_bounded(&bar[slot], (uint32_t)((g / kPairStages) & 1), errflag);
-      const float* nd = stg + slot * kPStageFloats;
+      const float* nd = stg + slot * SF;
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -290,10 +319,14 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
         n0[c] = padd(plane[c][0], make_float2(r1a, tx > 0 ? r1b : r1a));
         xb[c][ty][tx] = padd(plane[c][2], make_float2(r3a, tx > 0 ? r3b : r3a));
       }
-      __syncthreads();  // also retires this stage's slot
-      if (tid == 0 && t + kPairStages < nst) {
+      __syncthreads();
+      // the slot this barrier retires: stage t's (its node data is read), or
+      // with staged operands stage t-1's (its epilogue, before this barrier,
+      // was the last reader; stage 0's slot was refilled after the seed)
+      const int freed = NA > 0 ? t - 1 : t;
+      if (tid == 0 && freed >= 1 && freed + kPairStages < nst) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(t + kPairStages);
+        issue(freed + kPairStages);
       }
       const int ez = kb - 2 + t;
       if (ty > 0 && t >= 2) {
@@ -309,14 +342,27 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
         const int ii[2] = {exA, exA + 32};
         const long long oo[2] = {oA, oA + 32};
         const bool own[2] = {ownA, ownB};
+        float av[epi_slots<Epi>()][2][3];
+        const float* ap = stg + ((gs + t) % kPairStages) * SF + kPStageFloats +
+                          (ty - 1) * kPBoxX + lx;
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            av[q][0][c] = ap[q * kPAuxStride + c * (kPAuxY * kPBoxX)];
+            av[q][1][c] = ap[q * kPAuxStride + c * (kPAuxY * kPBoxX) + 32];
+          }
         if (clean)
-          part += epi.template run<2>(ii, ey, ez, oo, own, res, cc, fd);
+          part += epi.template finish<2>(ii, ey, ez, oo, own, res, cc, av, fd);
         else
-          part += epi.template run<2>(ii, ey, ez, oo, own, res, cc, d);
+          part += epi.template finish<2>(ii, ey, ez, oo, own, res, cc, av, d);
         oA += d.plane_stride();
       }
     }
     gs += nst;
+    // the next segment's prologue refills every slot, this segment's last
+    // operand planes included: their readers must be done
+    if (NA > 0) __syncthreads();
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
@@ -326,6 +372,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
 
 bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
                CUtensorMap* emap);
+bool pair_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map);
 
 // CTAs per design of the paired kernel: one resident wave over the designs
 // of the launch (two CTAs per SM), at least 4 node planes of work each, and
@@ -344,19 +391,23 @@ template <class Epi>
 cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, const Dims& d,
                               const ModalCoef<float>& kc, const Epi& epi, const Red& red,
                               const int* done, int* errflag, cudaStream_t s, const Bat& bt) {
+  constexpr size_t smem = pair_smem(Epi::kAux);
   static bool attr = false;  // per instantiation; setting it twice is harmless
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_modal_pair<Epi>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kPairSmem);
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_modal_pair<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  CUtensorMap am[2];
+  std::memset(am, 0, sizeof(am));
+  for (int q = 0; q < Epi::kAux; ++q)
+    if (!pair_aux_map(epi.aux(q), d, bt, &am[q])) return cudaErrorInvalidValue;
   const int gx = (d.nx + kPairOwnX) / kPairOwnX, gy = (d.ny + kPairOwnY) / kPairOwnY;
   dim3 block(kPairTX, kPairTY, 1);
   dim3 grid(pair_ctas(d, bt.nb), 1, bt.nb);
-  return launch_pdl(k_modal_pair<Epi>, grid, block, kPairSmem, s, xm, em, d, pair_coef(kc), epi,
-                    red, gx, gy, bt.S, done, errflag);
+  return launch_pdl(k_modal_pair<Epi>, grid, block, smem, s, xm, em, am[0], am[1], d,
+                    pair_coef(kc), epi, red, gx, gy, bt.S, done, errflag);
 }
 
 // Smallest nx for which the automatic form picks the paired kernel.  Measured

@@ -20,12 +20,15 @@ namespace {
 template <typename T, bool DOT>
 struct EpiApply {
   static constexpr bool kReduce = DOT;
+  static constexpr int kAux = 0;
   T* y;
   __device__ EpiApply shifted(long long off) const { return EpiApply{bshift(y, off)}; }
+  __host__ __device__ const T* aux(int) const { return nullptr; }
   template <int N, class DD>
-  __device__ __forceinline__ T run(const int (&i)[N], int j, int k, const long long (&o)[N],
-                                   const bool (&own)[N], const T (&acc)[N][3],
-                                   const T (&ctr)[N][3], const DD& d) const {
+  __device__ __forceinline__ T finish(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                      const bool (&own)[N], const T (&acc)[N][3],
+                                      const T (&ctr)[N][3], const T (&)[1][N][3],
+                                      const DD& d) const {
     T part = T(0);
 #pragma unroll
     for (int n = 0; n < N; ++n)
@@ -44,28 +47,25 @@ struct EpiApply {
 template <typename T>
 struct EpiResid {
   static constexpr bool kReduce = true;
+  static constexpr int kAux = 1;  // f
   T* y;
   const T* f;
   __device__ EpiResid shifted(long long off) const {
     return EpiResid{bshift(y, off), bshift(f, off)};
   }
+  __host__ __device__ const T* aux(int) const { return f; }
   template <int N, class DD>
-  __device__ __forceinline__ T run(const int (&i)[N], int j, int k, const long long (&o)[N],
-                                   const bool (&own)[N], const T (&acc)[N][3],
-                                   const T (&)[N][3], const DD& d) const {
-    T fv[N][3];
-#pragma unroll
-    for (int n = 0; n < N; ++n)
-      if (own[n])
-#pragma unroll
-        for (int r = 0; r < 3; ++r) fv[n][r] = f[r * d.comp + o[n]];
+  __device__ __forceinline__ T finish(const int (&i)[N], int j, int k, const long long (&o)[N],
+                                      const bool (&own)[N], const T (&acc)[N][3],
+                                      const T (&)[N][3], const T (&av)[1][N][3],
+                                      const DD& d) const {
     T part = T(0);
 #pragma unroll
     for (int n = 0; n < N; ++n)
       if (own[n])
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-          const T out = d.fixed(r, i[n], j, k) ? T(0) : (fv[n][r] - acc[n][r]);
+          const T out = d.fixed(r, i[n], j, k) ? T(0) : (av[0][n][r] - acc[n][r]);
           y[r * d.comp + o[n]] = out;
           part = fma(out, out, part);
         }

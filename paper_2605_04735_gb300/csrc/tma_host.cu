@@ -128,4 +128,12 @@ bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUt
          cached_map(E, 1, d, kPBoxX, kPBoxEY, bt, emap);
 }
 
+bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map) {
+  return v != nullptr && cached_map(v, 0, d, kMAuxX, kMAuxY, bt, map);
+}
+
+bool pair_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map) {
+  return v != nullptr && cached_map(v, 0, d, kPBoxX, kPAuxY, bt, map);
+}
+
 }  // namespace topo
