@@ -2,12 +2,15 @@
 SIMP state solve + compliance + sensitivities, on the MBB half-beam
 96x32x32 workload (cone-smoothed seeded densities), one JSON line.
 
-A step is one pass of the whole hot path over one design: density upload
-and SIMP interpolation (Eq. (1)), the state solve K(rho) u = f (Eq. (2)) to
-rel. residual 1e-8, the compliance f^T u and the element sensitivities
-(Eq. (3)).  `value` times steps with inputs already in HBM (device
-timeline, CUDA events on the library's stream, L2 flushed between steps);
-`e2e` times the same through the public API with host buffers.
+A step is one pass of the whole hot path over a batch of B independent
+designs (default 64, one mesh group solved in lockstep; `--streams` for
+independent meshes): density upload and SIMP interpolation (Eq. (1)), the
+state solve K(rho) u = f (Eq. (2)) to rel. residual 1e-8, the compliance
+f^T u and the element sensitivities (Eq. (3)).  `value` times steps with
+inputs already in HBM (device timeline, CUDA events on the library's
+stream, L2 flushed between steps); `e2e` times the same through the public
+API with host buffers.  `roofline` is the FP32 operator's CG applies timed
+live over the timed steps, against the FP32 pipe (1152 flop per element).
 
 Under torchrun every rank solves its own independent designs (weak
 scaling); the only collectives are the timing barrier and max-reduction.
@@ -59,17 +62,41 @@ def operator_bytes(w: I.Workload) -> int:
     return 24 * w.n_nodes + 4 * w.n_elem
 
 
-def roofline(w: I.Workload, avg_ms: float, peaks: dict, peaks_src: str, op: int = 0) -> dict:
-    achieved = operator_bytes(w) / (avg_ms * 1e-3) / 1e9
-    peak = float(peaks["hbm_gbs"])
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(w.name) if op == 0 else None,
+FLOP_PER_ELEM = 2 * 24 * 24  # the dense K0 U_e product per element (multiply + add)
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x the SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(w: I.Workload, avg_ms: float, peaks: dict, peaks_src: str, op: int = 0,
+             designs: float = 1.0, traffic: float | None = None) -> dict:
+    """The FP32 SIMT operator is bound by the FP32 pipe: achieved = the dense
+    algorithmic 1152 flop per element x the elements one launch processes
+    (`designs` grids) / the average launch time, against the FP32 peak from
+    the unit counts and the maximum SM clock.  The HBM view (28 B per node
+    of algorithmic traffic against the measured copy bandwidth) is given
+    beside it."""
+    t = avg_ms * 1e-3
+    flops = FLOP_PER_ELEM * w.n_elem * designs
+    achieved = flops / t / 1e12
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(mhz)
+    hbm = operator_bytes(w) * designs / t / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
             "kernel": operator_kernel(op, w.nx), "workload": w.name,
-            "bytes_per_launch": operator_bytes(w),
-            "avg_launch_us": avg_ms * 1e3,
-            "gdofs": 3.0 * w.n_nodes / (avg_ms * 1e-3) / 1e9,
-            "peak_source": f"{peaks_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth), "
-                           f"frac is of {peaks_src}"}
+            "designs_per_launch": designs,
+            "flop_per_launch": flops, "avg_launch_us": avg_ms * 1e3,
+            "gdofs": 3.0 * w.n_nodes * designs / t / 1e9,
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz; "
+                           "1152 flop per element is the dense K0.U_e product (the modal "
+                           "kernel computes the same result with ~165 FP32 lane-ops)",
+            "hbm": {"bytes_per_launch": operator_bytes(w) * designs, "achieved": hbm,
+                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                    "frac": hbm / float(peaks["hbm_gbs"]),
+                    "peak_source": f"{peaks_src}: MEASURED_PEAKS.json hbm_gbs"}}
 
 
 def large_operator(topo, stream, flush, op: int = 0, reps: int = 20):
@@ -273,8 +300,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched", action="store_true",
-                    help="one mesh group solved as a batch instead of independent meshes")
+    ap.add_argument("--streams", action="store_true",
+                    help="independent meshes on their own streams instead of one mesh group "
+                         "solved in lockstep (one launch per step for all designs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -305,9 +333,10 @@ def main():
     dc_dev = [torch.empty(w.n_elem, dtype=torch.float64, device="cuda") for _ in range(B)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
-    # independent meshes on their own streams, or (--batched) one mesh group
-    # that solve_many runs as one batch (one launch per step for all designs)
-    if not args.batched:
+    # one mesh group that solve_many runs as one batch (one launch per step
+    # for all designs), or (--streams) independent meshes on their own streams
+    batched = not args.streams and B > 1
+    if not batched:
         meshes = [topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) for _ in range(B)]
     else:
         meshes = topo.create_batch(B, w.nx, w.ny, w.nz, w.bc, w.load, stream=stream, opts=opts)
@@ -330,6 +359,11 @@ def main():
         m.sensitivity(dc)
         return info, c
 
+    m0 = meshes[0]
+    # the batch's CG applies are timed live with events (design 0 holds the
+    # group's timing); a warm-up step captures the profiled graphs
+    if batched:
+        m0.profile(True)
     for _ in range(args.warmup):
         step_batch(rho_dev, dc_dev, opts)
     torch.cuda.synchronize()
@@ -356,11 +390,13 @@ def main():
     if dist:
         dist.barrier()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    launches = sum(m.profile_read(reset=True)[2] for m in meshes)
+    reads = [m.profile_read(reset=True) for m in meshes]
+    launches = sum(r[2] for r in reads)
+    batch_op_ms, batch_op_units = reads[0][0], reads[0][1]  # design-launches of the group
+    m0.profile(False)
     value, total_ms = job_throughput(float(step_ms.sum()), B * args.steps, dist, "cuda")
 
     # ---- single-design latency and the operator kernel's own timing ----
-    m0 = meshes[0]
     m0.profile(True)
     lat = []
     for k in range(args.steps):
@@ -416,9 +452,26 @@ def main():
 
     peaks, peaks_src = _peaks()
     avg_ms = prof_ms / max(prof_n, 1)
-    large = roofline(I.WORKLOADS[LARGE_WORKLOAD],
-                     large_operator(topo, stream, flush, args.operator), peaks, peaks_src,
-                     args.operator)
+    lw = I.WORKLOADS[LARGE_WORKLOAD]
+    large = roofline(lw, large_operator(topo, stream, flush, args.operator), peaks, peaks_src,
+                     args.operator,
+                     traffic=NCU_TRAFFIC.get(lw.name) if args.operator == 0 else None)
+    single = roofline(w, avg_ms, peaks, peaks_src, args.operator,
+                      traffic=NCU_TRAFFIC.get(w.name) if args.operator == 0 else None)
+    single["timed"] = "CG applies of the single-design loop (one design alone)"
+    single["launches"] = prof_n
+    if batched and batch_op_units > 0:
+        # design-launch units: the flops of the timed launches over their
+        # summed duration (each launch covered the designs still iterating)
+        main = roofline(w, batch_op_ms / batch_op_units, peaks, peaks_src, args.operator)
+        main["designs_per_launch"] = "varies (designs still iterating)"
+        main["avg_launch_us"] = None
+        main["timed"] = ("every CG apply of the timed batched steps, CUDA events on the "
+                         "library's stream; flops counted per design the launch advanced")
+        main["design_launches"] = batch_op_units
+        main["total_ms"] = batch_op_ms
+    else:
+        main = single
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(w)
@@ -431,6 +484,8 @@ def main():
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz,
                    "n_dof": 3 * w.n_nodes, "bc": "mbb" if w.bc == 1 else "cantilever",
                    "density": w.recipe, "rtol": 1e-8, "batch": B,
+                   "layout": ("one mesh group solved in lockstep (one launch per step for "
+                              "all designs)" if batched else "independent meshes on streams"),
                    "solver": ("FP32 PCG + FP64 refinement" if args.precision == 1 else "FP64 PCG")
                    + (" / Jacobi" if args.precond == 0 else " / GMG V-cycle"),
                    "l2": "flushed between steps (256 MB write)"},
@@ -442,12 +497,12 @@ def main():
                   "rel_residual_max": float(max(r[2] for r in recs)),
                   "compliance_design0": recs[0][3]},
         "fp64_jacobi_pcg": fp64,
-        # the CG apply (operator fused with p.Ap) of the single-design loop,
-        # timed live with CUDA events on the mesh's stream around every launch
-        "roofline": dict(roofline(w, avg_ms, peaks, peaks_src, args.operator), launches=prof_n,
-                         timed="CG applies of the single-design loop (one design alone)"),
-        # the same kernel on the 320x160x160 grid, alone, inputs above L2
-        "roofline_large": dict(large, timed="20 back-to-back applies, CUDA events"),
+        # the CG apply (operator fused with p.Ap): over the timed batched
+        # steps, alone for one design, and alone on the 320x160x160 grid
+        "roofline": main,
+        "roofline_single": single,
+        "roofline_large": dict(large, timed="20 back-to-back applies, CUDA events, inputs "
+                                            "above L2"),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem * B,
                 "d2h_bytes_per_step": (8 * w.n_elem + 8) * B},

@@ -152,7 +152,8 @@ typedef struct {
 void topo_default_params(topo_params* p);
 void topo_default_opts(topo_solve_opts* o);
 
-/* Create a mesh of nx*ny*nz elements (each >= 1) with the given boundary
+/* Create a mesh of nx*ny*nz elements (each in [1, 4096], fewer than 2^31
+ * nodes in all; TOPO_ERR_INVALID otherwise) with the given boundary
  * condition and load, on the current CUDA device.  stream: the caller's
  * cudaStream_t to order against (NULL = legacy default stream).  Allocates all device state of the
  * FP32/FP64 Jacobi paths; the multigrid hierarchy is built on first use.

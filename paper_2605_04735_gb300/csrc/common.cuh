@@ -120,10 +120,12 @@ struct PcgScalars {
   unsigned counter[8];  // last-block counters of the reductions (reset by the last block)
   // per-design settings of the next inner solve, written by the host for
   // batched solves (FIN_INIT with a negative launch tolerance reads rtol2_next;
-  // rtol2_next >= 1 finishes the inner solve at once: the design sits out)
+  // rtol2_next >= 1 finishes the inner solve at once: the design sits out,
+  // and sat_out = 1 lets the batched refinement kernels skip it: its u and
+  // FP64 residual stay as they are)
   double rtol2_next;
   int max_iter_next;
-  int pad_;
+  int sat_out;
 };
 
 // A batch of designs with identical grids whose buffers sit at a fixed byte
@@ -241,6 +243,17 @@ __device__ __forceinline__ void finalize(const Red& red, const double* tot, int 
     default:
       break;
   }
+}
+
+// (i, j, k) of the linear index n = i + X (j + Y k) of an X x Y x Z box, in
+// 32-bit unsigned arithmetic (n < 2^32: meshes hold fewer than 2^31 nodes)
+__device__ __forceinline__ void unflatten3(long long n, int X, int Y, int& i, int& j, int& k) {
+  const unsigned u = (unsigned)n;
+  const unsigned t = u / (unsigned)X;
+  i = (int)(u - t * (unsigned)X);
+  const unsigned kk = t / (unsigned)Y;
+  j = (int)(t - kk * (unsigned)Y);
+  k = (int)kk;
 }
 
 // *p += v as a fire-and-forget reduction performed at L2 (no load round trip

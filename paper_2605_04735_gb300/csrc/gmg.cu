@@ -20,9 +20,12 @@ namespace {
 constexpr int kCoarseMaxDof = 400;  // target size of the dense coarsest problem
 constexpr int kPT = 256;
 
-inline int grid1d(long long n) {
+// blocks per design: one item per thread up to 16 blocks per SM in all,
+// shared among the nb designs of a batched launch
+inline int grid1d(long long n, int nb = 1) {
   long long b = (n + kPT - 1) / kPT;
-  return (int)std::max(1LL, std::min(b, 152LL * 16));
+  const long long cap = std::max(4LL, 152LL * 16 / std::max(nb, 1));
+  return (int)std::max(1LL, std::min(b, cap));
 }
 
 // ---------------------------------------------------------------- smoother
@@ -185,9 +188,8 @@ __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* 
   const long long n = (long long)dc.nx * dc.ny * dc.nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(e % dc.nx);
-    const int J = (int)((e / dc.nx) % dc.ny);
-    const int K = (int)(e / ((long long)dc.nx * dc.ny));
+    int I, J, K;
+    unflatten3(e, dc.nx, dc.ny, I, J, K);
     float s = 0.0f;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
@@ -215,9 +217,8 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
   const long long nn = (long long)(dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(n % (dc.nx + 1));
-    const int J = (int)((n / (dc.nx + 1)) % (dc.ny + 1));
-    const int K = (int)(n / ((long long)(dc.nx + 1) * (dc.ny + 1)));
+    int I, J, K;
+    unflatten3(n, dc.nx + 1, dc.ny + 1, I, J, K);
     float s[3] = {0.f, 0.f, 0.f};
     for (int dk = -1; dk <= 1; ++dk) {
       const int k = 2 * K + dk;
@@ -256,19 +257,26 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
   const long long nn = (long long)(df.nx + 1) * (df.ny + 1) * (df.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (df.nx + 1));
-    const int j = (int)((n / (df.nx + 1)) % (df.ny + 1));
-    const int k = (int)(n / ((long long)(df.nx + 1) * (df.ny + 1)));
+    int i, j, k;
+    unflatten3(n, df.nx + 1, df.ny + 1, i, j, k);
+    // the 2 x 2 x 2 coarse nodes around (i, j, k) with their trilinear
+    // weights (1 and 0 on an even index, 1/2 and 1/2 on an odd one), the same
+    // arithmetic for every node: no divergent loop bounds
     const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const float wi = (i & 1) ? 0.5f : 1.0f, wj = (j & 1) ? 0.5f : 1.0f,
-                wk = (k & 1) ? 0.5f : 1.0f;
+    const int i1 = min(i0 + 1, dc.nx), j1 = min(j0 + 1, dc.ny), k1 = min(k0 + 1, dc.nz);
+    const float wi[2] = {(i & 1) ? 0.5f : 1.0f, (i & 1) ? 0.5f : 0.0f};
+    const float wj[2] = {(j & 1) ? 0.5f : 1.0f, (j & 1) ? 0.5f : 0.0f};
+    const float wk[2] = {(k & 1) ? 0.5f : 1.0f, (k & 1) ? 0.5f : 0.0f};
+    const int ci[2] = {i0, i1}, cj[2] = {j0, j1}, ck[2] = {k0, k1};
     float s[3] = {0.f, 0.f, 0.f};
-    for (int c2 = 0; c2 < nk; ++c2)
-      for (int b2 = 0; b2 < nj; ++b2)
-        for (int a2 = 0; a2 < ni; ++a2) {
-          const long long o = dc.node(i0 + a2, j0 + b2, k0 + c2);
-          const float wt = wi * wj * wk;
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+        for (int a2 = 0; a2 < 2; ++a2) {
+          const long long o = dc.node(ci[a2], cj[b2], ck[c2]);
+          const float wt = wi[a2] * wj[b2] * wk[c2];
 #pragma unroll
           for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, xc[c * dc.comp + o], s[c]);
         }
@@ -346,23 +354,28 @@ __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __
   colk = bshift(colk, off);
   rown = bshift(rown, off);
   coln = bshift(coln, off);
-  const long long nn = (long long)n * n;
-  const double p = 1.0 / rowk[k];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    double v;
-    if (i == k && j == k)
-      v = p;
-    else if (i == k)
-      v = rowk[j] * p;
-    else if (j == k)
-      v = -colk[i] * p;
-    else
-      v = A[t] - colk[i] * rowk[j] * p;
-    A[t] = v;
-    if (i == k + 1) rown[j] = v;
-    if (j == k + 1) coln[i] = v;
+  __shared__ double sp;  // the pivot's reciprocal, one division per block
+  if (threadIdx.x == 0) sp = 1.0 / rowk[k];
+  __syncthreads();
+  const double p = sp;
+  // block b: rows b, b + gridDim.x, ...; threads across the row
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    double* Ai = A + (long long)i * n;
+    const double ci = colk[i];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double v;
+      if (i == k && j == k)
+        v = p;
+      else if (i == k)
+        v = rowk[j] * p;
+      else if (j == k)
+        v = -ci * p;
+      else
+        v = Ai[j] - ci * rowk[j] * p;
+      Ai[j] = v;
+      if (i == k + 1) rown[j] = v;
+      if (j == k + 1) coln[i] = v;
+    }
   }
 }
 
@@ -554,15 +567,15 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     const GmgLevel& F = g.lv[l - 1];
     GmgLevel& C = g.lv[l];
     const long long ne = (long long)C.d.nx * C.d.ny * C.d.nz;
-    GCK(launch_pdl(k_coarsen_E, dim3(grid1d(ne), bt.nb), dim3(kPT), 0, s, F.E, F.d, C.E, C.d,
-                   bt.S));
+    GCK(launch_pdl(k_coarsen_E, dim3(grid1d(ne, bt.nb), bt.nb), dim3(kPT), 0, s, F.E, F.d, C.E,
+                   C.d, bt.S));
     GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s, bt));
     *launches += 2;
   }
   const GmgLevel& Lc = g.lv.back();
   const long long nn = (long long)g.nc * g.nc;
-  GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d, Lc.E,
-                 k0d, bt.S));
+  GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn, bt.nb), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d,
+                 Lc.E, k0d, bt.S));
   // the pivot chain, captured once per batch shape as a graph and replayed per density
   if (g.gj_exec && (g.gj_nb != bt.nb || g.gj_S != bt.S)) {
     cudaGraphExecDestroy(g.gj_exec);
@@ -580,8 +593,8 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
       for (int k = 0; k < g.nc && e == cudaSuccess; ++k) {
         double** cur = buf[k & 1];
         double** nxt = buf[(k + 1) & 1];
-        e = launch_pdl(k_gj_step, dim3(grid1d(nn), bt.nb), dim3(kPT), 0, cs, g.Ainv, g.nc, k,
-                       cur[0], cur[1], nxt[0], nxt[1], bt.S);
+        e = launch_pdl(k_gj_step, dim3(std::min(g.nc, 1024), bt.nb), dim3(128), 0, cs, g.Ainv,
+                       g.nc, k, cur[0], cur[1], nxt[0], nxt[1], bt.S);
       }
       const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
       if (e == cudaSuccess) e = ec;
@@ -621,8 +634,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   for (int l = 0; l < nl - 1; ++l) {
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
-    GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4), bt.nb), dim3(kPT), 0, s, B(l), L.r, L.dv[0],
-                   X(l), L.dinv, n4, cc.inv_theta, done, bt.S));
+    GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
+                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, done, bt.S));
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
@@ -632,8 +645,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s, bt));
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
-    GCK(launch_pdl(k_restrict, dim3(grid1d(nnc), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b, C.d,
-                   done, bt.S));
+    GCK(launch_pdl(k_restrict, dim3(grid1d(nnc, bt.nb), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b,
+                   C.d, done, bt.S));
     *launches += 2;
   }
   // coarsest
@@ -652,8 +665,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
-    GCK(launch_pdl(k_prolong_add, dim3(grid1d(nnf), bt.nb), dim3(kPT), 0, s, X(l + 1), C.d, X(l),
-                   L.d, done, bt.S));
+    GCK(launch_pdl(k_prolong_add, dim3(grid1d(nnf, bt.nb), bt.nb), dim3(kPT), 0, s, X(l + 1), C.d,
+                   X(l), L.d, done, bt.S));
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
@@ -663,8 +676,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
       ++*launches;
     }
     if (m == 1) {
-      GCK(launch_pdl(k_axpy1, dim3(grid1d(L.nvec / 4), bt.nb), dim3(kPT), 0, s, X(l), L.dv[0],
-                     L.nvec / 4, done, bt.S));
+      GCK(launch_pdl(k_axpy1, dim3(grid1d(L.nvec / 4, bt.nb), bt.nb), dim3(kPT), 0, s, X(l),
+                     L.dv[0], L.nvec / 4, done, bt.S));
       ++*launches;
     }
   }

@@ -56,6 +56,7 @@ template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
                         cudaStream_t s, const Bat& bt = Bat{});
 // b32 = float(r64 * scale), scale = 1 / sqrt(sc->aux[0]) read on the device
+// (batched launches skip the designs with sc->sat_out set, as does accumulate)
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt = Bat{});
 // u64 += scale * x, scale = sqrt(sc->aux[0]) read on the device (T = float or double)

@@ -36,9 +36,8 @@ __global__ void __launch_bounds__(kLsThreads)
   const long long sx = d.nx + 1, sxy = (long long)(d.nx + 1) * (d.ny + 1);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d.nx);
-    const int j = (int)((e / d.nx) % d.ny);
-    const int k = (int)(e / ((long long)d.nx * d.ny));
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
     const long long n0 = i + sx * j + sxy * k;
     double pc[8];
     double lo = 1e300, hi = -1e300;
@@ -117,9 +116,8 @@ __global__ void __launch_bounds__(kLsThreads)
   const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (d.nx + 1));
-    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
-    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    int i, j, k;
+    unflatten3(n, d.nx + 1, d.ny + 1, i, j, k);
     double sJ = 0.0, sV = 0.0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {  // element (i - 1 + ax, j - 1 + ay, k - 1 + az)

@@ -24,9 +24,8 @@ __global__ void k_simp(const float* __restrict__ rho, float* __restrict__ rho_g,
   int nbad = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d.nx);
-    const int j = (int)((e / d.nx) % d.ny);
-    const int k = (int)(e / ((long long)d.nx * d.ny));
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
     float r = rho[e];
     if (!(r >= 0.0f && r <= 1.0f)) {  // catches NaN too
       ++nbad;
@@ -99,9 +98,8 @@ __global__ void k_pack(const T* __restrict__ soa, double* __restrict__ aos, cons
   const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (d.nx + 1));
-    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
-    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    int i, j, k;
+    unflatten3(n, d.nx + 1, d.ny + 1, i, j, k);
     const long long o = d.node(i, j, k);
 #pragma unroll
     for (int c = 0; c < 3; ++c) aos[3 * n + c] = (double)soa[c * d.comp + o];
@@ -113,9 +111,8 @@ __global__ void k_unpack(const double* __restrict__ aos, T* __restrict__ soa, co
   const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (d.nx + 1));
-    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
-    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    int i, j, k;
+    unflatten3(n, d.nx + 1, d.ny + 1, i, j, k);
     const long long o = d.node(i, j, k);
 #pragma unroll
     for (int c = 0; c < 3; ++c) soa[c * d.comp + o] = d.fixed(c, i, j, k) ? T(0) : (T)aos[3 * n + c];
@@ -137,9 +134,8 @@ __global__ void __launch_bounds__(256)
   double part = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d.nx);
-    const int j = (int)((e / d.nx) % d.ny);
-    const int k = (int)(e / ((long long)d.nx * d.ny));
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
     double uh[3][8];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -190,9 +186,8 @@ __global__ void __launch_bounds__(256)
   int nbad = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d.nx);
-    const int j = (int)((e / d.nx) % d.ny);
-    const int k = (int)(e / ((long long)d.nx * d.ny));
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
     const long long n0 = i + sx * j + sxy * k;
     double pe = 0.0;
 #pragma unroll

@@ -40,9 +40,8 @@ __global__ void __launch_bounds__(kSimpThreads)
   const long long n = (long long)d.nx * d.ny * d.nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e % d.nx);
-    const int j = (int)((e / d.nx) % d.ny);
-    const int k = (int)(e / ((long long)d.nx * d.ny));
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
     double num = 0.0, den = 0.0;
     for (int t = 0; t < taps.n; ++t) {
       const int ii = i + taps.di[t], jj = j + taps.dj[t], kk = k + taps.dk[t];

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -201,10 +202,10 @@ struct MeshGroup {
   std::map<long long, ChunkGraph> graphs;  // batched CG chunks
   PcgScalars* h_sc = nullptr;              // nb pinned host copies
   int* h_flag = nullptr;                   // nb
-  struct Next {
+  struct Next {  // the layout of PcgScalars' rtol2_next, max_iter_next, sat_out
     double rtol2;
     int max_iter;
-    int pad;
+    int sat_out;
   };
   Next* h_next = nullptr;  // nb: per-design settings of the next inner solve
   int gmg_levels = -1, gmg_degree = -1;
@@ -1001,6 +1002,7 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
   if (!out) return TOPO_ERR_INVALID;
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
+  if ((long long)(nx + 1) * (ny + 1) * (nz + 1) >= (1LL << 31)) return TOPO_ERR_INVALID;
   if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
   if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
@@ -1058,6 +1060,7 @@ topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const to
     return TOPO_ERR_INVALID;
   for (int b = 0; b < n_designs; ++b) out[b] = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
+  if ((long long)(nx + 1) * (ny + 1) * (nz + 1) >= (1LL << 31)) return TOPO_ERR_INVALID;
   if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
   if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
@@ -1496,14 +1499,18 @@ topo_status group_read_scalars(MeshGroup* G) {
   return TOPO_OK;
 }
 
-topo_status group_enqueue_iters(MeshGroup* G, int count) {
+// profile: events around every CG apply (design 0's events; one launch covers
+// every design still iterating)
+topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile) {
   topo_mesh* m = G->meshes[0];
   cudaStream_t s = m->stream;
   const Bat bt{G->nb, G->S};
   const int* done = &m->sc->done;
   for (int c = 0; c < count; ++c) {
+    if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c], s, cudaEventRecordExternal));
     LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
                               red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
+    if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
     LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
                                    red_of(m, FIN_RR_ONLY), false, s, bt));
     CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
@@ -1513,13 +1520,14 @@ topo_status group_enqueue_iters(MeshGroup* G, int count) {
   return TOPO_OK;
 }
 
-topo_status group_run_iters(MeshGroup* G, int count) {
+topo_status group_run_iters(MeshGroup* G, int count, bool profile) {
   topo_mesh* m = G->meshes[0];
-  auto it = G->graphs.find(count);
+  const long long key = (long long)count | ((long long)profile << 16);
+  auto it = G->graphs.find(key);
   if (it == G->graphs.end()) {
     const long long l0 = m->launches;
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    const topo_status st = group_enqueue_iters(G, count);
+    const topo_status st = group_enqueue_iters(G, count, profile);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (st != TOPO_OK || e != cudaSuccess) {
@@ -1535,7 +1543,7 @@ topo_status group_run_iters(MeshGroup* G, int count) {
     cg.exec = ex;
     cg.launches = m->launches - l0;
     m->launches = l0;
-    it = G->graphs.emplace(count, cg).first;
+    it = G->graphs.emplace(key, cg).first;
   }
   CK(cudaGraphLaunch(it->second.exec, m->stream));
   m->launches += it->second.launches;
@@ -1554,7 +1562,7 @@ MeshGroup* batchable(topo_mesh* const* meshes, int n, const topo_solve_opts& o) 
     return nullptr;
   for (int a = 0; a < n; ++a) {
     topo_mesh* m = meshes[a];
-    if (m->group != G || !m->use_modal || m->mcf.form != G->meshes[0]->mcf.form || m->prof ||
+    if (m->group != G || !m->use_modal || m->mcf.form != G->meshes[0]->mcf.form ||
         !m->gmg.arena || !m->gmg_built || m->gmg_levels_req != G->gmg_levels ||
         m->gmg_degree != G->gmg_degree)
       return nullptr;
@@ -1595,6 +1603,8 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     }
   }
   for (topo_mesh* q : G->meshes) q->solved = false;
+  const bool prof = m->prof;  // design 0 holds the batch's operator timing
+  if (prof) CKS(ensure_profile_events(m, o.check_every));
   CK(cudaMemset2DAsync(m->flags + 1, (size_t)G->S, 0, sizeof(int), nb, s));
   if (o.warm_start) {
     LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
@@ -1617,6 +1627,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
       MeshGroup::Next& nx = G->h_next[b];
       nx.rtol2 = 4.0;  // sit out
       nx.max_iter = 1;
+      nx.sat_out = 1;
       if (!running[b]) continue;
       const PcgScalars& h = G->h_sc[b];
       const double fn = std::sqrt(G->meshes[b]->fnorm2), rr = h.aux[0];
@@ -1646,11 +1657,16 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
       const double inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * fn / std::sqrt(rr)), 0.5);
       nx.rtol2 = inner * inner;
       nx.max_iter = o.max_iter - total[b];
+      nx.sat_out = 0;
       ++live;
     }
     if (!live) break;
+    static_assert(sizeof(MeshGroup::Next) == 2 * sizeof(double) &&
+                      offsetof(PcgScalars, sat_out) - offsetof(PcgScalars, rtol2_next) ==
+                          offsetof(MeshGroup::Next, sat_out),
+                  "Next mirrors the tail of PcgScalars");
     CK(cudaMemcpy2DAsync(&m->sc->rtol2_next, (size_t)G->S, G->h_next, sizeof(MeshGroup::Next),
-                         sizeof(double) + sizeof(int), nb, cudaMemcpyHostToDevice, s));
+                         sizeof(MeshGroup::Next), nb, cudaMemcpyHostToDevice, s));
     // inner start: b = r / ||r|| in FP32, x = 0, z = V(r), p = z
     const int* done = &m->sc->done;
     LK(m, launch_set_max_iter(m->sc, -1, s, bt));
@@ -1660,9 +1676,9 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
     LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s, bt));
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
-    std::vector<int> before(nb, -1);
+    std::vector<int> before(nb, -1), at(nb, 0);
     for (int chunk = 0;; ++chunk) {
-      CKS(group_run_iters(G, o.check_every));
+      CKS(group_run_iters(G, o.check_every, prof));
       CKS(group_read_scalars(G));
       bool all_done = true, progress = false;
       for (int b = 0; b < nb; ++b) {
@@ -1670,6 +1686,18 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         if (!h.done) all_done = false;
         if (h.iter != before[b]) progress = true;
         before[b] = h.iter;
+      }
+      if (prof) {  // launch c of the chunk advanced the designs with more than c iterations
+        for (int c = 0; c < o.check_every; ++c) {
+          int active = 0;
+          for (int b = 0; b < nb; ++b) active += (G->h_sc[b].iter - at[b]) > c;
+          if (!active) break;
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
+          m->prof_ms += ms;
+          m->prof_launches += active;
+        }
+        for (int b = 0; b < nb; ++b) at[b] = G->h_sc[b].iter;
       }
       if (all_done) break;
       if (!progress) return TOPO_ERR_CUDA;  // no design moved without stopping: a bug
@@ -1685,10 +1713,12 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         running[b] = 0;
       }
     }
-    // u += ||r|| x (designs that sat out have x = 0), then the FP64 residual
+    // u += ||r|| x, then the FP64 residual, for the designs that took part
+    // (those that sat out keep u and their residual)
     LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s, bt));
     LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
-                               red_of(m, FIN_AUX), APPLY_RESID, nullptr, m->flags + 1, s, bt));
+                               red_of(m, FIN_AUX), APPLY_RESID, &m->sc->sat_out, m->flags + 1, s,
+                               bt));
     CKS(group_read_scalars(G));
   }
   // every design's stream after the batch

@@ -43,9 +43,8 @@ __global__ void __launch_bounds__(kTrThreads)
   const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (d.nx + 1));
-    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
-    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    int i, j, k;
+    unflatten3(n, d.nx + 1, d.ny + 1, i, j, k);
     double xs[8][3], v[8];
     int m = 0;
     for (int c = 0; c < 8; ++c) {
@@ -373,9 +372,8 @@ __global__ void __launch_bounds__(kTrThreads)
   const int rmax = max(d.nx, max(d.ny, d.nz)) + 1;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (d.nx + 1));
-    const int j = (int)((n / (d.nx + 1)) % (d.ny + 1));
-    const int k = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    int i, j, k;
+    unflatten3(n, d.nx + 1, d.ny + 1, i, j, k);
     const double p[3] = {i * h, j * h, k * h};
     double best = INFINITY;
     for (int r = 0; r <= rmax; ++r) {

@@ -12,6 +12,8 @@
 // (deterministic order), which also takes the CG scalar decisions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,12 +23,18 @@ namespace {
 
 constexpr int kThreads = 256;
 
-inline int reduce_blocks(long long n4) {
+// blocks per design: one float4 per thread up to 8 blocks per SM in all,
+// shared among the nb designs of a batched launch (so each thread of a
+// large batch streams several float4 and the reductions have fewer partials)
+inline int reduce_blocks(long long n4, int nb = 1) {
   long long b = (n4 + kThreads - 1) / kThreads;
-  if (b > 152 * 8) b = 152 * 8;
+  const long long cap = std::max(4LL, 152LL * 8 * 2 / std::max(nb, 1));
+  b = std::min(b, std::min(cap, 152LL * 8));
   if (b < 1) b = 1;
   return (int)b;
 }
+
+inline dim3 vgrid(long long n4, const Bat& bt) { return dim3(reduce_blocks(n4, bt.nb), bt.nb); }
 
 template <typename T>
 struct Vec4;
@@ -202,12 +210,13 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void __launch_bounds__(kThreads)
     k_narrow_scaled(float* __restrict__ b32, const double* __restrict__ r64, long long n4,
-                    const PcgScalars* __restrict__ sc, long long S) {
+                    const PcgScalars* __restrict__ sc, int skip, long long S) {
   pdl_start();
   const long long off = blockIdx.y * S;
   b32 = bshift(b32, off);
   r64 = bshift(r64, off);
   sc = bshift(sc, off);
+  if (skip && sc->sat_out) return;
   const double nrm2 = sc->aux[0];
   const double s = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
@@ -225,12 +234,13 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_accumulate(double* __restrict__ u, const T* __restrict__ x, long long n4,
-                 const PcgScalars* __restrict__ sc, int scaled, long long S) {
+                 const PcgScalars* __restrict__ sc, int scaled, int skip, long long S) {
   pdl_start();
   const long long off = blockIdx.y * S;
   u = bshift(u, off);
   x = bshift(x, off);
   sc = bshift(sc, off);
+  if (skip && sc->sat_out) return;
   const double s = scaled ? sqrt(sc->aux[0]) : 1.0;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
        q += (long long)gridDim.x * blockDim.x) {
@@ -276,15 +286,15 @@ __global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, long long S
 }  // namespace
 
 cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s, const Bat& bt) {
-  return launch_pdl(k_set_max_iter, dim3((bt.nb + 127) / 128), dim3(128), 0, s, sc, max_iter,
-                    bt.nb, bt.S);
+  return launch_pdl(k_set_max_iter, dim3((bt.nb + 127) / 128), dim3(128), 0, s, sc, max_iter, bt.nb,
+                    bt.S);
 }
 
 template <typename T>
 cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, long long n,
                             const Red& red, bool jacobi, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  const dim3 g(reduce_blocks(n4), bt.nb);
+  const dim3 g = vgrid(n4, bt);
   if (jacobi)
     return launch_pdl(k_pcg_init<T, true>, g, dim3(kThreads), 0, s, b, x, r, z, p, dinv, n4, red,
                       bt.S);
@@ -296,10 +306,10 @@ template <typename T>
 cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
                               const Red& red, bool jacobi, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  const dim3 g(reduce_blocks(n4), bt.nb);
+  const dim3 g = vgrid(n4, bt);
   if (jacobi)
-    return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4,
-                      red, bt.S);
+    return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
+                      bt.S);
   return launch_pdl(k_pcg_update<T, false>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
                     bt.S);
 }
@@ -308,47 +318,44 @@ template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_pcg_direction<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, p,
-                    z, n4, sc, bt.S);
+  return launch_pdl(k_pcg_direction<T>, vgrid(n4, bt), dim3(kThreads), 0, s, p, z, n4, sc, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cudaStream_t s,
                        const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_dot<T, false>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, a, b,
-                    nullptr, n4, red, bt.S);
+  return launch_pdl(k_dot<T, false>, vgrid(n4, bt), dim3(kThreads), 0, s, a, b, nullptr, n4, red,
+                    bt.S);
 }
 
 template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
                         cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_dot<T, true>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, a, b,
-                    c, n4, red, bt.S);
+  return launch_pdl(k_dot<T, true>, vgrid(n4, bt), dim3(kThreads), 0, s, a, b, c, n4, red, bt.S);
 }
 
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_narrow_scaled, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, b32,
-                    r64, n4, sc, bt.S);
+  return launch_pdl(k_narrow_scaled, vgrid(n4, bt), dim3(kThreads), 0, s, b32, r64, n4, sc,
+                    bt.nb > 1 ? 1 : 0, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgScalars* sc,
                               bool scaled, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_accumulate<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, u64, x,
-                    n4, sc, scaled ? 1 : 0, bt.S);
+  return launch_pdl(k_accumulate<T>, vgrid(n4, bt), dim3(kThreads), 0, s, u64, x, n4, sc,
+                    scaled ? 1 : 0, bt.nb > 1 ? 1 : 0, bt.S);
 }
 
 template <typename T>
 cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
                              const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_copy_cast<T>, dim3(reduce_blocks(n4), bt.nb), dim3(kThreads), 0, s, dst,
-                    src, n4, bt.S);
+  return launch_pdl(k_copy_cast<T>, vgrid(n4, bt), dim3(kThreads), 0, s, dst, src, n4, bt.S);
 }
 
 #define TOPO_INST(T)                                                                           \

@@ -4,6 +4,8 @@
         one mesh, density set, `reps` internal applications of the FP32
         operator (the CG apply with its fused p.Ap reduction) on a
         non-default stream: the capture target of the operator kernel.
+    python -m paper_2605_04735_gb300.profile_run apply64 <workload> [reps]
+        the same with the FP64 operator (the kernel of the FP64 residual).
     python -m paper_2605_04735_gb300.profile_run solve <workload> [reps]
         `reps` full steps (density, FP32 GMG-PCG + FP64 refinement to 1e-8,
         compliance, sensitivities) on one mesh: the launch list of a step.
@@ -31,7 +33,7 @@ def main(argv):
 
     mode = argv[0] if argv else "apply"
     name = argv[1] if len(argv) > 1 else "cantilever_voids_320x160x160"
-    reps = int(argv[2]) if len(argv) > 2 else (1 if mode == "apply" else 3)
+    reps = int(argv[2]) if len(argv) > 2 else (1 if mode.startswith("apply") else 3)
     w = I.WORKLOADS[name]
     torch.cuda.set_device(0)
     s = torch.cuda.Stream()
@@ -57,9 +59,9 @@ def main(argv):
         return
     with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=s) as m:
         rho = w.density()
-        if mode == "apply":
+        if mode in ("apply", "apply64"):
             m.set_density(rho)
-            m.apply_internal(1, 3 * reps)
+            m.apply_internal(1 if mode == "apply" else 0, 3 * reps)
             torch.cuda.synchronize()
             print("ok", mode, name, reps)
         elif mode == "solve":
