@@ -3,7 +3,7 @@ SIMP state solve + compliance + sensitivities, on the MBB half-beam
 96x32x32 workload (cone-smoothed seeded densities), one JSON line.
 
 A step is one pass of the whole hot path over a batch of B independent
-designs (default 64, one mesh group solved in lockstep; `--streams` for
+designs (default 256, one mesh group solved in lockstep; `--streams` for
 independent meshes): density upload and SIMP interpolation (Eq. (1)), the
 state solve K(rho) u = f (Eq. (2)) to rel. residual 1e-8, the compliance
 f^T u and the element sensitivities (Eq. (3)).  `value` times steps with
@@ -290,9 +290,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mbb_96x32x32", choices=sorted(I.WORKLOADS))
-    ap.add_argument("--batch", type=int, default=64,
-                    help="independent designs solved concurrently per step (throughput "
-                         "saturates near 64 on 96x32x32)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="independent designs solved concurrently per step")
+    ap.add_argument("--groups", type=int, default=1,
+                    help="mesh groups the batch is split into, each solved in lockstep by its "
+                         "own host thread (their launches overlap on the GPU)")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--operator", type=int, default=0, choices=[0, 1, 2, 3],
@@ -336,17 +338,31 @@ def main():
     # one mesh group that solve_many runs as one batch (one launch per step
     # for all designs), or (--streams) independent meshes on their own streams
     batched = not args.streams and B > 1
+    ng = max(1, min(args.groups, B // 2)) if batched else 1
     if not batched:
         meshes = [topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) for _ in range(B)]
+        groups = [meshes]
     else:
-        meshes = topo.create_batch(B, w.nx, w.ny, w.nz, w.bc, w.load, stream=stream, opts=opts)
+        sizes = [B // ng + (1 if g < B % ng else 0) for g in range(ng)]
+        groups = [topo.create_batch(n, w.nx, w.ny, w.nz, w.bc, w.load, stream=stream, opts=opts)
+                  for n in sizes]
+        meshes = [m for g in groups for m in g]
     for m in meshes:
         m.set_operator(args.operator)
+
+    pool = None
+    if len(groups) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        pool = ThreadPoolExecutor(max_workers=len(groups))
 
     def step_batch(rhos, dcs, opt):
         for m, r in zip(meshes, rhos):
             m.set_density(r)
-        infos = topo.solve_many(meshes, opt)
+        if pool is None:
+            infos = topo.solve_many(meshes, opt)
+        else:  # the groups' solves overlap on the GPU (the library calls release the GIL)
+            infos = [i for f in [pool.submit(topo.solve_many, g, opt) for g in groups]
+                     for i in f.result()]
         cs = [m.compliance() for m in meshes]
         for m, d in zip(meshes, dcs):
             m.sensitivity(d)
@@ -360,10 +376,12 @@ def main():
         return info, c
 
     m0 = meshes[0]
-    # the batch's CG applies are timed live with events (design 0 holds the
-    # group's timing); a warm-up step captures the profiled graphs
+    heads = [g[0] for g in groups]
+    # the batch's CG applies are timed live with events (design 0 of each
+    # group holds the group's timing); a warm-up step captures the profiled graphs
     if batched:
-        m0.profile(True)
+        for h in heads:
+            h.profile(True)
     for _ in range(args.warmup):
         step_batch(rho_dev, dc_dev, opts)
     torch.cuda.synchronize()
@@ -392,8 +410,12 @@ def main():
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     reads = [m.profile_read(reset=True) for m in meshes]
     launches = sum(r[2] for r in reads)
-    batch_op_ms, batch_op_units = reads[0][0], reads[0][1]  # design-launches of the group
-    m0.profile(False)
+    # summed over the groups: their launches overlap, so with several groups
+    # the per-launch time includes the sharing of the GPU
+    batch_op_ms = sum(r[0] for m, r in zip(meshes, reads) if m in heads)
+    batch_op_units = sum(r[1] for m, r in zip(meshes, reads) if m in heads)
+    for h in heads:
+        h.profile(False)
     value, total_ms = job_throughput(float(step_ms.sum()), B * args.steps, dist, "cuda")
 
     # ---- single-design latency and the operator kernel's own timing ----
@@ -444,6 +466,8 @@ def main():
                 "iters": int(np.mean(its)), "batch": 1}
 
     if rank != 0:
+        if pool is not None:
+            pool.shutdown()
         for m in meshes:
             m.close()
         if dist:
@@ -484,8 +508,9 @@ def main():
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz,
                    "n_dof": 3 * w.n_nodes, "bc": "mbb" if w.bc == 1 else "cantilever",
                    "density": w.recipe, "rtol": 1e-8, "batch": B,
-                   "layout": ("one mesh group solved in lockstep (one launch per step for "
-                              "all designs)" if batched else "independent meshes on streams"),
+                   "layout": (f"{len(groups)} mesh group(s) solved in lockstep (one launch "
+                              "per step for all designs of a group; groups on their own host "
+                              "threads)" if batched else "independent meshes on streams"),
                    "solver": ("FP32 PCG + FP64 refinement" if args.precision == 1 else "FP64 PCG")
                    + (" / Jacobi" if args.precond == 0 else " / GMG V-cycle"),
                    "l2": "flushed between steps (256 MB write)"},
@@ -511,6 +536,8 @@ def main():
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.shutdown()
     for m in meshes:
         m.close()
     if dist:
