@@ -128,12 +128,28 @@ struct PcgScalars {
   int sat_out;
 };
 
+// The designs of a batched launch, as kernels see them: grid slot b (a grid
+// dimension) runs design id(b), whose buffers sit at id(b) * S bytes from
+// design 0's; ids == nullptr means slot b is design b.
+struct DSel {
+  long long S;
+  const int* ids;
+  __device__ __forceinline__ int id(int b) const { return ids ? __ldg(ids + b) : b; }
+  __device__ __forceinline__ long long off(int b) const { return (long long)id(b) * S; }
+};
+
 // A batch of designs with identical grids whose buffers sit at a fixed byte
-// stride S from design 0's (the designs of a mesh group share one arena):
-// a kernel launched for nb designs offsets every pointer by design * S.
+// stride S from design 0's (the designs of a mesh group share one arena): a
+// kernel launched for nb designs offsets every pointer by design * S.  With
+// ids (device, nb entries) the launch covers only the listed designs of a
+// group of ntot (the TMA maps span all ntot designs).
 struct Bat {
   int nb = 1;
   long long S = 0;
+  const int* ids = nullptr;
+  int ntot = 0;
+  DSel sel() const { return DSel{S, ids}; }
+  int designs() const { return ntot > 0 ? ntot : nb; }
 };
 
 template <typename T>

@@ -38,9 +38,9 @@ inline int grid1d(long long n, int nb = 1) {
 __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
                             float* __restrict__ d0, float* __restrict__ x,
                             const float* __restrict__ dinv, long long n4, float inv_theta,
-                            const int* __restrict__ done, long long S) {
+                            const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   b = bshift(b, off);
@@ -64,9 +64,9 @@ __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
 }
 
 __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long long n4,
-                        const int* __restrict__ done, long long S) {
+                        const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   x = bshift(x, off);
@@ -181,10 +181,10 @@ struct EpiChebResid {
 // doubled edge (k0 of an element of edge 2h is 2h times the unit k0);
 // children beyond an odd fine grid are ghosts with E = 0
 __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* __restrict__ Ec,
-                            const Dims dc, long long S) {
+                            const Dims dc, const DSel S) {
   pdl_start();
-  Ef = bshift(Ef, blockIdx.y * S);
-  Ec = bshift(Ec, blockIdx.y * S);
+  Ef = bshift(Ef, S.off(blockIdx.y));
+  Ec = bshift(Ec, S.off(blockIdx.y));
   const long long n = (long long)dc.nx * dc.ny * dc.nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -207,9 +207,9 @@ __global__ void k_coarsen_E(const float* __restrict__ Ef, const Dims df, float* 
 // b_c = P^T r_f for trilinear P: coarse node (I,J,K) sits on fine node
 // (2I,2J,2K) and collects fine neighbours with weights 1, 1/2 per axis offset
 __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* __restrict__ bc,
-                           const Dims dc, const int* __restrict__ done, long long S) {
+                           const Dims dc, const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   rf = bshift(rf, off);
@@ -247,9 +247,9 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
 // x_f += P x_c (trilinear interpolation from the coarse nodes around each
 // fine node), fixed fine DOFs untouched
 __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float* __restrict__ xf,
-                              const Dims df, const int* __restrict__ done, long long S) {
+                              const Dims df, const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   xc = bshift(xc, off);
@@ -292,10 +292,10 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
 // per thread, summed over the elements shared by the two nodes (a gather:
 // deterministic, no atomics)
 __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const float* __restrict__ E,
-                                 const __grid_constant__ K0<double> k0, long long S) {
+                                 const __grid_constant__ K0<double> k0, const DSel S) {
   pdl_start();
-  A = bshift(A, blockIdx.y * S);
-  E = bshift(E, blockIdx.y * S);
+  A = bshift(A, S.off(blockIdx.y));
+  E = bshift(E, S.off(blockIdx.y));
   const int n = 3 * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   const long long nn = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
@@ -332,11 +332,11 @@ __global__ void k_dense_assemble(double* __restrict__ A, const Dims d, const flo
 // when many meshes set up concurrently on their own streams.)  The chain of
 // n launches is captured once per hierarchy as a CUDA graph.
 __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restrict__ row,
-                          double* __restrict__ col, long long S) {
+                          double* __restrict__ col, const DSel S) {
   pdl_start();
-  A = bshift(A, blockIdx.y * S);
-  row = bshift(row, blockIdx.y * S);
-  col = bshift(col, blockIdx.y * S);
+  A = bshift(A, S.off(blockIdx.y));
+  row = bshift(row, S.off(blockIdx.y));
+  col = bshift(col, S.off(blockIdx.y));
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
     row[t] = A[t];
@@ -346,9 +346,9 @@ __global__ void k_gj_seed(const double* __restrict__ A, int n, double* __restric
 
 __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __restrict__ rowk,
                           const double* __restrict__ colk, double* __restrict__ rown,
-                          double* __restrict__ coln, long long S) {
+                          double* __restrict__ coln, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   A = bshift(A, off);
   rowk = bshift(rowk, off);
   colk = bshift(colk, off);
@@ -380,9 +380,9 @@ __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __
 }
 
 __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, double* __restrict__ bd,
-                                const int* __restrict__ done, long long S) {
+                                const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   b = bshift(b, off);
@@ -400,9 +400,9 @@ __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, doubl
 // x = A^-1 b, one warp per row (A^-1 symmetric, rows read coalesced), FP64
 __global__ void k_coarse_apply(const double* __restrict__ Ainv, const double* __restrict__ bd,
                                int n, float* __restrict__ x, const Dims d,
-                               const int* __restrict__ done, long long S) {
+                               const int* __restrict__ done, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
   if (*done) return;
   Ainv = bshift(Ainv, off);
@@ -561,6 +561,7 @@ cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, dou
 
 cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
                       const K0<double>& k0d, cudaStream_t s, long long* launches, const Bat& bt) {
+  if (bt.ids) return cudaErrorInvalidValue;  // the setup covers every design of a batch
   g.lv[0].E = const_cast<float*>(E0);
   g.lv[0].dinv = const_cast<float*>(dinv0);
   for (size_t l = 1; l < g.lv.size(); ++l) {
@@ -568,14 +569,14 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     GmgLevel& C = g.lv[l];
     const long long ne = (long long)C.d.nx * C.d.ny * C.d.nz;
     GCK(launch_pdl(k_coarsen_E, dim3(grid1d(ne, bt.nb), bt.nb), dim3(kPT), 0, s, F.E, F.d, C.E,
-                   C.d, bt.S));
+                   C.d, bt.sel()));
     GCK(launch_diag_inv<float>(C.dinv, C.E, C.d, k0f, s, bt));
     *launches += 2;
   }
   const GmgLevel& Lc = g.lv.back();
   const long long nn = (long long)g.nc * g.nc;
   GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn, bt.nb), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d,
-                 Lc.E, k0d, bt.S));
+                 Lc.E, k0d, bt.sel()));
   // the pivot chain, captured once per batch shape as a graph and replayed per density
   if (g.gj_exec && (g.gj_nb != bt.nb || g.gj_S != bt.S)) {
     cudaGraphExecDestroy(g.gj_exec);
@@ -589,12 +590,12 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     if (e == cudaSuccess) {
       double* buf[2][2] = {{g.side, g.side + g.nc}, {g.side + 2 * g.nc, g.side + 3 * g.nc}};
       e = launch_pdl(k_gj_seed, dim3((g.nc + kPT - 1) / kPT, bt.nb), dim3(kPT), 0, cs, g.Ainv,
-                     g.nc, buf[0][0], buf[0][1], bt.S);
+                     g.nc, buf[0][0], buf[0][1], bt.sel());
       for (int k = 0; k < g.nc && e == cudaSuccess; ++k) {
         double** cur = buf[k & 1];
         double** nxt = buf[(k + 1) & 1];
         e = launch_pdl(k_gj_step, dim3(std::min(g.nc, 1024), bt.nb), dim3(128), 0, cs, g.Ainv,
-                       g.nc, k, cur[0], cur[1], nxt[0], nxt[1], bt.S);
+                       g.nc, k, cur[0], cur[1], nxt[0], nxt[1], bt.sel());
       }
       const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
       if (e == cudaSuccess) e = ec;
@@ -635,7 +636,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
     GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
-                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, done, bt.S));
+                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, done, bt.sel()));
     ++*launches;
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
@@ -646,7 +647,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     const GmgLevel& C = g.lv[l + 1];
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     GCK(launch_pdl(k_restrict, dim3(grid1d(nnc, bt.nb), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b,
-                   C.d, done, bt.S));
+                   C.d, done, bt.sel()));
     *launches += 2;
   }
   // coarsest
@@ -654,10 +655,10 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     const GmgLevel& C = g.lv[nl - 1];
     const int nnc = (C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     GCK(launch_pdl(k_coarse_gather, dim3((nnc + kPT - 1) / kPT, bt.nb), dim3(kPT), 0, s,
-                   B(nl - 1), C.d, g.bd, done, bt.S));
+                   B(nl - 1), C.d, g.bd, done, bt.sel()));
     const long long thr = 32LL * g.nc;
     GCK(launch_pdl(k_coarse_apply, dim3((int)((thr + kPT - 1) / kPT), bt.nb), dim3(kPT), 0, s,
-                   g.Ainv, g.bd, g.nc, X(nl - 1), C.d, done, bt.S));
+                   g.Ainv, g.bd, g.nc, X(nl - 1), C.d, done, bt.sel()));
     *launches += 2;
   }
   // up
@@ -666,7 +667,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     const GmgLevel& C = g.lv[l + 1];
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
     GCK(launch_pdl(k_prolong_add, dim3(grid1d(nnf, bt.nb), bt.nb), dim3(kPT), 0, s, X(l + 1), C.d,
-                   X(l), L.d, done, bt.S));
+                   X(l), L.d, done, bt.sel()));
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
@@ -677,7 +678,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     }
     if (m == 1) {
       GCK(launch_pdl(k_axpy1, dim3(grid1d(L.nvec / 4, bt.nb), bt.nb), dim3(kPT), 0, s, X(l),
-                     L.dv[0], L.nvec / 4, done, bt.S));
+                     L.dv[0], L.nvec / 4, done, bt.sel()));
       ++*launches;
     }
   }

@@ -218,14 +218,15 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
                 const __grid_constant__ CUtensorMap amap0,
                 const __grid_constant__ CUtensorMap amap1, const Dims d,
                 const __grid_constant__ ModalCoef<float> kc, const Epi epi0, const Red red0,
-                const int zchunk, const int zc, const long long S, const int* __restrict__ done,
+                const int zchunk, const int zc, const DSel S, const int* __restrict__ done,
                 int* __restrict__ errflag) {
   constexpr int NA = Epi::kAux;
   static_assert(NA <= 2, "at most two staged operand vectors");
   constexpr int SF = modal_stage_floats(NA);
   pdl_start();
-  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
-  const long long off = design * S;
+  const int slot = blockIdx.z / zc, chunk = blockIdx.z - slot * zc;
+  const int design = S.id(slot);
+  const long long off = design * S.S;
   done = bshift(done, off);
   errflag = bshift(errflag, off);
   if (done != nullptr && *done) return;  // uniform over the design's blocks
@@ -341,11 +342,11 @@ template <typename T, class Epi>
 __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_plain(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
                   const __grid_constant__ ModalCoef<T> kc, const Epi epi0, const Red red0,
-                  const int zchunk, const int zc, const long long S,
+                  const int zchunk, const int zc, const DSel S,
                   const int* __restrict__ done) {
   pdl_start();
-  const int design = blockIdx.z / zc, chunk = blockIdx.z - design * zc;
-  const long long off = design * S;
+  const int slot = blockIdx.z / zc, chunk = blockIdx.z - slot * zc;
+  const long long off = S.off(slot);
   done = bshift(done, off);
   if (done != nullptr && *done) return;
   x = bshift(x, off);
@@ -439,10 +440,10 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
         attr = true;
       }
       return launch_pdl(k_modal_tma<Epi>, grid, block, smem, s, xm, em, am[0], am[1], d, kc, epi,
-                        red, z, zc, bt.S, done, errflag);
+                        red, z, zc, bt.sel(), done, errflag);
     }
   }
-  return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.S,
+  return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.sel(),
                     done);
 }
 

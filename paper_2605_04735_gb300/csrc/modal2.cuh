@@ -196,14 +196,14 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
                  const __grid_constant__ CUtensorMap amap0,
                  const __grid_constant__ CUtensorMap amap1, const Dims d,
                  const __grid_constant__ ModalCoef2 kc, const Epi epi0, const Red red0,
-                 const int gx, const int gy, const long long S, const int* __restrict__ done,
+                 const int gx, const int gy, const DSel S, const int* __restrict__ done,
                  int* __restrict__ errflag) {
   constexpr int NA = Epi::kAux;
   static_assert(NA <= 2, "at most two staged operand vectors");
   constexpr int SF = pair_stage_floats(NA);
   pdl_start();
-  const int design = blockIdx.z;
-  const long long off = design * S;
+  const int design = S.id(blockIdx.z);
+  const long long off = design * S.S;
   done = bshift(done, off);
   errflag = bshift(errflag, off);
   if (done != nullptr && *done) return;  // uniform over the design's blocks
@@ -407,7 +407,7 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
   dim3 block(kPairTX, kPairTY, 1);
   dim3 grid(pair_ctas(d, bt.nb), 1, bt.nb);
   return launch_pdl(k_modal_pair<Epi>, grid, block, smem, s, xm, em, am[0], am[1], d,
-                    pair_coef(kc), epi, red, gx, gy, bt.S, done, errflag);
+                    pair_coef(kc), epi, red, gx, gy, bt.sel(), done, errflag);
 }
 
 // Smallest nx for which the automatic form picks the paired kernel.  Measured

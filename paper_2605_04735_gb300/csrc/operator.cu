@@ -77,14 +77,14 @@ struct EpiResid {
 // and 1 on fixed DOFs (and on nodes that touch no stiffness at all).
 template <typename T>
 __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const Dims d,
-                           const __grid_constant__ K0<T> k0, long long S) {
+                           const __grid_constant__ K0<T> k0, const DSel S) {
   pdl_start();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int design = blockIdx.z / (d.nz + 1);
-  const int k = blockIdx.z - design * (d.nz + 1);
-  dinv = bshift(dinv, design * S);
-  E = bshift(E, design * S);
+  const int slot = blockIdx.z / (d.nz + 1);
+  const int k = blockIdx.z - slot * (d.nz + 1);
+  dinv = bshift(dinv, S.off(slot));
+  E = bshift(E, S.off(slot));
   if (i > d.nx || j > d.ny) return;
   T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -136,7 +136,7 @@ cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0,
                             const Bat& bt) {
   dim3 block(32, 4, 1);
   dim3 grid((d.nx + 32) / 32, (d.ny + 4) / 4, (d.nz + 1) * bt.nb);
-  return launch_pdl(k_diag_inv<T>, grid, block, 0, s, dinv, E, d, k0, bt.S);
+  return launch_pdl(k_diag_inv<T>, grid, block, 0, s, dinv, E, d, k0, bt.sel());
 }
 
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,

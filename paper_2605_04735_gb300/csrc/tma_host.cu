@@ -44,15 +44,17 @@ std::mutex g_mu;
 std::map<Key, CUtensorMap> g_cache;
 
 // kind 0: node vector (x, y, z, component, design); kind 1: element array
-// (x, y, z, design).  The design dimension has bt.nb entries bt.S bytes apart
-// (stride 16 bytes when there is one design: unused).
+// (x, y, z, design).  The design dimension has all bt.designs() entries of
+// the batch, bt.S bytes apart (a launch over a subset of the designs reads
+// them by design index; one design: the dimension has one entry).
 bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y, const Bat& bt,
                 CUtensorMap* out) {
   // one design: the natural size of the array (the dimension has one entry)
+  const int nd = bt.designs();
   const long long natural = kind ? d.ecount * 4 : 3 * d.comp * 4;
-  const long long dstride = (bt.nb > 1) ? bt.S : natural;
-  if (bt.nb > 1 && (bt.S < natural || bt.S % 16 != 0)) return false;
-  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz, box_x, box_y, bt.nb, dstride};
+  const long long dstride = (nd > 1) ? bt.S : natural;
+  if (nd > 1 && (bt.S < natural || bt.S % 16 != 0)) return false;
+  const Key key{base, kind, kind ? d.ex : d.px, d.ny, d.nz, box_x, box_y, nd, dstride};
   std::lock_guard<std::mutex> lock(g_mu);
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
@@ -63,7 +65,7 @@ bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y,
   bool ok;
   if (kind == 0) {  // node vector: (x, y, z, component, design)
     const uint64_t dims[5] = {(uint64_t)d.px, (uint64_t)(d.ny + 3), (uint64_t)(d.nz + 3), 3,
-                              (uint64_t)bt.nb};
+                              (uint64_t)nd};
     const uint64_t strides[4] = {(uint64_t)d.px * 4, (uint64_t)d.px * (d.ny + 3) * 4,
                                  (uint64_t)d.comp * 4, (uint64_t)dstride};
     const uint32_t box[5] = {(uint32_t)box_x, (uint32_t)box_y, 1, 3, 1};
@@ -71,7 +73,7 @@ bool cached_map(const void* base, int kind, const Dims& d, int box_x, int box_y,
                           strides, box);
   } else {  // element array: (x, y, z, design)
     const uint64_t dims[4] = {(uint64_t)d.ex, (uint64_t)(d.ny + 2), (uint64_t)(d.nz + 2),
-                              (uint64_t)bt.nb};
+                              (uint64_t)nd};
     const uint64_t strides[3] = {(uint64_t)d.ex * 4, (uint64_t)d.ex * (d.ny + 2) * 4,
                                  (uint64_t)dstride};
     const uint32_t box[4] = {(uint32_t)box_x, (uint32_t)box_y, 1, 1};

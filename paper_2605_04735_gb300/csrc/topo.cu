@@ -208,6 +208,8 @@ struct MeshGroup {
     int sat_out;
   };
   Next* h_next = nullptr;  // nb: per-design settings of the next inner solve
+  int* h_ids = nullptr;    // nb pinned: the designs a compacted CG chunk covers
+  int* d_ids = nullptr;    // nb: their device copy
   int gmg_levels = -1, gmg_degree = -1;
   topo_params prm{};
 };
@@ -921,6 +923,8 @@ void topo_free(topo_mesh* m) {
       if (G->h_sc) cudaFreeHost(G->h_sc);
       if (G->h_flag) cudaFreeHost(G->h_flag);
       if (G->h_next) cudaFreeHost(G->h_next);
+      if (G->h_ids) cudaFreeHost(G->h_ids);
+      if (G->d_ids) cudaFree(G->d_ids);
       delete G;
     }
   }
@@ -1085,6 +1089,8 @@ topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const to
       if (G->h_sc) cudaFreeHost(G->h_sc);
       if (G->h_flag) cudaFreeHost(G->h_flag);
       if (G->h_next) cudaFreeHost(G->h_next);
+      if (G->h_ids) cudaFreeHost(G->h_ids);
+      if (G->d_ids) cudaFree(G->d_ids);
       delete G;
     } else {
       for (topo_mesh* m : made) topo_free(m);  // the last one frees the group
@@ -1099,8 +1105,12 @@ topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const to
   if (cudaMemset(G->arena, 0, (size_t)(G->nb * G->S)) != cudaSuccess) return fail(TOPO_ERR_CUDA);
   if (cudaMallocHost(&G->h_sc, sizeof(PcgScalars) * G->nb) != cudaSuccess ||
       cudaMallocHost(&G->h_flag, sizeof(int) * G->nb) != cudaSuccess ||
-      cudaMallocHost(&G->h_next, sizeof(MeshGroup::Next) * G->nb) != cudaSuccess)
+      cudaMallocHost(&G->h_next, sizeof(MeshGroup::Next) * G->nb) != cudaSuccess ||
+      cudaMallocHost(&G->h_ids, sizeof(int) * G->nb) != cudaSuccess ||
+      cudaMalloc(&G->d_ids, sizeof(int) * G->nb) != cudaSuccess) {
+    cudaGetLastError();
     return fail(TOPO_ERR_OOM);
+  }
   for (int b = 0; b < n_designs; ++b) {
     topo_mesh* m = new (std::nothrow) topo_mesh();
     if (!m) return fail(TOPO_ERR_OOM);
@@ -1501,10 +1511,21 @@ topo_status group_read_scalars(MeshGroup* G) {
 
 // profile: events around every CG apply (design 0's events; one launch covers
 // every design still iterating)
-topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile) {
+// Launch width for n live designs of a group of nb: 1, 2, 3, 4, 6, 8, 12,
+// 16, 24, ... (at most 50 % padding, few distinct graphs), capped at nb.
+int live_bucket(int n, int nb) {
+  int w = 1;
+  for (int p = 1;; p *= 2) {
+    if (p >= n) { w = p; break; }
+    if (p >= 2 && p + p / 2 >= n) { w = p + p / 2; break; }
+  }
+  return std::min(w, nb);
+}
+
+// bt: the designs the chunk covers (all of them, or the compacted list)
+topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile, const Bat& bt) {
   topo_mesh* m = G->meshes[0];
   cudaStream_t s = m->stream;
-  const Bat bt{G->nb, G->S};
   const int* done = &m->sc->done;
   for (int c = 0; c < count; ++c) {
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c], s, cudaEventRecordExternal));
@@ -1520,14 +1541,19 @@ topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile) {
   return TOPO_OK;
 }
 
-topo_status group_run_iters(MeshGroup* G, int count, bool profile) {
+// One chunk of CG iterations over `n` designs: all of the group (n == nb)
+// or the first n entries of G->d_ids (already on the device).  One graph per
+// (chunk length, profiling, n), so n takes few values (live_bucket).
+topo_status group_run_iters(MeshGroup* G, int count, bool profile, int n) {
   topo_mesh* m = G->meshes[0];
-  const long long key = (long long)count | ((long long)profile << 16);
+  const bool all = n >= G->nb;
+  const Bat bt{all ? G->nb : n, G->S, all ? nullptr : G->d_ids, G->nb};
+  const long long key = (long long)count | ((long long)profile << 16) | ((long long)bt.nb << 20);
   auto it = G->graphs.find(key);
   if (it == G->graphs.end()) {
     const long long l0 = m->launches;
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    const topo_status st = group_enqueue_iters(G, count, profile);
+    const topo_status st = group_enqueue_iters(G, count, profile, bt);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (st != TOPO_OK || e != cudaSuccess) {
@@ -1677,8 +1703,23 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s, bt));
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
     std::vector<int> before(nb, -1), at(nb, 0);
+    std::vector<char> iterating(running);  // designs not done (first chunk: taking part)
     for (int chunk = 0;; ++chunk) {
-      CKS(group_run_iters(G, o.check_every, prof));
+      // compact the chunk's launches to the live designs, padded with a
+      // finished design (its CTAs return at once) up to the launch width
+      int n_live = 0, idle = -1;
+      for (int b = 0; b < nb; ++b) {
+        if (iterating[b])
+          G->h_ids[n_live++] = b;
+        else if (idle < 0)
+          idle = b;
+      }
+      const int width = live_bucket(n_live, nb);
+      if (width < nb) {
+        for (int q = n_live; q < width; ++q) G->h_ids[q] = idle;
+        CK(cudaMemcpyAsync(G->d_ids, G->h_ids, sizeof(int) * width, cudaMemcpyHostToDevice, s));
+      }
+      CKS(group_run_iters(G, o.check_every, prof, width));
       CKS(group_read_scalars(G));
       bool all_done = true, progress = false;
       for (int b = 0; b < nb; ++b) {
@@ -1686,6 +1727,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         if (!h.done) all_done = false;
         if (h.iter != before[b]) progress = true;
         before[b] = h.iter;
+        iterating[b] = !h.done;
       }
       if (prof) {  // launch c of the chunk advanced the designs with more than c iterations
         for (int c = 0; c < o.check_every; ++c) {

@@ -62,9 +62,9 @@ template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_init(const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                T* __restrict__ p, const T* __restrict__ dinv, long long n4, const Red red0,
-               long long S) {
+               const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   b = bshift(b, off);
   x = bshift(x, off);
   r = bshift(r, off);
@@ -104,9 +104,9 @@ template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
                  const T* __restrict__ qv, const T* __restrict__ dinv, long long n4,
-                 const Red red0, long long S) {
+                 const Red red0, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   x = bshift(x, off);
   r = bshift(r, off);
   z = bshift(z, off);
@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_direction(T* __restrict__ p, const T* __restrict__ z, long long n4,
-                    const PcgScalars* __restrict__ sc, long long S) {
+                    const PcgScalars* __restrict__ sc, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   p = bshift(p, off);
   z = bshift(z, off);
   sc = bshift(sc, off);
@@ -183,9 +183,9 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T, bool TWO>
 __global__ void __launch_bounds__(kThreads)
     k_dot(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c, long long n4,
-          const Red red0, long long S) {
+          const Red red0, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   a = bshift(a, off);
   b = bshift(b, off);
   c = bshift(c, off);
@@ -210,9 +210,9 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void __launch_bounds__(kThreads)
     k_narrow_scaled(float* __restrict__ b32, const double* __restrict__ r64, long long n4,
-                    const PcgScalars* __restrict__ sc, int skip, long long S) {
+                    const PcgScalars* __restrict__ sc, int skip, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   b32 = bshift(b32, off);
   r64 = bshift(r64, off);
   sc = bshift(sc, off);
@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     k_accumulate(double* __restrict__ u, const T* __restrict__ x, long long n4,
-                 const PcgScalars* __restrict__ sc, int scaled, int skip, long long S) {
+                 const PcgScalars* __restrict__ sc, int scaled, int skip, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   u = bshift(u, off);
   x = bshift(x, off);
   sc = bshift(sc, off);
@@ -256,9 +256,9 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-    k_copy_cast(T* __restrict__ dst, const double* __restrict__ src, long long n4, long long S) {
+    k_copy_cast(T* __restrict__ dst, const double* __restrict__ src, long long n4, const DSel S) {
   pdl_start();
-  const long long off = blockIdx.y * S;
+  const long long off = S.off(blockIdx.y);
   dst = bshift(dst, off);
   src = bshift(src, off);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
@@ -273,11 +273,11 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// thread b: design b; max_iter < 0 takes each design's max_iter_next
-__global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, long long S) {
+// thread b: the design of slot b; max_iter < 0 takes each design's max_iter_next
+__global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, const DSel S) {
   const int b = threadIdx.x + blockIdx.x * blockDim.x;
   if (b >= nb) return;
-  PcgScalars* t = bshift(sc, b * S);
+  PcgScalars* t = bshift(sc, S.off(b));
   t->max_iter = (max_iter >= 0) ? max_iter : t->max_iter_next;
   t->done = 0;
   t->status = 0;
@@ -287,7 +287,7 @@ __global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, long long S
 
 cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s, const Bat& bt) {
   return launch_pdl(k_set_max_iter, dim3((bt.nb + 127) / 128), dim3(128), 0, s, sc, max_iter, bt.nb,
-                    bt.S);
+                    bt.sel());
 }
 
 template <typename T>
@@ -297,9 +297,9 @@ cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, l
   const dim3 g = vgrid(n4, bt);
   if (jacobi)
     return launch_pdl(k_pcg_init<T, true>, g, dim3(kThreads), 0, s, b, x, r, z, p, dinv, n4, red,
-                      bt.S);
+                      bt.sel());
   return launch_pdl(k_pcg_init<T, false>, g, dim3(kThreads), 0, s, b, x, r, z, p, dinv, n4, red,
-                    bt.S);
+                    bt.sel());
 }
 
 template <typename T>
@@ -309,16 +309,16 @@ cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T*
   const dim3 g = vgrid(n4, bt);
   if (jacobi)
     return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
-                      bt.S);
+                      bt.sel());
   return launch_pdl(k_pcg_update<T, false>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
-                    bt.S);
+                    bt.sel());
 }
 
 template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_pcg_direction<T>, vgrid(n4, bt), dim3(kThreads), 0, s, p, z, n4, sc, bt.S);
+  return launch_pdl(k_pcg_direction<T>, vgrid(n4, bt), dim3(kThreads), 0, s, p, z, n4, sc, bt.sel());
 }
 
 template <typename T>
@@ -326,21 +326,21 @@ cudaError_t launch_dot(const T* a, const T* b, long long n, const Red& red, cuda
                        const Bat& bt) {
   const long long n4 = n / 4;
   return launch_pdl(k_dot<T, false>, vgrid(n4, bt), dim3(kThreads), 0, s, a, b, nullptr, n4, red,
-                    bt.S);
+                    bt.sel());
 }
 
 template <typename T>
 cudaError_t launch_dot2(const T* a, const T* b, const T* c, long long n, const Red& red,
                         cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_dot<T, true>, vgrid(n4, bt), dim3(kThreads), 0, s, a, b, c, n4, red, bt.S);
+  return launch_pdl(k_dot<T, true>, vgrid(n4, bt), dim3(kThreads), 0, s, a, b, c, n4, red, bt.sel());
 }
 
 cudaError_t launch_narrow_scaled(float* b32, const double* r64, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
   return launch_pdl(k_narrow_scaled, vgrid(n4, bt), dim3(kThreads), 0, s, b32, r64, n4, sc,
-                    bt.nb > 1 ? 1 : 0, bt.S);
+                    bt.nb > 1 ? 1 : 0, bt.sel());
 }
 
 template <typename T>
@@ -348,14 +348,14 @@ cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgSca
                               bool scaled, cudaStream_t s, const Bat& bt) {
   const long long n4 = n / 4;
   return launch_pdl(k_accumulate<T>, vgrid(n4, bt), dim3(kThreads), 0, s, u64, x, n4, sc,
-                    scaled ? 1 : 0, bt.nb > 1 ? 1 : 0, bt.S);
+                    scaled ? 1 : 0, bt.nb > 1 ? 1 : 0, bt.sel());
 }
 
 template <typename T>
 cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
                              const Bat& bt) {
   const long long n4 = n / 4;
-  return launch_pdl(k_copy_cast<T>, vgrid(n4, bt), dim3(kThreads), 0, s, dst, src, n4, bt.S);
+  return launch_pdl(k_copy_cast<T>, vgrid(n4, bt), dim3(kThreads), 0, s, dst, src, n4, bt.sel());
 }
 
 #define TOPO_INST(T)                                                                           \
