@@ -87,7 +87,9 @@ enum {
 /* Arithmetic of the inner (preconditioned CG) solve. */
 enum {
   TOPO_PREC_FP64 = 0, /* plain FP64 PCG (the reference GPU path) */
-  TOPO_PREC_FP32 = 1  /* FP32 PCG inside FP64 iterative refinement */
+  TOPO_PREC_FP32 = 1, /* FP32 PCG inside FP64 iterative refinement */
+  TOPO_PREC_DWORD = 2 /* topo_apply / topo_apply_internal only: the operator in double-word
+                         arithmetic (two FP32 words per value, ~48 significand bits) */
 };
 
 /* Operator kernels (both compute the same K x; results agree to rounding). */
@@ -126,7 +128,17 @@ typedef struct {
   int gmg_levels;    /* 0: as many 2:1 levels as the grid allows (coarsest <= ~3000 DOF) */
   int smooth_degree; /* Chebyshev smoother degree per pre/post smoothing (default 3) */
   int check_every;   /* inner iterations between host convergence checks (default 16) */
+  int residual;      /* TOPO_RESIDUAL_*: arithmetic of the refinement residual f - K u of
+                        TOPO_PREC_FP32 solves (default DWORD); FP64 solves use FP64 */
 } topo_solve_opts;
+
+enum {
+  /* K u in double-word arithmetic (two FP32 words, ~48 significand bits: rounding
+     error ~2^-48 per operation, against 2^-53 in FP64), f - K u and ||r||^2 in
+     FP64.  GB300 issues FP32 64 times as fast as FP64. */
+  TOPO_RESIDUAL_DWORD = 0,
+  TOPO_RESIDUAL_FP64 = 1 /* every operation in FP64 */
+};
 
 /* Where a failed solve stopped (topo_solve_info.detail). */
 enum {
@@ -219,14 +231,16 @@ topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, i
 /* y = M K M x with M the diagonal mask of free DOFs: entries of x on fixed
  * DOFs are taken as 0 and y is 0 there (the operator the solver inverts on
  * the free DOFs, Eq. (2)).  K comes from the current densities.  precision
- * TOPO_PREC_FP64 or TOPO_PREC_FP32 selects the kernel (FP32 rounds x to
- * float and returns y widened to double).  n_dof values in DOF order. */
+ * TOPO_PREC_FP64, TOPO_PREC_FP32 or TOPO_PREC_DWORD selects the kernel (FP32
+ * rounds x to float and returns y widened to double; DWORD splits x into two
+ * FP32 words and evaluates K x in double-word arithmetic, the residual's
+ * kernel).  n_dof values in DOF order. */
 topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, size_t n_dof,
                        int on_device);
 
-/* Launch the fine-grid FP32 (or FP64) operator kernel `reps` times on the
- * mesh's stream over the mesh's internal vectors (no copies, no sync), for
- * timing.  Cites Eq. (2) (K u). */
+/* Launch the fine-grid FP32 (or FP64, or double-word) operator kernel
+ * `reps` times on the mesh's stream over the mesh's internal vectors (no
+ * copies, no sync), for timing.  Cites Eq. (2) (K u). */
 topo_status topo_apply_internal(topo_mesh* m, int precision, int reps);
 
 /* ---------------------------------------------------------------------

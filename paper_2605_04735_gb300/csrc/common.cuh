@@ -126,6 +126,11 @@ struct PcgScalars {
   double rtol2_next;
   int max_iter_next;
   int sat_out;
+  // the refinement residual of a batched outer step: in double-word
+  // arithmetic for some designs, in FP64 for the others; each launch skips
+  // the designs whose flag is set
+  int skip_dword;
+  int skip_fp64;
 };
 
 // The designs of a batched launch, as kernels see them: grid slot b (a grid

@@ -28,6 +28,13 @@ template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
                          const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
                          int* errflag, cudaStream_t s, const Bat& bt = Bat{});
+// The same operator (modal form) evaluated in double-word arithmetic (two
+// FP32 words per value, ~48 significand bits): x given pre-split into hi and
+// lo FP32 vectors (launch_split_dw), moduli E and f in FP64, y in FP64.
+cudaError_t launch_apply_dw(const float* xh, const float* xl, double* y, const double* E,
+                            const double* f, const Dims& d, const ModalCoef<double>& mc,
+                            const Red& red, int mode, const int* done, cudaStream_t s,
+                            const Bat& bt = Bat{});
 // modal coefficients of k0 (returns false if k0 does not have the expected pattern)
 bool build_modal_coef(const double* k0, ModalCoef<double>* out);
 template <typename T>
@@ -66,6 +73,10 @@ cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgSca
 template <typename T>
 cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_t s,
                              const Bat& bt = Bat{});
+// hi = float(u), lo = float(u - hi): the double-word split of an FP64 vector
+// (skip: per-design flag, design-0 address; designs with it set are left alone)
+cudaError_t launch_split_dw(const double* u, float* hi, float* lo, long long n, const int* skip,
+                            cudaStream_t s, const Bat& bt = Bat{});
 
 // ---- mesh data (meshdata.cu) -------------------------------------------
 // rho (dense element order) -> ghosted rho32, E32, E64; counts bad values into *bad

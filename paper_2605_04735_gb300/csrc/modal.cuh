@@ -45,6 +45,12 @@ struct ModalCoef {
   int form;  // FP32 kernel form: 0 automatic, 1 one column per thread, 2 two columns (packed)
 };
 
+// a * b + c (overloaded for the double-word type)
+template <typename T>
+__device__ __forceinline__ T fmadd(T a, T b, T c) {
+  return fma(a, b, c);
+}
+
 // in-place 8-point Walsh-Hadamard transform: v[m] <- sum_b (-1)^{b.m} v[b]
 template <typename T>
 __device__ __forceinline__ void fwht8(T (&v)[8]) {
@@ -127,7 +133,7 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
       for (int q = 0; q < 3; ++q) {
         if (q == p) continue;
         if (((m >> p) & 1) == ((m >> q) & 1)) continue;
-        acc = fma(kc.C[p][q][m], uh[q][m ^ (1 << p) ^ (1 << q)], acc);
+        acc = fmadd(kc.C[p][q][m], uh[q][m ^ (1 << p) ^ (1 << q)], acc);
       }
       yh[p][m] = acc;
     }
@@ -152,6 +158,12 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
   }
 }
 
+// the value of lane - 1 (overloaded for the double-word type)
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) {
+  return __shfl_up_sync(0xffffffffu, v, 1);
+}
+
 // exchange a finished plane's corners with the neighbours: res = the sums at
 // the node (ex, ey) of the plane (includes the CTA barrier)
 template <typename T>
@@ -160,8 +172,8 @@ __device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[
   T n0[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T r1 = __shfl_up_sync(0xffffffffu, plane[c][1], 1);
-    const T r3 = __shfl_up_sync(0xffffffffu, plane[c][3], 1);
+    const T r1 = shfl_up1(plane[c][1]);
+    const T r3 = shfl_up1(plane[c][3]);
     n0[c] = plane[c][0] + (tx > 0 ? r1 : T(0));
     xch[ty][tx][c] = plane[c][2] + (tx > 0 ? r3 : T(0));
   }

@@ -10,6 +10,7 @@
 #include "kernels.h"
 #include "modal.cuh"
 #include "modal2.cuh"
+#include "modal_dw.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -128,6 +129,20 @@ cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d
       return launch_stencil<T>(x, E, d, k0, EpiApply<T, true>{y}, red, done, errflag, s);
     default:
       return launch_stencil<T>(x, E, d, k0, EpiResid<T>{y, f}, red, done, errflag, s);
+  }
+}
+
+cudaError_t launch_apply_dw(const float* xh, const float* xl, double* y, const double* E,
+                            const double* f, const Dims& d, const ModalCoef<double>& mc,
+                            const Red& red, int mode, const int* done, cudaStream_t s,
+                            const Bat& bt) {
+  switch (mode) {
+    case APPLY_PLAIN:
+      return launch_modal_dw(xh, xl, E, d, mc, EpiApply<double, false>{y}, red, done, s, bt);
+    case APPLY_DOT:
+      return launch_modal_dw(xh, xl, E, d, mc, EpiApply<double, true>{y}, red, done, s, bt);
+    default:
+      return launch_modal_dw(xh, xl, E, d, mc, EpiResid<double>{y, f}, red, done, s, bt);
   }
 }
 

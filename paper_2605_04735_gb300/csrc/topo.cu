@@ -202,10 +202,12 @@ struct MeshGroup {
   std::map<long long, ChunkGraph> graphs;  // batched CG chunks
   PcgScalars* h_sc = nullptr;              // nb pinned host copies
   int* h_flag = nullptr;                   // nb
-  struct Next {  // the layout of PcgScalars' rtol2_next, max_iter_next, sat_out
+  struct Next {  // the layout of PcgScalars' tail from rtol2_next on
     double rtol2;
     int max_iter;
     int sat_out;
+    int skip_dword;
+    int skip_fp64;
   };
   Next* h_next = nullptr;  // nb: per-design settings of the next inner solve
   int* h_ids = nullptr;    // nb pinned: the designs a compacted CG chunk covers
@@ -453,6 +455,8 @@ struct SolveTask {
   int detail = TOPO_FAIL_NONE;
   bool profile = false;
   double fn = 0.0;
+  double expect = 1.0;      // relative residual the running inner solve aims at
+  bool resid_dword = false; // the last residual was evaluated in double-word arithmetic
   Timer timer;
 };
 
@@ -481,11 +485,32 @@ void task_finish(SolveTask& t, topo_status st) {
   }
 }
 
-// FP64 residual r = f - K u (fixed DOFs 0), ||r||^2 -> aux[0]
-topo_status enqueue_residual64(topo_mesh* m) {
-  LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m), red_of(m, FIN_AUX),
-                             APPLY_RESID, nullptr, m->flags + 1, m->stream));
+// Refinement residual r = f - K u (fixed DOFs 0), ||r||^2 -> aux[0]: in FP64,
+// or (dword) K u in double-word arithmetic from u split into the FP32
+// vectors p32 / q32, which are free between inner solves.  bt / skip: the
+// designs of a mesh group, skipping those that sat out the step.
+topo_status enqueue_residual(topo_mesh* m, bool dword, const int* skip = nullptr,
+                             const Bat& bt = Bat{}) {
+  if (dword) {
+    LK(m, launch_split_dw(m->u64, m->p32, m->q32, m->nvec, skip, m->stream, bt));
+    LK(m, launch_apply_dw(m->p32, m->q32, m->r64, m->E64, m->f64, m->d, m->mcd,
+                          red_of(m, FIN_AUX), APPLY_RESID, skip, m->stream, bt));
+  } else {
+    LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
+                               red_of(m, FIN_AUX), APPLY_RESID, skip, m->flags + 1, m->stream,
+                               bt));
+  }
   return TOPO_OK;
+}
+
+// The residual after an inner solve that aimed at relative residual `expect`
+// is evaluated in double-word arithmetic only when it cannot certify
+// convergence (expect at least 100 x rtol: it only sets the next right-hand
+// side, where ~1e-13 relative rounding is far below what the next inner
+// solve resolves); every residual that may end the solve is FP64.
+bool dword_residual(const topo_solve_opts& o, double expect) {
+  return o.precision == TOPO_PREC_FP32 && o.residual == TOPO_RESIDUAL_DWORD &&
+         expect >= 100.0 * o.rtol;
 }
 
 // start of an inner CG from x = 0 on the current right-hand side
@@ -525,6 +550,8 @@ topo_status task_start(SolveTask& t) {
   if (!(o->rtol > 0.0) || o->max_iter < 1 || o->max_outer < 1 || o->check_every < 1 ||
       o->check_every > 1024)
     return TOPO_ERR_INVALID;
+  if (o->residual != TOPO_RESIDUAL_DWORD && o->residual != TOPO_RESIDUAL_FP64)
+    return TOPO_ERR_INVALID;
   cudaStream_t s = m->stream;
   if (o->precision == TOPO_PREC_FP64) {
     t.kind = IK_JAC64;
@@ -547,7 +574,7 @@ topo_status task_start(SolveTask& t) {
   t.fn = std::sqrt(m->fnorm2);
   CK(cudaMemsetAsync(m->flags + 1, 0, sizeof(int), s));  // bounded-wait timeout flag
   if (o->warm_start) {
-    CKS(enqueue_residual64(m));
+    CKS(enqueue_residual(m, false));  // a warm start may already be converged
   } else {
     CK(cudaMemsetAsync(m->u64, 0, sizeof(double) * m->nvec, s));
     CK(cudaMemcpyAsync(m->r64, m->f64, sizeof(double) * m->nvec, cudaMemcpyDeviceToDevice, s));
@@ -575,7 +602,7 @@ topo_status task_step(SolveTask& t) {
     }
     const double rel = t.fn > 0 ? std::sqrt(rr) / t.fn : 0.0;
     if (t.info) t.info->rel_residual = rel;
-    if (rel <= o.rtol) {
+    if (rel <= o.rtol && !t.resid_dword) {  // only an FP64 residual certifies
       task_finish(t, TOPO_OK);
       return TOPO_OK;
     }
@@ -585,6 +612,7 @@ topo_status task_step(SolveTask& t) {
       inner = std::min(std::max(0.5 * o.rtol * t.fn / std::sqrt(rr), 1e-15), 0.5);
     else
       inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * t.fn / std::sqrt(rr)), 0.5);
+    t.expect = inner * rel;
     CKS(enqueue_inner_start(t, inner, o.max_iter - t.total));
     CKS(run_iters(m, t.kind, o.check_every, t.profile));
     t.it_before = 0;
@@ -617,7 +645,8 @@ topo_status task_step(SolveTask& t) {
     LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, m->stream));
   else  // scale back by ||r|| (aux[0] still holds ||r||^2 from the residual)
     LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, m->stream));
-  CKS(enqueue_residual64(m));
+  t.resid_dword = t.kind != IK_JAC64 && dword_residual(o, t.expect);
+  CKS(enqueue_residual(m, t.resid_dword));
   t.phase = SolveTask::P_RESID;
   return request_scalars(m);
 }
@@ -877,6 +906,7 @@ void topo_default_opts(topo_solve_opts* o) {
   o->gmg_levels = 0;
   o->smooth_degree = 3;
   o->check_every = 16;
+  o->residual = TOPO_RESIDUAL_DWORD;
 }
 
 const char* topo_status_string(int status) {
@@ -1633,8 +1663,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
   if (prof) CKS(ensure_profile_events(m, o.check_every));
   CK(cudaMemset2DAsync(m->flags + 1, (size_t)G->S, 0, sizeof(int), nb, s));
   if (o.warm_start) {
-    LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
-                               red_of(m, FIN_AUX), APPLY_RESID, nullptr, m->flags + 1, s, bt));
+    CKS(enqueue_residual(m, false, nullptr, bt));  // a warm start may already be converged
   } else {
     CK(cudaMemset2DAsync(m->u64, (size_t)G->S, 0, sizeof(double) * m->nvec, nb, s));
     CK(cudaMemcpy2DAsync(m->r64, (size_t)G->S, m->f64, (size_t)G->S, sizeof(double) * m->nvec,
@@ -1645,7 +1674,8 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
   std::vector<int> outer(nb, 0), total(nb, 0), detail(nb, TOPO_FAIL_NONE);
   std::vector<topo_status> st(nb, TOPO_OK);
   std::vector<char> running(nb, 1);
-  std::vector<double> rel(nb, 0.0);
+  std::vector<double> rel(nb, 0.0), expect(nb, 1.0);
+  std::vector<char> last_dword(nb, 0);  // design b's last residual was double-word
   for (;;) {
     // decisions on the fresh FP64 residuals
     int live = 0;
@@ -1654,6 +1684,8 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
       nx.rtol2 = 4.0;  // sit out
       nx.max_iter = 1;
       nx.sat_out = 1;
+      nx.skip_dword = 1;
+      nx.skip_fp64 = 1;
       if (!running[b]) continue;
       const PcgScalars& h = G->h_sc[b];
       const double fn = std::sqrt(G->meshes[b]->fnorm2), rr = h.aux[0];
@@ -1670,7 +1702,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         continue;
       }
       rel[b] = fn > 0 ? std::sqrt(rr) / fn : 0.0;
-      if (rel[b] <= o.rtol) {
+      if (rel[b] <= o.rtol && !last_dword[b]) {  // only an FP64 residual certifies
         running[b] = 0;
         continue;
       }
@@ -1681,15 +1713,21 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         continue;
       }
       const double inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * fn / std::sqrt(rr)), 0.5);
+      expect[b] = inner * rel[b];
+      const bool dw = dword_residual(o, expect[b]);
+      nx.skip_dword = dw ? 0 : 1;
+      nx.skip_fp64 = dw ? 1 : 0;
       nx.rtol2 = inner * inner;
       nx.max_iter = o.max_iter - total[b];
       nx.sat_out = 0;
       ++live;
     }
     if (!live) break;
-    static_assert(sizeof(MeshGroup::Next) == 2 * sizeof(double) &&
-                      offsetof(PcgScalars, sat_out) - offsetof(PcgScalars, rtol2_next) ==
-                          offsetof(MeshGroup::Next, sat_out),
+    static_assert(sizeof(MeshGroup::Next) == 3 * sizeof(double) &&
+                      offsetof(PcgScalars, skip_fp64) - offsetof(PcgScalars, rtol2_next) ==
+                          offsetof(MeshGroup::Next, skip_fp64) &&
+                      sizeof(PcgScalars) - offsetof(PcgScalars, rtol2_next) ==
+                          sizeof(MeshGroup::Next),
                   "Next mirrors the tail of PcgScalars");
     CK(cudaMemcpy2DAsync(&m->sc->rtol2_next, (size_t)G->S, G->h_next, sizeof(MeshGroup::Next),
                          sizeof(MeshGroup::Next), nb, cudaMemcpyHostToDevice, s));
@@ -1758,9 +1796,17 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     // u += ||r|| x, then the FP64 residual, for the designs that took part
     // (those that sat out keep u and their residual)
     LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s, bt));
-    LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
-                               red_of(m, FIN_AUX), APPLY_RESID, &m->sc->sat_out, m->flags + 1, s,
-                               bt));
+    // double-word for the designs whose residual cannot end their solve,
+    // FP64 for the others: one launch each, skipping the designs of the other
+    bool any_dw = false, any_64 = false;
+    for (int b = 0; b < nb; ++b) {
+      const MeshGroup::Next& nx = G->h_next[b];
+      any_dw |= nx.skip_dword == 0;
+      any_64 |= nx.skip_fp64 == 0;
+      if (!nx.sat_out) last_dword[b] = nx.skip_dword == 0;
+    }
+    if (any_dw) CKS(enqueue_residual(m, true, &m->sc->skip_dword, bt));
+    if (any_64) CKS(enqueue_residual(m, false, &m->sc->skip_fp64, bt));
     CKS(group_read_scalars(G));
   }
   // every design's stream after the batch
@@ -1930,7 +1976,8 @@ topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, i
 topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, size_t n_dof,
                        int on_device) {
   if (!m || !x || !y) return TOPO_ERR_INVALID;
-  if (precision != TOPO_PREC_FP64 && precision != TOPO_PREC_FP32) return TOPO_ERR_INVALID;
+  if (precision != TOPO_PREC_FP64 && precision != TOPO_PREC_FP32 && precision != TOPO_PREC_DWORD)
+    return TOPO_ERR_INVALID;
   const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
   if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
   if (!m->has_density) return TOPO_ERR_NO_DENSITY;
@@ -1947,6 +1994,13 @@ topo_status topo_apply(topo_mesh* m, int precision, const double* x, double* y, 
     LK(m, launch_unpack<double>(src, m->p64, m->d, s));
     LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, MCD(m), red_of(m, FIN_NONE),
                             APPLY_PLAIN, nullptr, m->flags + 1, s));
+    LK(m, launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
+  } else if (precision == TOPO_PREC_DWORD) {
+    CKS(ensure_fp64_inner(m));
+    LK(m, launch_unpack<double>(src, m->p64, m->d, s));
+    LK(m, launch_split_dw(m->p64, m->p32, m->q32, m->nvec, nullptr, s));
+    LK(m, launch_apply_dw(m->p32, m->q32, m->q64, m->E64, nullptr, m->d, m->mcd,
+                          red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, s));
     LK(m, launch_pack<double>(m->q64, on_device ? y : m->aos, m->d, s));
   } else {
     LK(m, launch_unpack<float>(src, m->p32, m->d, s));
@@ -1974,6 +2028,10 @@ topo_status topo_apply_internal(topo_mesh* m, int precision, int reps) {
     } else if (precision == TOPO_PREC_FP32) {
       LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m), red_of(m, FIN_NONE),
                              APPLY_PLAIN, nullptr, m->flags + 1, m->stream));
+    } else if (precision == TOPO_PREC_DWORD) {
+      CKS(ensure_fp64_inner(m));
+      LK(m, launch_apply_dw(m->p32, m->q32, m->q64, m->E64, nullptr, m->d, m->mcd,
+                            red_of(m, FIN_NONE), APPLY_PLAIN, nullptr, m->stream));
     } else {
       return TOPO_ERR_INVALID;
     }

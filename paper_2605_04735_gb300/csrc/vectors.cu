@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "dword.cuh"
 #include "kernels.h"
 
 namespace topo {
@@ -273,6 +274,25 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+__global__ void __launch_bounds__(kThreads)
+    k_split_dw(const double* __restrict__ u, float* __restrict__ hi, float* __restrict__ lo,
+               long long n4, const int* __restrict__ skip, const DSel S) {
+  pdl_start();
+  const long long off = S.off(blockIdx.y);
+  skip = bshift(skip, off);
+  if (skip && *skip) return;
+  u = bshift(u, off);
+  hi = bshift(hi, off);
+  lo = bshift(lo, off);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double4_32a v = ld4(u, q);
+    const Dw a = dw_from(v.x), b = dw_from(v.y), c = dw_from(v.z), e = dw_from(v.w);
+    st4(hi, q, make_float4(a.hi, b.hi, c.hi, e.hi));
+    st4(lo, q, make_float4(a.lo, b.lo, c.lo, e.lo));
+  }
+}
+
 // thread b: the design of slot b; max_iter < 0 takes each design's max_iter_next
 __global__ void k_set_max_iter(PcgScalars* sc, int max_iter, int nb, const DSel S) {
   const int b = threadIdx.x + blockIdx.x * blockDim.x;
@@ -349,6 +369,13 @@ cudaError_t launch_accumulate(double* u64, const T* x, long long n, const PcgSca
   const long long n4 = n / 4;
   return launch_pdl(k_accumulate<T>, vgrid(n4, bt), dim3(kThreads), 0, s, u64, x, n4, sc,
                     scaled ? 1 : 0, bt.nb > 1 ? 1 : 0, bt.sel());
+}
+
+cudaError_t launch_split_dw(const double* u, float* hi, float* lo, long long n, const int* skip,
+                            cudaStream_t s, const Bat& bt) {
+  const long long n4 = n / 4;
+  return launch_pdl(k_split_dw, vgrid(n4, bt), dim3(kThreads), 0, s, u, hi, lo, n4, skip,
+                    bt.sel());
 }
 
 template <typename T>

@@ -5,7 +5,9 @@
         operator (the CG apply with its fused p.Ap reduction) on a
         non-default stream: the capture target of the operator kernel.
     python -m paper_2605_04735_gb300.profile_run apply64 <workload> [reps]
-        the same with the FP64 operator (the kernel of the FP64 residual).
+        the same with the FP64 operator.
+    python -m paper_2605_04735_gb300.profile_run applydw <workload> [reps]
+        the same with the double-word operator (the refinement residual's).
     python -m paper_2605_04735_gb300.profile_run solve <workload> [reps]
         `reps` full steps (density, FP32 GMG-PCG + FP64 refinement to 1e-8,
         compliance, sensitivities) on one mesh: the launch list of a step.
@@ -59,9 +61,9 @@ def main(argv):
         return
     with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=s) as m:
         rho = w.density()
-        if mode in ("apply", "apply64"):
+        if mode in ("apply", "apply64", "applydw"):
             m.set_density(rho)
-            m.apply_internal(1 if mode == "apply" else 0, 3 * reps)
+            m.apply_internal({"apply": 1, "apply64": 0, "applydw": 2}[mode], 3 * reps)
             torch.cuda.synchronize()
             print("ok", mode, name, reps)
         elif mode == "solve":

@@ -21,7 +21,8 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NO_DENSITY, ERR_NOT_SOLVED, ERR_NOT_CONV
 BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX, BC_CORNERS, BC_MBB_STRIP = 0, 1, 2, 3, 4
 LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
 LOAD_DISC_XL, LOAD_HALFDISC_X0_TOP = 3, 4
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_DWORD = 0, 1, 2
+RESIDUAL_DWORD, RESIDUAL_FP64 = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
 OPERATOR_MODAL, OPERATOR_GATHER, OPERATOR_MODAL_SINGLE, OPERATOR_MODAL_PAIR = 0, 1, 2, 3
 
@@ -35,7 +36,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("rtol", C.c_double),
                 ("inner_rtol", C.c_double), ("max_iter", C.c_int), ("max_outer", C.c_int),
                 ("warm_start", C.c_int), ("gmg_levels", C.c_int), ("smooth_degree", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("residual", C.c_int)]
 
 
 class SolveInfo(C.Structure):
