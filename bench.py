@@ -330,9 +330,10 @@ def main():
     w = workload
     B = max(1, args.batch)
     # independent designs: rank r, slot b gets seed + 1000 r + b (weak scaling)
-    rhos_np = [I.dataclasses.replace(w, seed=sd).density() for sd in design_seeds(w.seed, rank, B)]
-    rho_dev = [torch.from_numpy(r).cuda() for r in rhos_np]
-    dc_dev = [torch.empty(w.n_elem, dtype=torch.float64, device="cuda") for _ in range(B)]
+    rhos_np = np.stack([I.dataclasses.replace(w, seed=sd).density()
+                        for sd in design_seeds(w.seed, rank, B)])  # (B, n_elem)
+    rho_dev = torch.from_numpy(rhos_np).cuda()
+    dc_dev = torch.empty((B, w.n_elem), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
     # one mesh group that solve_many runs as one batch (one launch per step
@@ -355,17 +356,22 @@ def main():
         from concurrent.futures import ThreadPoolExecutor
         pool = ThreadPoolExecutor(max_workers=len(groups))
 
+    bounds = np.cumsum([0] + [len(g) for g in groups])
+
     def step_batch(rhos, dcs, opt):
-        for m, r in zip(meshes, rhos):
-            m.set_density(r)
+        """rhos, dcs: (B, n_elem) arrays (numpy on the host or CUDA tensors);
+        densities, compliances and sensitivities go through the batched
+        entry points (one launch per group)."""
+        for g, a, b in zip(groups, bounds[:-1], bounds[1:]):
+            topo.set_density_many(g, rhos[a:b])
         if pool is None:
             infos = topo.solve_many(meshes, opt)
         else:  # the groups' solves overlap on the GPU (the library calls release the GIL)
             infos = [i for f in [pool.submit(topo.solve_many, g, opt) for g in groups]
                      for i in f.result()]
-        cs = [m.compliance() for m in meshes]
-        for m, d in zip(meshes, dcs):
-            m.sensitivity(d)
+        cs = np.concatenate([topo.compliance_many(g) for g in groups])
+        for g, a, b in zip(groups, bounds[:-1], bounds[1:]):
+            topo.sensitivity_many(g, dcs[a:b])
         return infos, cs
 
     def step_one(m, opt, rho, dc):
@@ -434,15 +440,15 @@ def main():
     lat = np.array(lat)
 
     # ---- e2e through the public API with pinned host buffers ----
-    rho_host = [torch.from_numpy(r).pin_memory() for r in rhos_np]
-    dc_host = [torch.empty(w.n_elem, dtype=torch.float64).pin_memory() for _ in range(B)]
+    rho_host = torch.from_numpy(rhos_np).pin_memory()
+    dc_host = torch.empty((B, w.n_elem), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2e_t = []
     for k in range(max(3, args.steps // 2)):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step_batch([r.numpy() for r in rho_host], [d.numpy() for d in dc_host], opts)
+        step_batch(rho_host.numpy(), dc_host.numpy(), opts)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = ws * B / float(np.mean(e2e_t))

@@ -221,6 +221,23 @@ topo_status topo_compliance_energy(topo_mesh* m, double* c);
  * n_elem values in element order. */
 topo_status topo_sensitivity(topo_mesh* m, double* dc, size_t n_elem, int on_device);
 
+/* Batched forms of topo_set_density, topo_compliance and topo_sensitivity
+ * for n meshes of one grid (n_elem elements each): design b's densities
+ * (floats) or sensitivities (doubles) at b * n_elem in one contiguous array
+ * (host, or device with on_device != 0); c receives n compliances (host).
+ * Results equal the per-mesh calls'.  When the meshes are a whole mesh group
+ * in its own order (topo_create_batch), each is one kernel launch for all
+ * designs and one host synchronisation (set_density: the validity flags;
+ * compliance: the values); otherwise the per-mesh calls run in turn.
+ * Errors: TOPO_ERR_INVALID (NULL or repeated mesh, n < 1, n_elem not the
+ * grid's), TOPO_ERR_NAN (set_density: a density outside [0, 1] in some
+ * design, which then has none), TOPO_ERR_NOT_SOLVED.  Eqs. (1), (2), (3). */
+topo_status topo_set_density_many(topo_mesh* const* meshes, int n, const float* rho,
+                                  size_t n_elem, int on_device);
+topo_status topo_compliance_many(topo_mesh* const* meshes, int n, double* c);
+topo_status topo_sensitivity_many(topo_mesh* const* meshes, int n, double* dc, size_t n_elem,
+                                  int on_device);
+
 /* Copy the stored FP64 displacement out (n_dof = 3 * nodes, DOF order). */
 topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_device);
 

@@ -79,10 +79,13 @@ cudaError_t launch_split_dw(const double* u, float* hi, float* lo, long long n, 
                             cudaStream_t s, const Bat& bt = Bat{});
 
 // ---- mesh data (meshdata.cu) -------------------------------------------
-// rho (dense element order) -> ghosted rho32, E32, E64; counts bad values into *bad
+// rho (dense element order) -> ghosted rho32, E32, E64; counts bad values into *bad.
+// Batched (bt): design b's input at b * src_stride floats from rho; rho_keep
+// (optional) receives a copy of the input.
 cudaError_t launch_simp(const float* rho, float* rho_g, float* E32, double* E64, const Dims& d,
                         double E0, double Emin, double penal, double hscale, int* bad,
-                        cudaStream_t s);
+                        cudaStream_t s, float* rho_keep = nullptr, long long src_stride = 0,
+                        const Bat& bt = Bat{});
 cudaError_t launch_build_load(double* f, const Dims& d, int load, double magnitude, double h,
                               cudaStream_t s);
 // AoS (3n + c, dense node order) <-> ghosted SoA; unpack zeroes fixed DOFs
@@ -120,9 +123,11 @@ cudaError_t launch_sdf(const double* tris, const long long* offsets, const doubl
 cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
                           double E0, double eta, double eps0, double hscale, const Red& red,
                           int* bad, cudaStream_t s);
+// batched (bt): design b's output at b * dc_stride doubles from dc
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
                                const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
-                               const Red& red, cudaStream_t s);
+                               const Red& red, cudaStream_t s, long long dc_stride = 0,
+                               const Bat& bt = Bat{});
 
 // ---- SIMP update (simp.cu) -------------------------------------------------
 cudaError_t launch_filter(const double* dc, const float* rho_g, double* dcf, const Dims& d,

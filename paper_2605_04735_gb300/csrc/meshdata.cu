@@ -4,6 +4,8 @@
 // the compliance (Eq. (2)) fused into the same pass.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 
 #include "common.cuh"
@@ -17,9 +19,20 @@ namespace {
 // Eq. (1): E_e = Emin + rho_e^p (E0 - Emin), evaluated in FP64 and stored
 // both in FP64 and rounded to FP32; each scaled by the element size h
 // (k0 of an element of edge h is h times the unit-cube k0 in 3-D).
+// blockIdx.y: the design slot; its input at id * src_stride floats from
+// rho, its buffers at id * S bytes; rho_keep (optional) keeps the input
 __global__ void k_simp(const float* __restrict__ rho, float* __restrict__ rho_g,
-                       float* __restrict__ E32, double* __restrict__ E64, const Dims d, double E0,
-                       double Emin, double penal, double hscale, int* __restrict__ bad) {
+                       float* __restrict__ E32, double* __restrict__ E64,
+                       float* __restrict__ rho_keep, const Dims d, double E0, double Emin,
+                       double penal, double hscale, int* __restrict__ bad, long long src_stride,
+                       const DSel S) {
+  const long long off = S.off(blockIdx.y);
+  rho += S.id(blockIdx.y) * src_stride;
+  rho_g = bshift(rho_g, off);
+  E32 = bshift(E32, off);
+  E64 = bshift(E64, off);
+  rho_keep = bshift(rho_keep, off);
+  bad = bshift(bad, off);
   const long long n = (long long)d.nx * d.ny * d.nz;
   int nbad = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -27,6 +40,7 @@ __global__ void k_simp(const float* __restrict__ rho, float* __restrict__ rho_g,
     int i, j, k;
     unflatten3(e, d.nx, d.ny, i, j, k);
     float r = rho[e];
+    if (rho_keep) rho_keep[e] = r;
     if (!(r >= 0.0f && r <= 1.0f)) {  // catches NaN too
       ++nbad;
       r = 0.0f;
@@ -129,7 +143,14 @@ __global__ void __launch_bounds__(256)
     k_sensitivity(const double* __restrict__ u, const float* __restrict__ rho_g,
                   const double* __restrict__ E64, double* __restrict__ dc, const Dims d,
                   const __grid_constant__ ModalCoef<double> kc, double penal, double dE,
-                  const Red red) {
+                  const Red red0, long long dc_stride, const DSel S) {
+  // blockIdx.y: the design slot; its output at id * dc_stride doubles from dc
+  const long long off = S.off(blockIdx.y);
+  u = bshift(u, off);
+  rho_g = bshift(rho_g, off);
+  E64 = bshift(E64, off);
+  dc += S.id(blockIdx.y) * dc_stride;
+  const Red red = red0.shifted(off);
   const long long n = (long long)d.nx * d.ny * d.nz;
   double part = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -167,7 +188,7 @@ __global__ void __launch_bounds__(256)
     part = fma(E64[og], s, part);
   }
   double v[1] = {part};
-  reduce_finalize<1>(v, red);
+  reduce_finalize<1>(v, red, blockIdx.x, gridDim.x);
 }
 
 // Ersatz material of the level-set stage (Sec. 2.2.2): phi at the element
@@ -228,9 +249,11 @@ inline int grid_for(long long n, int threads) {
 
 cudaError_t launch_simp(const float* rho, float* rho_g, float* E32, double* E64, const Dims& d,
                         double E0, double Emin, double penal, double hscale, int* bad,
-                        cudaStream_t s) {
+                        cudaStream_t s, float* rho_keep, long long src_stride, const Bat& bt) {
   const long long n = (long long)d.nx * d.ny * d.nz;
-  k_simp<<<grid_for(n, 256), 256, 0, s>>>(rho, rho_g, E32, E64, d, E0, Emin, penal, hscale, bad);
+  const dim3 grid(std::max(1, grid_for(n, 256) / bt.nb), bt.nb);
+  k_simp<<<grid, 256, 0, s>>>(rho, rho_g, E32, E64, rho_keep, d, E0, Emin, penal, hscale, bad,
+                              src_stride, bt.sel());
   return cudaGetLastError();
 }
 
@@ -266,9 +289,12 @@ cudaError_t launch_unpack(const double* aos, T* soa, const Dims& d, cudaStream_t
 
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
                                const Dims& d, const ModalCoef<double>& kc, double penal, double dE,
-                               const Red& red, cudaStream_t s) {
+                               const Red& red, cudaStream_t s, long long dc_stride,
+                               const Bat& bt) {
   const long long n = (long long)d.nx * d.ny * d.nz;
-  k_sensitivity<<<grid_for(n, 256), 256, 0, s>>>(u, rho_g, E64, dc, d, kc, penal, dE, red);
+  const dim3 grid(std::min(std::max(1, grid_for(n, 256) / bt.nb), kMaxPartials), bt.nb);
+  k_sensitivity<<<grid, 256, 0, s>>>(u, rho_g, E64, dc, d, kc, penal, dE, red, dc_stride,
+                                     bt.sel());
   return cudaGetLastError();
 }
 

@@ -212,6 +212,8 @@ struct MeshGroup {
   Next* h_next = nullptr;  // nb: per-design settings of the next inner solve
   int* h_ids = nullptr;    // nb pinned: the designs a compacted CG chunk covers
   int* d_ids = nullptr;    // nb: their device copy
+  void* stage = nullptr;   // batched host<->device transfers of densities / sensitivities
+  size_t stage_bytes = 0;
   int gmg_levels = -1, gmg_degree = -1;
   topo_params prm{};
 };
@@ -955,6 +957,7 @@ void topo_free(topo_mesh* m) {
       if (G->h_next) cudaFreeHost(G->h_next);
       if (G->h_ids) cudaFreeHost(G->h_ids);
       if (G->d_ids) cudaFree(G->d_ids);
+      if (G->stage) cudaFree(G->stage);
       delete G;
     }
   }
@@ -999,6 +1002,7 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
     for (size_t t = 0; t < sizeof(m->mcd) / sizeof(double); ++t) dst[t] = (float)src[t];
   }
   const long long ne = m->d.ecount;
+  CKS(dalloc(m, &m->rho_in, (long long)nx * ny * nz));
   CKS(dalloc(m, &m->rho_g, ne));
   CKS(dalloc(m, &m->E32, ne));
   CKS(dalloc(m, &m->E64, ne));
@@ -1061,6 +1065,7 @@ static long long group_region_bytes(const Dims& d, int levels) {
   const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
   long long b = 0;
   auto add = [&](long long bytes) { b += (bytes + 255) / 256 * 256 + 256; };
+  add((long long)d.nx * d.ny * d.nz * 4);  // rho_in
   add(ne * 4);
   add(ne * 4);
   add(ne * 8);
@@ -1121,6 +1126,7 @@ topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const to
       if (G->h_next) cudaFreeHost(G->h_next);
       if (G->h_ids) cudaFreeHost(G->h_ids);
       if (G->d_ids) cudaFree(G->d_ids);
+      if (G->stage) cudaFree(G->stage);
       delete G;
     } else {
       for (topo_mesh* m : made) topo_free(m);  // the last one frees the group
@@ -1900,6 +1906,166 @@ topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_op
   for (const SolveTask& t : tasks)
     if (t.st != TOPO_OK && first == TOPO_OK) first = t.st;
   return first;
+}
+
+namespace {
+
+// The meshes, in order, are a whole mesh group: its group, else nullptr.
+MeshGroup* whole_group(topo_mesh* const* meshes, int n) {
+  if (n < 2 || !meshes || !meshes[0]) return nullptr;
+  MeshGroup* G = meshes[0]->group;
+  if (!G || G->nb != n) return nullptr;
+  for (int b = 0; b < n; ++b)
+    if (meshes[b] != G->meshes[b]) return nullptr;
+  return G;
+}
+
+// Orders one batched operation of a whole group on design 0's stream: after
+// the callers' streams and every design's earlier work, and every design's
+// stream (then its caller's) after it.
+struct GroupScope {
+  MeshGroup* G;
+  std::vector<std::unique_ptr<Fence>> fences;
+  topo_status st = TOPO_OK;
+  explicit GroupScope(MeshGroup* g) : G(g) {
+    for (topo_mesh* m : G->meshes) {
+      fences.emplace_back(new Fence(m));
+      if (fences.back()->st != TOPO_OK) st = fences.back()->st;
+    }
+    cudaStream_t s0 = G->meshes[0]->stream;
+    for (int b = 1; b < G->nb && st == TOPO_OK; ++b)
+      if (cudaEventRecord(G->meshes[b]->ev_in, G->meshes[b]->stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s0, G->meshes[b]->ev_in, 0) != cudaSuccess)
+        st = TOPO_ERR_CUDA;
+  }
+  ~GroupScope() {
+    topo_mesh* m0 = G->meshes[0];
+    if (cudaEventRecord(m0->ev_in, m0->stream) == cudaSuccess)
+      for (int b = 1; b < G->nb; ++b) cudaStreamWaitEvent(G->meshes[b]->stream, m0->ev_in, 0);
+  }
+  GroupScope(const GroupScope&) = delete;
+  GroupScope& operator=(const GroupScope&) = delete;
+};
+
+topo_status ensure_stage(MeshGroup* G, size_t bytes) {
+  if (G->stage_bytes >= bytes) return TOPO_OK;
+  if (G->stage) cudaFree(G->stage);
+  G->stage = nullptr;
+  G->stage_bytes = 0;
+  if (cudaMalloc(&G->stage, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return TOPO_ERR_OOM;
+  }
+  G->stage_bytes = bytes;
+  return TOPO_OK;
+}
+
+// Every mesh non-null, distinct, of the grid n_elem describes (0: any).
+topo_status check_many(topo_mesh* const* meshes, int n, long long n_elem) {
+  if (n < 1 || !meshes) return TOPO_ERR_INVALID;
+  for (int a = 0; a < n; ++a) {
+    if (!meshes[a]) return TOPO_ERR_INVALID;
+    const Dims& d = meshes[a]->d;
+    if (n_elem && (long long)d.nx * d.ny * d.nz != n_elem) return TOPO_ERR_INVALID;
+    for (int b = 0; b < a; ++b)
+      if (meshes[a] == meshes[b]) return TOPO_ERR_INVALID;
+  }
+  return TOPO_OK;
+}
+
+}  // namespace
+
+topo_status topo_set_density_many(topo_mesh* const* meshes, int n, const float* rho,
+                                  size_t n_elem, int on_device) {
+  if (!rho) return TOPO_ERR_INVALID;
+  CKS(check_many(meshes, n, (long long)n_elem));
+  MeshGroup* G = whole_group(meshes, n);
+  if (!G) {
+    topo_status first = TOPO_OK;
+    for (int b = 0; b < n; ++b) {
+      const topo_status st = topo_set_density(meshes[b], rho + (size_t)b * n_elem, n_elem, on_device);
+      if (st != TOPO_OK && first == TOPO_OK) first = st;
+    }
+    return first;
+  }
+  GroupScope scope(G);
+  if (scope.st != TOPO_OK) return scope.st;
+  topo_mesh* m0 = G->meshes[0];
+  cudaStream_t s = m0->stream;
+  const float* src = rho;
+  if (!on_device) {
+    CKS(ensure_stage(G, sizeof(float) * n_elem * n));
+    CK(cudaMemcpyAsync(G->stage, rho, sizeof(float) * n_elem * n, cudaMemcpyHostToDevice, s));
+    src = static_cast<const float*>(G->stage);
+  }
+  const Bat bt{G->nb, G->S};
+  CK(cudaMemset2DAsync(m0->flags, (size_t)G->S, 0, sizeof(int), G->nb, s));
+  LK(m0, launch_simp(src, m0->rho_g, m0->E32, m0->E64, m0->d, G->prm.E0, G->prm.Emin,
+                     G->prm.penal, G->prm.h, m0->flags, s, m0->rho_in, (long long)n_elem, bt));
+  CK(cudaMemcpy2DAsync(G->h_flag, sizeof(int), m0->flags, (size_t)G->S, sizeof(int), G->nb,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  topo_status first = TOPO_OK;
+  for (int b = 0; b < n; ++b) {
+    topo_mesh* m = G->meshes[b];
+    m->diag32 = m->diag64 = false;
+    m->gmg.ready = false;
+    m->solved = false;
+    m->has_density = (G->h_flag[b] == 0);
+    if (!m->has_density && first == TOPO_OK) first = TOPO_ERR_NAN;
+  }
+  return first;
+}
+
+topo_status topo_compliance_many(topo_mesh* const* meshes, int n, double* c) {
+  if (!c) return TOPO_ERR_INVALID;
+  CKS(check_many(meshes, n, 0));
+  MeshGroup* G = whole_group(meshes, n);
+  if (!G) {
+    for (int b = 0; b < n; ++b) CKS(topo_compliance(meshes[b], &c[b]));
+    return TOPO_OK;
+  }
+  for (int b = 0; b < n; ++b)
+    if (!meshes[b]->solved) return TOPO_ERR_NOT_SOLVED;
+  GroupScope scope(G);
+  if (scope.st != TOPO_OK) return scope.st;
+  topo_mesh* m0 = G->meshes[0];
+  LK(m0, launch_dot<double>(m0->f64, m0->u64, m0->nvec, red_of(m0, FIN_AUX), m0->stream,
+                            Bat{G->nb, G->S}));
+  CKS(group_read_scalars(G));
+  for (int b = 0; b < n; ++b) c[b] = G->h_sc[b].aux[0];
+  return TOPO_OK;
+}
+
+topo_status topo_sensitivity_many(topo_mesh* const* meshes, int n, double* dc, size_t n_elem,
+                                  int on_device) {
+  if (!dc) return TOPO_ERR_INVALID;
+  CKS(check_many(meshes, n, (long long)n_elem));
+  MeshGroup* G = whole_group(meshes, n);
+  if (!G) {
+    for (int b = 0; b < n; ++b)
+      CKS(topo_sensitivity(meshes[b], dc + (size_t)b * n_elem, n_elem, on_device));
+    return TOPO_OK;
+  }
+  for (int b = 0; b < n; ++b)
+    if (!meshes[b]->solved) return TOPO_ERR_NOT_SOLVED;
+  GroupScope scope(G);
+  if (scope.st != TOPO_OK) return scope.st;
+  topo_mesh* m0 = G->meshes[0];
+  cudaStream_t s = m0->stream;
+  double* out = dc;
+  if (!on_device) {
+    CKS(ensure_stage(G, sizeof(double) * n_elem * n));
+    out = static_cast<double*>(G->stage);
+  }
+  LK(m0, launch_sensitivity(m0->u64, m0->rho_g, m0->E64, out, m0->d, m0->mcd, G->prm.penal,
+                            (G->prm.E0 - G->prm.Emin) * G->prm.h, red_of(m0, FIN_AUX), s,
+                            (long long)n_elem, Bat{G->nb, G->S}));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(dc, out, sizeof(double) * n_elem * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return TOPO_OK;
 }
 
 topo_status topo_compliance(topo_mesh* m, double* c) {

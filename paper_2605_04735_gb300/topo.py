@@ -114,6 +114,9 @@ def lib():
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
             "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
+            "topo_set_density_many": (i, [vp, i, vp, sz, i]),
+            "topo_compliance_many": (i, [vp, i, vp]),
+            "topo_sensitivity_many": (i, [vp, i, vp, sz, i]),
             "topo_server_create": (i, [C.c_longlong, i, C.POINTER(Params), C.POINTER(SolveOpts), vp,
                                        C.POINTER(vp)]),
             "topo_server_open": (i, [vp, i, i, i, i, i, C.POINTER(i)]),
@@ -215,6 +218,44 @@ def solve_many(meshes, opts: SolveOpts | None = None, check: bool = True):
     if check:
         _check(st, "topo_solve_many")
     return list(infos)
+
+
+def _handles(meshes):
+    return (C.c_void_p * len(meshes))(*[m._h for m in meshes])
+
+
+def set_density_many(meshes, rho):
+    """Densities of n meshes of one grid at once (topo_set_density_many):
+    rho is an (n, n_elem) float32 array or CUDA tensor, row b for meshes[b]."""
+    n = len(meshes)
+    p, cnt, dev = _ptr(rho, np.float32)
+    if n == 0 or cnt % n:
+        raise ValueError("rho must hold n_elem values per mesh")
+    _check(lib().topo_set_density_many(_handles(meshes), n, p, cnt // n, dev),
+           "topo_set_density_many")
+
+
+def compliance_many(meshes) -> np.ndarray:
+    """f^T u of each solved mesh (topo_compliance_many)."""
+    n = len(meshes)
+    c = np.empty(n, np.float64)
+    _check(lib().topo_compliance_many(_handles(meshes), n, c.ctypes.data), "topo_compliance_many")
+    return c
+
+
+def sensitivity_many(meshes, out=None):
+    """Element sensitivities of n solved meshes of one grid
+    (topo_sensitivity_many) into `out`, an (n, n_elem) float64 array or CUDA
+    tensor (default: a new numpy array)."""
+    n = len(meshes)
+    if out is None:
+        out = np.empty((n, meshes[0].n_elem), np.float64)
+    p, cnt, dev = _ptr(out, np.float64)
+    if n == 0 or cnt % n:
+        raise ValueError("out must hold n_elem values per mesh")
+    _check(lib().topo_sensitivity_many(_handles(meshes), n, p, cnt // n, dev),
+           "topo_sensitivity_many")
+    return out
 
 
 def _stream_arg(stream):

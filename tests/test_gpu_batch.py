@@ -152,3 +152,64 @@ def test_batch_rejects_bad_arguments(topo):
         topo.create_batch(0, 8, 4, 4)
     with pytest.raises(RuntimeError):
         topo.create_batch(2, 8, 5, 4, I.BC_MBB, I.LOAD_EDGE_X0_TOP)  # MBB needs an even ny
+
+
+def test_batched_density_compliance_sensitivity_match_per_mesh_calls(topo):
+    """topo_set_density_many / compliance_many / sensitivity_many on a whole
+    group (one launch each) against the per-mesh calls on the same designs:
+    densities from host and from device, sensitivities to host and device.
+    The batched reductions sum in another block order, so compliances agree
+    to rounding (1e-12 relative); sensitivities are elementwise identical."""
+    import torch
+    nx, ny, nz, nb = 36, 10, 10, 4
+    opts = topo.default_opts(rtol=1e-9)
+    rhos = np.stack([I.density_cone_smoothed(nx, ny, nz, 120 + b) for b in range(nb)])
+    meshes = topo.create_batch(nb, nx, ny, nz, I.BC_MBB, I.LOAD_EDGE_X0_TOP, opts=opts)
+    try:
+        for src in (rhos, torch.from_numpy(rhos).cuda()):
+            topo.set_density_many(meshes, src)
+            topo.solve_many(meshes, opts)
+            c = topo.compliance_many(meshes)
+            dc = topo.sensitivity_many(meshes)
+            dc_dev = topo.sensitivity_many(meshes, torch.empty((nb, nx * ny * nz),
+                                                               dtype=torch.float64, device="cuda"))
+            for b, m in enumerate(meshes):
+                assert c[b] == pytest.approx(m.compliance(), rel=1e-12)
+                ref = m.sensitivity()
+                assert np.array_equal(dc[b], ref)
+                assert np.array_equal(dc_dev[b].cpu().numpy(), ref)
+                assert np.array_equal(m.density(), rhos[b])
+    finally:
+        for m in meshes:
+            m.close()
+
+
+def test_batched_io_on_separate_meshes_and_bad_input(topo):
+    nx, ny, nz, nb = 12, 6, 6, 3
+    rhos = np.stack([I.density_uniform(nx, ny, nz, 0.1, 1.0, 130 + b) for b in range(nb)])
+    meshes = [topo.Mesh(nx, ny, nz) for _ in range(nb)]  # not a group: per-mesh calls
+    try:
+        topo.set_density_many(meshes, rhos)
+        topo.solve_many(meshes, topo.default_opts())
+        c = topo.compliance_many(meshes)
+        dc = topo.sensitivity_many(meshes)
+        for b, m in enumerate(meshes):
+            assert c[b] == m.compliance()
+            assert np.array_equal(dc[b], m.sensitivity())
+        with pytest.raises(RuntimeError):
+            topo.sensitivity_many(meshes, np.empty((nb, nx * ny * nz + 1), np.float64))
+    finally:
+        for m in meshes:
+            m.close()
+    group = topo.create_batch(nb, nx, ny, nz)
+    try:
+        bad = rhos.copy()
+        bad[1, 5] = np.nan  # design 1 gets no density; the others do
+        with pytest.raises(RuntimeError):
+            topo.set_density_many(group, bad)
+        with pytest.raises(RuntimeError):
+            group[1].solve()
+        assert group[0].solve().status == 0
+    finally:
+        for m in group:
+            m.close()
