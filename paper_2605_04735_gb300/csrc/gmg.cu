@@ -379,6 +379,71 @@ __global__ void k_gj_step(double* __restrict__ A, int n, int k, const double* __
   }
 }
 
+// The coarsest inverse in one kernel per design, for batched setups (one
+// design alone keeps the pivot chain below: a single SM's FP64 rate makes
+// this kernel no faster than the chain for one design, but a batch fills the
+// SMs with designs and saves the chain's n launches).  The symmetric sweep
+// operator on the packed lower triangle in shared memory: sweeping pivot k
+// maps a_kk -> -1/a_kk, a_ik -> a_ik/a_kk (i != k) and a_ij -> a_ij -
+// a_ik a_kj / a_kk; after all n pivots the matrix holds -A^-1 (no pivoting:
+// every pivot is a Schur-complement diagonal of the SPD A, as in
+// Gauss-Jordan).  CTA barriers separate the pivots.  In: the dense n x n A
+// at A; out: A^-1 (full, symmetric).
+constexpr int kSweepThreads = 1024;
+constexpr int kSweepMaxN = 222;  // n (n + 1) / 2 + 2 n doubles within 200 KB
+constexpr int kSweepPer = (kSweepMaxN * (kSweepMaxN + 1) / 2 + kSweepThreads - 1) / kSweepThreads;
+
+__global__ void __launch_bounds__(kSweepThreads)
+    k_gj_sweep(double* __restrict__ A, int n, const DSel S) {
+  pdl_start();
+  A = bshift(A, S.off(blockIdx.y));
+  extern __shared__ double sweep_smem[];
+  double* P = sweep_smem;        // packed: (i, j), i >= j at i (i + 1) / 2 + j
+  const int np = n * (n + 1) / 2;
+  double* col = P + np;          // column k before pivot k
+  double* cs = col + n;          // the same divided by the pivot
+  // this thread's packed entries t = tid + q * blockDim.x as (i, j)
+  int ij[kSweepPer];
+#pragma unroll
+  for (int q = 0; q < kSweepPer; ++q) {
+    const int t = threadIdx.x + q * kSweepThreads;
+    int i = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    if (i * (i + 1) / 2 > t) --i;
+    if ((i + 1) * (i + 2) / 2 <= t) ++i;
+    ij[q] = (i << 16) | (t - i * (i + 1) / 2);
+    if (t < np) P[t] = A[(long long)i * n + (t - i * (i + 1) / 2)];
+  }
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();  // the previous pivot's updates are done
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      col[i] = i >= k ? P[i * (i + 1) / 2 + k] : P[k * (k + 1) / 2 + i];
+    __syncthreads();
+    const double inv = 1.0 / col[k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) cs[i] = col[i] * inv;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSweepPer; ++q) {
+      const int t = threadIdx.x + q * kSweepThreads;
+      if (t >= np) break;
+      const int i = ij[q] >> 16, j = ij[q] & 0xffff;
+      double v;
+      if (i == k)
+        v = (j == k) ? -inv : cs[j];
+      else if (j == k)
+        v = cs[i];
+      else
+        v = fma(-col[i], cs[j], P[t]);
+      P[t] = v;
+    }
+  }
+  __syncthreads();
+  const long long nn = (long long)n * n;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t - (long long)i * n);
+    A[t] = -(i >= j ? P[i * (i + 1) / 2 + j] : P[j * (j + 1) / 2 + i]);
+  }
+}
+
 __global__ void k_coarse_gather(const float* __restrict__ b, const Dims d, double* __restrict__ bd,
                                 const int* __restrict__ done, const DSel S) {
   pdl_start();
@@ -577,6 +642,21 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
   const long long nn = (long long)g.nc * g.nc;
   GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn, bt.nb), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d,
                  Lc.E, k0d, bt.sel()));
+  if (bt.nb > 1 && g.nc <= kSweepMaxN) {  // a batch: the whole inverse in one kernel per design
+    const size_t smem = sizeof(double) * ((size_t)g.nc * (g.nc + 1) / 2 + 2 * g.nc);
+    static bool attr = false;
+    if (!attr) {
+      GCK(cudaFuncSetAttribute(k_gj_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(double) * ((size_t)kSweepMaxN * (kSweepMaxN + 1) / 2 +
+                                                       2 * kSweepMaxN))));
+      attr = true;
+    }
+    GCK(launch_pdl(k_gj_sweep, dim3(1, bt.nb), dim3(kSweepThreads), smem, s, g.Ainv, g.nc,
+                   bt.sel()));
+    *launches += 2;  // the dense assembly and the sweep
+    g.ready = true;
+    return cudaSuccess;
+  }
   // the pivot chain, captured once per batch shape as a graph and replayed per density
   if (g.gj_exec && (g.gj_nb != bt.nb || g.gj_S != bt.S)) {
     cudaGraphExecDestroy(g.gj_exec);
@@ -608,7 +688,7 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
     GCK(e);
   }
   GCK(cudaGraphLaunch(g.gj_exec, s));
-  *launches += 1 + g.nc;
+  *launches += 2 + g.nc;  // the dense assembly, the seed and the pivot steps
   g.ready = true;
   return cudaSuccess;
 }
