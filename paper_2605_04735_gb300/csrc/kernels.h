@@ -25,9 +25,12 @@ enum ApplyMode {
 // mc != nullptr: element-centric modal kernel; nullptr: node-centric gather
 // (one design only).  bt: designs of a mesh group (all pointers are design 0's).
 template <typename T>
+// energy (FP64 modal only, else nullptr): element energies
+// (u_e - u_0)^T k0 (u_e - u_0) of x, written in the element layout.
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
                          const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
-                         int* errflag, cudaStream_t s, const Bat& bt = Bat{});
+                         int* errflag, cudaStream_t s, const Bat& bt = Bat{},
+                         T* energy = nullptr);
 // The same operator (modal form) evaluated in double-word arithmetic (two
 // FP32 words per value, ~48 significand bits): x given pre-split into hi and
 // lo FP32 vectors (launch_split_dw), moduli E and f in FP64, y in FP64.
@@ -123,6 +126,10 @@ cudaError_t launch_sdf(const double* tris, const long long* offsets, const doubl
 cudaError_t launch_ersatz(const double* phi, float* rho_g, float* E32, double* E64, const Dims& d,
                           double E0, double eta, double eps0, double hscale, const Red& red,
                           int* bad, cudaStream_t s);
+// the same from stored element energies (the FP64 residual's by-product)
+cudaError_t launch_sens_energy(const double* energy, const float* rho_g, const double* E64,
+                               double* dc, const Dims& d, double penal, double dE, const Red& red,
+                               cudaStream_t s, long long dc_stride = 0, const Bat& bt = Bat{});
 // batched (bt): design b's output at b * dc_stride doubles from dc
 cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double* E64, double* dc,
                                const Dims& d, const ModalCoef<double>& kc, double penal, double dE,

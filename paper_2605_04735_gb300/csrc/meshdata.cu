@@ -191,6 +191,37 @@ __global__ void __launch_bounds__(256)
   reduce_finalize<1>(v, red, blockIdx.x, gridDim.x);
 }
 
+// Eq. (3) from element energies the FP64 residual kernel stored
+// (energy_e = (u_e - u_0)^T k0 (u_e - u_0) of the current u): dc_e =
+// -p rho_e^(p-1) dE energy_e, and sum_e E_e energy_e -> red.  Batched as
+// k_sensitivity.
+__global__ void __launch_bounds__(256)
+    k_sens_energy(const double* __restrict__ energy, const float* __restrict__ rho_g,
+                  const double* __restrict__ E64, double* __restrict__ dc, const Dims d,
+                  double penal, double dE, const Red red0, long long dc_stride, const DSel S) {
+  const long long off = S.off(blockIdx.y);
+  energy = bshift(energy, off);
+  rho_g = bshift(rho_g, off);
+  E64 = bshift(E64, off);
+  dc += S.id(blockIdx.y) * dc_stride;
+  const Red red = red0.shifted(off);
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  double part = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    unflatten3(e, d.nx, d.ny, i, j, k);
+    const long long og = d.elem(i, j, k);
+    const double w = energy[og];
+    const double r = (double)rho_g[og];
+    const double rp1 = (penal == 3.0) ? r * r : pow(r, penal - 1.0);
+    dc[e] = -penal * rp1 * dE * w;
+    part = fma(E64[og], w, part);
+  }
+  double v[1] = {part};
+  reduce_finalize<1>(v, red, blockIdx.x, gridDim.x);
+}
+
 // Ersatz material of the level-set stage (Sec. 2.2.2): phi at the element
 // centroid (mean of the 8 corner values of the Q1 interpolant of the nodal
 // level set, node n = i + (nx+1)(j + (ny+1)k)), H_eta of Eq. (8),
@@ -294,6 +325,16 @@ cudaError_t launch_sensitivity(const double* u, const float* rho_g, const double
   const long long n = (long long)d.nx * d.ny * d.nz;
   const dim3 grid(std::min(std::max(1, grid_for(n, 256) / bt.nb), kMaxPartials), bt.nb);
   k_sensitivity<<<grid, 256, 0, s>>>(u, rho_g, E64, dc, d, kc, penal, dE, red, dc_stride,
+                                     bt.sel());
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sens_energy(const double* energy, const float* rho_g, const double* E64,
+                               double* dc, const Dims& d, double penal, double dE, const Red& red,
+                               cudaStream_t s, long long dc_stride, const Bat& bt) {
+  const long long n = (long long)d.nx * d.ny * d.nz;
+  const dim3 grid(std::min(std::max(1, grid_for(n, 256) / bt.nb), kMaxPartials), bt.nb);
+  k_sens_energy<<<grid, 256, 0, s>>>(energy, rho_g, E64, dc, d, penal, dE, red, dc_stride,
                                      bt.sel());
   return cudaGetLastError();
 }

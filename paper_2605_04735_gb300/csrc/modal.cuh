@@ -106,7 +106,7 @@ __device__ __forceinline__ void modal_seed(ModalColumn<T>& col, const T (&raw)[2
 template <typename T>
 __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[2][2][3], T E,
                                            const ModalCoef<T>& kc, T (&plane)[3][4],
-                                           T (&ctr)[3]) {
+                                           T (&ctr)[3], T* dot = nullptr) {
   T uh[3][8];
   T txy[3][4];
 #pragma unroll
@@ -137,6 +137,14 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
       }
       yh[p][m] = acc;
     }
+  }
+  if (dot) {  // uh . K~ uh = E^2 (u_e - u_0)^T k0 (u_e - u_0): the element's energy times E^2
+    T e = T(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int m = 1; m < 8; ++m) e = fmadd(uh[p][m], yh[p][m], e);
+    *dot = e;
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -355,7 +363,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     k_modal_plain(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
                   const __grid_constant__ ModalCoef<T> kc, const Epi epi0, const Red red0,
                   const int zchunk, const int zc, const DSel S,
-                  const int* __restrict__ done) {
+                  const int* __restrict__ done, T* __restrict__ energy) {
   pdl_start();
   const int slot = blockIdx.z / zc, chunk = blockIdx.z - slot * zc;
   const long long off = S.off(slot);
@@ -363,6 +371,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   if (done != nullptr && *done) return;
   x = bshift(x, off);
   E = bshift(E, off);
+  energy = bshift(energy, off);
   const Epi epi = epi0.shifted(off);
   const Red red = red0.shifted(off);
   __shared__ T xch[2][kModalTY][kModalTX][3];
@@ -397,8 +406,12 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
         for (int c = 0; c < 3; ++c) top[dy][dx][c] = node_val(ex + dx, ey + dy, ez + 1, c);
     const T Ee = (ex <= d.nx && ey <= d.ny && ez <= d.nz) ? __ldg(E + d.elem(ex, ey, ez)) : T(0);
-    T plane[3][4], ctr[3];
-    modal_layer<T>(col, top, Ee, kc, plane, ctr);
+    T plane[3][4], ctr[3], dot;
+    modal_layer<T>(col, top, Ee, kc, plane, ctr, energy ? &dot : nullptr);
+    // element energies (u_e - u_0)^T k0 (u_e - u_0), written by the CTA and
+    // z-chunk that own the element (the others compute it as halo / warm-up)
+    if (energy && tx > 0 && ty > 0 && ex < d.nx && ey < d.ny && ez >= kb && ez < d.nz)
+      energy[d.elem(ex, ey, ez)] = Ee != T(0) ? dot / (Ee * Ee) : T(0);
     part += modal_finish<T, Epi>(plane, xch[(ez - kb + 1) & 1], tx, ty, ex, ey, ez,
                                  own && ez >= kb, ctr, d, epi);
   }
@@ -432,12 +445,13 @@ bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* ma
 template <typename T, class Epi>
 cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                                 const Epi& epi, const Red& red, const int* done, int* errflag,
-                                cudaStream_t s, const Bat& bt) {
+                                cudaStream_t s, const Bat& bt, T* energy = nullptr) {
   const int z = modal_zchunk(d, bt.nb);
   const int zc = (d.nz + z) / z;
   dim3 block(kModalTX, kModalTY, 1);
   dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY, zc * bt.nb);
   if constexpr (sizeof(T) == 4) {
+    if (energy) return cudaErrorInvalidValue;  // element energies: the FP64 kernel only
     CUtensorMap xm, em, am[2];
     std::memset(am, 0, sizeof(am));
     bool ok = modal_maps(x, E, d, bt, &xm, &em);
@@ -456,7 +470,7 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
     }
   }
   return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.sel(),
-                    done);
+                    done, energy);
 }
 
 }  // namespace topo

@@ -422,14 +422,14 @@ constexpr int kPairAutoMinNx = 150;
 template <typename T, class Epi>
 cudaError_t launch_modal(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                          const Epi& epi, const Red& red, const int* done, int* errflag,
-                         cudaStream_t s, const Bat& bt = Bat{}) {
+                         cudaStream_t s, const Bat& bt = Bat{}, T* energy = nullptr) {
   if constexpr (sizeof(T) == 4) {
     CUtensorMap xm, em;
     const bool want = kc.form == 2 || (kc.form == 0 && d.nx >= kPairAutoMinNx);
     if (want && pair_maps(x, E, d, bt, &xm, &em))
       return launch_modal_pair<Epi>(xm, em, d, kc, epi, red, done, errflag, s, bt);
   }
-  return launch_modal_single<T, Epi>(x, E, d, kc, epi, red, done, errflag, s, bt);
+  return launch_modal_single<T, Epi>(x, E, d, kc, epi, red, done, errflag, s, bt, energy);
 }
 
 }  // namespace topo

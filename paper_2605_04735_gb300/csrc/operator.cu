@@ -110,7 +110,7 @@ __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const 
 template <typename T>
 cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d, const K0<T>& k0,
                          const ModalCoef<T>* mc, const Red& red, int mode, const int* done,
-                         int* errflag, cudaStream_t s, const Bat& bt) {
+                         int* errflag, cudaStream_t s, const Bat& bt, T* energy) {
   if (mc) {
     switch (mode) {
       case APPLY_PLAIN:
@@ -118,9 +118,11 @@ cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d
       case APPLY_DOT:
         return launch_modal<T>(x, E, d, *mc, EpiApply<T, true>{y}, red, done, errflag, s, bt);
       default:
-        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s, bt);
+        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s, bt,
+                               energy);
     }
   }
+  if (energy) return cudaErrorInvalidValue;    // element energies: the modal kernels only
   if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
   switch (mode) {
     case APPLY_PLAIN:
@@ -157,11 +159,11 @@ cudaError_t launch_diag_inv(T* dinv, const T* E, const Dims& d, const K0<T>& k0,
 template cudaError_t launch_apply<float>(const float*, float*, const float*, const float*,
                                          const Dims&, const K0<float>&, const ModalCoef<float>*,
                                          const Red&, int, const int*, int*, cudaStream_t,
-                                         const Bat&);
+                                         const Bat&, float*);
 template cudaError_t launch_apply<double>(const double*, double*, const double*, const double*,
                                           const Dims&, const K0<double>&,
                                           const ModalCoef<double>*, const Red&, int, const int*,
-                                          int*, cudaStream_t, const Bat&);
+                                          int*, cudaStream_t, const Bat&, double*);
 
 bool build_modal_coef(const double* k0, ModalCoef<double>* out) {
   // corner a of the local numbering -> binary index b = ax + 2 ay + 4 az

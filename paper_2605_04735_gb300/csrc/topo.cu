@@ -139,6 +139,9 @@ struct topo_mesh {
   int* flags = nullptr;
   double* aos = nullptr;       // n_dof doubles (ABI transfers)
   double* dc = nullptr;        // n_elem doubles
+  double* energy = nullptr;    // element energies of u (element layout), by the FP64 residual
+  bool energy_fresh = false;   // energy belongs to the current u
+  bool e_positive = false;     // every element modulus > 0 (energies are recoverable)
   float* rho_in = nullptr;     // n_elem floats: the current densities, dense element order
   double* phi_in = nullptr;    // n_node doubles: the nodal level set (ersatz material)
   // level-set stage (lazily allocated): second level-set buffer, shape
@@ -340,6 +343,11 @@ topo_status ensure_profile_events(topo_mesh* m, int n) {
 
 enum InnerKind { IK_JAC32 = 0, IK_JAC64 = 1, IK_GMG32 = 2 };
 
+// An inner FP32 solve that could finish the solve aims at kInnerMargin x the
+// target relative residual: the FP32 recursion's residual drifts from the
+// true one, and a miss costs a whole further outer step.
+constexpr double kInnerMargin = 0.25;
+
 // Enqueue `count` CG iterations of the given kind.  Every kernel returns at
 // once when the device-side `done` flag is set, so iterations past
 // convergence are no-ops and a chunk can be replayed blindly.
@@ -497,10 +505,10 @@ topo_status enqueue_residual(topo_mesh* m, bool dword, const int* skip = nullptr
     LK(m, launch_split_dw(m->u64, m->p32, m->q32, m->nvec, skip, m->stream, bt));
     LK(m, launch_apply_dw(m->p32, m->q32, m->r64, m->E64, m->f64, m->d, m->mcd,
                           red_of(m, FIN_AUX), APPLY_RESID, skip, m->stream, bt));
-  } else {
+  } else {  // FP64; the modal kernel also stores the element energies of u
     LK(m, launch_apply<double>(m->u64, m->r64, m->E64, m->f64, m->d, m->k0d, MCD(m),
                                red_of(m, FIN_AUX), APPLY_RESID, skip, m->flags + 1, m->stream,
-                               bt));
+                               bt, m->use_modal ? m->energy : nullptr));
   }
   return TOPO_OK;
 }
@@ -577,10 +585,12 @@ topo_status task_start(SolveTask& t) {
   CK(cudaMemsetAsync(m->flags + 1, 0, sizeof(int), s));  // bounded-wait timeout flag
   if (o->warm_start) {
     CKS(enqueue_residual(m, false));  // a warm start may already be converged
+    m->energy_fresh = m->use_modal;
   } else {
     CK(cudaMemsetAsync(m->u64, 0, sizeof(double) * m->nvec, s));
     CK(cudaMemcpyAsync(m->r64, m->f64, sizeof(double) * m->nvec, cudaMemcpyDeviceToDevice, s));
     LK(m, launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s));
+    m->energy_fresh = false;
   }
   CKS(request_scalars(m));
   t.phase = SolveTask::P_RESID;
@@ -613,7 +623,7 @@ topo_status task_step(SolveTask& t) {
     if (t.kind == IK_JAC64)  // the final tolerance directly, with margin
       inner = std::min(std::max(0.5 * o.rtol * t.fn / std::sqrt(rr), 1e-15), 0.5);
     else
-      inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * t.fn / std::sqrt(rr)), 0.5);
+      inner = std::min(std::max(o.inner_rtol, kInnerMargin * o.rtol * t.fn / std::sqrt(rr)), 0.5);
     t.expect = inner * rel;
     CKS(enqueue_inner_start(t, inner, o.max_iter - t.total));
     CKS(run_iters(m, t.kind, o.check_every, t.profile));
@@ -649,6 +659,7 @@ topo_status task_step(SolveTask& t) {
     LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, m->stream));
   t.resid_dword = t.kind != IK_JAC64 && dword_residual(o, t.expect);
   CKS(enqueue_residual(m, t.resid_dword));
+  m->energy_fresh = !t.resid_dword && m->use_modal;  // u changed; FP64 residuals store energies
   t.phase = SolveTask::P_RESID;
   return request_scalars(m);
 }
@@ -1003,6 +1014,7 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
   }
   const long long ne = m->d.ecount;
   CKS(dalloc(m, &m->rho_in, (long long)nx * ny * nz));
+  CKS(dalloc(m, &m->energy, ne));
   CKS(dalloc(m, &m->rho_g, ne));
   CKS(dalloc(m, &m->E32, ne));
   CKS(dalloc(m, &m->E64, ne));
@@ -1066,6 +1078,7 @@ static long long group_region_bytes(const Dims& d, int levels) {
   long long b = 0;
   auto add = [&](long long bytes) { b += (bytes + 255) / 256 * 256 + 256; };
   add((long long)d.nx * d.ny * d.nz * 4);  // rho_in
+  add(ne * 8);                             // element energies
   add(ne * 4);
   add(ne * 4);
   add(ne * 8);
@@ -1191,6 +1204,8 @@ static topo_status set_density_impl(topo_mesh* m, const float* src_dev) {
   m->diag32 = m->diag64 = false;
   m->gmg.ready = false;
   m->solved = false;
+  m->energy_fresh = false;
+  m->e_positive = m->prm.Emin > 0.0;
   m->has_density = (bad == 0);
   return bad ? TOPO_ERR_NAN : TOPO_OK;
 }
@@ -1235,6 +1250,8 @@ topo_status topo_set_levelset(topo_mesh* m, const double* phi, size_t n_nodes, i
   m->solved = false;
   m->has_density = (bad == 0);
   m->ls_ready = (bad == 0);
+  m->energy_fresh = false;
+  m->e_positive = eps0 > 0.0;
   if (volume) *volume = m->h_sc->aux[0] * m->prm.h * m->prm.h * m->prm.h;
   return bad ? TOPO_ERR_NAN : TOPO_OK;
 }
@@ -1670,8 +1687,10 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
   CK(cudaMemset2DAsync(m->flags + 1, (size_t)G->S, 0, sizeof(int), nb, s));
   if (o.warm_start) {
     CKS(enqueue_residual(m, false, nullptr, bt));  // a warm start may already be converged
+    for (topo_mesh* q : G->meshes) q->energy_fresh = q->use_modal;
   } else {
     CK(cudaMemset2DAsync(m->u64, (size_t)G->S, 0, sizeof(double) * m->nvec, nb, s));
+    for (topo_mesh* q : G->meshes) q->energy_fresh = false;
     CK(cudaMemcpy2DAsync(m->r64, (size_t)G->S, m->f64, (size_t)G->S, sizeof(double) * m->nvec,
                          nb, cudaMemcpyDeviceToDevice, s));
     LK(m, launch_dot<double>(m->r64, m->r64, m->nvec, red_of(m, FIN_AUX), s, bt));
@@ -1718,7 +1737,8 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         running[b] = 0;
         continue;
       }
-      const double inner = std::min(std::max(o.inner_rtol, 0.25 * o.rtol * fn / std::sqrt(rr)), 0.5);
+      const double inner =
+          std::min(std::max(o.inner_rtol, kInnerMargin * o.rtol * fn / std::sqrt(rr)), 0.5);
       expect[b] = inner * rel[b];
       const bool dw = dword_residual(o, expect[b]);
       nx.skip_dword = dw ? 0 : 1;
@@ -1813,6 +1833,9 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     }
     if (any_dw) CKS(enqueue_residual(m, true, &m->sc->skip_dword, bt));
     if (any_64) CKS(enqueue_residual(m, false, &m->sc->skip_fp64, bt));
+    for (int b = 0; b < nb; ++b)  // designs that took part have a new u
+      if (!G->h_next[b].sat_out)
+        G->meshes[b]->energy_fresh = G->h_next[b].skip_fp64 == 0 && G->meshes[b]->use_modal;
     CKS(group_read_scalars(G));
   }
   // every design's stream after the batch
@@ -1907,6 +1930,9 @@ topo_status topo_solve_many(topo_mesh* const* meshes, int n, const topo_solve_op
     if (t.st != TOPO_OK && first == TOPO_OK) first = t.st;
   return first;
 }
+
+// the element energies the last FP64 residual stored are those of u
+static bool energies_usable(const topo_mesh* m) { return m->energy_fresh && m->e_positive; }
 
 namespace {
 
@@ -2011,6 +2037,8 @@ topo_status topo_set_density_many(topo_mesh* const* meshes, int n, const float* 
     m->diag32 = m->diag64 = false;
     m->gmg.ready = false;
     m->solved = false;
+    m->energy_fresh = false;
+    m->e_positive = G->prm.Emin > 0.0;
     m->has_density = (G->h_flag[b] == 0);
     if (!m->has_density && first == TOPO_OK) first = TOPO_ERR_NAN;
   }
@@ -2058,9 +2086,15 @@ topo_status topo_sensitivity_many(topo_mesh* const* meshes, int n, double* dc, s
     CKS(ensure_stage(G, sizeof(double) * n_elem * n));
     out = static_cast<double*>(G->stage);
   }
-  LK(m0, launch_sensitivity(m0->u64, m0->rho_g, m0->E64, out, m0->d, m0->mcd, G->prm.penal,
-                            (G->prm.E0 - G->prm.Emin) * G->prm.h, red_of(m0, FIN_AUX), s,
-                            (long long)n_elem, Bat{G->nb, G->S}));
+  bool all_fresh = true;
+  for (topo_mesh* q : G->meshes) all_fresh &= energies_usable(q);
+  const double dE = (G->prm.E0 - G->prm.Emin) * G->prm.h;
+  if (all_fresh)
+    LK(m0, launch_sens_energy(m0->energy, m0->rho_g, m0->E64, out, m0->d, G->prm.penal, dE,
+                              red_of(m0, FIN_AUX), s, (long long)n_elem, Bat{G->nb, G->S}));
+  else
+    LK(m0, launch_sensitivity(m0->u64, m0->rho_g, m0->E64, out, m0->d, m0->mcd, G->prm.penal,
+                              dE, red_of(m0, FIN_AUX), s, (long long)n_elem, Bat{G->nb, G->S}));
   if (!on_device) {
     CK(cudaMemcpyAsync(dc, out, sizeof(double) * n_elem * n, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -2082,8 +2116,13 @@ topo_status topo_compliance(topo_mesh* m, double* c) {
 static topo_status sens_impl(topo_mesh* m) {
   const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
   if (!m->dc) CKS(dalloc(m, &m->dc, ne));
-  LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->mcd, m->prm.penal,
-                        (m->prm.E0 - m->prm.Emin) * m->prm.h, red_of(m, FIN_AUX), m->stream));
+  const double dE = (m->prm.E0 - m->prm.Emin) * m->prm.h;
+  if (energies_usable(m))
+    LK(m, launch_sens_energy(m->energy, m->rho_g, m->E64, m->dc, m->d, m->prm.penal, dE,
+                             red_of(m, FIN_AUX), m->stream));
+  else
+    LK(m, launch_sensitivity(m->u64, m->rho_g, m->E64, m->dc, m->d, m->mcd, m->prm.penal, dE,
+                             red_of(m, FIN_AUX), m->stream));
   return TOPO_OK;
 }
 
@@ -2135,6 +2174,7 @@ topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, i
   if (fence.st != TOPO_OK) return fence.st;
   CKS(upload_f64(m, u, m->u64, n_dof, on_device));
   m->solved = false;
+  m->energy_fresh = false;
   if (!on_device) CK(cudaStreamSynchronize(m->stream));
   return TOPO_OK;
 }
@@ -2233,7 +2273,7 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
   if (nx < 1 || ny < 1 || nz < 1) return -1;
   Dims d = make_dims(nx, ny, nz, 0, ny / 2);
   const long long nvec = 3 * d.comp;
-  long long b = d.ecount * (4 + 4 + 8);      // rho, E32, E64
+  long long b = d.ecount * (4 + 4 + 8 + 8);  // rho, E32, E64, element energies
   b += nvec * (3 * 8 + 7 * 4);                // f, u, r (FP64) + 7 FP32 CG vectors
   b += (long long)sizeof(PcgScalars) + 4LL * kMaxPartials * 8 + 16;
   b += 3LL * (nx + 1) * (ny + 1) * (nz + 1) * 8;  // ABI staging

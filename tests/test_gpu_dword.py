@@ -113,3 +113,30 @@ def test_residual_option_is_validated(topo):
         m.set_density(np.ones(8 * 4 * 4, np.float32))
         with pytest.raises(RuntimeError):
             m.solve(topo.default_opts(residual=7))
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[4]])
+def test_sensitivity_from_residual_energies(topo, case):
+    """After a solve the sensitivities come from the element energies the
+    certifying FP64 residual kernel stored.  Reference: the energies of the
+    same displacement in numpy FP64, each element's u shifted by its corner 0
+    (k0 annihilates translations, so the shift changes the energy only by
+    rounding, and keeps a large displacement from swamping a small strain
+    energy); tolerance 1e-11 of the max |dc| (FP64 rounding of ~50-term sums
+    of the element's terms)."""
+    nx, ny, nz, bc, load = case
+    rho = I.density_uniform(nx, ny, nz, 0.01, 1.0, 37)
+    P = fem.Problem(nx, ny, nz, bc, load, rho)
+    with topo.Mesh(nx, ny, nz, bc, load) as m:
+        m.set_density(rho)
+        m.solve(topo.default_opts())
+        u = m.displacement()
+        dc = m.sensitivity()
+        ce = m.compliance_energy()
+        c = m.compliance()
+    ue = u[P.grid.element_dofs()].reshape(-1, 8, 3)
+    ue = (ue - ue[:, :1, :]).reshape(-1, 24)
+    w = np.einsum("ea,ab,eb->e", ue, P.k0, ue)
+    ref = -3.0 * rho.astype(np.float64) ** 2 * (1.0 - 1e-9) * w
+    assert np.abs(dc - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert ce == pytest.approx(c, rel=1e-9)
