@@ -297,6 +297,15 @@ __host__ __device__ constexpr int epi_slots() {
   return Epi::kAux > 0 ? Epi::kAux : 1;
 }
 
+// Operand vectors a TMA kernel stages: all but the Jacobi inverse diagonal
+// (Epi::kDinvAux, the last aux when present), which those kernels form from
+// the element moduli they already hold: D^-1 = 1 / (kdiag * sum of the 8
+// moduli around the node).
+template <class Epi>
+__host__ __device__ constexpr int epi_staged() {
+  return Epi::kAux - (Epi::kDinvAux >= 0 ? 1 : 0);
+}
+
 template <class Epi, int N, typename T, class DD>
 __device__ __forceinline__ T epi_run(const Epi& e, const int (&i)[N], int j, int k,
                                      const long long (&o)[N], const bool (&own)[N],

@@ -88,6 +88,7 @@ __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long
 struct EpiChebStep {
   static constexpr bool kReduce = false;
   static constexpr int kAux = 2;  // r, D^-1
+  static constexpr int kDinvAux = 1;
   float* r;
   float* dn;
   float* x;
@@ -125,6 +126,7 @@ struct EpiChebStep {
 struct EpiChebLast {
   static constexpr bool kReduce = false;
   static constexpr int kAux = 0;
+  static constexpr int kDinvAux = -1;
   float* r;
   __device__ EpiChebLast shifted(long long off) const { return EpiChebLast{bshift(r, off)}; }
   __host__ __device__ const float* aux(int) const { return nullptr; }
@@ -147,6 +149,7 @@ struct EpiChebLast {
 struct EpiChebResid {
   static constexpr bool kReduce = false;
   static constexpr int kAux = 2;  // b, D^-1
+  static constexpr int kDinvAux = 1;
   const float* b;
   float* r;
   float* d0;

@@ -42,6 +42,7 @@ template <typename T>
 struct ModalCoef {
   T D[3][8];     // diagonal of K~ per component and mode (mode 0 unused)
   T C[3][3][8];  // coupling of (p, m) with (q, m ^ (1<<p) ^ (1<<q)), bits p, q of m differ
+  T kdiag;       // every diagonal entry of k0 (the cube's symmetry makes them equal)
   int form;  // FP32 kernel form: 0 automatic, 1 one column per thread, 2 two columns (packed)
 };
 
@@ -240,8 +241,10 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
                 const __grid_constant__ ModalCoef<float> kc, const Epi epi0, const Red red0,
                 const int zchunk, const int zc, const DSel S, const int* __restrict__ done,
                 int* __restrict__ errflag) {
-  constexpr int NA = Epi::kAux;
+  constexpr int NA = epi_staged<Epi>();  // staged operand vectors
+  constexpr int DI = Epi::kDinvAux;      // >= 0: D^-1 formed from the moduli
   static_assert(NA <= 2, "at most two staged operand vectors");
+  static_assert(DI < 0 || DI == Epi::kAux - 1, "D^-1 is the last operand");
   constexpr int SF = modal_stage_floats(NA);
   pdl_start();
   const int slot = blockIdx.z / zc, chunk = blockIdx.z - slot * zc;
@@ -299,10 +302,16 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
   ModalColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
+  float es_prev = 0.f;  // (DI) moduli of the 2 x 2 elements below node (ex, ey), layer before
   for (int t = 0; t < nst; ++t) {
     const int slot = t % kModalStages;
     mbar_wait_bounded(&bar[slot], (uint32_t)((t / kModalStages) & 1), errflag);
     const float* nd = stg + slot * SF;
+    float es = 0.f;  // (DI) moduli of the 2 x 2 elements around (ex, ey) in this stage's layer
+    if (DI >= 0 && own) {
+      const float* e0 = nd + kMElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
+      es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
+    }
     float top[2][2][3];  // [dy][dx][c]
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
@@ -319,6 +328,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
         issue(kModalStages);
       }
       modal_seed<float>(col, top);
+      es_prev = es;
       continue;
     }
     float plane[3][4], ctr[3];
@@ -346,8 +356,15 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
       for (int q = 0; q < NA; ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) av[q][0][c] = ap[q * kMAuxStride + c * (kMAuxY * kMAuxX)];
+      if constexpr (DI >= 0) {  // D^-1 of the masked operator, 1 where no stiffness
+        const float sum = es_prev + es;
+        const float dv = sum > 0.f ? 1.0f / (kc.kdiag * sum) : 1.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) av[DI][0][c] = dv;
+      }
       part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
     }
+    es_prev = es;
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
@@ -455,9 +472,9 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
     CUtensorMap xm, em, am[2];
     std::memset(am, 0, sizeof(am));
     bool ok = modal_maps(x, E, d, bt, &xm, &em);
-    for (int q = 0; q < Epi::kAux && ok; ++q) ok = modal_aux_map(epi.aux(q), d, bt, &am[q]);
+    for (int q = 0; q < epi_staged<Epi>() && ok; ++q) ok = modal_aux_map(epi.aux(q), d, bt, &am[q]);
     if (ok) {
-      constexpr size_t smem = modal_smem(Epi::kAux);
+      constexpr size_t smem = modal_smem(epi_staged<Epi>());
       static bool attr = false;  // per instantiation; setting it twice is harmless
       if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(

@@ -60,6 +60,7 @@ __device__ __forceinline__ void pfwht4(float2 (&v)[4]) {
 struct ModalCoef2 {
   float2 D[3][8];
   float2 C[3][3][8];
+  float kdiag;  // every diagonal entry of k0
 };
 
 inline ModalCoef2 pair_coef(const ModalCoef<float>& k) {
@@ -69,6 +70,7 @@ inline ModalCoef2 pair_coef(const ModalCoef<float>& k) {
       p.D[a][m] = make_float2(k.D[a][m], k.D[a][m]);
       for (int b = 0; b < 3; ++b) p.C[a][b][m] = make_float2(k.C[a][b][m], k.C[a][b][m]);
     }
+  p.kdiag = k.kdiag;
   return p;
 }
 
@@ -198,8 +200,10 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
                  const __grid_constant__ ModalCoef2 kc, const Epi epi0, const Red red0,
                  const int gx, const int gy, const DSel S, const int* __restrict__ done,
                  int* __restrict__ errflag) {
-  constexpr int NA = Epi::kAux;
+  constexpr int NA = epi_staged<Epi>();  // staged operand vectors
+  constexpr int DI = Epi::kDinvAux;      // >= 0: D^-1 formed from the moduli
   static_assert(NA <= 2, "at most two staged operand vectors");
+  static_assert(DI < 0 || DI == Epi::kAux - 1, "D^-1 is the last operand");
   constexpr int SF = pair_stage_floats(NA);
   pdl_start();
   const int design = S.id(blockIdx.z);
@@ -273,7 +277,8 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     long long oA = d.node(exA, ey, kb);
 
     // stage t -> registers: the top node plane (pairs A, B) and the element moduli
-    auto load_stage = [&](int t, float2(&top)[2][2][3], float2& E) {
+    // (DI) es: moduli of the 2 x 2 elements around the nodes (A, B) in the stage's layer
+    auto load_stage = [&](int t, float2(&top)[2][2][3], float2& E, float2& es) {
       const int g = gs + t;
       const int slot = g % kPairStages;
       mbar_wait_bounded(&bar[slot], (uint32_t)((g / kPairStages) & 1), errflag);
@@ -289,13 +294,19 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
           }
       const float* el = nd + kPNodeStride + ty * kPBoxX + lx;
       E = make_float2(el[0], el[32]);
+      es = make_float2(0.f, 0.f);
+      if (DI >= 0 && ty > 0) {  // owned nodes only: no read left of the box
+        const float* e0 = el - kPBoxX - 1;
+        if (tx > 0) es.x = (e0[0] + e0[1]) + (e0[kPBoxX] + e0[kPBoxX + 1]);
+        es.y = (e0[32] + e0[33]) + (e0[kPBoxX + 32] + e0[kPBoxX + 33]);
+      }
     };
     // one stage per layer: wait, read, compute, exchange, barrier, refill,
     // epilogue.  (Reading stage t+1 before the barrier, to overlap its latency
     // with the exchange, measured slower: it spills at the 128-register cap.)
     PairColumn col;
-    float2 top[2][2][3], E;
-    load_stage(0, top, E);
+    float2 top[2][2][3], E, es, es_prev;
+    load_stage(0, top, E, es_prev);
     pair_seed(col, top);
     __syncthreads();  // stage 0 read everywhere; the previous segment's exchange slots retired
     if (tid == 0 && kPairStages < nst) {
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
     }
 #pragma unroll 2
     for (int t = 1; t < nst; ++t) {
-      load_stage(t, top, E);
+      load_stage(t, top, E, es);
       const float2 nE = make_float2(-E.x, -E.y);
       float2 plane[3][4], ctr[3];
       pair_layer(col, top, E, nE, kc, plane, ctr);
@@ -352,12 +363,23 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
             av[q][0][c] = ap[q * kPAuxStride + c * (kPAuxY * kPBoxX)];
             av[q][1][c] = ap[q * kPAuxStride + c * (kPAuxY * kPBoxX) + 32];
           }
+        if constexpr (DI >= 0) {  // D^-1 of the masked operator, 1 where no stiffness
+          const float sa = es_prev.x + es.x, sb = es_prev.y + es.y;
+          const float da = sa > 0.f ? 1.0f / (kc.kdiag * sa) : 1.0f;
+          const float db = sb > 0.f ? 1.0f / (kc.kdiag * sb) : 1.0f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            av[DI][0][c] = da;
+            av[DI][1][c] = db;
+          }
+        }
         if (clean)
           part += epi.template finish<2>(ii, ey, ez, oo, own, res, cc, av, fd);
         else
           part += epi.template finish<2>(ii, ey, ez, oo, own, res, cc, av, d);
         oA += d.plane_stride();
       }
+      es_prev = es;
     }
     gs += nst;
     // the next segment's prologue refills every slot, this segment's last
@@ -391,7 +413,7 @@ template <class Epi>
 cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, const Dims& d,
                               const ModalCoef<float>& kc, const Epi& epi, const Red& red,
                               const int* done, int* errflag, cudaStream_t s, const Bat& bt) {
-  constexpr size_t smem = pair_smem(Epi::kAux);
+  constexpr size_t smem = pair_smem(epi_staged<Epi>());
   static bool attr = false;  // per instantiation; setting it twice is harmless
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(
@@ -401,7 +423,7 @@ cudaError_t launch_modal_pair(const CUtensorMap& xm, const CUtensorMap& em, cons
   }
   CUtensorMap am[2];
   std::memset(am, 0, sizeof(am));
-  for (int q = 0; q < Epi::kAux; ++q)
+  for (int q = 0; q < epi_staged<Epi>(); ++q)
     if (!pair_aux_map(epi.aux(q), d, bt, &am[q])) return cudaErrorInvalidValue;
   const int gx = (d.nx + kPairOwnX) / kPairOwnX, gy = (d.ny + kPairOwnY) / kPairOwnY;
   dim3 block(kPairTX, kPairTY, 1);

@@ -28,6 +28,7 @@ inline ModalCoef<Dw> dw_coef(const ModalCoef<double>& k) {
       c.D[a][m] = dw_from(k.D[a][m]);
       for (int b = 0; b < 3; ++b) c.C[a][b][m] = dw_from(k.C[a][b][m]);
     }
+  c.kdiag = dw_from(k.kdiag);
   c.form = k.form;
   return c;
 }

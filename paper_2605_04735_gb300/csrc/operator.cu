@@ -22,6 +22,7 @@ template <typename T, bool DOT>
 struct EpiApply {
   static constexpr bool kReduce = DOT;
   static constexpr int kAux = 0;
+  static constexpr int kDinvAux = -1;
   T* y;
   __device__ EpiApply shifted(long long off) const { return EpiApply{bshift(y, off)}; }
   __host__ __device__ const T* aux(int) const { return nullptr; }
@@ -49,6 +50,7 @@ template <typename T>
 struct EpiResid {
   static constexpr bool kReduce = true;
   static constexpr int kAux = 1;  // f
+  static constexpr int kDinvAux = -1;
   T* y;
   const T* f;
   __device__ EpiResid shifted(long long off) const {
@@ -199,6 +201,10 @@ bool build_modal_coef(const double* k0, ModalCoef<double>* out) {
   for (int r = 0; r < 24; ++r)
     for (int c = 0; c < 24; ++c)
       if (!used[r][c] && std::fabs(Kt[r][c]) > 1e-12 * scale) return false;
+  // the Jacobi diagonal is kdiag times the sum of the moduli around a node
+  out->kdiag = k0[0];
+  for (int a = 1; a < 24; ++a)
+    if (std::fabs(k0[a * 24 + a] - out->kdiag) > 1e-12 * std::fabs(out->kdiag)) return false;
   return true;
 }
 template cudaError_t launch_diag_inv<float>(float*, const float*, const Dims&, const K0<float>&,

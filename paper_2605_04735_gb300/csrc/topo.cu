@@ -1008,9 +1008,14 @@ static topo_status create_impl(int nx, int ny, int nz, int bc, int load, const t
   m->lam_max = k0_jacobi_bound(k);
   if (!build_modal_coef(k, &m->mcd)) return TOPO_ERR_INVALID;
   {
-    const double* src = &m->mcd.D[0][0];
-    float* dst = &m->mcf.D[0][0];
-    for (size_t t = 0; t < sizeof(m->mcd) / sizeof(double); ++t) dst[t] = (float)src[t];
+    m->mcf = ModalCoef<float>{};
+    for (int a = 0; a < 3; ++a)
+      for (int q = 0; q < 8; ++q) {
+        m->mcf.D[a][q] = (float)m->mcd.D[a][q];
+        for (int b = 0; b < 3; ++b) m->mcf.C[a][b][q] = (float)m->mcd.C[a][b][q];
+      }
+    m->mcf.kdiag = (float)m->mcd.kdiag;
+    m->mcf.form = m->mcd.form;
   }
   const long long ne = m->d.ecount;
   CKS(dalloc(m, &m->rho_in, (long long)nx * ny * nz));
