@@ -292,6 +292,10 @@ def main():
     ap.add_argument("--workload", default="mbb_96x32x32", choices=sorted(I.WORKLOADS))
     ap.add_argument("--batch", type=int, default=256,
                     help="independent designs solved concurrently per step")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="CG iterations between host convergence checks (0: the library's "
+                         "default); a batch compacts its launches to the live designs at "
+                         "each check")
     ap.add_argument("--groups", type=int, default=1,
                     help="mesh groups the batch is split into, each solved in lockstep by its "
                          "own host thread (their launches overlap on the GPU)")
@@ -336,6 +340,8 @@ def main():
     dc_dev = torch.empty((B, w.n_elem), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
+    if args.check_every > 0:
+        opts.check_every = args.check_every
     # one mesh group that solve_many runs as one batch (one launch per step
     # for all designs), or (--streams) independent meshes on their own streams
     batched = not args.streams and B > 1

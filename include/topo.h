@@ -127,7 +127,7 @@ typedef struct {
   int warm_start;    /* 1: start from the stored displacement, 0: from zero */
   int gmg_levels;    /* 0: as many 2:1 levels as the grid allows (coarsest <= ~3000 DOF) */
   int smooth_degree; /* Chebyshev smoother degree per pre/post smoothing (default 3) */
-  int check_every;   /* inner iterations between host convergence checks (default 16) */
+  int check_every;   /* inner iterations between host convergence checks (default 8) */
   int residual;      /* TOPO_RESIDUAL_*: arithmetic of the refinement residual f - K u of
                         TOPO_PREC_FP32 solves (default DWORD); FP64 solves use FP64 */
 } topo_solve_opts;

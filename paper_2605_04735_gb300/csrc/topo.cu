@@ -918,7 +918,7 @@ void topo_default_opts(topo_solve_opts* o) {
   o->warm_start = 0;
   o->gmg_levels = 0;
   o->smooth_degree = 3;
-  o->check_every = 16;
+  o->check_every = 8;
   o->residual = TOPO_RESIDUAL_DWORD;
 }
 
