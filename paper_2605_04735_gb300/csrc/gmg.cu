@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "gmg.h"
+#include "gmg_tail.h"
 #include "kernels.h"
 #include "modal2.cuh"
 #include "stencil.cuh"
@@ -620,6 +621,11 @@ cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, dou
       GCK(dmalloc(&L.x, L.nvec, &g.bytes, s, alloc));
     }
   }
+  {
+    std::vector<Dims> dims;
+    for (const GmgLevel& L : g.lv) dims.push_back(L.d);
+    g.tail_l0 = tail_first_level(dims, g.degree);
+  }
   GCK(dmalloc(&g.Ainv, (long long)g.nc * g.nc, &g.bytes, s, alloc));
   GCK(dmalloc(&g.side, 4LL * g.nc, &g.bytes, s, alloc));
   GCK(dmalloc(&g.bd, (long long)g.nc, &g.bytes, s, alloc));
@@ -714,8 +720,14 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   const int nl = (int)g.lv.size();
   auto B = [&](int l) { return l == 0 ? b0 : g.lv[l].b; };
   auto X = [&](int l) { return l == 0 ? x0 : g.lv[l].x; };
+  // Levels >= l_end run as one kernel per design (the tail) when several
+  // designs share the launch: one SM per design is then the better use of the
+  // GPU than a few-microsecond launch per coarse step.  A single design keeps
+  // the per-level kernels, which spread each level over many SMs.
+  const bool tail = g.tail_l0 > 0 && bt.nb > 1;
+  const int l_end = tail ? g.tail_l0 : nl - 1;
   // down
-  for (int l = 0; l < nl - 1; ++l) {
+  for (int l = 0; l < l_end; ++l) {
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
     GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
@@ -733,8 +745,28 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                    C.d, done, bt.sel()));
     *launches += 2;
   }
-  // coarsest
-  {
+  if (tail) {  // levels l_end .. coarsest in one kernel per design
+    TailPlan p{};
+    p.nt = nl - 1 - l_end;
+    p.degree = m;
+    p.inv_theta = cc.inv_theta;
+    for (int k = 1; k < m; ++k) {
+      p.c1[k] = cc.c1[k];
+      p.c2[k] = cc.c2[k];
+    }
+    p.kdiag = k0f.v[0];
+    p.nc = g.nc;
+    std::vector<Dims> dims;
+    for (const GmgLevel& L : g.lv) dims.push_back(L.d);
+    const size_t smem = tail_plan_smem(dims, l_end, p.off);
+    for (int t = 0; t <= p.nt; ++t) p.d[t] = g.lv[l_end + t].d;
+    for (int t = 0; t < p.nt; ++t) p.E[t] = g.lv[l_end + t].E;
+    p.b = g.lv[l_end].b;
+    p.x = g.lv[l_end].x;
+    p.Ainv = g.Ainv;
+    GCK(launch_vcycle_tail(p, smem, k0f, done, s, bt));
+    ++*launches;
+  } else {  // coarsest
     const GmgLevel& C = g.lv[nl - 1];
     const int nnc = (C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     GCK(launch_pdl(k_coarse_gather, dim3((nnc + kPT - 1) / kPT, bt.nb), dim3(kPT), 0, s,
@@ -745,7 +777,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     *launches += 2;
   }
   // up
-  for (int l = nl - 2; l >= 0; --l) {
+  for (int l = l_end - 1; l >= 0; --l) {
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);

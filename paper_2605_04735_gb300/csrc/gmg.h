@@ -41,6 +41,7 @@ struct Gmg {
   int gj_nb = 0;             // ... for this many designs
   long long gj_S = 0;        // ... at this design stride
   long long bytes = 0;
+  int tail_l0 = -1;          // levels tail_l0 .. coarsest run as one kernel per design (-1: none)
   bool ready = false;        // set up for the current densities
   bool arena = false;        // buffers come from a mesh group's arena (not freed here)
 };
