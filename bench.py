@@ -299,6 +299,8 @@ def main():
     ap.add_argument("--groups", type=int, default=1,
                     help="mesh groups the batch is split into, each solved in lockstep by its "
                          "own host thread (their launches overlap on the GPU)")
+    ap.add_argument("--smooth-degree", type=int, default=0,
+                    help="Chebyshev smoothing degree of the V-cycle (0: the library's default)")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--operator", type=int, default=0, choices=[0, 1, 2, 3],
@@ -342,6 +344,8 @@ def main():
     opts = topo.default_opts(precision=args.precision, precond=args.precond, rtol=1e-8)
     if args.check_every > 0:
         opts.check_every = args.check_every
+    if args.smooth_degree > 0:
+        opts.smooth_degree = args.smooth_degree
     # one mesh group that solve_many runs as one batch (one launch per step
     # for all designs), or (--streams) independent meshes on their own streams
     batched = not args.streams and B > 1

@@ -1,16 +1,17 @@
 // The coarse end of the multigrid V-cycle in one kernel per design.
 //
-// The levels from l0 down (grids of a few thousand nodes or fewer) are too
-// small to fill the GPU: each of their ~20 launches per V-cycle is a few
-// microseconds of latency for a few microseconds of work.  This kernel runs
-// them in one CTA per design, every vector of those levels in shared memory:
+// The levels from l0 down (at most kTailMaxNodes nodes each) are too small to
+// fill the GPU even for a batch of designs: each of their launches is a few
+// microseconds of latency for less work than that.  For batched V-cycles this
+// kernel runs them in one CTA per design, every vector of those levels in
+// shared memory:
 // on each level Chebyshev(Jacobi) pre-smoothing, restriction, the coarsest
 // solve by the FP64 explicit inverse, and on the way up prolongation and
 // post-smoothing — the same steps, coefficients and transfers as the
 // per-level kernels of gmg.cu, with CTA barriers between them.  The operator
-// is the node-centric gather with the dense k0 (576 FMAs per node: at these
-// sizes the FP32 pipe of one SM is not the bound), D^-1 = 1 / (kdiag * the
-// sum of the moduli around the node).
+// is the node-centric gather with the dense k0 (576 FMAs per node; k0 sits in
+// the constant bank as a kernel parameter), D^-1 = 1 / (kdiag * the sum of
+// the moduli around the node).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -368,11 +369,11 @@ __global__ void __launch_bounds__(kTailThreads)
   }
 }
 
-// Shared-memory plan of the tail from level l0: floats for k0, then per
-// smoothed level 5 node vectors and the dense moduli, then the coarsest
-// level's b and x and (8-byte aligned) its FP64 right-hand side.
+// Shared-memory plan of the tail from level l0: per smoothed level 5 node
+// vectors and the dense moduli, then the coarsest level's b and x and
+// (8-byte aligned) its FP64 right-hand side.
 size_t tail_plan_smem(const std::vector<Dims>& lv, int l0, int* offsets) {
-  size_t f = 576;
+  size_t f = 0;
   const int nl = (int)lv.size();
   for (int l = l0; l < nl; ++l) {
     if (offsets) offsets[l - l0] = (int)f;

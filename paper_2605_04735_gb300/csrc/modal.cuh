@@ -13,7 +13,8 @@
 // 24x24 product; the values are shifted by corner 0 first so that large rigid
 // displacements never meet in one FP32 sum.
 //
-// Work split (no atomics): a CTA is 32 x 8 threads; thread (tx, ty) owns the
+// Work split (no atomics): a CTA is kModalTX x kModalTY threads (32 x 8 by
+// default, see below); thread (tx, ty) owns the
 // element column (x0-1+tx, y0-1+ty, *) and marches up in z, one element
 // layer per step.  The transform is split into its x-y part (per node plane)
 // and its z part (per element): the x-y transform of a node plane is computed
@@ -24,8 +25,8 @@
 // to lane tx+1 by warp shuffle and the +y corner to thread row ty+1 through a
 // double-buffered shared-memory slot.  Thread (tx, ty) with tx, ty >= 1 then
 // holds the complete result of node (x0-1+tx, y0-1+ty, z): a CTA owns a
-// 31 x 7 tile of node columns, recomputing one halo element layer on its -x
-// and -y sides.
+// (kModalTX-1) x (kModalTY-1) tile of node columns, recomputing one halo
+// element layer on its -x and -y sides.
 #pragma once
 
 #include <cuda.h>
@@ -173,10 +174,25 @@ __device__ __forceinline__ T shfl_up1(T v) {
   return __shfl_up_sync(0xffffffffu, v, 1);
 }
 
+// Thread tile of the single-column kernels: kModalTX threads along x (a
+// divisor of 32: a warp then holds 32 / kModalTX thread rows, and the +x
+// shuffle from the previous row's last lane reaches only a halo thread, which
+// discards it) by kModalTY rows.  A tile owns (kModalTX - 1) x (kModalTY - 1)
+// node columns.
+#ifndef TOPO_MODAL_TX
+#define TOPO_MODAL_TX 16
+#endif
+#ifndef TOPO_MODAL_TY
+#define TOPO_MODAL_TY 12
+#endif
+constexpr int kModalTX = TOPO_MODAL_TX, kModalTY = TOPO_MODAL_TY;
+static_assert(32 % kModalTX == 0 && kModalTX >= 8, "x tile: 8, 16 or 32 threads");
+static_assert(kModalTX * kModalTY % 32 == 0 && kModalTX * kModalTY <= 512, "whole warps");
+
 // exchange a finished plane's corners with the neighbours: res = the sums at
 // the node (ex, ey) of the plane (includes the CTA barrier)
 template <typename T>
-__device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[32][3], int tx,
+__device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[kModalTX][3], int tx,
                                                int ty, T (&res)[3]) {
   T n0[3];
 #pragma unroll
@@ -194,7 +210,8 @@ __device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[
 // the exchange, then the epilogue on the owned node (ex, ey, ez), operands
 // read from global memory
 template <typename T, class Epi>
-__device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3], int tx, int ty,
+__device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[kModalTX][3], int tx,
+                                          int ty,
                                           int ex, int ey, int ez, bool emit, const T (&ctr)[3],
                                           const Dims& d, const Epi& epi) {
   T res[3];
@@ -202,21 +219,21 @@ __device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[32][3
   return emit ? epi_one(epi, ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
 }
 
-constexpr int kModalTX = 32, kModalTY = 8;
 constexpr int kModalOwnX = kModalTX - 1, kModalOwnY = kModalTY - 1;
 constexpr int kModalStages = 4;
-constexpr int kMBoxX = 40;               // >= 3 (alignment slack) + 33 columns
-constexpr int kMBoxNY = kModalTY + 1;    // node rows y0-1 .. y0+7
-constexpr int kMBoxEY = kModalTY;        // element rows y0-1 .. y0+6
+// node box columns: >= 3 (alignment slack) + kModalTX + 1, a multiple of 4
+constexpr int kMBoxX = kModalTX == 32 ? 40 : (kModalTX + 4 + 3) / 4 * 4;
+constexpr int kMBoxNY = kModalTY + 1;    // node rows y0-1 .. y0+kModalOwnY
+constexpr int kMBoxEY = kModalTY;        // element rows y0-1 .. y0+kModalOwnY-1
 constexpr int kMNode = 3 * kMBoxNY * kMBoxX;
 constexpr int kMElem = kMBoxEY * kMBoxX;
 constexpr uint32_t kMStageTx = (uint32_t)(kMNode + kMElem) * 4u;
 // stage layout (floats): node box, element box at a 128-byte boundary, then
-// the epilogue's operand planes (Epi::kAux boxes of 36 x 7 x 3 nodes: the
-// owned rows y0 .. y0+6 of the node plane the stage's epilogue writes)
+// the epilogue's operand planes (Epi::kAux boxes of kMAuxX x kModalOwnY x 3
+// nodes: the owned rows of the node plane the stage's epilogue writes)
 constexpr int kMElemOff = (kMNode + 31) / 32 * 32;
 constexpr int kMStageBase = (kMElemOff + kMElem + 31) / 32 * 32;
-constexpr int kMAuxX = 36;  // >= 3 (alignment slack) + 32 columns
+constexpr int kMAuxX = (kModalTX + 3 + 3) / 4 * 4;  // >= 3 (alignment slack) + kModalTX columns
 constexpr int kMAuxY = kModalOwnY;
 constexpr int kMAux = 3 * kMAuxY * kMAuxX;
 constexpr int kMAuxStride = (kMAux + 31) / 32 * 32;

@@ -68,6 +68,42 @@ def test_batch_matches_single_solves(topo, nx, ny, nz, bc, load, nb):
         assert _rel(res[0][0], ref) <= 1e-8
 
 
+@pytest.mark.parametrize("nx,ny,nz,degree,levels", [
+    (40, 12, 10, 1, 0),    # two smoothed levels in the one-kernel coarse end
+    (40, 12, 10, 3, 0),
+    (33, 9, 7, 6, 0),      # odd extents at every level
+    (96, 32, 32, 2, 0),
+    (40, 12, 10, 2, 3),    # three levels: one smoothed level and the coarsest in the kernel
+    (48, 12, 12, 2, 0),
+])
+def test_batch_coarse_levels_match_single_solves(topo, nx, ny, nz, degree, levels):
+    """Batched V-cycles run the levels of <= 1024 nodes in one kernel per
+    design; single designs run them level by level.  Same smoothing degree and
+    level count on both sides: the solves agree to the stopping tolerance and
+    take the same number of outer steps (inner counts may differ by the FP32
+    rounding of the two operator evaluations; convergence is checked after
+    every iteration so the counts are comparable)."""
+    opts = topo.default_opts(rtol=1e-10, smooth_degree=degree, gmg_levels=levels, check_every=1)
+    nb = 3
+    rhos = [I.density_cone_smoothed(nx, ny, nz, 70 + b) for b in range(nb)]
+    meshes = topo.create_batch(nb, nx, ny, nz, opts=opts)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_density(r)
+        infos = topo.solve_many(meshes, opts)
+        us = [m.displacement() for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    for b in range(nb):
+        u1, _, _, info1 = _alone(topo, nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM,
+                                 rhos[b], opts)
+        assert infos[b].status == 0 and infos[b].rel_residual <= 1e-10
+        assert infos[b].outer == info1.outer
+        assert abs(infos[b].iters - info1.iters) <= max(2, info1.iters // 10)
+        assert _rel(us[b], u1) <= 1e-8
+
+
 def test_batch_designs_converge_at_different_outer_steps(topo):
     """A solid design converges in fewer outer steps than near-binary void
     designs; it sits out the later steps and its result is unchanged."""
