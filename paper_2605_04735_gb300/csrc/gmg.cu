@@ -263,27 +263,33 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
        n += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     unflatten3(n, df.nx + 1, df.ny + 1, i, j, k);
-    // the 2 x 2 x 2 coarse nodes around (i, j, k) with their trilinear
-    // weights (1 and 0 on an even index, 1/2 and 1/2 on an odd one), the same
-    // arithmetic for every node: no divergent loop bounds
+    // trilinear interpolation: an even index sits on coarse node i/2 (weight
+    // 1), an odd one halfway between i/2 and i/2+1 (1/2 each; clamped to the
+    // last coarse node where the coarse grid rounded up).  Rows are read only
+    // where their weight is non-zero: the y-z parity is the same along a row.
     const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int i1 = min(i0 + 1, dc.nx), j1 = min(j0 + 1, dc.ny), k1 = min(k0 + 1, dc.nz);
-    const float wi[2] = {(i & 1) ? 0.5f : 1.0f, (i & 1) ? 0.5f : 0.0f};
-    const float wj[2] = {(j & 1) ? 0.5f : 1.0f, (j & 1) ? 0.5f : 0.0f};
-    const float wk[2] = {(k & 1) ? 0.5f : 1.0f, (k & 1) ? 0.5f : 0.0f};
-    const int ci[2] = {i0, i1}, cj[2] = {j0, j1}, ck[2] = {k0, k1};
+    const bool oi = i & 1, oj = j & 1, ok = k & 1;
+    const int di = min(i0 + 1, dc.nx) - i0;
+    const long long dy = (long long)(min(j0 + 1, dc.ny) - j0) * dc.row_stride();
+    const long long dz = (long long)(min(k0 + 1, dc.nz) - k0) * dc.plane_stride();
+    const long long cb = dc.node(i0, j0, k0);
+    const float wjk = (oj ? 0.5f : 1.0f) * (ok ? 0.5f : 1.0f);
     float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2)
+    for (int c2 = 0; c2 < 2; ++c2) {
+      if (c2 && !ok) break;
 #pragma unroll
-      for (int b2 = 0; b2 < 2; ++b2)
+      for (int b2 = 0; b2 < 2; ++b2) {
+        if (b2 && !oj) break;
+        const long long o = cb + (b2 ? dy : 0) + (c2 ? dz : 0);
 #pragma unroll
-        for (int a2 = 0; a2 < 2; ++a2) {
-          const long long o = dc.node(ci[a2], cj[b2], ck[c2]);
-          const float wt = wi[a2] * wj[b2] * wk[c2];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, xc[c * dc.comp + o], s[c]);
+        for (int c = 0; c < 3; ++c) {
+          const float* p = xc + c * dc.comp + o;
+          const float v = oi ? 0.5f * (p[0] + p[di]) : p[0];
+          s[c] = fmaf(wjk, v, s[c]);
         }
+      }
+    }
     const long long o = df.node(i, j, k);
 #pragma unroll
     for (int c = 0; c < 3; ++c)

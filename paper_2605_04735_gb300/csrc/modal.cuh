@@ -104,12 +104,15 @@ __device__ __forceinline__ void modal_seed(ModalColumn<T>& col, const T (&raw)[2
 
 // One element layer: top node plane raw values in, the finished result of
 // node plane ez (x-y corners [c][dx + 2 dy], before the neighbour exchange)
-// out.  ctr receives the raw displacement of node (ex, ey, ez).
+// out.  ctr receives the raw displacement of node (ex, ey, ez).  The modal
+// product runs on the unscaled displacement (E multiplies the two z faces of
+// the result), so `dot` is the element's strain energy
+// (u_e - u_0)^T k0 (u_e - u_0) itself.
 template <typename T>
 __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[2][2][3], T E,
                                            const ModalCoef<T>& kc, T (&plane)[3][4],
                                            T (&ctr)[3], T* dot = nullptr) {
-  T uh[3][8];
+  T uh[3][8];  // [c][0], the rigid mode, is never formed (no K~ entry touches it)
   T txy[3][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -120,14 +123,13 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       txy[c][q] = v[q];
-      uh[c][q] = (col.bxy[c][q] + v[q]) * E;      // z mode 0
-      uh[c][q + 4] = (col.bxy[c][q] - v[q]) * E;  // z mode 1
+      if (q > 0) uh[c][q] = col.bxy[c][q] + v[q];  // z mode 0
+      uh[c][q + 4] = col.bxy[c][q] - v[q];         // z mode 1
     }
   }
   T yh[3][8];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    yh[p][0] = T(0);
 #pragma unroll
     for (int m = 1; m < 8; ++m) {
       T acc = kc.D[p][m] * uh[p][m];
@@ -140,7 +142,7 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
       yh[p][m] = acc;
     }
   }
-  if (dot) {  // uh . K~ uh = E^2 (u_e - u_0)^T k0 (u_e - u_0): the element's energy times E^2
+  if (dot) {  // uh . K~ uh = (u_e - u_0)^T k0 (u_e - u_0)
     T e = T(0);
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -148,22 +150,27 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
       for (int m = 1; m < 8; ++m) e = fmadd(uh[p][m], yh[p][m], e);
     *dot = e;
   }
+  const T nE = -E;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
+    // bottom face E (yh_q + yh_q+4) plus the previous element's top face;
+    // this element's top face E (yh_q - yh_q+4) is carried up (yh_0 = 0)
     T w[4];
+    w[0] = fmadd(E, yh[c][4], col.carry[c][0]);
+    col.carry[c][0] = nE * yh[c][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      w[q] = yh[c][q] + yh[c][q + 4] + col.carry[c][q];  // bottom face + previous top face
-      col.carry[c][q] = yh[c][q] - yh[c][q + 4];         // this element's top face
+    for (int q = 1; q < 4; ++q) {
+      w[q] = fmadd(E, yh[c][q] + yh[c][q + 4], col.carry[c][q]);
+      col.carry[c][q] = E * (yh[c][q] - yh[c][q + 4]);
     }
     fwht4(w);
 #pragma unroll
     for (int q = 0; q < 4; ++q) plane[c][q] = w[q];
     // the top plane becomes the next bottom plane, re-referenced to its corner 0
     const T nref = top[0][0][c];
+    col.bxy[c][0] = fmadd(T(4), col.ref[c] - nref, txy[c][0]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) col.bxy[c][q] = txy[c][q];
-    col.bxy[c][0] += T(4) * (col.ref[c] - nref);
+    for (int q = 1; q < 4; ++q) col.bxy[c][q] = txy[c][q];
     col.ref[c] = nref;
   }
 }
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     // element energies (u_e - u_0)^T k0 (u_e - u_0), written by the CTA and
     // z-chunk that own the element (the others compute it as halo / warm-up)
     if (energy && tx > 0 && ty > 0 && ex < d.nx && ey < d.ny && ez >= kb && ez < d.nz)
-      energy[d.elem(ex, ey, ez)] = Ee != T(0) ? dot / (Ee * Ee) : T(0);
+      energy[d.elem(ex, ey, ez)] = Ee != T(0) ? dot : T(0);
     part += modal_finish<T, Epi>(plane, xch[(ez - kb + 1) & 1], tx, ty, ex, ey, ez,
                                  own && ez >= kb, ctr, d, epi);
   }
@@ -458,7 +465,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 
 // z planes per CTA for the modal kernels: a few waves over 152 SMs counting
 // all `nb` designs of a launch, a one-layer warm-up below ~10%, and no more
-// CTAs per design than partial-sum slots
+// CTAs per design than partial-sum slots; a launch of many designs marches
+// whole columns (up to 64 planes), and the chunks of a column are equal
 // (a floor of 8 or 16 planes measured 1-5 % more solves/s with 64 designs in
 // flight on 96x32x32 but 57-147 % more latency for one design: 4 it is)
 inline int modal_zchunk(const Dims& d, int nb = 1) {
@@ -467,9 +475,11 @@ inline int modal_zchunk(const Dims& d, int nb = 1) {
   const int planes = d.nz + 1;
   int z = (int)((xy * planes * nb) / (152 * 2 * 4));
   if (z < 4) z = 4;
-  if (z > 32) z = 32;
+  if (z > 64) z = 64;
   while (xy * ((planes + z - 1) / z) > kMaxPartials) ++z;
-  return z;
+  // equal chunks: each costs one warm-up layer, a short last one more than its share
+  const int zc = (planes + z - 1) / z;
+  return (planes + zc - 1) / zc;
 }
 
 bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
