@@ -39,7 +39,7 @@ inline int grid1d(long long n, int nb = 1) {
 __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
                             float* __restrict__ d0, float* __restrict__ x,
                             const float* __restrict__ dinv, long long n4, float inv_theta,
-                            const int* __restrict__ done, const DSel S) {
+                            int d_only, const int* __restrict__ done, const DSel S) {
   pdl_start();
   const long long off = S.off(blockIdx.y);
   done = bshift(done, off);
@@ -58,9 +58,11 @@ __global__ void k_cheb_init(const float* __restrict__ b, float* __restrict__ r,
     o.y = dv.y * bv.y * inv_theta;
     o.z = dv.z * bv.z * inv_theta;
     o.w = dv.w * bv.w * inv_theta;
-    reinterpret_cast<float4*>(r)[q] = bv;
     reinterpret_cast<float4*>(d0)[q] = o;
-    reinterpret_cast<float4*>(x)[q] = o;
+    if (!d_only) {
+      reinterpret_cast<float4*>(r)[q] = bv;
+      reinterpret_cast<float4*>(x)[q] = o;
+    }
   }
 }
 
@@ -88,19 +90,23 @@ __global__ void k_axpy1(float* __restrict__ x, const float* __restrict__ d, long
 // d_k = c1 d_{k-1} + c2 D^-1 r; x += d_k (+ d_{k-1} when it was not yet added)
 struct EpiChebStep {
   static constexpr bool kReduce = false;
-  static constexpr int kAux = 2;  // r, D^-1
+  static constexpr int kAux = 2;  // r (read from rin), D^-1
   static constexpr int kDinvAux = 1;
+  // how the step's direction reaches x: x += d_q; x += d_{q-1} + d_q (the
+  // previous step did not add its own); x = d_{q-1} + d_q (x not yet set)
+  enum : int { kXAdd = 0, kXAddPrev = 1, kXStore = 2 };
   float* r;
+  const float* rin;  // the residual before the step (r itself, or b on the first step)
   float* dn;
   float* x;
   const float* dinv;
   float c1, c2;
-  int add_prev;
+  int xmode;
   __device__ EpiChebStep shifted(long long off) const {
-    return EpiChebStep{bshift(r, off), bshift(dn, off), bshift(x, off), bshift(dinv, off),
-                       c1, c2, add_prev};
+    return EpiChebStep{bshift(r, off), bshift(rin, off), bshift(dn, off), bshift(x, off),
+                       bshift(dinv, off), c1, c2, xmode};
   }
-  __host__ __device__ const float* aux(int q) const { return q == 0 ? r : dinv; }
+  __host__ __device__ const float* aux(int q) const { return q == 0 ? rin : dinv; }
   template <int N, class DD>
   __device__ __forceinline__ float finish(const int (&i)[N], int j, int k,
                                           const long long (&o)[N], const bool (&own)[N],
@@ -117,7 +123,10 @@ struct EpiChebStep {
           const float dd = fmaf(c1, ctr[n][c], c2 * av[1][n][c] * rn);
           r[oc] = rn;
           dn[oc] = dd;
-          red_add(x + oc, add_prev ? (dd + ctr[n][c]) : dd);
+          if (xmode == kXStore)
+            x[oc] = dd + ctr[n][c];
+          else
+            red_add(x + oc, xmode == kXAddPrev ? (dd + ctr[n][c]) : dd);
         }
     return 0.0f;
   }
@@ -736,11 +745,14 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   for (int l = 0; l < l_end; ++l) {
     GmgLevel& L = g.lv[l];
     const long long n4 = L.nvec / 4;
+    // d0 = D^-1 b / theta; with further steps the first one reads b as its
+    // residual and sets x = d0 + d1, so r = b and x = d0 are not written here
     GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
-                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, done, bt.sel()));
+                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, m > 1 ? 1 : 0, done, bt.sel()));
     ++*launches;
     for (int k = 1; k < m; ++k) {
-      EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], 0};
+      EpiChebStep ep{L.r, k == 1 ? B(l) : L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
+                     k == 1 ? EpiChebStep::kXStore : EpiChebStep::kXAdd};
       GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
       ++*launches;
     }
@@ -793,7 +805,8 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
     for (int k = 1; k < m; ++k) {
-      EpiChebStep ep{L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
+      EpiChebStep ep{L.r, L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
+                     k == 1 ? EpiChebStep::kXAddPrev : EpiChebStep::kXAdd};
       GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
       ++*launches;
     }
