@@ -84,6 +84,13 @@ struct Dims {
   }
 };
 
+// A view of Dims for a region that holds no fixed DOF: the epilogues skip
+// their support test.
+struct FreeDims {
+  long long comp;
+  __device__ __forceinline__ bool fixed(int, int, int, int) const { return false; }
+};
+
 // Layout of a grid of nx*ny*nz elements (pitches padded to 4 entries).
 inline Dims make_dims(int nx, int ny, int nz, int bc, int pin_j) {
   Dims d{};

@@ -215,15 +215,17 @@ __device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[
 }
 
 // the exchange, then the epilogue on the owned node (ex, ey, ez), operands
-// read from global memory
+// read from global memory; `clean`: the tile holds no fixed DOF (no support test)
 template <typename T, class Epi>
 __device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[kModalTX][3], int tx,
-                                          int ty,
-                                          int ex, int ey, int ez, bool emit, const T (&ctr)[3],
-                                          const Dims& d, const Epi& epi) {
+                                          int ty, int ex, int ey, int ez, bool emit, bool clean,
+                                          const T (&ctr)[3], const Dims& d, const Epi& epi) {
   T res[3];
   modal_exchange<T>(plane, xch, tx, ty, res);
-  return emit ? epi_one(epi, ex, ey, ez, d.node(ex, ey, ez), res, ctr, d) : T(0);
+  if (!emit) return T(0);
+  const long long o = d.node(ex, ey, ez);
+  return clean ? epi_one(epi, ex, ey, ez, o, res, ctr, FreeDims{d.comp})
+               : epi_one(epi, ex, ey, ez, o, res, ctr, d);
 }
 
 constexpr int kModalOwnX = kModalTX - 1, kModalOwnY = kModalTY - 1;
@@ -324,6 +326,9 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   if (tid == 0)
     for (int t = 0; t < kModalStages && t < nst; ++t) issue(t);
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
+  // tiles without any fixed DOF run the epilogue without the per-DOF support test
+  const bool clean = !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
+  const FreeDims fd{d.comp};
   ModalColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   float es_prev = 0.f;  // (DI) moduli of the 2 x 2 elements below node (ex, ey), layer before
@@ -386,7 +391,10 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
         for (int c = 0; c < 3; ++c) av[DI][0][c] = dv;
       }
-      part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
+      if (clean)
+        part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, fd);
+      else
+        part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
     }
     es_prev = es;
   }
@@ -422,6 +430,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   const int kb = chunk * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
+  const bool clean = !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
   auto node_val = [&](int i, int j, int k, int c) -> T {
     if (i > d.nx + 1 || j > d.ny + 1 || k > d.nz + 1) return T(0);  // beyond the ghost ring
     return __ldg(x + c * d.comp + d.node(i, j, k));
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     if (energy && tx > 0 && ty > 0 && ex < d.nx && ey < d.ny && ez >= kb && ez < d.nz)
       energy[d.elem(ex, ey, ez)] = Ee != T(0) ? dot : T(0);
     part += modal_finish<T, Epi>(plane, xch[(ez - kb + 1) & 1], tx, ty, ex, ey, ez,
-                                 own && ez >= kb, ctr, d, epi);
+                                 own && ez >= kb, clean, ctr, d, epi);
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};

@@ -149,13 +149,6 @@ __device__ __forceinline__ void pair_layer(PairColumn& col, const float2 (&top)[
   }
 }
 
-// A view of Dims for a region that holds no fixed DOF: the epilogues skip
-// their support test.
-struct FreeDims {
-  long long comp;
-  __device__ __forceinline__ bool fixed(int, int, int, int) const { return false; }
-};
-
 constexpr int kPairTX = 32, kPairTY = 8;
 constexpr int kPairOwnX = 2 * kPairTX - 1, kPairOwnY = kPairTY - 1;
 constexpr int kPairStages = 4;

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   const int kb = chunk * zchunk;
   const int ke = min(kb + zchunk, d.nz + 1);
   const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
+  const bool clean = !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
   auto node_val = [&](int i, int j, int k, int c) -> Dw {
     if (i > d.nx + 1 || j > d.ny + 1 || k > d.nz + 1) return Dw(0.0f);  // beyond the ghosts
     const long long o = c * d.comp + d.node(i, j, k);
@@ -90,7 +91,9 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     if (own && ez >= kb) {
       const double acc[3] = {dw_to(res[0]), dw_to(res[1]), dw_to(res[2])};
       const double cen[3] = {dw_to(ctr[0]), dw_to(ctr[1]), dw_to(ctr[2])};
-      part += epi_one(epi, ex, ey, ez, d.node(ex, ey, ez), acc, cen, d);
+      const long long o = d.node(ex, ey, ez);
+      part += clean ? epi_one(epi, ex, ey, ez, o, acc, cen, FreeDims{d.comp})
+                    : epi_one(epi, ex, ey, ez, o, acc, cen, d);
     }
   }
   if (Epi::kReduce) {

@@ -15,8 +15,9 @@
         `iters` SIMP iterations (solve, sensitivity, filter, OC update).
     python -m paper_2605_04735_gb300.profile_run batch <workload> [designs]
         one mesh group of `designs` seeded designs (default 16) solved in
-        lockstep twice (a warm-up and the captured step), compliance and
-        sensitivities included: the launch list of a batched step.
+        lockstep twice (a warm-up and the captured step) through the batched
+        entry points (densities, solve, compliances, sensitivities): the
+        launch list of a batched step.
 
 Workloads are the seeded recipes of `inputs.WORKLOADS`; nothing is read
 from disk.  Each command prints one line starting with "ok".
@@ -45,14 +46,14 @@ def main(argv):
         rhos = [I.dataclasses.replace(w, seed=w.seed + b).density() for b in range(n)]
         opts = topo.default_opts(rtol=1e-8)
         meshes = topo.create_batch(n, w.nx, w.ny, w.nz, w.bc, w.load, stream=s, opts=opts)
+        rho_dev = torch.from_numpy(np.stack(rhos)).cuda()
+        dc_dev = torch.empty((n, w.nx * w.ny * w.nz), dtype=torch.float64, device="cuda")
         try:
-            for _ in range(2):
-                for m, r in zip(meshes, rhos):
-                    m.set_density(r)
+            for _ in range(2):  # the batched entry points, as the benchmark's step
+                topo.set_density_many(meshes, rho_dev)
                 infos = topo.solve_many(meshes, opts)
-                for m in meshes:
-                    m.compliance()
-                    m.sensitivity()
+                topo.compliance_many(meshes)
+                topo.sensitivity_many(meshes, dc_dev)
             torch.cuda.synchronize()
         finally:
             for m in meshes:
