@@ -164,6 +164,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines: list[str] = []
+        self.first = threading.Event()
 
     def __enter__(self):
         try:
@@ -173,6 +174,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # the sampler's start-up (driver queries) is over before the
+            # caller's timed region begins: it measured up to ~130 ms of
+            # stalled launches when it overlapped the first timed step
+            self.first.wait(timeout=3.0)
         except OSError:
             self.proc = None
         return self
@@ -180,6 +185,8 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
+        self.first.set()
 
     def __exit__(self, *a):
         if self.proc:
@@ -408,11 +415,11 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     recs = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local) as clk:  # sampling from before the barrier to after the sync
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.fill_(float(k))  # evict the previous step's data from L2
             ev[k][0].record(stream)
@@ -420,7 +427,7 @@ def main():
             ev[k][1].record(stream)
             recs.extend((i.iters, i.outer, i.rel_residual, c) for i, c in zip(infos, cs))
         torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
+        wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])

@@ -407,8 +407,13 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 
 // Plain-load variant (FP64, and FP32 grids too small for the TMA boxes):
 // same work split, inputs read with bounds checks from the ghosted arrays.
+// The FP64 form asks for registers that leave TOPO_PLAIN64_MINB CTAs per SM
+// (its FP64 pipe needs warps to hide latency across the per-plane barriers).
+#ifndef TOPO_PLAIN64_MINB
+#define TOPO_PLAIN64_MINB 2
+#endif
 template <typename T, class Epi>
-__global__ void __launch_bounds__(kModalTX* kModalTY)
+__global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAIN64_MINB : 1)
     k_modal_plain(const T* __restrict__ x, const T* __restrict__ E, const Dims d,
                   const __grid_constant__ ModalCoef<T> kc, const Epi epi0, const Red red0,
                   const int zchunk, const int zc, const DSel S,

@@ -34,8 +34,11 @@ inline ModalCoef<Dw> dw_coef(const ModalCoef<double>& k) {
 }
 
 // Grid and z-chunks as k_modal_plain; Epi runs on FP64 values.
+#ifndef TOPO_DW_MINB
+#define TOPO_DW_MINB 2
+#endif
 template <class Epi>
-__global__ void __launch_bounds__(kModalTX* kModalTY)
+__global__ void __launch_bounds__(kModalTX* kModalTY, TOPO_DW_MINB)
     k_modal_dw(const float* __restrict__ xh, const float* __restrict__ xl,
                const double* __restrict__ E, const Dims d,
                const __grid_constant__ ModalCoef<Dw> kc, const Epi epi0, const Red red0,
