@@ -539,6 +539,7 @@ def main():
                    "l2": "flushed between steps (256 MB write)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "batch_step_p50": float(np.percentile(step_ms, 50)),
+                       "batch_steps_ms": [round(float(t), 3) for t in step_ms],
                        "what": "one design alone: density, solve, compliance, sensitivities"},
         "solve": {"iters_mean": float(np.mean([r[0] for r in recs])),
                   "outer_mean": float(np.mean([r[1] for r in recs])),

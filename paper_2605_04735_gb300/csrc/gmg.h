@@ -31,7 +31,7 @@ struct Gmg {
   std::vector<GmgLevel> lv;
   int degree = 3;            // Chebyshev degree per pre/post smoothing
   double lam_max = 0.0;      // bound on lambda_max(D^-1 A) (from k0)
-  double lam_ratio = 10.0;   // smoothing interval [lam_max / lam_ratio, lam_max]
+  double lam_ratio = 15.0;   // smoothing interval [lam_max / lam_ratio, lam_max]
   // coarsest level: explicit inverse
   int nc = 0;                // dense size (3 * nodes of the coarsest grid)
   double* Ainv = nullptr;    // nc * nc
