@@ -306,6 +306,9 @@ def main():
     ap.add_argument("--groups", type=int, default=1,
                     help="mesh groups the batch is split into, each solved in lockstep by its "
                          "own host thread (their launches overlap on the GPU)")
+    ap.add_argument("--inner-rtol", type=float, default=0.0,
+                    help="relative residual reduction of each inner FP32 solve (0: the "
+                         "library's default)")
     ap.add_argument("--smooth-degree", type=int, default=0,
                     help="Chebyshev smoothing degree of the V-cycle (0: the library's default)")
     ap.add_argument("--precision", type=int, default=1)
@@ -353,6 +356,8 @@ def main():
         opts.check_every = args.check_every
     if args.smooth_degree > 0:
         opts.smooth_degree = args.smooth_degree
+    if args.inner_rtol > 0:
+        opts.inner_rtol = args.inner_rtol
     # one mesh group that solve_many runs as one batch (one launch per step
     # for all designs), or (--streams) independent meshes on their own streams
     batched = not args.streams and B > 1
