@@ -13,7 +13,7 @@
 // 24x24 product; the values are shifted by corner 0 first so that large rigid
 // displacements never meet in one FP32 sum.
 //
-// Work split (no atomics): a CTA is kModalTX x kModalTY threads (32 x 8 by
+// Work split (no atomics): a CTA is kModalTX x kModalTY threads (16 x 12 by
 // default, see below); thread (tx, ty) owns the
 // element column (x0-1+tx, y0-1+ty, *) and marches up in z, one element
 // layer per step.  The transform is split into its x-y part (per node plane)
@@ -26,7 +26,9 @@
 // double-buffered shared-memory slot.  Thread (tx, ty) with tx, ty >= 1 then
 // holds the complete result of node (x0-1+tx, y0-1+ty, z): a CTA owns a
 // (kModalTX-1) x (kModalTY-1) tile of node columns, recomputing one halo
-// element layer on its -x and -y sides.
+// element layer on its -x and -y sides.  The K~ product runs on the
+// unscaled displacement; E multiplies the element's two z faces of the
+// result.
 #pragma once
 
 #include <cuda.h>
