@@ -334,16 +334,16 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   ModalColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   float es_prev = 0.f;  // (DI) moduli of the 2 x 2 elements below node (ex, ey), layer before
-  for (int t = 0; t < nst; ++t) {
-    const int slot = t % kModalStages;
-    mbar_wait_bounded(&bar[slot], (uint32_t)((t / kModalStages) & 1), errflag);
-    const float* nd = stg + slot * SF;
-    float es = 0.f;  // (DI) moduli of the 2 x 2 elements around (ex, ey) in this stage's layer
+  // stage (slot, phase) -> registers: the top node plane, the element
+  // modulus and (DI) the moduli of the 2 x 2 elements around (ex, ey)
+  auto read_stage = [&](int r, uint32_t ph, float(&top)[2][2][3], float& E, float& es) {
+    mbar_wait_bounded(&bar[r], ph, errflag);
+    const float* nd = stg + r * SF;
+    es = 0.f;
     if (DI >= 0 && own) {
       const float* e0 = nd + kMElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
       es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
     }
-    float top[2][2][3];  // [dy][dx][c]
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -351,17 +351,25 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           top[dy][dx][c] = nd[c * (kMBoxNY * kMBoxX) + (ty + dy) * kMBoxX + ox + tx + dx];
-    const float E = nd[kMElemOff + ty * kMBoxX + ox + tx];
-    if (t == 0) {  // the first node plane only seeds the march
-      __syncthreads();
-      if (tid == 0 && kModalStages < nst) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(kModalStages);
-      }
-      modal_seed<float>(col, top);
-      es_prev = es;
-      continue;
+    E = nd[kMElemOff + ty * kMBoxX + ox + tx];
+  };
+  {  // the first node plane only seeds the march
+    float top[2][2][3], E;
+    read_stage(0, 0u, top, E, es_prev);
+    __syncthreads();
+    if (tid == 0 && kModalStages < nst) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(kModalStages);
     }
+    modal_seed<float>(col, top);
+  }
+  const long long o_col = d.node(ex, ey, 0), ps = d.plane_stride();  // node (ex, ey, ez): + ez ps
+  int rs = 1;  // stage t's ring slot t % kModalStages, and its mbarrier phase
+  uint32_t phase = 0u;
+  for (int t = 1; t < nst; ++t) {
+    const float* nd = stg + rs * SF;
+    float top[2][2][3], E, es;
+    read_stage(rs, phase, top, E, es);
     float plane[3][4], ctr[3];
     modal_layer<float>(col, top, E, kc, plane, ctr);
     const int ez = kb - 2 + t;
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     }
     if (own && t >= 2) {
       const int ii[1] = {ex};
-      const long long oo[1] = {d.node(ex, ey, ez)};
+      const long long oo[1] = {o_col + (long long)ez * ps};
       const bool ow[1] = {true};
       const float rr[1][3] = {{res[0], res[1], res[2]}};
       const float cc[1][3] = {{ctr[0], ctr[1], ctr[2]}};
@@ -399,6 +407,10 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
         part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
     }
     es_prev = es;
+    if (++rs == kModalStages) {
+      rs = 0;
+      phase ^= 1u;
+    }
   }
   if (Epi::kReduce) {
     double v[1] = {(double)part};
