@@ -132,6 +132,56 @@ struct EpiChebStep {
   }
 };
 
+// The last post-smoothing step of the finest level with the CG's r.z fused:
+// z = x + d_q (+ d_{q-1}) is stored (not added: x is read here, one owner
+// per entry), neither r nor d is (nothing reads them after the V-cycle),
+// and the per-thread partial of b . z (b: the V-cycle's right-hand side,
+// the CG residual) goes to the launch's reduction.
+struct EpiChebStepDot {
+  static constexpr bool kReduce = true;
+  static constexpr int kAux = 2;  // r, D^-1
+  static constexpr int kDinvAux = 1;
+  const float* r;
+  float* x;
+  const float* b;
+  const float* dinv;
+  float c1, c2;
+  int add_prev;
+  __device__ EpiChebStepDot shifted(long long off) const {
+    return EpiChebStepDot{bshift(r, off), bshift(x, off), bshift(b, off), bshift(dinv, off), c1,
+                          c2, add_prev};
+  }
+  __host__ __device__ const float* aux(int q) const { return q == 0 ? r : dinv; }
+  template <int N, class DD>
+  __device__ __forceinline__ float finish(const int (&i)[N], int j, int k,
+                                          const long long (&o)[N], const bool (&own)[N],
+                                          const float (&acc)[N][3], const float (&ctr)[N][3],
+                                          const float (&av)[2][N][3], const DD& d) const {
+    float part = 0.0f;
+#pragma unroll
+    for (int n = 0; n < N; ++n)
+      if (own[n]) {
+        float xo[3], bo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {  // both loads before the stores
+          xo[c] = x[c * d.comp + o[n]];
+          bo[c] = b[c * d.comp + o[n]];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long oc = c * d.comp + o[n];
+          const float Ad = d.fixed(c, i[n], j, k) ? 0.0f : acc[n][c];
+          const float rn = av[0][n][c] - Ad;
+          const float dd = fmaf(c1, ctr[n][c], c2 * av[1][n][c] * rn);
+          const float z = xo[c] + (add_prev ? (dd + ctr[n][c]) : dd);
+          x[oc] = z;
+          part = fmaf(bo[c], z, part);
+        }
+      }
+    return part;
+  }
+};
+
 // r -= A d (the residual after pre-smoothing)
 struct EpiChebLast {
   static constexpr bool kReduce = false;
@@ -720,16 +770,15 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 template <class Epi>
 cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
                      const ModalCoef<float>* mcf, const Epi& ep, const int* done, int* errflag,
-                     cudaStream_t s, const Bat& bt) {
-  Red nored{};
-  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, nored, done, errflag, s, bt);
+                     cudaStream_t s, const Bat& bt, const Red& red = Red{}) {
+  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, red, done, errflag, s, bt);
   if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
-  return launch_stencil<float>(x, L.E, L.d, k0f, ep, nored, done, errflag, s);
+  return launch_stencil<float>(x, L.E, L.d, k0f, ep, red, done, errflag, s);
 }
 
 cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
-                       cudaStream_t s, long long* launches, const Bat& bt) {
+                       cudaStream_t s, long long* launches, const Bat& bt, const Red* zdot) {
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
@@ -795,6 +844,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     *launches += 2;
   }
   // up
+  bool fused = false;  // b . x reduced by the last finest-level step
   for (int l = l_end - 1; l >= 0; --l) {
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
@@ -805,9 +855,15 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;
     for (int k = 1; k < m; ++k) {
-      EpiChebStep ep{L.r, L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
-                     k == 1 ? EpiChebStep::kXAddPrev : EpiChebStep::kXAdd};
-      GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
+      if (l == 0 && zdot && k == m - 1) {  // the V-cycle's last step, with b . z
+        EpiChebStepDot ep{L.r, X(0), b0, L.dinv, cc.c1[k], cc.c2[k], k == 1 ? 1 : 0};
+        GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt, *zdot));
+        fused = true;
+      } else {
+        EpiChebStep ep{L.r, L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
+                       k == 1 ? EpiChebStep::kXAddPrev : EpiChebStep::kXAdd};
+        GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
+      }
       ++*launches;
     }
     if (m == 1) {
@@ -815,6 +871,10 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                      L.dv[0], L.nvec / 4, done, bt.sel()));
       ++*launches;
     }
+  }
+  if (zdot && !fused) {  // no finest-level smoothing step to fuse the product into
+    GCK(launch_dot<float>(b0, x0, g.lv[0].nvec, *zdot, s, bt));
+    ++*launches;
   }
   return cudaSuccess;
 }

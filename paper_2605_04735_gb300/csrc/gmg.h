@@ -68,9 +68,12 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 // x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
 // when *done is set.
 // mcf != nullptr: smoother passes use the modal operator kernel
+// zdot (optional): the reduction b . x of the result (the CG's r . z), fused
+// into the finest level's last smoothing step
 cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
-                       cudaStream_t s, long long* launches, const Bat& bt = Bat{});
+                       cudaStream_t s, long long* launches, const Bat& bt = Bat{},
+                       const Red* zdot = nullptr);
 void gmg_free(Gmg& g);
 // lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
 double k0_jacobi_bound(const double* k0);

@@ -378,8 +378,11 @@ topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
       default:
         LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
                                        red_of(m, FIN_RR_ONLY), false, s));
-        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches));
-        LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_RZ_BETA), s));
+        {  // z = V(r), with r . z (beta) fused into the V-cycle's last smoothing step
+          const Red zr = red_of(m, FIN_RZ_BETA);
+          CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s,
+                        &m->launches, Bat{}, &zr));
+        }
         LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
         break;
     }
@@ -540,8 +543,11 @@ topo_status enqueue_inner_start(SolveTask& t, double rtol, int max_iter) {
     } else {
       LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
                                    red_of(m, FIN_INIT, rtol * rtol), false, s));
-      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches));
-      LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s));
+      {
+        const Red zr = red_of(m, FIN_SET_RZ);
+        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s,
+                      &m->launches, Bat{}, &zr));
+      }
       LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
     }
   }
@@ -1592,8 +1598,11 @@ topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile, const Bat
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
     LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
                                    red_of(m, FIN_RR_ONLY), false, s, bt));
-    CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
-    LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_RZ_BETA), s, bt));
+    {  // z = V(r), with r . z (beta) fused into the V-cycle's last smoothing step
+      const Red zr = red_of(m, FIN_RZ_BETA);
+      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches,
+                    bt, &zr));
+    }
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
   }
   return TOPO_OK;
@@ -1768,8 +1777,11 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s, bt));
     LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
                                  red_of(m, FIN_INIT, -1.0), false, s, bt));
-    CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches, bt));
-    LK(m, launch_dot<float>(m->r32, m->z32, m->nvec, red_of(m, FIN_SET_RZ), s, bt));
+    {
+      const Red zr = red_of(m, FIN_SET_RZ);
+      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches,
+                    bt, &zr));
+    }
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
     std::vector<int> before(nb, -1), at(nb, 0);
     std::vector<char> iterating(running);  // designs not done (first chunk: taking part)
