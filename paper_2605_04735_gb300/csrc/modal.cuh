@@ -234,35 +234,42 @@ constexpr int kModalOwnX = kModalTX - 1, kModalOwnY = kModalTY - 1;
 constexpr int kModalStages = 4;
 // node box columns: >= 3 (alignment slack) + kModalTX + 1, a multiple of 4
 constexpr int kMBoxX = kModalTX == 32 ? 40 : (kModalTX + 4 + 3) / 4 * 4;
-constexpr int kMBoxNY = kModalTY + 1;    // node rows y0-1 .. y0+kModalOwnY
-constexpr int kMBoxEY = kModalTY;        // element rows y0-1 .. y0+kModalOwnY-1
-constexpr int kMNode = 3 * kMBoxNY * kMBoxX;
-constexpr int kMElem = kMBoxEY * kMBoxX;
-constexpr uint32_t kMStageTx = (uint32_t)(kMNode + kMElem) * 4u;
-// stage layout (floats): node box, element box at a 128-byte boundary, then
-// the epilogue's operand planes (Epi::kAux boxes of kMAuxX x kModalOwnY x 3
-// nodes: the owned rows of the node plane the stage's epilogue writes)
-constexpr int kMElemOff = (kMNode + 31) / 32 * 32;
-constexpr int kMStageBase = (kMElemOff + kMElem + 31) / 32 * 32;
 constexpr int kMAuxX = (kModalTX + 3 + 3) / 4 * 4;  // >= 3 (alignment slack) + kModalTX columns
-constexpr int kMAuxY = kModalOwnY;
-constexpr int kMAux = 3 * kMAuxY * kMAuxX;
-constexpr int kMAuxStride = (kMAux + 31) / 32 * 32;
-constexpr uint32_t kMAuxTx = (uint32_t)kMAux * 4u;
-__host__ __device__ constexpr int modal_stage_floats(int naux) {
-  return kMStageBase + naux * kMAuxStride;
-}
-constexpr size_t kModalXchBytes = sizeof(float) * 2 * kModalTY * kModalTX * 3;
-__host__ __device__ constexpr size_t modal_smem(int naux) {
-  return sizeof(float) * modal_stage_floats(naux) * kModalStages + kModalXchBytes +
-         sizeof(uint64_t) * kModalStages + 128;  // + alignment slack
-}
+
+// Boxes and shared-memory layout of the TMA kernel for a tile of TY thread
+// rows (TY - 1 owned node rows).  Stage layout (floats): node box, element
+// box at a 128-byte boundary, then the epilogue's operand planes (Epi::kAux
+// boxes of kMAuxX x (TY - 1) x 3 nodes: the owned rows of the node plane the
+// stage's epilogue writes).
+template <int TY>
+struct MTile {
+  static constexpr int OwnY = TY - 1;
+  static constexpr int BoxNY = TY + 1;  // node rows y0-1 .. y0+OwnY
+  static constexpr int BoxEY = TY;      // element rows y0-1 .. y0+OwnY-1
+  static constexpr int Node = 3 * BoxNY * kMBoxX;
+  static constexpr int Elem = BoxEY * kMBoxX;
+  static constexpr uint32_t StageTx = (uint32_t)(Node + Elem) * 4u;
+  static constexpr int ElemOff = (Node + 31) / 32 * 32;
+  static constexpr int StageBase = (ElemOff + Elem + 31) / 32 * 32;
+  static constexpr int AuxY = OwnY;
+  static constexpr int Aux = 3 * AuxY * kMAuxX;
+  static constexpr int AuxStride = (Aux + 31) / 32 * 32;
+  static constexpr uint32_t AuxTx = (uint32_t)Aux * 4u;
+  static constexpr size_t XchBytes = sizeof(float) * 2 * TY * kModalTX * 3;
+  __host__ __device__ static constexpr int stage_floats(int naux) {
+    return StageBase + naux * AuxStride;
+  }
+  __host__ __device__ static constexpr size_t smem(int naux) {
+    return sizeof(float) * stage_floats(naux) * kModalStages + XchBytes +
+           sizeof(uint64_t) * kModalStages + 128;  // + alignment slack
+  }
+};
 
 // Grid: (x tiles, y tiles, zc z-chunks x designs); design b reads and writes
 // its own buffers at b * S bytes from design 0's (the TMA maps carry the
 // design as their outermost dimension).
-template <class Epi>
-__global__ void __launch_bounds__(kModalTX* kModalTY)
+template <class Epi, int TY>
+__global__ void __launch_bounds__(kModalTX* TY)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
                 const __grid_constant__ CUtensorMap amap0,
                 const __grid_constant__ CUtensorMap amap1, const Dims d,
@@ -273,7 +280,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   constexpr int DI = Epi::kDinvAux;      // >= 0: D^-1 formed from the moduli
   static_assert(NA <= 2, "at most two staged operand vectors");
   static_assert(DI < 0 || DI == Epi::kAux - 1, "D^-1 is the last operand");
-  constexpr int SF = modal_stage_floats(NA);
+  using Tl = MTile<TY>;
+  constexpr int SF = Tl::stage_floats(NA);
   pdl_start();
   const int slot = blockIdx.z / zc, chunk = blockIdx.z - slot * zc;
   const int design = S.id(slot);
@@ -287,13 +295,13 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
   // TMA destinations on 128-byte boundaries whatever the dynamic window's offset
   unsigned char* base = modal_dyn + ((128u - (smem_u32(modal_dyn) & 127u)) & 127u);
   float* stg = reinterpret_cast<float*>(base);
-  auto xch = reinterpret_cast<float(*)[kModalTY][kModalTX][3]>(
+  auto xch = reinterpret_cast<float(*)[TY][kModalTX][3]>(
       base + sizeof(float) * SF * kModalStages);
   uint64_t* bar =
-      reinterpret_cast<uint64_t*>(base + sizeof(float) * SF * kModalStages + kModalXchBytes);
+      reinterpret_cast<uint64_t*>(base + sizeof(float) * SF * kModalStages + Tl::XchBytes);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kModalTX + tx;
-  const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * kModalOwnY;
+  const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * Tl::OwnY;
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
   const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
   const int ox = x0 - bx;
@@ -315,13 +323,13 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     const int slot = t % kModalStages;
     float* sp = stg + slot * SF;
     const bool ax = NA > 0 && t >= 2;
-    mbar_arrive_expect_tx(&bar[slot], kMStageTx + (ax ? NA * kMAuxTx : 0u));
+    mbar_arrive_expect_tx(&bar[slot], Tl::StageTx + (ax ? NA * Tl::AuxTx : 0u));
     tma_load_5d(sp, &xmap, &bar[slot], bx, y0, kb + t, 0, design);
-    tma_load_4d(sp + kMElemOff, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
+    tma_load_4d(sp + Tl::ElemOff, &emap, &bar[slot], bx, y0, kb - 1 + t, design);
     if (ax) {
-      tma_load_5d(sp + kMStageBase, &amap0, &bar[slot], bx, y0 + 1, kb - 1 + t, 0, design);
+      tma_load_5d(sp + Tl::StageBase, &amap0, &bar[slot], bx, y0 + 1, kb - 1 + t, 0, design);
       if (NA > 1)
-        tma_load_5d(sp + kMStageBase + kMAuxStride, &amap1, &bar[slot], bx, y0 + 1, kb - 1 + t,
+        tma_load_5d(sp + Tl::StageBase + Tl::AuxStride, &amap1, &bar[slot], bx, y0 + 1, kb - 1 + t,
                     0, design);
     }
   };
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
     const float* nd = stg + r * SF;
     es = 0.f;
     if (DI >= 0 && own) {
-      const float* e0 = nd + kMElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
+      const float* e0 = nd + Tl::ElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
       es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
     }
 #pragma unroll
@@ -350,8 +358,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
       for (int dx = 0; dx < 2; ++dx)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          top[dy][dx][c] = nd[c * (kMBoxNY * kMBoxX) + (ty + dy) * kMBoxX + ox + tx + dx];
-    E = nd[kMElemOff + ty * kMBoxX + ox + tx];
+          top[dy][dx][c] = nd[c * (Tl::BoxNY * kMBoxX) + (ty + dy) * kMBoxX + ox + tx + dx];
+    E = nd[Tl::ElemOff + ty * kMBoxX + ox + tx];
   };
   {  // the first node plane only seeds the march
     float top[2][2][3], E;
@@ -390,11 +398,11 @@ __global__ void __launch_bounds__(kModalTX* kModalTY)
       const float rr[1][3] = {{res[0], res[1], res[2]}};
       const float cc[1][3] = {{ctr[0], ctr[1], ctr[2]}};
       float av[epi_slots<Epi>()][1][3];
-      const float* ap = nd + kMStageBase + (ty - 1) * kMAuxX + ox + tx;
+      const float* ap = nd + Tl::StageBase + (ty - 1) * kMAuxX + ox + tx;
 #pragma unroll
       for (int q = 0; q < NA; ++q)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) av[q][0][c] = ap[q * kMAuxStride + c * (kMAuxY * kMAuxX)];
+        for (int c = 0; c < 3; ++c) av[q][0][c] = ap[q * Tl::AuxStride + c * (Tl::AuxY * kMAuxX)];
       if constexpr (DI >= 0) {  // D^-1 of the masked operator, 1 where no stiffness
         const float sum = es_prev + es;
         const float dv = sum > 0.f ? 1.0f / (kc.kdiag * sum) : 1.0f;
@@ -497,9 +505,9 @@ __global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAI
 // whole columns (up to 64 planes), and the chunks of a column are equal
 // (a floor of 8 or 16 planes measured 1-5 % more solves/s with 64 designs in
 // flight on 96x32x32 but 57-147 % more latency for one design: 4 it is)
-inline int modal_zchunk(const Dims& d, int nb = 1) {
+inline int modal_zchunk(const Dims& d, int nb = 1, int own_y = kModalOwnY) {
   const long long xy = (long long)((d.nx + kModalOwnX) / kModalOwnX) *
-                       ((d.ny + kModalOwnY) / kModalOwnY);
+                       ((d.ny + own_y) / own_y);
   const int planes = d.nz + 1;
   int z = (int)((xy * planes * nb) / (152 * 2 * 4));
   if (z < 4) z = 4;
@@ -510,37 +518,72 @@ inline int modal_zchunk(const Dims& d, int nb = 1) {
   return (planes + zc - 1) / zc;
 }
 
-bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
-                CUtensorMap* emap);
-bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map);
+// ty: thread rows of the tile (box heights ty + 1 node rows, ty element rows)
+bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, int ty,
+                CUtensorMap* xmap, CUtensorMap* emap);
+bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, int ty, CUtensorMap* map);
+
+// Tile height of a launch: kModalTY, or kModalTallTY where a batched launch
+// (several designs; one design keeps more, smaller CTAs for its latency)
+// would run fewer thread rows per x column of tiles and the box fits the grid.
+// 96x32x32: the second level's 17 node rows take one 18-row tile instead of
+// two 12-row ones (72 % of the threads own a node instead of 54 %).
+constexpr int kModalTallTY = 18;
+
+inline int modal_pick_ty(const Dims& d, int nb) {
+  if (nb < 2 || kModalTallTY + 1 > d.ny + 3) return kModalTY;
+  const auto rows = [&](int ty) { return (long long)((d.ny + ty - 1) / (ty - 1)) * ty; };
+  return rows(kModalTallTY) < rows(kModalTY) ? kModalTallTY : kModalTY;
+}
+
+template <class Epi, int TY>
+cudaError_t launch_modal_tma(const float* x, const float* E, const Dims& d,
+                             const ModalCoef<float>& kc, const Epi& epi, const Red& red,
+                             const int* done, int* errflag, cudaStream_t s, const Bat& bt,
+                             bool* launched) {
+  *launched = false;
+  CUtensorMap xm, em, am[2];
+  std::memset(am, 0, sizeof(am));
+  bool ok = modal_maps(x, E, d, bt, TY, &xm, &em);
+  for (int q = 0; q < epi_staged<Epi>() && ok; ++q)
+    ok = modal_aux_map(epi.aux(q), d, bt, TY, &am[q]);
+  if (!ok) return cudaSuccess;  // the boxes do not fit: the plain kernel
+  constexpr size_t smem = MTile<TY>::smem(epi_staged<Epi>());
+  static bool attr = false;  // per instantiation; setting it twice is harmless
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_modal_tma<Epi, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int z = modal_zchunk(d, bt.nb, TY - 1);
+  const int zc = (d.nz + z) / z;
+  dim3 block(kModalTX, TY, 1);
+  dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + TY - 1) / (TY - 1), zc * bt.nb);
+  *launched = true;
+  return launch_pdl(k_modal_tma<Epi, TY>, grid, block, smem, s, xm, em, am[0], am[1], d, kc, epi,
+                    red, z, zc, bt.sel(), done, errflag);
+}
 
 template <typename T, class Epi>
 cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const ModalCoef<T>& kc,
                                 const Epi& epi, const Red& red, const int* done, int* errflag,
                                 cudaStream_t s, const Bat& bt, T* energy = nullptr) {
+  if constexpr (sizeof(T) == 4) {
+    if (energy) return cudaErrorInvalidValue;  // element energies: the FP64 kernel only
+    bool launched = false;
+    const cudaError_t e =
+        modal_pick_ty(d, bt.nb) == kModalTallTY
+            ? launch_modal_tma<Epi, kModalTallTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
+                                                  &launched)
+            : launch_modal_tma<Epi, kModalTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
+                                              &launched);
+    if (e != cudaSuccess || launched) return e;
+  }
   const int z = modal_zchunk(d, bt.nb);
   const int zc = (d.nz + z) / z;
   dim3 block(kModalTX, kModalTY, 1);
   dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + kModalOwnY) / kModalOwnY, zc * bt.nb);
-  if constexpr (sizeof(T) == 4) {
-    if (energy) return cudaErrorInvalidValue;  // element energies: the FP64 kernel only
-    CUtensorMap xm, em, am[2];
-    std::memset(am, 0, sizeof(am));
-    bool ok = modal_maps(x, E, d, bt, &xm, &em);
-    for (int q = 0; q < epi_staged<Epi>() && ok; ++q) ok = modal_aux_map(epi.aux(q), d, bt, &am[q]);
-    if (ok) {
-      constexpr size_t smem = modal_smem(epi_staged<Epi>());
-      static bool attr = false;  // per instantiation; setting it twice is harmless
-      if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_modal_tma<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
-      return launch_pdl(k_modal_tma<Epi>, grid, block, smem, s, xm, em, am[0], am[1], d, kc, epi,
-                        red, z, zc, bt.sel(), done, errflag);
-    }
-  }
   return launch_pdl(k_modal_plain<T, Epi>, grid, block, 0, s, x, E, d, kc, epi, red, z, zc, bt.sel(),
                     done, energy);
 }

@@ -118,10 +118,9 @@ bool stencil_maps(const float* x, const float* E, const Dims& d, CUtensorMap* xm
          cached_map(E, 1, d, kBoxX, kBoxYE, Bat{}, emap);
 }
 
-bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
-                CUtensorMap* emap) {
-  return cached_map(x, 0, d, kMBoxX, kMBoxNY, bt, xmap) &&
-         cached_map(E, 1, d, kMBoxX, kMBoxEY, bt, emap);
+bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, int ty,
+                CUtensorMap* xmap, CUtensorMap* emap) {
+  return cached_map(x, 0, d, kMBoxX, ty + 1, bt, xmap) && cached_map(E, 1, d, kMBoxX, ty, bt, emap);
 }
 
 bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUtensorMap* xmap,
@@ -130,8 +129,8 @@ bool pair_maps(const float* x, const float* E, const Dims& d, const Bat& bt, CUt
          cached_map(E, 1, d, kPBoxX, kPBoxEY, bt, emap);
 }
 
-bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map) {
-  return v != nullptr && cached_map(v, 0, d, kMAuxX, kMAuxY, bt, map);
+bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, int ty, CUtensorMap* map) {
+  return v != nullptr && cached_map(v, 0, d, kMAuxX, ty - 1, bt, map);
 }
 
 bool pair_aux_map(const float* v, const Dims& d, const Bat& bt, CUtensorMap* map) {
