@@ -523,17 +523,24 @@ bool modal_maps(const float* x, const float* E, const Dims& d, const Bat& bt, in
                 CUtensorMap* xmap, CUtensorMap* emap);
 bool modal_aux_map(const float* v, const Dims& d, const Bat& bt, int ty, CUtensorMap* map);
 
-// Tile height of a launch: kModalTY, or kModalTallTY where a batched launch
-// (several designs; one design keeps more, smaller CTAs for its latency)
-// would run fewer thread rows per x column of tiles and the box fits the grid.
+// Tile height of a launch: kModalTY, or for a batched launch (several
+// designs; one design keeps the 12-row tiles, more and smaller CTAs, for its
+// latency) kModalTallTY or kModalShortTY where that launches fewer thread
+// rows per x column of tiles and its node box fits the grid (ty + 1 <= ny + 3).
 // 96x32x32: the second level's 17 node rows take one 18-row tile instead of
-// two 12-row ones (72 % of the threads own a node instead of 54 %).
-constexpr int kModalTallTY = 18;
+// two 12-row ones (72 % of the threads own a node instead of 54 %); the
+// third level's 9 rows one 10-row tile (the 12-row box does not fit there,
+// which left that level to the plain-load kernel).
+constexpr int kModalTallTY = 18, kModalShortTY = 10;
 
 inline int modal_pick_ty(const Dims& d, int nb) {
-  if (nb < 2 || kModalTallTY + 1 > d.ny + 3) return kModalTY;
+  const auto fits = [&](int ty) { return ty + 1 <= d.ny + 3; };
   const auto rows = [&](int ty) { return (long long)((d.ny + ty - 1) / (ty - 1)) * ty; };
-  return rows(kModalTallTY) < rows(kModalTY) ? kModalTallTY : kModalTY;
+  if (nb < 2) return kModalTY;
+  int best = fits(kModalTY) ? kModalTY : -1;
+  for (int ty : {kModalTallTY, kModalShortTY})
+    if (fits(ty) && (best < 0 || rows(ty) < rows(best))) best = ty;
+  return best < 0 ? kModalTY : best;
 }
 
 template <class Epi, int TY>
@@ -572,12 +579,21 @@ cudaError_t launch_modal_single(const T* x, const T* E, const Dims& d, const Mod
   if constexpr (sizeof(T) == 4) {
     if (energy) return cudaErrorInvalidValue;  // element energies: the FP64 kernel only
     bool launched = false;
-    const cudaError_t e =
-        modal_pick_ty(d, bt.nb) == kModalTallTY
-            ? launch_modal_tma<Epi, kModalTallTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
-                                                  &launched)
-            : launch_modal_tma<Epi, kModalTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
-                                              &launched);
+    cudaError_t e;
+    switch (modal_pick_ty(d, bt.nb)) {
+      case kModalTallTY:
+        e = launch_modal_tma<Epi, kModalTallTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
+                                                &launched);
+        break;
+      case kModalShortTY:
+        e = launch_modal_tma<Epi, kModalShortTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
+                                                 &launched);
+        break;
+      default:
+        e = launch_modal_tma<Epi, kModalTY>(x, E, d, kc, epi, red, done, errflag, s, bt,
+                                            &launched);
+        break;
+    }
     if (e != cudaSuccess || launched) return e;
   }
   const int z = modal_zchunk(d, bt.nb);
