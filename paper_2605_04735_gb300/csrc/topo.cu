@@ -346,7 +346,7 @@ enum InnerKind { IK_JAC32 = 0, IK_JAC64 = 1, IK_GMG32 = 2 };
 // An inner FP32 solve that could finish the solve aims at kInnerMargin x the
 // target relative residual: the FP32 recursion's residual drifts from the
 // true one, and a miss costs a whole further outer step.
-constexpr double kInnerMargin = 0.25;
+constexpr double kInnerMargin = 0.5;
 
 // Enqueue `count` CG iterations of the given kind.  Every kernel returns at
 // once when the device-side `done` flag is set, so iterations past
