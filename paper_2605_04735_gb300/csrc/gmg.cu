@@ -278,26 +278,34 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
   rf = bshift(rf, off);
   bc = bshift(bc, off);
   const long long nn = (long long)(dc.nx + 1) * (dc.ny + 1) * (dc.nz + 1);
+  // fine node (i, j, k) of component c at rc[c] + i + px j + pz k (one design's
+  // vector holds < 2^31 entries)
+  const float* rc[3] = {rf + df.node(0, 0, 0), rf + df.comp + df.node(0, 0, 0),
+                        rf + 2 * df.comp + df.node(0, 0, 0)};
+  const int px = (int)df.row_stride(), pz = (int)df.plane_stride();
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
        n += (long long)gridDim.x * blockDim.x) {
     int I, J, K;
     unflatten3(n, dc.nx + 1, dc.ny + 1, I, J, K);
     float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
       const int k = 2 * K + dk;
       if (k < 0 || k > df.nz) continue;
       const float wk = dk ? 0.5f : 1.0f;
+#pragma unroll
       for (int dj = -1; dj <= 1; ++dj) {
         const int j = 2 * J + dj;
         if (j < 0 || j > df.ny) continue;
         const float wjk = wk * (dj ? 0.5f : 1.0f);
+        const int row = px * j + pz * k;
+#pragma unroll
         for (int di = -1; di <= 1; ++di) {
           const int i = 2 * I + di;
           if (i < 0 || i > df.nx) continue;
           const float wt = wjk * (di ? 0.5f : 1.0f);
-          const long long o = df.node(i, j, k);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, rf[c * df.comp + o], s[c]);
+          for (int c = 0; c < 3; ++c) s[c] = fmaf(wt, rc[c][row + i], s[c]);
         }
       }
     }
