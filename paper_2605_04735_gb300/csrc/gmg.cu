@@ -784,9 +784,16 @@ cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
   return launch_stencil<float>(x, L.E, L.d, k0f, ep, red, done, errflag, s);
 }
 
+float gmg_first_direction(const Gmg& g, float** d0) {
+  if (g.lv.size() < 2 || g.degree < 2) return 0.0f;  // no finest-level smoothing step
+  *d0 = g.lv[0].dv[0];
+  return cheb_coef(g.lam_max, g.lam_ratio, g.degree).inv_theta;
+}
+
 cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
-                       cudaStream_t s, long long* launches, const Bat& bt, const Red* zdot) {
+                       cudaStream_t s, long long* launches, const Bat& bt, const Red* zdot,
+                       bool d0_ready) {
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
@@ -804,9 +811,12 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     const long long n4 = L.nvec / 4;
     // d0 = D^-1 b / theta; with further steps the first one reads b as its
     // residual and sets x = d0 + d1, so r = b and x = d0 are not written here
-    GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
-                   L.dv[0], X(l), L.dinv, n4, cc.inv_theta, m > 1 ? 1 : 0, done, bt.sel()));
-    ++*launches;
+    // (on the finest level the CG update may have written d0 already)
+    if (!(l == 0 && d0_ready && m > 1)) {
+      GCK(launch_pdl(k_cheb_init, dim3(grid1d(n4, bt.nb), bt.nb), dim3(kPT), 0, s, B(l), L.r,
+                     L.dv[0], X(l), L.dinv, n4, cc.inv_theta, m > 1 ? 1 : 0, done, bt.sel()));
+      ++*launches;
+    }
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, k == 1 ? B(l) : L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
                      k == 1 ? EpiChebStep::kXStore : EpiChebStep::kXAdd};

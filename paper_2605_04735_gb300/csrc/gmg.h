@@ -70,10 +70,16 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 // mcf != nullptr: smoother passes use the modal operator kernel
 // zdot (optional): the reduction b . x of the result (the CG's r . z), fused
 // into the finest level's last smoothing step
+// d0_ready: the finest level's first Chebyshev direction D^-1 b / theta is
+// already in its buffer (gmg_first_direction)
 cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
                        cudaStream_t s, long long* launches, const Bat& bt = Bat{},
-                       const Red* zdot = nullptr);
+                       const Red* zdot = nullptr, bool d0_ready = false);
+// Where a V-cycle's first finest-level Chebyshev direction goes (*d0) and its
+// scale 1/theta, for a caller that forms it (D^-1 of the finest level is the
+// one the hierarchy was set up with); 0 when the finest level is not smoothed.
+float gmg_first_direction(const Gmg& g, float** d0);
 void gmg_free(Gmg& g);
 // lambda_max of diag(k0)^-1 k0 (bounds lambda_max(D^-1 A) on every level)
 double k0_jacobi_bound(const double* k0);

@@ -53,9 +53,11 @@ cudaError_t launch_set_max_iter(PcgScalars* sc, int max_iter, cudaStream_t s,
 template <typename T>
 cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, long long n,
                             const Red& red, bool jacobi, cudaStream_t s, const Bat& bt = Bat{});
+// jacobi: z = D^-1 r and r.z; otherwise with dinv given z = D^-1 r scale
 template <typename T>
 cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
-                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt = Bat{});
+                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt = Bat{},
+                              T scale = T(1));
 template <typename T>
 cudaError_t launch_pcg_direction(T* p, const T* z, long long n, const PcgScalars* sc,
                                  cudaStream_t s, const Bat& bt = Bat{});

@@ -376,12 +376,16 @@ topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
         LK(m, launch_pcg_direction<double>(m->p64, m->z64, m->nvec, m->sc, s));
         break;
       default:
-        LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
-                                       red_of(m, FIN_RR_ONLY), false, s));
-        {  // z = V(r), with r . z (beta) fused into the V-cycle's last smoothing step
+        {  // the update also forms the V-cycle's first direction; z = V(r), with
+           // r . z (beta) fused into the V-cycle's last smoothing step
+          float* d0 = nullptr;
+          const float th = gmg_first_direction(m->gmg, &d0);
+          LK(m, launch_pcg_update<float>(m->x32, m->r32, d0 ? d0 : m->z32, m->p32, m->q32,
+                                         d0 ? m->dinv32 : nullptr, m->nvec,
+                                         red_of(m, FIN_RR_ONLY), false, s, Bat{}, th));
           const Red zr = red_of(m, FIN_RZ_BETA);
           CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s,
-                        &m->launches, Bat{}, &zr));
+                        &m->launches, Bat{}, &zr, d0 != nullptr));
         }
         LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
         break;
@@ -1596,12 +1600,16 @@ topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile, const Bat
     LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
                               red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
-    LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, nullptr, m->nvec,
-                                   red_of(m, FIN_RR_ONLY), false, s, bt));
-    {  // z = V(r), with r . z (beta) fused into the V-cycle's last smoothing step
+    {  // the update also forms the V-cycle's first direction; z = V(r), with
+       // r . z (beta) fused into the V-cycle's last smoothing step
+      float* d0 = nullptr;
+      const float th = gmg_first_direction(m->gmg, &d0);
+      LK(m, launch_pcg_update<float>(m->x32, m->r32, d0 ? d0 : m->z32, m->p32, m->q32,
+                                     d0 ? m->dinv32 : nullptr, m->nvec, red_of(m, FIN_RR_ONLY),
+                                     false, s, bt, th));
       const Red zr = red_of(m, FIN_RZ_BETA);
       CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches,
-                    bt, &zr));
+                    bt, &zr, d0 != nullptr));
     }
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
   }

@@ -100,12 +100,13 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // x += alpha p, r -= alpha q; Jacobi: z = D^-1 r, reduce (r.z, r.r) -> FIN_UPDATE;
-// otherwise reduce r.r -> FIN_RR_ONLY
+// otherwise reduce r.r -> FIN_RR_ONLY, and with dinv given also z = D^-1 r scale
+// (the multigrid's first Chebyshev direction on the finest level)
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(kThreads)
     k_pcg_update(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z, const T* __restrict__ p,
                  const T* __restrict__ qv, const T* __restrict__ dinv, long long n4,
-                 const Red red0, const DSel S) {
+                 const T scale, const Red red0, const DSel S) {
   pdl_start();
   const long long off = S.off(blockIdx.y);
   x = bshift(x, off);
@@ -144,6 +145,14 @@ __global__ void __launch_bounds__(kThreads)
       zv.w = dv.w * rv.w;
       st4(z, q, zv);
       rz += (double)(rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w);
+    } else if (dinv != nullptr) {
+      const auto dv = ld4(dinv, q);
+      typename Vec4<T>::type zv;
+      zv.x = dv.x * rv.x * scale;
+      zv.y = dv.y * rv.y * scale;
+      zv.z = dv.z * rv.z * scale;
+      zv.w = dv.w * rv.w * scale;
+      st4(z, q, zv);
     }
     rr += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
   }
@@ -324,14 +333,15 @@ cudaError_t launch_pcg_init(const T* b, T* x, T* r, T* z, T* p, const T* dinv, l
 
 template <typename T>
 cudaError_t launch_pcg_update(T* x, T* r, T* z, const T* p, const T* q, const T* dinv, long long n,
-                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt) {
+                              const Red& red, bool jacobi, cudaStream_t s, const Bat& bt,
+                              T scale) {
   const long long n4 = n / 4;
   const dim3 g = vgrid(n4, bt);
   if (jacobi)
-    return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
-                      bt.sel());
-  return launch_pdl(k_pcg_update<T, false>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4, red,
-                    bt.sel());
+    return launch_pdl(k_pcg_update<T, true>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4,
+                      scale, red, bt.sel());
+  return launch_pdl(k_pcg_update<T, false>, g, dim3(kThreads), 0, s, x, r, z, p, q, dinv, n4,
+                    scale, red, bt.sel());
 }
 
 template <typename T>
@@ -390,7 +400,7 @@ cudaError_t launch_copy_cast(T* dst, const double* src, long long n, cudaStream_
                                           const Red&, bool, cudaStream_t, const Bat&);         \
   template cudaError_t launch_pcg_update<T>(T*, T*, T*, const T*, const T*, const T*,          \
                                             long long, const Red&, bool, cudaStream_t,         \
-                                            const Bat&);                                       \
+                                            const Bat&, T);                                    \
   template cudaError_t launch_pcg_direction<T>(T*, const T*, long long, const PcgScalars*,     \
                                                cudaStream_t, const Bat&);                      \
   template cudaError_t launch_dot<T>(const T*, const T*, long long, const Red&, cudaStream_t,  \
