@@ -424,25 +424,30 @@ topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launche
 
 /* Element sensitivities (as topo_sensitivity) and the element-form
  * compliance (as topo_compliance_energy) of a given displacement, for
- * callers that must not allocate GPU memory: code running while a stream is
- * being captured into a CUDA graph (where cudaMalloc is not allowed), or
- * code whose device memory budget is fixed up front (real-time loops,
- * embedded hosts, processes that hand all memory to their own allocator).
- * It needs no mesh and calls no cudaMalloc, cudaFree or allocating library
- * routine.  The paper has no counterpart: this is an interface variant.
+ * callers that cannot allocate GPU memory: processes that hand all device
+ * memory to their own allocator or budget it once at start-up, real-time
+ * loops in which an allocation's latency or failure is not acceptable, and
+ * embedded hosts with a fixed memory map.  It needs no mesh and calls no
+ * cudaMalloc, cudaFree or allocating library routine.  The paper has no
+ * counterpart: this is an interface variant of the Eq. (3) kernel.
  *   u   : device, n_dof = 3 (nx+1)(ny+1)(nz+1) doubles, DOF order above
  *         (fixed DOFs must hold 0, as a solved displacement does);
- *   rho : device, nx*ny*nz floats in [0, 1], element order;
+ *   rho : device, nx*ny*nz floats in [0, 1], element order (not checked:
+ *         a value outside [0, 1] gives NaN or a meaningless dc and c);
  *   dc  : device output, nx*ny*nz doubles;  c : device output, 1 double.
+ * The pointers' lengths cannot be checked here: arrays shorter than the
+ * grid needs are read or written past their end.
  * prm NULL = defaults.  Work is enqueued on `stream` (NULL = legacy default
  * stream); the call does not synchronise.
  * Scratch: a fixed 32 KiB device array inside the library (one per GPU that
  * loads it, held until the process exits).  This bounds the size: at most
- * 8,388,608 elements; larger grids return TOPO_ERR_INVALID.  Every call
- * shares the array and keeps its last contents, so calls that overlap on
+ * 8,388,608 elements; larger grids return TOPO_ERR_INVALID before anything
+ * is enqueued.  Every call shares the array and keeps its last contents (the
+ * call clears the part that must start at zero), so calls that overlap on
  * the GPU (e.g. on two streams without ordering) race: serialise them.  The
- * first call on each device looks the array up (cudaGetSymbolAddress); make
- * that first call before any stream capture begins. */
+ * first call on each device sets up the array's device address
+ * (cudaGetSymbolAddress, again after the device's context has been
+ * re-created); make that first call before any stream capture begins. */
 topo_status topo_sensitivity_noalloc(int nx, int ny, int nz, const topo_params* prm,
                                      const double* u, const float* rho, double* dc, double* c,
                                      void* stream);

@@ -6,6 +6,7 @@
 // ever passes the array's device address, which it obtains once per device
 // with cudaGetSymbolAddress (the symbol itself is a host-side stand-in that
 // must never reach a kernel).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -34,7 +35,11 @@ static __device__ __align__(256) NaScratch g_na_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
+// per device: the scratch address and the id of the context it belongs to
+// (a context that was destroyed, e.g. by cudaDeviceReset, and re-created has
+// another id, so its address is looked up again)
 NaScratch* g_na_ptr[kMaxDevices] = {};
+unsigned long long g_na_ctx[kMaxDevices] = {};
 
 __host__ __device__ constexpr int na_lidx(int dx, int dy, int dz) {
   return 4 * dz + (dy ? (dx ? 2 : 3) : (dx ? 1 : 0));
@@ -114,19 +119,57 @@ __global__ void __launch_bounds__(kNaThreads)
   }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress may load the module: not during capture).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+CtxGetCurrentFn g_get_cur = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+
+// Whether the driver can name contexts (entry points resolved once).
+bool ctx_ids_available() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  return g_get_cur && g_get_id;
+}
+
+// Id of the current context, 0 if none is current.
+unsigned long long current_ctx_id() {
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_get_cur(&ctx) != CUDA_SUCCESS || !ctx || g_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up on
+// the first call per device, and again only if the device's context has been
+// destroyed and re-created since (e.g. by cudaDeviceReset: the old address
+// would be stale).  cudaGetSymbolAddress may load the module, which a stream
+// capture in progress does not allow: the first call must come before any.
 cudaError_t scratch_address(NaScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const bool ids = ctx_ids_available();
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
+  if (!g_na_ptr[dev] || (ids && current_ctx_id() != g_na_ctx[dev])) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_na_scratch);
+    e = cudaGetSymbolAddress(&p, g_na_scratch);  // also makes the device's context current
     if (e != cudaSuccess) return e;
     g_na_ptr[dev] = static_cast<NaScratch*>(p);
+    g_na_ctx[dev] = ids ? current_ctx_id() : 0;
   }
   *out = g_na_ptr[dev];
   return cudaSuccess;

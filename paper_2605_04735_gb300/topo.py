@@ -182,11 +182,23 @@ def footprint_bytes(nx, ny, nz, opts: SolveOpts | None = None) -> int:
 
 def sensitivity_noalloc(nx, ny, nz, u, rho, dc, c, params: Params | None = None, stream=None):
     """topo_sensitivity_noalloc on CUDA tensors (u: float64 DOFs, rho: float32
-    elements, dc: float64 elements, c: one float64); enqueued, not synchronised."""
+    elements, dc: float64 elements, c: one float64); enqueued, not synchronised.
+
+    The C entry point receives raw pointers and cannot see how long they are,
+    so the sizes are checked here, before anything is launched: u must hold
+    3 (nx+1)(ny+1)(nz+1) values, rho and dc nx ny nz, c at least one
+    (ValueError otherwise)."""
     pu, nu_, du = _ptr(u, np.float64)
     pr, nr, dr = _ptr(rho, np.float32)
     pd, nd, dd = _ptr(dc, np.float64)
     pc, nc, dcc = _ptr(c, np.float64)
+    n_elem = int(nx) * int(ny) * int(nz)
+    n_dof = 3 * (int(nx) + 1) * (int(ny) + 1) * (int(nz) + 1)
+    if min(nx, ny, nz) < 1:
+        raise ValueError("grid sizes must be positive")
+    if nu_ != n_dof or nr != n_elem or nd != n_elem or nc < 1:
+        raise ValueError(f"sizes do not match the {nx}x{ny}x{nz} grid: u {nu_} (want {n_dof}), "
+                         f"rho {nr} and dc {nd} (want {n_elem}), c {nc} (want >= 1)")
     if not (du and dr and dd and dcc):
         raise TypeError("topo_sensitivity_noalloc takes device arrays only")
     s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)

@@ -46,3 +46,23 @@ def test_binding_loads_and_reports_status_strings(libpath):
     o = topo.default_opts()
     assert o.rtol == 1e-8 and o.precision == topo.PREC_FP32
     assert topo.footprint_bytes(96, 32, 32) > 0
+
+
+def test_noalloc_binding_refuses_arrays_that_do_not_fit_the_grid(libpath):
+    """topo_sensitivity_noalloc only sees pointers, so its binding checks the
+    lengths against the grid before anything is passed to the library."""
+    import numpy as np
+    from paper_2605_04735_gb300 import topo
+    nx, ny, nz = 4, 2, 2
+    ok_u = np.zeros(3 * 5 * 3 * 3)
+    ok_r = np.zeros(nx * ny * nz, np.float32)
+    ok_d = np.zeros(nx * ny * nz)
+    c = np.zeros(1)
+    bad = [(ok_u[:-3], ok_r, ok_d, c), (ok_u, ok_r[:-1], ok_d, c), (ok_u, ok_r, ok_d[:-1], c),
+           (ok_u, ok_r, ok_d, np.zeros(0))]
+    for u, r, d, cc in bad:
+        with pytest.raises(ValueError):
+            topo.sensitivity_noalloc(nx, ny, nz, u, r, d, cc)
+    # the right sizes pass the size check and stop at the device check (host arrays)
+    with pytest.raises(TypeError):
+        topo.sensitivity_noalloc(nx, ny, nz, ok_u, ok_r, ok_d, c)

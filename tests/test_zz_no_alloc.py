@@ -1,5 +1,6 @@
 """topo_sensitivity_noalloc: the entry point for callers that cannot allocate
-GPU memory (inside stream capture, fixed memory budgets).  Its results must
+GPU memory (their own allocator owns the device memory, or the budget is
+fixed up front).  Its results must
 match the mesh-based entry points (topo_sensitivity, topo_compliance_energy)
 on the same displacement, on two calls in a row (the second call reuses the
 shared scratch array left behind by the first)."""
@@ -52,10 +53,15 @@ def test_noalloc_matches_mesh_entry_points_twice(topo, case):
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(topo):
+    import ctypes
     import torch
     tiny = torch.zeros(8, dtype=torch.float64, device="cuda")
     tiny32 = torch.zeros(8, dtype=torch.float32, device="cuda")
-    with pytest.raises(topo.TopoError) as e:
-        # 256 * 256 * 129 elements > 8,388,608: refused before any launch
-        topo.sensitivity_noalloc(256, 256, 129, tiny, tiny32, tiny, tiny)
-    assert e.value.status == topo.ERR_INVALID
+    # through the C ABI itself: 256 * 256 * 129 elements > 8,388,608 is
+    # refused before anything is enqueued (the pointers are never touched)
+    p = [ctypes.c_void_p(t.data_ptr()) for t in (tiny, tiny32, tiny, tiny)]
+    st = topo.lib().topo_sensitivity_noalloc(256, 256, 129, None, *p, None)
+    assert st == topo.ERR_INVALID
+    # the binding refuses arrays that do not fit the grid, before the call
+    with pytest.raises(ValueError):
+        topo.sensitivity_noalloc(4, 2, 2, tiny, tiny32, tiny, tiny)
