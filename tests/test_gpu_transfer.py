@@ -4,12 +4,14 @@ against the FP64 oracle, through the C ABI.
 Tolerances: nodal densities and every triangle vertex are FP64 on both sides
 with the same formulas (the least-squares solve differs in rounding only):
 1e-12 absolute for densities in [0, 1], 1e-10 for coordinates and distances
-in element units.  The triangle lists must agree in count and order (cells in
-element order, tetrahedra and their triangles in a fixed order)."""
+in element units.  The triangle soups are compared as sets: the same count,
+and a one-to-one matching of triangles whose vertex sets agree within the
+tolerance (the emission order is the kernel's business)."""
 import numpy as np
 import pytest
 
 from oracle import transfer as T
+from tests.geometry_compare import assert_same_triangle_set
 from paper_2605_04735_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -55,7 +57,7 @@ def test_levelset_from_density_matches_oracle(topo, nx, ny, nz, make):
         vol = m.set_levelset(None, eta=1.0)
     ref_phi, ref_rn, ref_tris = T.levelset_from_density(rho, nx, ny, nz, 0.5)
     assert ntri == len(ref_tris) > 0
-    assert np.abs(tris - ref_tris).max() <= 1e-10
+    assert_same_triangle_set(tris, ref_tris)
     assert np.abs(phi - ref_phi).max() <= 1e-10
     assert np.all((phi < 0) == (ref_rn >= 0.5))
     assert 0.0 < vol < nx * ny * nz
@@ -83,7 +85,7 @@ def test_paper_problem_simp_to_levelset_round_trip(topo):
     assert np.abs(phi[sample] - ref_phi).max() <= 1e-10
     ref2 = T.iso_surface(phi, nx, ny, nz, 0.0, inside_above=False)
     assert n2 == len(ref2)
-    assert np.abs(tris2 - ref2).max() <= 1e-10
+    assert_same_triangle_set(tris2, ref2)
 
 
 def test_transfer_without_a_boundary_is_rejected(topo):

@@ -106,3 +106,90 @@ def test_levelset_from_density_of_a_half_space():
     assert np.allclose(tris[:, :, 0], c, atol=1e-12)
     assert np.allclose(phi, X[:, 0] - c, atol=1e-12)
     assert np.all((phi < 0) == (rn >= 0.5))
+
+
+def _brute_distance(p, tri, n=401):
+    """min over a fine barycentric lattice of the triangle (brute force)."""
+    s = np.linspace(0, 1, n)
+    L1, L2 = np.meshgrid(s, s)
+    keep = (L1 + L2) <= 1.0
+    lam = np.stack([L1[keep], L2[keep], 1 - L1[keep] - L2[keep]], 1)
+    pts = lam @ tri
+    return np.min(np.linalg.norm(p[:, None, :] - pts[None], axis=2), axis=1)
+
+
+def test_closest_many_closed_forms_face_edge_vertex():
+    """The broadcast form of Eq. (28)/(29) on the unit right triangle in z = 0,
+    at points whose nearest feature is the face, each edge or each vertex:
+    the distances are the closed forms (and independent of triangle order)."""
+    tri = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    p = np.array([
+        [0.2, 0.3, 0.7],     # above the face: |z|
+        [0.25, 0.25, -1.5],  # below the face
+        [0.5, -0.4, 0.3],    # nearest the edge y = 0: sqrt(0.4^2 + 0.3^2)
+        [-0.6, 0.5, 0.0],    # nearest the edge x = 0, in plane: 0.6
+        [0.8, 0.8, 0.2],     # nearest the hypotenuse x + y = 1 at (0.5, 0.5, 0)
+        [-0.3, -0.4, 1.2],   # nearest vertex (0, 0, 0)
+        [1.5, -0.2, 0.0],    # nearest vertex (1, 0, 0)
+        [-0.1, 1.9, -0.3],   # nearest vertex (0, 1, 0)
+    ])
+    want = np.array([0.7, 1.5, 0.5, 0.6, np.sqrt(2 * 0.3 ** 2 + 0.2 ** 2),
+                     np.sqrt(0.09 + 0.16 + 1.44), np.sqrt(0.25 + 0.04),
+                     np.sqrt(0.01 + 0.81 + 0.09)])
+    for order in ([0, 1, 2], [2, 0, 1], [1, 0, 2]):
+        d = T._closest_many(p, tri[order][None])[:, 0]
+        assert np.allclose(d, want, atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_closest_many_against_sampling_many_triangles(seed):
+    """Every (point, triangle) pair of the broadcast form against brute-force
+    sampling of each triangle, with triangles of every shape: general, thin,
+    collinear (degenerate) and all three vertices equal (a point)."""
+    g = np.random.default_rng(100 + seed)
+    tris = g.normal(size=(6, 3, 3))
+    tris[1, 2] = tris[1, 0] + 0.02 * g.normal(size=3) + 0.5 * (tris[1, 1] - tris[1, 0])  # thin
+    tris[2, 2] = tris[2, 0] + 0.3 * (tris[2, 1] - tris[2, 0])                            # collinear
+    tris[3, 1] = tris[3, 0]
+    tris[3, 2] = tris[3, 0]                                                                # a point
+    p = g.normal(size=(50, 3)) * 2
+    # points just above the face, just off an edge and just off a vertex of tris[0]
+    a, b, c = tris[0]
+    n = np.cross(b - a, c - a)
+    n /= np.linalg.norm(n)
+    p[:3] = [(a + b + c) / 3 + 0.3 * n, (a + b) / 2 + 0.4 * ((a + b) / 2 - c), a + 0.5 * (a - (b + c) / 2)]
+    d = T._closest_many(p, tris)
+    assert d.shape == (len(p), len(tris))
+    for m in range(len(tris)):
+        brute = _brute_distance(p, tris[m])
+        edge = max(np.linalg.norm(tris[m, 0] - tris[m, 1]), np.linalg.norm(tris[m, 1] - tris[m, 2]),
+                   np.linalg.norm(tris[m, 2] - tris[m, 0]))
+        assert np.all(d[:, m] <= brute + 1e-12)
+        assert np.all(d[:, m] >= brute - 2 * edge / 400 - 1e-12)
+        # the scalar form of the same rule agrees exactly in case
+        assert np.allclose(d[:, m], T.closest_point_distance(p, tris[m]), atol=1e-13, rtol=0)
+    # the point triangle is the distance to its vertex
+    assert np.allclose(d[:, 3], np.linalg.norm(p - tris[3, 0], axis=1), atol=1e-13)
+
+
+def test_triangle_set_comparison_ignores_order_but_not_geometry():
+    """The order-free comparison the device parity tests use: a permuted soup
+    with rotated vertex orders matches; a moved vertex does not."""
+    from tests.geometry_compare import assert_same_triangle_set
+    n = 10
+    X = T._node_xyz(n, n, n)
+    f = np.linalg.norm(X - np.array([4.9, 5.2, 5.1]), axis=1) - 3.3
+    tris = T.iso_surface(f, n, n, n, 0.0, inside_above=False)
+    g = np.random.default_rng(5)
+    perm = tris[g.permutation(len(tris))]
+    perm = np.stack([np.roll(t, g.integers(3), axis=0) for t in perm])
+    assert_same_triangle_set(perm, tris)
+    bad = perm.copy()
+    bad[7, 1] += 1e-6
+    with pytest.raises(AssertionError):
+        assert_same_triangle_set(bad, tris)
+    # a duplicated triangle in place of another is not the same set
+    dup = perm.copy()
+    dup[3] = dup[4]
+    with pytest.raises(AssertionError):
+        assert_same_triangle_set(dup, tris)
