@@ -9,12 +9,18 @@ state solve K(rho) u = f (Eq. (2)) to rel. residual 1e-8, the compliance
 f^T u and the element sensitivities (Eq. (3)).  `value` times steps with
 inputs already in HBM (device timeline, CUDA events on the library's
 stream, L2 flushed between steps); `e2e` times the same through the public
-API with host buffers.  `roofline` is the FP32 operator's CG applies timed
-live over the timed steps, against the FP32 pipe (1152 flop per element).
+API with host buffers.  `roofline` is the step's largest kernel, the FP32
+operator with the multigrid's Chebyshev-step epilogue on the finest level,
+timed live over the timed steps against the HBM copy bandwidth (algorithmic
+bytes); `roofline_cg_apply` the CG applies the same way (28 B per node).
+`same_batch` times one step of the same batch with plain FP64 Jacobi-PCG and
+with FP32 Jacobi-PCG inside FP64 refinement; `serving` runs the serving
+stream; `cpu_baseline` is one full oracle solve on the host's cores.
 
 Under torchrun every rank solves its own independent designs (weak
 scaling); the only collectives are the timing barrier and max-reduction.
-`--impl reference` times the CPU oracle (banded Cholesky) instead.
+`--impl reference` times the CPU oracle (banded Cholesky of the full
+problem, one design per step) instead.
 """
 from __future__ import annotations
 
@@ -47,56 +53,64 @@ def operator_kernel(op: int, nx: int) -> str:
     if op == 3 or (op == 0 and nx >= PAIR_AUTO_MIN_NX):
         return "k_modal_pair (FP32 modal operator, two element columns per thread, packed f32x2)"
     return "k_modal_tma (FP32 modal operator, one element column per thread)"
-# DRAM bytes (read + write) per launch of the default operator kernel from one
-# ncu capture of the same kernel source, by workload; None until captured
-# (k_modal_tma on 96x32x32: its 2.9 MB working set stays in L2, so the
-# output is never written back during the launch; k_modal_pair on 320x160x160)
+
+
+# DRAM bytes (read + write) per launch of the CG apply (operator + p.Ap) from
+# one ncu capture of the same kernel source, by workload; None until captured
+# (k_modal_tma on one 96x32x32 design: its 2.9 MB working set stays in L2, so
+# the output is never written back during the launch; k_modal_pair on
+# 320x160x160)
 NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": 1957888.0 + 0.0,
                                         LARGE_WORKLOAD: 183507712.0 + 69900032.0}
-
-
-def operator_bytes(w: I.Workload) -> int:
-    """Algorithmic HBM bytes of one operator application y = K(rho) x in
-    FP32: x read and y written once per node (3 x 4 B each), E read once per
-    element (4 B)."""
-    return 24 * w.n_nodes + 4 * w.n_elem
-
-
+# FP32 lane-operations per element the modal kernels execute for one K u
+# (ncu instruction counts: the Walsh-Hadamard form of k0 instead of the dense
+# 2 x 24 x 24 product), the basis of the executed-operation floor
+EXEC_FP32_OPS_PER_ELEM = {"k_modal_pair": 165.0, "k_modal_tma": 200.0}
 FLOP_PER_ELEM = 2 * 24 * 24  # the dense K0 U_e product per element (multiply + add)
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x the SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def operator_bytes(w: I.Workload) -> int:
+    """Algorithmic HBM bytes of one CG apply y = K(rho) x (+ x.y) in FP32: x
+    read and y written once per node (3 x 4 B each), the modulus read once
+    per element (4 B)."""
+    return 24 * w.n_nodes + 4 * w.n_elem
 
 
-def roofline(w: I.Workload, avg_ms: float, peaks: dict, peaks_src: str, op: int = 0,
-             designs: float = 1.0, traffic: float | None = None) -> dict:
-    """The FP32 SIMT operator is bound by the FP32 pipe: achieved = the dense
-    algorithmic 1152 flop per element x the elements one launch processes
-    (`designs` grids) / the average launch time, against the FP32 peak from
-    the unit counts and the maximum SM clock.  The HBM view (28 B per node
-    of algorithmic traffic against the measured copy bandwidth) is given
-    beside it."""
+def fp32_lane_ops_per_s(sm_mhz: float) -> float:
+    """FP32 SIMT issue rate: 152 SMs x 128 FP32 lanes x the SM clock."""
+    return 152 * 128 * sm_mhz * 1e6
+
+
+def hbm_roofline(kernel: str, w: I.Workload, bytes_per_launch: float, avg_ms: float,
+                 designs: float, peaks: dict, peaks_src: str, traffic: float | None = None) -> dict:
+    """An operator kernel against the HBM roofline: achieved = its
+    algorithmic bytes per launch / its average launch time (CUDA events),
+    peak = the measured copy bandwidth.  Beside it the arithmetic view: the
+    dense-equivalent rate (1152 flop per element) and the floor the FP32
+    pipe sets for the operations the kernel actually executes."""
     t = avg_ms * 1e-3
-    flops = FLOP_PER_ELEM * w.n_elem * designs
-    achieved = flops / t / 1e12
+    peak = float(peaks["hbm_gbs"])
+    achieved = bytes_per_launch / t / 1e9
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(mhz)
-    hbm = operator_bytes(w) * designs / t / 1e9
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "kernel": operator_kernel(op, w.nx), "workload": w.name,
-            "designs_per_launch": designs,
-            "flop_per_launch": flops, "avg_launch_us": avg_ms * 1e3,
-            "gdofs": 3.0 * w.n_nodes * designs / t / 1e9,
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz; "
-                           "1152 flop per element is the dense K0.U_e product (the modal "
-                           "kernel computes the same result with ~165 FP32 lane-ops)",
-            "hbm": {"bytes_per_launch": operator_bytes(w) * designs, "achieved": hbm,
-                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                    "frac": hbm / float(peaks["hbm_gbs"]),
-                    "peak_source": f"{peaks_src}: MEASURED_PEAKS.json hbm_gbs"}}
+    elems = w.n_elem * designs
+    name = kernel.split(" ")[0]
+    ops = EXEC_FP32_OPS_PER_ELEM.get(name)
+    alu = {"dense_equivalent_tflops": FLOP_PER_ELEM * elems / t / 1e12,
+           "note": "1152 flop per element is the dense K0.U_e product; the modal kernels reach "
+                   "the same result with fewer executed operations"}
+    if ops is not None:
+        floor_s = elems * ops / fp32_lane_ops_per_s(mhz)
+        alu.update({"executed_fp32_ops_per_element": ops,
+                    "executed_floor_us": floor_s * 1e6,
+                    "executed_frac_of_fp32_pipe": floor_s / t,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz"})
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "workload": w.name,
+            "bytes_per_launch": bytes_per_launch, "designs_per_launch": designs,
+            "avg_launch_us": avg_ms * 1e3, "gdofs": 3.0 * w.n_nodes * designs / t / 1e9,
+            "hbm_floor_us": bytes_per_launch / (peak * 1e9) * 1e6,
+            "peak_source": f"{peaks_src}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+            "alu_view": alu}
 
 
 def large_operator(topo, stream, flush, op: int = 0, reps: int = 20):
@@ -217,60 +231,53 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(workload: I.Workload, budget_s: float = 20.0):
-    """The oracle (assembled K, banded Cholesky, compliance, sensitivities)
-    timed on a slab of the workload with the same y-z cross-section and fewer
-    x layers, scaled to the full problem by the number of free DOFs (the
-    banded factorisation costs n * b^2 with the same band b)."""
+def oracle_step(workload: I.Workload, rho: np.ndarray) -> float:
+    """One full oracle pass of the workload on the host (assembled FP64 K,
+    LAPACK banded Cholesky of the whole problem, compliance, sensitivities);
+    returns its wall time in seconds."""
     from oracle import fem
-    nx_s = max(2, min(workload.nx, 12))
-    t_tot, n = 0.0, 0
-    rho_full = workload.density().reshape(workload.nz, workload.ny, workload.nx)
-    rho = np.ascontiguousarray(rho_full[:, :, :nx_s]).reshape(-1)
-    free_s = None
-    while t_tot < budget_s / 2 or n == 0:
-        t0 = time.perf_counter()
-        P = fem.Problem(nx_s, workload.ny, workload.nz, workload.bc, workload.load, rho)
-        u = P.solve()
-        P.compliance(u)
-        P.sensitivity(u)
-        t_tot += time.perf_counter() - t0
-        n += 1
-        free_s = int((~P.fixed).sum())
-        if n >= 3:
-            break
-    g = fem.Grid(workload.nx, workload.ny, workload.nz)
-    free_full = int((~fem.fixed_dofs(g, workload.bc)).sum())
-    t_full = (t_tot / n) * free_full / free_s
+    t0 = time.perf_counter()
+    P = fem.Problem(workload.nx, workload.ny, workload.nz, workload.bc, workload.load, rho)
+    u = P.solve()
+    P.compliance(u)
+    P.sensitivity(u)
+    return time.perf_counter() - t0
+
+
+def slab(workload: I.Workload, rho: np.ndarray, nx_s: int = 12):
+    """The first nx_s element layers of the workload (same cross-section and
+    band): a short oracle run that warms the host's BLAS threads up."""
+    w = I.dataclasses.replace(workload, nx=min(nx_s, workload.nx))
+    r = np.ascontiguousarray(rho.reshape(workload.nz, workload.ny, workload.nx)[:, :, :w.nx])
+    return w, r.reshape(-1)
+
+
+def cpu_baseline(workload: I.Workload):
+    """The oracle timed on the full workload: one complete direct solve of
+    design 0 with its compliance and sensitivities, on all host cores."""
+    rho = workload.density()
+    t = oracle_step(workload, rho)
     cores = os.cpu_count() or 1
-    return {"value": 1.0 / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} oracle solve(s) of the {nx_s}x{workload.ny}x{workload.nz} slab "
-                      f"(same cross-section and band), {t_tot / n:.2f} s each, scaled by free DOFs "
-                      f"{free_full}/{free_s}; LAPACK threads = all {cores} host cores"}
+    return {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 full oracle solve of {workload.name} (assembled FP64 K, LAPACK banded "
+                      f"Cholesky of all {3 * workload.n_nodes} DOFs, compliance, sensitivities) in "
+                      f"{t:.2f} s; LAPACK threads = all {cores} host cores"}
 
 
 def run_reference(args, workload):
+    """The CPU oracle as the reference arm: every timed step is one complete
+    oracle solve of the full workload (a design of the benchmark's batch);
+    warm-up steps solve the 12-layer slab of it (same band), which warms the
+    BLAS threads without spending minutes on untimed work."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    from oracle import fem
-    nx_s = max(2, min(workload.nx, 12))
-    rho_full = workload.density().reshape(workload.nz, workload.ny, workload.nx)
-    rho = np.ascontiguousarray(rho_full[:, :, :nx_s]).reshape(-1)
-    g = fem.Grid(workload.nx, workload.ny, workload.nz)
-    free_full = int((~fem.fixed_dofs(g, workload.bc)).sum())
-    times = []
-    free_s = None
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        P = fem.Problem(nx_s, workload.ny, workload.nz, workload.bc, workload.load, rho)
-        u = P.solve()
-        P.compliance(u)
-        P.sensitivity(u)
-        dt = time.perf_counter() - t0
-        free_s = int((~P.fixed).sum())
-        if it >= args.warmup:
-            times.append(dt * free_full / free_s)
+    rhos = [I.dataclasses.replace(workload, seed=sd).density()
+            for sd in design_seeds(workload.seed, 0, max(1, args.steps))]
+    for it in range(args.warmup):
+        w_s, r_s = slab(workload, rhos[it % len(rhos)])
+        oracle_step(w_s, r_s)
+    times = [oracle_step(workload, rhos[k % len(rhos)]) for k in range(args.steps)]
     ms = 1e3 * float(np.mean(times))
     value = 1e3 / ms
     cores = os.cpu_count() or 1
@@ -279,15 +286,35 @@ def run_reference(args, workload):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload.name, "nx": workload.nx, "ny": workload.ny,
-                       "nz": workload.nz, "rtol": 1e-8, "solver": "banded Cholesky (LAPACK)"},
+                       "nz": workload.nz, "rtol": 1e-8, "solver": "banded Cholesky (LAPACK)",
+                       "warmup": "12-layer slab solves (same band)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: oracle solve of the {nx_s}x{workload.ny}x"
-                                       f"{workload.nz} slab, scaled by free DOFs {free_full}/"
-                                       f"{free_s}"},
+                             "sample": f"each timed step: one full oracle solve of {workload.name} "
+                                       f"(all {3 * workload.n_nodes} DOFs), compliance and "
+                                       f"sensitivities; {args.steps} designs of the benchmark's "
+                                       f"seeds; step times {min(times):.2f}-{max(times):.2f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+
+
+def serving_summary(budget_gb: float = 40.0, loads=(0.5, 0.8, 1.0)):
+    """The serving workload (64 requests x 30 solves, grids 24x12x12 ..
+    128x64x64, half cantilever / half MBB) through the continuous-batching
+    server: saturated throughput, then Poisson arrivals at fractions of it."""
+    from paper_2605_04735_gb300 import serving as SV
+    budget = int(budget_gb * 2**30)
+    reqs = I.serving_stream(64, 30, rate=0.0)
+    sat = SV.summarize(*SV.run_stream(reqs, budget, 64, realtime=False))
+    lam = sat["solves_per_s"] / 30
+    out = {"workload": "64 requests x 30 solves, grids 2n x n x n, n in 12..64 step 4, half "
+                       "cantilever / half MBB, densities perturbed +-5 % per solve",
+           "budget_gb": budget_gb, "saturated": sat, "lambda_sat_req_per_s": lam, "runs": {}}
+    for f in loads:
+        reqs = I.serving_stream(64, 30, rate=f * lam)
+        out["runs"][f"{f:.2f}x"] = SV.summarize(*SV.run_stream(reqs, budget, 64))
+    return out
 
 
 def main():
@@ -318,6 +345,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--same-batch", type=int, default=1,
+                    help="1: also time one step of the same batch with FP32 Jacobi-PCG + FP64 "
+                         "refinement and with plain FP64 Jacobi-PCG")
+    ap.add_argument("--serving", type=int, default=1,
+                    help="1: also run the serving stream (64 requests x 30 solves) and report "
+                         "its latency and throughput")
     ap.add_argument("--streams", action="store_true",
                     help="independent meshes on their own streams instead of one mesh group "
                          "solved in lockstep (one launch per step for all designs)")
@@ -426,6 +459,7 @@ def main():
         torch.cuda.synchronize()
         for m in meshes:
             m.profile_read(reset=True)
+            m.profile_read_smoother(reset=True)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -447,6 +481,9 @@ def main():
     # the per-launch time includes the sharing of the GPU
     batch_op_ms = sum(r[0] for m, r in zip(meshes, reads) if m in heads)
     batch_op_units = sum(r[1] for m, r in zip(meshes, reads) if m in heads)
+    # the finest-level Chebyshev steps of the V-cycles (the step's largest kernel)
+    sreads = [h.profile_read_smoother(reset=True) for h in heads]
+    cheb_ms, cheb_units, cheb_bytes = (sum(r[q] for r in sreads) for q in range(3))
     for h in heads:
         h.profile(False)
     value, total_ms = job_throughput(float(step_ms.sum()), B * args.steps, dist, "cuda")
@@ -498,6 +535,36 @@ def main():
         fp64 = {"solves_per_s": 1e3 / float(np.mean(ts)), "ms_per_solve": float(np.mean(ts)),
                 "iters": int(np.mean(its)), "batch": 1}
 
+    # ---- the same batch (one step of every design, same group, same
+    # accuracy) with the plain FP64 Jacobi-PCG path and with FP32 Jacobi-PCG
+    # inside FP64 refinement: the precision and preconditioner gains apart ----
+    same_batch = None
+    if args.same_batch and batched and rank == 0:
+        same_batch = {"what": "one step of the same batch (densities, solve to true rel. "
+                              "residual 1e-8, compliances, sensitivities), one mesh group in "
+                              "lockstep, CUDA events, L2 flushed; graph capture included",
+                      "fp32_gmg_ir": {"solves_per_s": value,
+                                      "iters_mean": float(np.mean([r[0] for r in recs]))}}
+        for key, prec in (("fp32_jacobi_ir", topo.PREC_FP32), ("fp64_jacobi_pcg", topo.PREC_FP64)):
+            oj = topo.default_opts(precision=prec, precond=topo.PRECOND_JACOBI, rtol=1e-8)
+            flush.fill_(3.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            infos_j, _ = step_batch(rho_dev, dc_dev, oj)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            same_batch[key] = {"solves_per_s": B * 1e3 / ms, "ms_per_step": ms,
+                               "iters_mean": float(np.mean([i.iters for i in infos_j])),
+                               "outer_mean": float(np.mean([i.outer for i in infos_j])),
+                               "rel_residual_max": float(max(i.rel_residual for i in infos_j))}
+        same_batch["gain_fp32_over_fp64_jacobi"] = (same_batch["fp32_jacobi_ir"]["solves_per_s"] /
+                                                    same_batch["fp64_jacobi_pcg"]["solves_per_s"])
+        same_batch["gain_gmg_over_jacobi_fp32"] = (value /
+                                                   same_batch["fp32_jacobi_ir"]["solves_per_s"])
+        same_batch["gain_total_over_fp64_jacobi"] = (value /
+                                                     same_batch["fp64_jacobi_pcg"]["solves_per_s"])
+
     if rank != 0:
         if pool is not None:
             pool.shutdown()
@@ -510,25 +577,43 @@ def main():
     peaks, peaks_src = _peaks()
     avg_ms = prof_ms / max(prof_n, 1)
     lw = I.WORKLOADS[LARGE_WORKLOAD]
-    large = roofline(lw, large_operator(topo, stream, flush, args.operator), peaks, peaks_src,
-                     args.operator,
-                     traffic=NCU_TRAFFIC.get(lw.name) if args.operator == 0 else None)
-    single = roofline(w, avg_ms, peaks, peaks_src, args.operator,
-                      traffic=NCU_TRAFFIC.get(w.name) if args.operator == 0 else None)
-    single["timed"] = "CG applies of the single-design loop (one design alone)"
+    kern = operator_kernel(args.operator, w.nx)
+    large = hbm_roofline(operator_kernel(args.operator, lw.nx) + ", CG apply", lw,
+                         operator_bytes(lw), large_operator(topo, stream, flush, args.operator),
+                         1.0, peaks, peaks_src,
+                         traffic=NCU_TRAFFIC.get(lw.name) if args.operator == 0 else None)
+    large["timed"] = "20 back-to-back CG applies, CUDA events, inputs above L2"
+    single = hbm_roofline(kern + ", CG apply", w, operator_bytes(w), avg_ms, 1.0, peaks,
+                          peaks_src,
+                          traffic=NCU_TRAFFIC.get(w.name) if args.operator == 0 else None)
+    single["timed"] = "CG applies of the single-design loop (one design alone, 2.9 MB: L2-resident)"
     single["launches"] = prof_n
+    cg_apply = None
     if batched and batch_op_units > 0:
-        # design-launch units: the flops of the timed launches over their
+        # design-launch units: the bytes of the timed launches over their
         # summed duration (each launch covered the designs still iterating)
-        main = roofline(w, batch_op_ms / batch_op_units, peaks, peaks_src, args.operator)
-        main["designs_per_launch"] = "varies (designs still iterating)"
-        main["avg_launch_us"] = None
-        main["timed"] = ("every CG apply of the timed batched steps, CUDA events on the "
-                         "library's stream; flops counted per design the launch advanced")
-        main["design_launches"] = batch_op_units
-        main["total_ms"] = batch_op_ms
-    else:
-        main = single
+        cg_apply = hbm_roofline(kern + ", CG apply", w, operator_bytes(w),
+                                batch_op_ms / batch_op_units, 1.0, peaks, peaks_src)
+        cg_apply.update({"designs_per_launch": "varies (designs still iterating); figures per "
+                                              "design-launch",
+                         "avg_launch_us": None,
+                         "timed": "every CG apply of the timed batched steps, CUDA events on the "
+                                  "library's stream; bytes counted per design the launch advanced",
+                         "design_launches": batch_op_units, "total_ms": batch_op_ms})
+    main = cg_apply or single
+    if batched and cheb_units > 0:
+        # the dominant kernel of the batched step: the finest-level Chebyshev
+        # smoothing step (operator + smoothing epilogue)
+        main = hbm_roofline(kern + " with the Chebyshev-step epilogue", w,
+                            cheb_bytes / cheb_units, cheb_ms / cheb_units, 1.0, peaks, peaks_src)
+        main.update({"designs_per_launch": "varies (designs still iterating); figures per "
+                                          "design-launch",
+                     "avg_launch_us": None,
+                     "bytes_rule": "per node 60 B (x stored) or 72 B (x added), per element 4 B",
+                     "timed": "every finest-level Chebyshev step of the timed batched steps, CUDA "
+                              "events on the library's stream; bytes counted per design the "
+                              "launch advanced",
+                     "design_launches": cheb_units, "total_ms": cheb_ms})
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(w)
@@ -556,12 +641,14 @@ def main():
                   "rel_residual_max": float(max(r[2] for r in recs)),
                   "compliance_design0": recs[0][3]},
         "fp64_jacobi_pcg": fp64,
-        # the CG apply (operator fused with p.Ap): over the timed batched
-        # steps, alone for one design, and alone on the 320x160x160 grid
+        "same_batch": same_batch,
+        # the dominant kernel of the timed steps (finest-level Chebyshev step),
+        # the CG apply (operator fused with p.Ap) over the timed batched steps,
+        # alone for one design, and alone on the 320x160x160 grid
         "roofline": main,
+        "roofline_cg_apply": cg_apply,
         "roofline_single": single,
-        "roofline_large": dict(large, timed="20 back-to-back applies, CUDA events, inputs "
-                                            "above L2"),
+        "roofline_large": large,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem * B,
                 "d2h_bytes_per_step": (8 * w.n_elem + 8) * B},
@@ -569,11 +656,13 @@ def main():
         "clocks": clk.summary(),
         "wall_s": wall,
     }
-    print(json.dumps(line), flush=True)
     if pool is not None:
         pool.shutdown()
     for m in meshes:
         m.close()
+    if args.serving and ws == 1:
+        line["serving"] = serving_summary()
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

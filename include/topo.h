@@ -178,10 +178,15 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
  * now with gmg_levels / smooth_degree as in topo_solve_opts) shares one device
  * arena, design b at a fixed stride from design 0.  Each out[b] is an ordinary
  * mesh (every call works on it, topo_free frees it; the arena goes with the
- * last one).  topo_solve_many on exactly the group's meshes (any order), with
- * FP32 precision, the multigrid preconditioner and the group's gmg_levels and
- * smooth_degree, solves them as one batch: one kernel launch per step for all
- * designs, FP64 refinement in lockstep (a design that has converged sits out).
+ * last one).  topo_solve_many on exactly the group's meshes (any order)
+ * solves them as one batch (one kernel launch per step for all designs,
+ * FP64 refinement in lockstep, a design that has converged sits out) with
+ *   - FP32 precision and the multigrid preconditioner with the group's
+ *     gmg_levels and smooth_degree, or
+ *   - the Jacobi preconditioner in FP32 (inside FP64 refinement) or FP64
+ *     (the plain FP64 Jacobi-PCG path; its FP64 CG vectors are allocated
+ *     for the whole group on first use, at the group stride);
+ * other options solve the meshes one by one on their own streams.
  * Results equal the one-at-a-time solves up to FP rounding order. */
 topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const topo_params* prm,
                               void* stream, int n_designs, int gmg_levels, int smooth_degree,
@@ -421,6 +426,17 @@ long long topo_footprint_bytes(int nx, int ny, int nz, const topo_solve_opts* op
 topo_status topo_profile_enable(topo_mesh* m, int enable);
 topo_status topo_profile_read(topo_mesh* m, double* total_ms, long long* launches,
                               long long* all_launches, int reset);
+/* With timing enabled, the library also records CUDA events around every
+ * finest-level Chebyshev smoothing step of the multigrid V-cycle (the
+ * operator kernel with the smoothing epilogue; mesh groups: design 0 holds
+ * the batch's timing).  Returns (and with reset != 0 zeroes) their summed
+ * duration, the number of design-launches they covered (a batched launch
+ * counts once per design it advanced) and the algorithmic bytes those
+ * launches moved: per node 60 B when the step stores x, 72 B when it adds to
+ * it (direction and residual read, residual and new direction written, x),
+ * plus 4 B per element (the modulus).  Cites Eq. (2) (K u). */
+topo_status topo_profile_read_smoother(topo_mesh* m, double* total_ms, long long* launches,
+                                       double* bytes, int reset);
 
 /* Element sensitivities (as topo_sensitivity) and the element-form
  * compliance (as topo_compliance_energy) of a given displacement, for
@@ -500,6 +516,18 @@ topo_status topo_server_close(topo_server* s, int design);
 topo_status topo_server_stats(const topo_server* s, long long* bytes_in_use, long long* peak_bytes,
                               int* active, int* waiting);
 void topo_server_free(topo_server* s);
+
+/* Fault injection for tests of the failure path (no counterpart in the
+ * paper).  count = 1 arms the mesh so that the next launch of its
+ * TMA-staged FP32 operator kernel (the default operator on grids with
+ * nx < 150) runs one bounded device-side wait on a barrier that nothing ever
+ * completes, with a short poll limit: the wait runs out, the kernel records a
+ * timeout, and the solve that launched it ends with TOPO_ERR_TIMEOUT,
+ * detail TOPO_FAIL_TIMEOUT (in a mesh group: that design only).  The
+ * operator's own data transfers are not touched, so the GPU context and the
+ * mesh stay usable; the next solve starts with the flag cleared.  count = 0
+ * disarms.  Synchronises the mesh's stream. */
+topo_status topo_debug_inject_timeout(topo_mesh* m, int count);
 
 /* Release everything the mesh holds (NULL-safe). */
 void topo_free(topo_mesh* m);

@@ -793,7 +793,15 @@ float gmg_first_direction(const Gmg& g, float** d0) {
 cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
                        cudaStream_t s, long long* launches, const Bat& bt, const Red* zdot,
-                       bool d0_ready) {
+                       bool d0_ready, GmgProf* prof) {
+  // event pair around a finest-level Chebyshev step (prof given and room left)
+  auto mark = [&](int l, bool after, bool store) -> cudaError_t {
+    if (!prof || l != 0 || prof->n >= prof->cap) return cudaSuccess;
+    const cudaError_t e =
+        cudaEventRecordWithFlags(prof->ev[2 * prof->n + (after ? 1 : 0)], s, cudaEventRecordExternal);
+    if (after) prof->store[prof->n++] = store ? 1 : 0;
+    return e;
+  };
   const ChebCoef cc = cheb_coef(g.lam_max, g.lam_ratio, g.degree);
   const int m = g.degree;
   const int nl = (int)g.lv.size();
@@ -820,7 +828,9 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     for (int k = 1; k < m; ++k) {
       EpiChebStep ep{L.r, k == 1 ? B(l) : L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
                      k == 1 ? EpiChebStep::kXStore : EpiChebStep::kXAdd};
+      GCK(mark(l, false, false));
       GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
+      GCK(mark(l, true, ep.xmode == EpiChebStep::kXStore));
       ++*launches;
     }
     GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s, bt));
@@ -880,7 +890,9 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
       } else {
         EpiChebStep ep{L.r, L.r, L.dv[k & 1], X(l), L.dinv, cc.c1[k], cc.c2[k],
                        k == 1 ? EpiChebStep::kXAddPrev : EpiChebStep::kXAdd};
+        GCK(mark(l, false, false));
         GCK(level_op(L.dv[(k - 1) & 1], L, k0f, mcf, ep, done, errflag, s, bt));
+        GCK(mark(l, true, false));
       }
       ++*launches;
     }

@@ -65,6 +65,18 @@ cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, dou
 cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<float>& k0f,
                       const K0<double>& k0d, cudaStream_t s, long long* launches,
                       const Bat& bt = Bat{});
+// Timing of the finest level's Chebyshev steps (the k_modal_*<EpiChebStep>
+// launches of level 0): a V-cycle given one records an event pair around each
+// of them (ev[2 q], ev[2 q + 1], q < cap, external events: also inside stream
+// capture) and, per recorded launch, whether it stores x (kXStore) or adds to
+// it (the two move different bytes).
+struct GmgProf {
+  cudaEvent_t* ev = nullptr;
+  int cap = 0;
+  int n = 0;                  // launches recorded
+  unsigned char store[16] = {};
+};
+
 // x = V(b) on level 0 (x, b: fine-level vectors); every kernel returns at once
 // when *done is set.
 // mcf != nullptr: smoother passes use the modal operator kernel
@@ -75,7 +87,8 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
 cudaError_t gmg_vcycle(Gmg& g, const float* b, float* x, const K0<float>& k0f,
                        const ModalCoef<float>* mcf, const int* done, int* errflag,
                        cudaStream_t s, long long* launches, const Bat& bt = Bat{},
-                       const Red* zdot = nullptr, bool d0_ready = false);
+                       const Red* zdot = nullptr, bool d0_ready = false,
+                       GmgProf* prof = nullptr);
 // Where a V-cycle's first finest-level Chebyshev direction goes (*d0) and its
 // scale 1/theta, for a caller that forms it (D^-1 of the finest level is the
 // one the hierarchy was set up with); 0 when the finest level is not smoothed.

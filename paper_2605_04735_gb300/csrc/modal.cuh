@@ -315,6 +315,17 @@ __global__ void __launch_bounds__(kModalTX* TY)
     tma_prefetch_desc(&emap);
     if (NA > 0) tma_prefetch_desc(&amap0);
     if (NA > 1) tma_prefetch_desc(&amap1);
+    // Fault-injection hook (errflag[1] == 1, set by topo_debug_inject_timeout):
+    // one CTA of the design runs one bounded wait on a barrier that nothing
+    // ever completes (no copy is issued on it), with a 64-poll limit, so the
+    // wait runs out and records a timeout the way a lost transfer would.
+    // Nothing is in flight on that barrier; the stage copies are unaffected.
+    if (errflag != nullptr && atomicCAS(errflag + 1, 1, 0) == 1) {
+      __shared__ uint64_t never_bar;
+      mbar_init(&never_bar, 1);
+      fence_mbar_init();
+      mbar_wait_bounded(&never_bar, 0u, errflag, 64u);
+    }
   }
   __syncthreads();
   // stage t: node plane kb-1+t, element layer kb-2+t and, once that plane

@@ -180,6 +180,13 @@ struct topo_mesh {
   std::vector<cudaEvent_t> ev;
   double prof_ms = 0.0;
   long long prof_launches = 0;
+  // finest-level Chebyshev steps of the V-cycle (profiling): event pairs,
+  // kChebSlots per CG iteration; per slot whether the step stores x; totals
+  std::vector<cudaEvent_t> evc;
+  int cheb_slots = 0;
+  unsigned char cheb_store[16] = {};
+  double profc_ms = 0.0, profc_bytes = 0.0;
+  long long profc_launches = 0;
   long long launches = 0;  // every kernel this mesh launched
 
   // captured CG chunks, keyed by (kind, iterations, profiling)
@@ -217,6 +224,10 @@ struct MeshGroup {
   int* d_ids = nullptr;    // nb: their device copy
   void* stage = nullptr;   // batched host<->device transfers of densities / sensitivities
   size_t stage_bytes = 0;
+  // FP64 inner-CG vectors of every design (batched FP64 Jacobi-PCG), made on
+  // first use: design b's at arena64 + b * S, so they keep the group stride
+  char* arena64 = nullptr;
+  long long arena64_bytes = 0;
   int gmg_levels = -1, gmg_degree = -1;
   topo_params prm{};
 };
@@ -332,11 +343,52 @@ topo_status ensure_fp64_inner(topo_mesh* m) {
   return TOPO_OK;
 }
 
+constexpr int kChebSlots = 16;  // finest-level Chebyshev steps timed per V-cycle (at most)
+
 topo_status ensure_profile_events(topo_mesh* m, int n) {
   while ((int)m->ev.size() < 2 * n) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     m->ev.push_back(e);
+  }
+  while ((int)m->evc.size() < 2 * kChebSlots * n) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    m->evc.push_back(e);
+  }
+  return TOPO_OK;
+}
+
+// V-cycle timing hook for CG iteration c of a chunk (nullptr when not profiling)
+GmgProf* cheb_prof(topo_mesh* m, bool profile, int c, GmgProf& gp) {
+  if (!profile) return nullptr;
+  gp = GmgProf{};
+  gp.ev = m->evc.data() + 2 * kChebSlots * c;
+  gp.cap = kChebSlots;
+  return &gp;
+}
+
+// after capturing one V-cycle with the hook: the per-iteration slot pattern
+void cheb_prof_done(topo_mesh* m, const GmgProf* gp) {
+  if (!gp) return;
+  m->cheb_slots = gp->n;
+  for (int q = 0; q < gp->n; ++q) m->cheb_store[q] = gp->store[q];
+}
+
+// Add the timed Chebyshev steps of CG iteration c of the last chunk, which
+// advanced `designs` designs: durations and algorithmic bytes (per node: the
+// direction and residual read, r and the new direction written, x written
+// (store) or read and written (add); per element the modulus).
+topo_status cheb_prof_collect(topo_mesh* m, int c, int designs) {
+  const double nn = (double)(m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  const double ne = (double)m->d.nx * m->d.ny * m->d.nz;
+  for (int q = 0; q < m->cheb_slots; ++q) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m->evc[2 * (kChebSlots * c + q)],
+                            m->evc[2 * (kChebSlots * c + q) + 1]));
+    m->profc_ms += ms;
+    m->profc_launches += designs;
+    m->profc_bytes += designs * ((m->cheb_store[q] ? 60.0 : 72.0) * nn + 4.0 * ne);
   }
   return TOPO_OK;
 }
@@ -384,8 +436,11 @@ topo_status enqueue_iters(topo_mesh* m, int kind, int count, bool profile) {
                                          d0 ? m->dinv32 : nullptr, m->nvec,
                                          red_of(m, FIN_RR_ONLY), false, s, Bat{}, th));
           const Red zr = red_of(m, FIN_RZ_BETA);
+          GmgProf gp;
+          GmgProf* gpp = cheb_prof(m, profile, c, gp);
           CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s,
-                        &m->launches, Bat{}, &zr, d0 != nullptr));
+                        &m->launches, Bat{}, &zr, d0 != nullptr, gpp));
+          cheb_prof_done(m, gpp);
         }
         LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s));
         break;
@@ -649,6 +704,7 @@ topo_status task_step(SolveTask& t) {
       CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
       m->prof_ms += ms;
       m->prof_launches += 1;
+      if (t.kind == IK_GMG32) CKS(cheb_prof_collect(m, c, 1));
     }
   }
   if (!h.done) {
@@ -960,8 +1016,9 @@ void topo_free(topo_mesh* m) {
                   m->tr_counts, m->tr_off, m->tr_scratch, m->tr_tris};
   MeshGroup* G = m->group;
   auto in_arena = [&](void* p) {
-    return G && static_cast<char*>(p) >= G->arena &&
-           static_cast<char*>(p) < G->arena + (long long)G->nb * G->S;
+    const char* c = static_cast<char*>(p);
+    return G && ((c >= G->arena && c < G->arena + (long long)G->nb * G->S) ||
+                 (G->arena64 && c >= G->arena64 && c < G->arena64 + G->arena64_bytes));
   };
   for (void* p : ptrs)
     if (p && !in_arena(p)) cudaFree(p);
@@ -973,6 +1030,7 @@ void topo_free(topo_mesh* m) {
     if (--G->refs == 0) {
       for (auto& kv : G->graphs) cudaGraphExecDestroy(kv.second.exec);
       if (G->arena) cudaFree(G->arena);
+      if (G->arena64) cudaFree(G->arena64);
       if (G->h_sc) cudaFreeHost(G->h_sc);
       if (G->h_flag) cudaFreeHost(G->h_flag);
       if (G->h_next) cudaFreeHost(G->h_next);
@@ -987,6 +1045,7 @@ void topo_free(topo_mesh* m) {
   if (m->oc_host) cudaFreeHost(m->oc_host);
   if (m->ev_poll) cudaEventDestroy(m->ev_poll);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : m->evc) cudaEventDestroy(e);
   if (m->ev_in) cudaEventDestroy(m->ev_in);
   if (m->ev_out) cudaEventDestroy(m->ev_out);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -1590,26 +1649,44 @@ int live_bucket(int n, int nb) {
   return std::min(w, nb);
 }
 
-// bt: the designs the chunk covers (all of them, or the compacted list)
-topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile, const Bat& bt) {
+// bt: the designs the chunk covers (all of them, or the compacted list);
+// kind: IK_GMG32, IK_JAC32 or IK_JAC64 (the single-design iterations of
+// enqueue_iters with the design as a grid dimension)
+topo_status group_enqueue_iters(MeshGroup* G, int kind, int count, bool profile, const Bat& bt) {
   topo_mesh* m = G->meshes[0];
   cudaStream_t s = m->stream;
   const int* done = &m->sc->done;
   for (int c = 0; c < count; ++c) {
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c], s, cudaEventRecordExternal));
-    LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
-                              red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
+    if (kind == IK_JAC64)
+      LK(m, launch_apply<double>(m->p64, m->q64, m->E64, nullptr, m->d, m->k0d, MCD(m),
+                                 red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
+    else
+      LK(m, launch_apply<float>(m->p32, m->q32, m->E32, nullptr, m->d, m->k0f, MCF(m),
+                                red_of(m, FIN_ALPHA), APPLY_DOT, done, m->flags + 1, s, bt));
     if (profile) CK(cudaEventRecordWithFlags(m->ev[2 * c + 1], s, cudaEventRecordExternal));
-    {  // the update also forms the V-cycle's first direction; z = V(r), with
-       // r . z (beta) fused into the V-cycle's last smoothing step
+    if (kind == IK_JAC64) {
+      LK(m, launch_pcg_update<double>(m->x64, m->s64, m->z64, m->p64, m->q64, m->dinv64,
+                                      m->nvec, red_of(m, FIN_UPDATE), true, s, bt));
+      LK(m, launch_pcg_direction<double>(m->p64, m->z64, m->nvec, m->sc, s, bt));
+      continue;
+    }
+    if (kind == IK_JAC32) {
+      LK(m, launch_pcg_update<float>(m->x32, m->r32, m->z32, m->p32, m->q32, m->dinv32, m->nvec,
+                                     red_of(m, FIN_UPDATE), true, s, bt));
+    } else {  // the update also forms the V-cycle's first direction; z = V(r), with
+              // r . z (beta) fused into the V-cycle's last smoothing step
       float* d0 = nullptr;
       const float th = gmg_first_direction(m->gmg, &d0);
       LK(m, launch_pcg_update<float>(m->x32, m->r32, d0 ? d0 : m->z32, m->p32, m->q32,
                                      d0 ? m->dinv32 : nullptr, m->nvec, red_of(m, FIN_RR_ONLY),
                                      false, s, bt, th));
       const Red zr = red_of(m, FIN_RZ_BETA);
+      GmgProf gp;
+      GmgProf* gpp = cheb_prof(m, profile, c, gp);
       CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches,
-                    bt, &zr, d0 != nullptr));
+                    bt, &zr, d0 != nullptr, gpp));
+      cheb_prof_done(m, gpp);
     }
     LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
   }
@@ -1619,16 +1696,17 @@ topo_status group_enqueue_iters(MeshGroup* G, int count, bool profile, const Bat
 // One chunk of CG iterations over `n` designs: all of the group (n == nb)
 // or the first n entries of G->d_ids (already on the device).  One graph per
 // (chunk length, profiling, n), so n takes few values (live_bucket).
-topo_status group_run_iters(MeshGroup* G, int count, bool profile, int n) {
+topo_status group_run_iters(MeshGroup* G, int kind, int count, bool profile, int n) {
   topo_mesh* m = G->meshes[0];
   const bool all = n >= G->nb;
   const Bat bt{all ? G->nb : n, G->S, all ? nullptr : G->d_ids, G->nb};
-  const long long key = (long long)count | ((long long)profile << 16) | ((long long)bt.nb << 20);
+  const long long key = (long long)count | ((long long)profile << 16) | ((long long)bt.nb << 20) |
+                        ((long long)kind << 40);
   auto it = G->graphs.find(key);
   if (it == G->graphs.end()) {
     const long long l0 = m->launches;
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    const topo_status st = group_enqueue_iters(G, count, profile, bt);
+    const topo_status st = group_enqueue_iters(G, kind, count, profile, bt);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (st != TOPO_OK || e != cudaSuccess) {
@@ -1651,21 +1729,68 @@ topo_status group_run_iters(MeshGroup* G, int count, bool profile, int n) {
   return TOPO_OK;
 }
 
+// The FP64 inner-CG vectors of every design of the group in one arena at the
+// group stride (x64, s64, z64, p64, q64, dinv64 of design b at arena64 +
+// b * S + q * vb).  A design that already had its own (a single-design FP64
+// solve) gives them up: its stream is drained and its captured graphs, which
+// hold the old addresses, are dropped first.
+topo_status ensure_group_fp64(MeshGroup* G) {
+  if (G->arena64) return TOPO_OK;
+  topo_mesh* m0 = G->meshes[0];
+  const long long vb = (m0->nvec * (long long)sizeof(double) + 255) / 256 * 256;
+  if (6 * vb > G->S) return TOPO_ERR_INVALID;  // cannot happen: the region holds more
+  const long long bytes = (long long)(G->nb - 1) * G->S + 6 * vb;
+  void* a = nullptr;
+  if (cudaMalloc(&a, (size_t)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return TOPO_ERR_OOM;
+  }
+  G->arena64 = static_cast<char*>(a);
+  G->arena64_bytes = bytes;
+  CK(cudaMemsetAsync(a, 0, (size_t)bytes, m0->stream));
+  for (int b = 0; b < G->nb; ++b) {
+    topo_mesh* m = G->meshes[b];
+    double** v[6] = {&m->x64, &m->s64, &m->z64, &m->p64, &m->q64, &m->dinv64};
+    if (m->x64) {
+      CK(cudaStreamSynchronize(m->stream));
+      clear_graphs(m);
+      for (double** q : v) {
+        if (*q) cudaFree(*q);
+        m->bytes -= m->nvec * (long long)sizeof(double);
+      }
+    }
+    for (int q = 0; q < 6; ++q)
+      *v[q] = reinterpret_cast<double*>(G->arena64 + (long long)b * G->S + q * vb);
+    m->bytes += 6 * vb;
+    m->diag64 = false;
+  }
+  // every design's stream after the fill (design 0's stream runs the batch)
+  CK(cudaEventRecord(m0->ev_in, m0->stream));
+  for (int b = 1; b < G->nb; ++b) CK(cudaStreamWaitEvent(G->meshes[b]->stream, m0->ev_in, 0));
+  return TOPO_OK;
+}
+
 // Can these meshes (in any order) be solved as their group, with these options?
 MeshGroup* batchable(topo_mesh* const* meshes, int n, const topo_solve_opts& o) {
   if (n < 2) return nullptr;
   MeshGroup* G = meshes[0]->group;
   if (!G || G->nb != n) return nullptr;
-  if (o.precision != TOPO_PREC_FP32 || o.precond != TOPO_PRECOND_GMG) return nullptr;
-  if (o.gmg_levels != G->gmg_levels || o.smooth_degree != G->gmg_degree) return nullptr;
+  const bool gmg = o.precond == TOPO_PRECOND_GMG;
+  if (gmg ? o.precision != TOPO_PREC_FP32
+          : (o.precond != TOPO_PRECOND_JACOBI ||
+             (o.precision != TOPO_PREC_FP32 && o.precision != TOPO_PREC_FP64)))
+    return nullptr;
+  if (o.residual != TOPO_RESIDUAL_DWORD && o.residual != TOPO_RESIDUAL_FP64) return nullptr;
+  if (gmg && (o.gmg_levels != G->gmg_levels || o.smooth_degree != G->gmg_degree)) return nullptr;
   if (!(o.rtol > 0.0) || o.max_iter < 1 || o.max_outer < 1 || o.check_every < 1 ||
       o.check_every > 1024)
     return nullptr;
   for (int a = 0; a < n; ++a) {
     topo_mesh* m = meshes[a];
-    if (m->group != G || !m->use_modal || m->mcf.form != G->meshes[0]->mcf.form ||
-        !m->gmg.arena || !m->gmg_built || m->gmg_levels_req != G->gmg_levels ||
-        m->gmg_degree != G->gmg_degree)
+    if (m->group != G || !m->use_modal || m->mcf.form != G->meshes[0]->mcf.form)
+      return nullptr;
+    if (gmg && (!m->gmg.arena || !m->gmg_built || m->gmg_levels_req != G->gmg_levels ||
+                m->gmg_degree != G->gmg_degree))
       return nullptr;
   }
   for (topo_mesh* m : G->meshes)
@@ -1687,24 +1812,34 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     CK(cudaEventRecord(G->meshes[b]->ev_in, G->meshes[b]->stream));
     CK(cudaStreamWaitEvent(s, G->meshes[b]->ev_in, 0));
   }
+  const int kind = o.precond == TOPO_PRECOND_GMG      ? IK_GMG32
+                   : o.precision == TOPO_PREC_FP64    ? IK_JAC64
+                                                      : IK_JAC32;
+  if (kind == IK_JAC64) CKS(ensure_group_fp64(G));
   // setup for the current moduli (all designs at once)
   bool need_diag = false, need_gmg = false;
   for (topo_mesh* q : G->meshes) {
-    need_diag |= !q->diag32;
-    need_gmg |= !q->gmg.ready;
+    need_diag |= kind == IK_JAC64 ? !q->diag64 : !q->diag32;
+    need_gmg |= kind == IK_GMG32 && !q->gmg.ready;
   }
-  if (need_diag || need_gmg) {
+  if (kind == IK_JAC64 && need_diag) {
+    LK(m, launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, s, bt));
+    for (topo_mesh* q : G->meshes) q->diag64 = true;
+  } else if (need_diag || need_gmg) {
     LK(m, launch_diag_inv<float>(m->dinv32, m->E32, m->d, m->k0f, s, bt));
-    CK(gmg_setup(m->gmg, m->E32, m->dinv32, m->k0f, m->k0d, s, &m->launches, bt));
-    for (topo_mesh* q : G->meshes) {
-      q->diag32 = true;
-      q->gmg.ready = true;
-      q->gmg.lv[0].E = q->E32;  // each design's own hierarchy now describes its moduli
-      q->gmg.lv[0].dinv = q->dinv32;
+    for (topo_mesh* q : G->meshes) q->diag32 = true;
+    if (kind == IK_GMG32) {
+      CK(gmg_setup(m->gmg, m->E32, m->dinv32, m->k0f, m->k0d, s, &m->launches, bt));
+      for (topo_mesh* q : G->meshes) {
+        q->gmg.ready = true;
+        q->gmg.lv[0].E = q->E32;  // each design's own hierarchy now describes its moduli
+        q->gmg.lv[0].dinv = q->dinv32;
+      }
     }
   }
   for (topo_mesh* q : G->meshes) q->solved = false;
-  const bool prof = m->prof;  // design 0 holds the batch's operator timing
+  // design 0 holds the batch's FP32 operator timing
+  const bool prof = m->prof && kind != IK_JAC64;
   if (prof) CKS(ensure_profile_events(m, o.check_every));
   CK(cudaMemset2DAsync(m->flags + 1, (size_t)G->S, 0, sizeof(int), nb, s));
   if (o.warm_start) {
@@ -1759,8 +1894,11 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         running[b] = 0;
         continue;
       }
+      // FP64 inner CG: the final tolerance directly, with margin
       const double inner =
-          std::min(std::max(o.inner_rtol, kInnerMargin * o.rtol * fn / std::sqrt(rr)), 0.5);
+          kind == IK_JAC64
+              ? std::min(std::max(0.5 * o.rtol * fn / std::sqrt(rr), 1e-15), 0.5)
+              : std::min(std::max(o.inner_rtol, kInnerMargin * o.rtol * fn / std::sqrt(rr)), 0.5);
       expect[b] = inner * rel[b];
       const bool dw = dword_residual(o, expect[b]);
       nx.skip_dword = dw ? 0 : 1;
@@ -1779,18 +1917,26 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
                   "Next mirrors the tail of PcgScalars");
     CK(cudaMemcpy2DAsync(&m->sc->rtol2_next, (size_t)G->S, G->h_next, sizeof(MeshGroup::Next),
                          sizeof(MeshGroup::Next), nb, cudaMemcpyHostToDevice, s));
-    // inner start: b = r / ||r|| in FP32, x = 0, z = V(r), p = z
+    // inner start: b = r / ||r|| in FP32 (FP64: b = r), x = 0, z = M^-1 r, p = z
     const int* done = &m->sc->done;
     LK(m, launch_set_max_iter(m->sc, -1, s, bt));
-    LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s, bt));
-    LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
-                                 red_of(m, FIN_INIT, -1.0), false, s, bt));
-    {
-      const Red zr = red_of(m, FIN_SET_RZ);
-      CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s, &m->launches,
-                    bt, &zr));
+    if (kind == IK_JAC64) {
+      LK(m, launch_pcg_init<double>(m->r64, m->x64, m->s64, m->z64, m->p64, m->dinv64, m->nvec,
+                                    red_of(m, FIN_INIT, -1.0), true, s, bt));
+    } else {
+      LK(m, launch_narrow_scaled(m->b32, m->r64, m->nvec, m->sc, s, bt));
+      if (kind == IK_JAC32) {
+        LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, m->dinv32, m->nvec,
+                                     red_of(m, FIN_INIT, -1.0), true, s, bt));
+      } else {
+        LK(m, launch_pcg_init<float>(m->b32, m->x32, m->r32, m->z32, m->p32, nullptr, m->nvec,
+                                     red_of(m, FIN_INIT, -1.0), false, s, bt));
+        const Red zr = red_of(m, FIN_SET_RZ);
+        CK(gmg_vcycle(m->gmg, m->r32, m->z32, m->k0f, MCF(m), done, m->flags + 1, s,
+                      &m->launches, bt, &zr));
+        LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
+      }
     }
-    LK(m, launch_pcg_direction<float>(m->p32, m->z32, m->nvec, m->sc, s, bt));
     std::vector<int> before(nb, -1), at(nb, 0);
     std::vector<char> iterating(running);  // designs not done (first chunk: taking part)
     for (int chunk = 0;; ++chunk) {
@@ -1808,7 +1954,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
         for (int q = n_live; q < width; ++q) G->h_ids[q] = idle;
         CK(cudaMemcpyAsync(G->d_ids, G->h_ids, sizeof(int) * width, cudaMemcpyHostToDevice, s));
       }
-      CKS(group_run_iters(G, o.check_every, prof, width));
+      CKS(group_run_iters(G, kind, o.check_every, prof, width));
       CKS(group_read_scalars(G));
       bool all_done = true, progress = false;
       for (int b = 0; b < nb; ++b) {
@@ -1827,6 +1973,7 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
           CK(cudaEventElapsedTime(&ms, m->ev[2 * c], m->ev[2 * c + 1]));
           m->prof_ms += ms;
           m->prof_launches += active;
+          if (kind == IK_GMG32) CKS(cheb_prof_collect(m, c, active));
         }
         for (int b = 0; b < nb; ++b) at[b] = G->h_sc[b].iter;
       }
@@ -1846,7 +1993,10 @@ topo_status group_solve(MeshGroup* G, const topo_solve_opts& o, topo_solve_info*
     }
     // u += ||r|| x, then the FP64 residual, for the designs that took part
     // (those that sat out keep u and their residual)
-    LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s, bt));
+    if (kind == IK_JAC64)
+      LK(m, launch_accumulate<double>(m->u64, m->x64, m->nvec, m->sc, false, s, bt));
+    else
+      LK(m, launch_accumulate<float>(m->u64, m->x32, m->nvec, m->sc, true, s, bt));
     // double-word for the designs whose residual cannot end their solve,
     // FP64 for the others: one launch each, skipping the designs of the other
     bool any_dw = false, any_64 = false;
@@ -2432,6 +2582,29 @@ topo_status topo_set_stream(topo_mesh* m, void* stream) {
 topo_status topo_profile_enable(topo_mesh* m, int enable) {
   if (!m) return TOPO_ERR_INVALID;
   m->prof = enable != 0;
+  return TOPO_OK;
+}
+
+topo_status topo_debug_inject_timeout(topo_mesh* m, int count) {
+  if (!m || count < 0 || count > 1) return TOPO_ERR_INVALID;
+  Fence f(m);
+  if (f.st != TOPO_OK) return f.st;
+  CK(cudaMemcpyAsync(m->flags + 2, &count, sizeof(int), cudaMemcpyHostToDevice, m->stream));
+  CK(cudaStreamSynchronize(m->stream));
+  return TOPO_OK;
+}
+
+topo_status topo_profile_read_smoother(topo_mesh* m, double* total_ms, long long* launches,
+                                       double* bytes, int reset) {
+  if (!m) return TOPO_ERR_INVALID;
+  if (total_ms) *total_ms = m->profc_ms;
+  if (launches) *launches = m->profc_launches;
+  if (bytes) *bytes = m->profc_bytes;
+  if (reset) {
+    m->profc_ms = 0.0;
+    m->profc_bytes = 0.0;
+    m->profc_launches = 0;
+  }
   return TOPO_OK;
 }
 

@@ -113,6 +113,9 @@ def lib():
             "topo_profile_enable": (i, [vp, i]),
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
+            "topo_debug_inject_timeout": (i, [vp, i]),
+            "topo_profile_read_smoother": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
+                                               C.POINTER(d), i]),
             "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
             "topo_set_density_many": (i, [vp, i, vp, sz, i]),
             "topo_compliance_many": (i, [vp, i, vp]),
@@ -516,6 +519,18 @@ class Mesh:
         _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(a), int(reset)),
                "topo_profile_read")
         return ms.value, n.value, a.value
+
+    def debug_inject_timeout(self, count: int = 1):
+        """Arm (1) or disarm (0) the test hook of topo_debug_inject_timeout."""
+        _check(lib().topo_debug_inject_timeout(self._h, int(count)), "topo_debug_inject_timeout")
+
+    def profile_read_smoother(self, reset=True):
+        """(summed ms of the timed finest-level Chebyshev steps, design-launches,
+        their algorithmic bytes)."""
+        ms, n, b = C.c_double(), C.c_longlong(), C.c_double()
+        _check(lib().topo_profile_read_smoother(self._h, C.byref(ms), C.byref(n), C.byref(b),
+                                                int(reset)), "topo_profile_read_smoother")
+        return ms.value, n.value, b.value
 
 
 class Server:

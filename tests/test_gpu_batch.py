@@ -249,3 +249,46 @@ def test_batched_io_on_separate_meshes_and_bad_input(topo):
     finally:
         for m in group:
             m.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])  # FP32 Jacobi-PCG + FP64 refinement; plain FP64
+@pytest.mark.parametrize("nx,ny,nz,bc,load", [
+    (40, 12, 10, I.BC_MBB, I.LOAD_EDGE_X0_TOP),
+    (33, 9, 7, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM),
+])
+def test_batched_jacobi_matches_single_solves_and_the_oracle(topo, precision, nx, ny, nz, bc,
+                                                             load):
+    """Jacobi-preconditioned solves of a whole mesh group run as one batch
+    (design 0 launches every kernel, the others none) and give each design's
+    single-solve result; the FP64 batch also after design 0 had solved alone
+    in FP64 with vectors of its own (they move into the group's FP64 arena)."""
+    opts = topo.default_opts(precision=precision, precond=topo.PRECOND_JACOBI, rtol=1e-10)
+    nb = 3
+    rhos = [I.density_cone_smoothed(nx, ny, nz, 90 + b) for b in range(nb)]
+    meshes = topo.create_batch(nb, nx, ny, nz, bc, load)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_density(r)
+        if precision == 0:  # design 0 first alone: its own FP64 vectors and graphs
+            meshes[0].solve(opts)
+            u_first = meshes[0].displacement()
+        for m in meshes:
+            m.profile_read(reset=True)
+        infos = topo.solve_many(meshes, opts)
+        launches = [m.profile_read(reset=True)[2] for m in meshes]
+        res = [(m.displacement(), m.compliance(), m.sensitivity()) for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    assert launches[0] > 0 and launches[1] == 0 and launches[2] == 0
+    for b in range(nb):
+        u, c, dc = res[b]
+        u1, c1, dc1, info1 = _alone(topo, nx, ny, nz, bc, load, rhos[b], opts)
+        assert infos[b].status == 0 and infos[b].rel_residual <= 1e-10
+        assert _rel(u, u1) <= 1e-8
+        assert c == pytest.approx(c1, rel=1e-9)
+        assert np.abs(dc - dc1).max() <= 1e-7 * np.abs(dc1).max()
+    if precision == 0:
+        assert _rel(res[0][0], u_first) <= 1e-8
+    P = fem.Problem(nx, ny, nz, bc, load, rhos[1])
+    assert _rel(res[1][0], P.solve()) <= 1e-8

@@ -1,13 +1,15 @@
-"""Full-size workloads the oracle cannot assemble (1.8 M and 8.3 M nodes):
-the oracle checks the GPU displacement through quantities it computes one
-node or one element at a time (the FP64 residual f - K u at sampled nodes,
-element energies at sampled elements), and the compliance identity.  On the
-192x96x96 cantilever the autograd gradient is also checked against central
-finite differences of GPU solves on 50 seeded elements."""
+"""Full-size workloads the oracle cannot factor (1.8 M and 8.3 M nodes): the
+oracle checks the GPU displacement with its own FP64 matrix-free operator
+(oracle/fullsize.c, pinned to the assembled K) on every DOF: the true
+relative residual over all free DOFs, the compliance identity, and every
+element's sensitivity recomputed from u.  On the 192x96x96 cantilever the
+autograd gradient is also checked against central finite differences of GPU
+solves on 50 seeded elements."""
 import numpy as np
 import pytest
 
 from oracle import fem
+from oracle import fullsize as FS
 from paper_2605_04735_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -25,14 +27,6 @@ def topo():
     return t
 
 
-def _sample_nodes(g, count, seed):
-    rng = np.random.default_rng(seed)
-    nodes = rng.choice(g.n_nodes, size=count, replace=False)
-    corners = [g.node(g.nx, 0, 0), g.node(g.nx, g.ny, g.nz), g.node(g.nx, g.ny // 2, 0),
-               g.node(1, 1, 1), g.node(g.nx // 2, g.ny // 2, g.nz // 2)]
-    return np.unique(np.concatenate([nodes, corners]))
-
-
 def _check_solution(topo, w, m, u, info):
     g = fem.Grid(w.nx, w.ny, w.nz)
     rho = w.density()
@@ -41,22 +35,19 @@ def _check_solution(topo, w, m, u, info):
     f = fem.load_vector(g, w.load)
     fixed = fem.fixed_dofs(g, w.bc)
     f[fixed] = 0.0
-    nodes = _sample_nodes(g, 300, 1)
-    Ku = fem.apply_at_nodes(g, E, k0, u, nodes)
-    r = (f.reshape(-1, 3)[nodes] - Ku)
-    r[fixed.reshape(-1, 3)[nodes]] = 0.0
-    # every sampled nodal residual is below the global target ||f - K u|| <= 1e-8 ||f||
-    assert np.abs(r).max() <= 1.05e-8 * np.linalg.norm(f)
+    # the oracle's own FP64 residual over every free DOF meets the target
+    rel = FS.rel_residual(g, E, k0, f, fixed, u)
+    assert rel <= 1.01e-8, rel
     c = m.compliance()
     assert abs(c - float(f @ u)) <= 1e-12 * c
     assert abs(m.compliance_energy() - c) <= 1e-7 * c
+    # every element's sensitivity (Eq. (3)) from u by the oracle
     dc = m.sensitivity()
-    elems = I.fd_elements(rho, 60, 7)
-    en = fem.element_energies_at(g, u, k0, elems)
-    ref = -3.0 * rho[elems].astype(np.float64) ** 2 * (1 - 1e-9) * en
+    ref = -3.0 * rho.astype(np.float64) ** 2 * (1 - 1e-9) * FS.element_energies(g, k0, u)
     # both FP64, different formulas: soft elements carry a cancellation floor ~1e-11 of max|dc|
-    assert np.all(np.abs(dc[elems] - ref) <= 1e-8 * np.abs(ref) + 1e-9 * np.abs(ref).max())
+    assert np.all(np.abs(dc - ref) <= 1e-8 * np.abs(ref) + 1e-9 * np.abs(ref).max())
     assert np.all(dc <= 0.0)
+    return {"rel_residual_oracle": rel, "c": c}
 
 
 def test_cantilever_voids_192x96x96_solution_and_fd_gradient(topo):
