@@ -90,3 +90,42 @@ def test_mbb_96x32x32_benchmark_group_against_the_direct_solution(topo):
         # refined to 1e-10: u as well
         assert et["rel_residual_oracle"] <= 1.01e-10
         assert et["err_u"] <= 1e-8 and et["err_c"] <= 1e-9 and et["err_dc"] <= 1e-7
+
+
+def test_cantilever_voids_192x96x96_against_the_cg_reference(topo):
+    """5.4 M DOFs: the oracle's direct solve would need a ~1.2 TB band, so its
+    reference is its own matrix-free FP64 Jacobi-PCG driven to the FP64
+    floor (true relative residual <= 1e-12, a few thousand iterations on the
+    host's cores)."""
+    w = I.WORKLOADS["cantilever_voids_192x96x96"]
+    rho = w.density()
+    g = fem.Grid(w.nx, w.ny, w.nz)
+    E = fem.simp_modulus(rho)
+    k0 = fem.element_stiffness(1.0, 0.3)
+    f = fem.load_vector(g, w.load)
+    fixed = fem.fixed_dofs(g, w.bc)
+    f[fixed] = 0.0
+    results = {}
+    with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load) as m:
+        m.set_density(rho)
+        for rtol in (1e-8, 1e-10):
+            info = m.solve(topo.default_opts(rtol=rtol, warm_start=int(rtol < 1e-8), max_outer=20))
+            assert info.status == 0 and info.rel_residual <= rtol
+            results[rtol] = (m.displacement(), m.compliance(), m.sensitivity(), info)
+    u_ref, it, rel = FS.cg(g, E, k0, f, fixed, rtol=1e-12)
+    assert rel <= 1e-12
+    c_ref = float(f @ u_ref)
+    dc_ref = -3.0 * rho.astype(np.float64) ** 2 * (1 - 1e-9) * FS.element_energies(g, k0, u_ref)
+    for rtol, (u, c, dc, info) in results.items():
+        e = {"rel_residual_oracle": FS.rel_residual(g, E, k0, f, fixed, u),
+             "err_u": float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)),
+             "err_c": float(abs(c - c_ref) / abs(c_ref)),
+             "err_dc": float(np.abs(dc - dc_ref).max() / np.abs(dc_ref).max()),
+             "c": c, "c_ref": c_ref}
+        print("ACCURACY " + json.dumps({"workload": w.name, "rtol": rtol, "iters": info.iters,
+                                        "outer": info.outer, "ref": "oracle CG",
+                                        "ref_iters": it, "ref_rel_residual": rel, **e}))
+        assert e["rel_residual_oracle"] <= 1.01 * rtol
+        assert e["err_c"] <= 1e-8 and e["err_dc"] <= 1e-6
+        if rtol <= 1e-10:
+            assert e["err_u"] <= 1e-8
