@@ -98,9 +98,15 @@ enum {
                                the library picks the FP32 kernel form per grid) */
   TOPO_OPERATOR_GATHER = 1, /* node-centric 27-node gather with the dense 24x24 k0 */
   TOPO_OPERATOR_MODAL_SINGLE = 2, /* modal, one element column per thread */
-  TOPO_OPERATOR_MODAL_PAIR = 3    /* modal, two element columns per thread in packed two-wide
+  TOPO_OPERATOR_MODAL_PAIR = 3,   /* modal, two element columns per thread in packed two-wide
                                      FP32 arithmetic, on FP32 grids with nx >= 65 (others fall
                                      back to one column) */
+  TOPO_OPERATOR_TENSOR = 4  /* the element products K0 U_e (Eq. (3)'s k_e = E_e k0) as TF32
+                               GEMMs on the tensor cores (tcgen05, accumulator in TMEM): the
+                               CG operator and FP32 residuals in three TF32 passes (FP32-level
+                               accuracy), the multigrid smoother's operator in one TF32 pass;
+                               FP64 kernels and grids too small for the tiles (ny < 6) keep
+                               the modal SIMT kernels */
 };
 
 enum {

@@ -12,6 +12,7 @@
 #include "gmg_tail.h"
 #include "kernels.h"
 #include "modal2.cuh"
+#include "modal_tc.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -779,7 +780,10 @@ template <class Epi>
 cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
                      const ModalCoef<float>* mcf, const Epi& ep, const int* done, int* errflag,
                      cudaStream_t s, const Bat& bt, const Red& red = Red{}) {
-  if (mcf) return launch_modal<float>(x, L.E, L.d, *mcf, ep, red, done, errflag, s, bt);
+  // the smoother's operator: one TF32 pass on the tensor-core form (a fixed
+  // approximation of the level operator is all a smoother needs)
+  if (mcf)
+    return launch_modal_any<1, float>(x, L.E, L.d, *mcf, k0f, ep, red, done, errflag, s, bt);
   if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
   return launch_stencil<float>(x, L.E, L.d, k0f, ep, red, done, errflag, s);
 }

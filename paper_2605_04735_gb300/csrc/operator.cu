@@ -11,6 +11,7 @@
 #include "modal.cuh"
 #include "modal2.cuh"
 #include "modal_dw.cuh"
+#include "modal_tc.cuh"
 #include "stencil.cuh"
 
 namespace topo {
@@ -116,12 +117,14 @@ cudaError_t launch_apply(const T* x, T* y, const T* E, const T* f, const Dims& d
   if (mc) {
     switch (mode) {
       case APPLY_PLAIN:
-        return launch_modal<T>(x, E, d, *mc, EpiApply<T, false>{y}, red, done, errflag, s, bt);
+        return launch_modal_any<3, T>(x, E, d, *mc, k0, EpiApply<T, false>{y}, red, done,
+                                      errflag, s, bt);
       case APPLY_DOT:
-        return launch_modal<T>(x, E, d, *mc, EpiApply<T, true>{y}, red, done, errflag, s, bt);
+        return launch_modal_any<3, T>(x, E, d, *mc, k0, EpiApply<T, true>{y}, red, done, errflag,
+                                      s, bt);
       default:
-        return launch_modal<T>(x, E, d, *mc, EpiResid<T>{y, f}, red, done, errflag, s, bt,
-                               energy);
+        return launch_modal_any<3, T>(x, E, d, *mc, k0, EpiResid<T>{y, f}, red, done, errflag,
+                                      s, bt, energy);
     }
   }
   if (energy) return cudaErrorInvalidValue;    // element energies: the modal kernels only

@@ -2559,14 +2559,22 @@ topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_dev
 }
 
 topo_status topo_set_operator(topo_mesh* m, int kind) {
-  if (!m || kind < TOPO_OPERATOR_MODAL || kind > TOPO_OPERATOR_MODAL_PAIR)
-    return TOPO_ERR_INVALID;
+  if (!m || kind < TOPO_OPERATOR_MODAL || kind > TOPO_OPERATOR_TENSOR) return TOPO_ERR_INVALID;
   const bool modal = (kind != TOPO_OPERATOR_GATHER);
-  const int form = kind == TOPO_OPERATOR_MODAL_SINGLE ? 1 : kind == TOPO_OPERATOR_MODAL_PAIR ? 2 : 0;
+  const int form = kind == TOPO_OPERATOR_MODAL_SINGLE ? 1
+                   : kind == TOPO_OPERATOR_MODAL_PAIR ? 2
+                   : kind == TOPO_OPERATOR_TENSOR     ? 3
+                                                      : 0;
   if (modal != m->use_modal || form != m->mcf.form) {
     CK(cudaSetDevice(m->dev));
     CK(cudaStreamSynchronize(m->stream));
     clear_graphs(m);  // the captured chunks hold the old kernels
+    if (m->group) {   // and so do the group's batched chunks
+      for (topo_mesh* q : m->group->meshes)
+        if (q) CK(cudaStreamSynchronize(q->stream));
+      for (auto& kv : m->group->graphs) cudaGraphExecDestroy(kv.second.exec);
+      m->group->graphs.clear();
+    }
     m->use_modal = modal;
     m->mcf.form = form;
   }

@@ -1,9 +1,10 @@
 """Small, self-contained drivers for profiler captures of the hot path.
 
-    python -m paper_2605_04735_gb300.profile_run apply <workload> [reps]
+    python -m paper_2605_04735_gb300.profile_run apply <workload> [reps] [operator]
         one mesh, density set, `reps` internal applications of the FP32
         operator (the CG apply with its fused p.Ap reduction) on a
-        non-default stream: the capture target of the operator kernel.
+        non-default stream: the capture target of the operator kernel
+        (operator: topo.OPERATOR_*, default the automatic modal form).
     python -m paper_2605_04735_gb300.profile_run apply64 <workload> [reps]
         the same with the FP64 operator.
     python -m paper_2605_04735_gb300.profile_run applydw <workload> [reps]
@@ -14,6 +15,7 @@
     python -m paper_2605_04735_gb300.profile_run simp <workload> [iters]
         `iters` SIMP iterations (solve, sensitivity, filter, OC update).
     python -m paper_2605_04735_gb300.profile_run batch <workload> [designs]
+        (an optional last argument selects the operator for these modes too)
         one mesh group of `designs` seeded designs (default 16) solved in
         lockstep twice (a warm-up and the captured step) through the batched
         entry points (densities, solve, compliances, sensitivities): the
@@ -37,6 +39,7 @@ def main(argv):
     mode = argv[0] if argv else "apply"
     name = argv[1] if len(argv) > 1 else "cantilever_voids_320x160x160"
     reps = int(argv[2]) if len(argv) > 2 else (1 if mode.startswith("apply") else 3)
+    op = int(argv[3]) if len(argv) > 3 else 0
     w = I.WORKLOADS[name]
     torch.cuda.set_device(0)
     s = torch.cuda.Stream()
@@ -46,6 +49,8 @@ def main(argv):
         rhos = [I.dataclasses.replace(w, seed=w.seed + b).density() for b in range(n)]
         opts = topo.default_opts(rtol=1e-8)
         meshes = topo.create_batch(n, w.nx, w.ny, w.nz, w.bc, w.load, stream=s, opts=opts)
+        for m in meshes:
+            m.set_operator(op)
         rho_dev = torch.from_numpy(np.stack(rhos)).cuda()
         dc_dev = torch.empty((n, w.nx * w.ny * w.nz), dtype=torch.float64, device="cuda")
         try:
@@ -61,6 +66,7 @@ def main(argv):
         print("ok", mode, name, n, max(i.iters for i in infos), max(i.outer for i in infos))
         return
     with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=s) as m:
+        m.set_operator(op)
         rho = w.density()
         if mode in ("apply", "apply64", "applydw"):
             m.set_density(rho)

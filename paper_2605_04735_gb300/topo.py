@@ -25,6 +25,7 @@ PREC_FP64, PREC_FP32, PREC_DWORD = 0, 1, 2
 RESIDUAL_DWORD, RESIDUAL_FP64 = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
 OPERATOR_MODAL, OPERATOR_GATHER, OPERATOR_MODAL_SINGLE, OPERATOR_MODAL_PAIR = 0, 1, 2, 3
+OPERATOR_TENSOR = 4
 
 
 class Params(C.Structure):
