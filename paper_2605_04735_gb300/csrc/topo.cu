@@ -802,6 +802,11 @@ struct ServerDesign {
   SolveTask task;
   ServerJob current;
   topo_solve_info info{};
+  // a job's densities travel through a pinned buffer without a host wait;
+  // their validity count arrives in h_bad with the solve's first scalars
+  float* pinned = nullptr;
+  int* h_bad = nullptr;
+  bool check_bad = false;
 };
 
 struct topo_server {
@@ -821,11 +826,43 @@ namespace {
 
 void server_release(topo_server* s, ServerDesign& d) {
   if (d.mesh) {
-    topo_free(d.mesh);
+    topo_free(d.mesh);  // synchronises the design's stream first
     d.mesh = nullptr;
     s->in_use -= d.footprint;
     --s->active;
   }
+  if (d.pinned) cudaFreeHost(d.pinned);
+  if (d.h_bad) cudaFreeHost(d.h_bad);
+  d.pinned = nullptr;
+  d.h_bad = nullptr;
+}
+
+// A job's densities onto its design's mesh without a host wait (the server's
+// form of topo_set_density): the values go through the design's pinned
+// buffer, Eq. (1) runs on the mesh's stream after the caller's earlier work,
+// and the count of invalid densities is copied to d.h_bad behind it, to be
+// read when the solve's first scalars have arrived.
+topo_status server_set_density(ServerDesign& d, const std::vector<float>& rho) {
+  topo_mesh* m = d.mesh;
+  const long long ne = (long long)m->d.nx * m->d.ny * m->d.nz;
+  std::memcpy(d.pinned, rho.data(), (size_t)ne * sizeof(float));
+  cudaStream_t s = m->stream;
+  CK(cudaSetDevice(m->dev));
+  CK(cudaEventRecord(m->ev_in, m->user));
+  CK(cudaStreamWaitEvent(s, m->ev_in, 0));
+  CK(cudaMemcpyAsync(m->rho_in, d.pinned, ne * sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(m->flags, 0, sizeof(int), s));
+  LK(m, launch_simp(m->rho_in, m->rho_g, m->E32, m->E64, m->d, m->prm.E0, m->prm.Emin,
+                    m->prm.penal, m->prm.h, m->flags, s));
+  CK(cudaMemcpyAsync(d.h_bad, m->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  m->diag32 = m->diag64 = false;
+  m->gmg.ready = false;
+  m->solved = false;
+  m->energy_fresh = false;
+  m->e_positive = m->prm.Emin > 0.0;
+  m->has_density = true;  // provisionally: d.check_bad settles it
+  d.check_bad = true;
+  return TOPO_OK;
 }
 
 // one pass over the server: admit, start, advance, retire; true if anything moved
@@ -836,7 +873,16 @@ bool server_step(topo_server* s) {
     ServerDesign& d = s->designs[*it];
     if (s->active < s->max_active && s->in_use + d.footprint <= s->budget) {
       topo_mesh* m = nullptr;
-      const topo_status st = topo_create_mesh(d.nx, d.ny, d.nz, d.bc, d.load, &s->prm, s->user, &m);
+      topo_status st = topo_create_mesh(d.nx, d.ny, d.nz, d.bc, d.load, &s->prm, s->user, &m);
+      if (st == TOPO_OK &&
+          (cudaMallocHost(&d.pinned, sizeof(float) * (size_t)d.nx * d.ny * d.nz) != cudaSuccess ||
+           cudaMallocHost(&d.h_bad, sizeof(int)) != cudaSuccess)) {
+        cudaGetLastError();
+        topo_free(m);
+        if (d.pinned) cudaFreeHost(d.pinned);
+        d.pinned = nullptr;
+        st = TOPO_ERR_OOM;
+      }
       if (st == TOPO_OK) {
         d.mesh = m;
         d.waiting = false;
@@ -874,7 +920,14 @@ bool server_step(topo_server* s) {
       cudaSetDevice(d.mesh->dev);
       const cudaError_t q = cudaEventQuery(d.mesh->ev_poll);
       if (q == cudaSuccess) {
-        task_advance(d.task);
+        if (d.check_bad) {  // the job's densities were checked before these scalars
+          d.check_bad = false;
+          if (*d.h_bad) {
+            d.mesh->has_density = false;
+            task_finish(d.task, TOPO_ERR_NAN);
+          }
+        }
+        if (d.task.phase != SolveTask::P_FINISHED) task_advance(d.task);
         moved = true;
       } else if (q != cudaErrorNotReady) {
         cudaGetLastError();
@@ -911,7 +964,7 @@ bool server_step(topo_server* s) {
       d.queue.pop_front();
       d.current.start_s = s->clock.seconds();
       d.info = topo_solve_info{};
-      topo_status st = topo_set_density(d.mesh, d.current.rho.data(), d.current.rho.size(), 0);
+      topo_status st = server_set_density(d, d.current.rho);
       d.task = SolveTask();
       d.task.m = d.mesh;
       d.task.o = s->opts;

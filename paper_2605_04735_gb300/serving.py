@@ -3,9 +3,10 @@ continuous-batching solve server (topo_server_* in libtopo.so).
 
 Each request is a design (grid 2n x n x n, cantilever or MBB, cone-smoothed
 random densities) that arrives at a Poisson time and then asks for
-`n_steps` solves: after each solve the client perturbs the densities by a
-factor in [0.95, 1.05] (a SIMP-style step) and submits the next solve, which
-the server warm-starts from the previous displacement.  The server admits
+`n_steps` solves: after each solve the client submits the densities
+perturbed by a factor in [0.95, 1.05] (a SIMP-style step; the whole
+sequence is generated before the clock starts and replayed), which the
+server warm-starts from the previous displacement.  The server admits
 designs by device-memory footprint, keeps them resident, and overlaps all of
 their solves on the GPU; this module only schedules arrivals and records
 latencies.
@@ -24,12 +25,32 @@ from . import inputs as I
 from . import topo
 
 
+def trace(requests):
+    """Every density each request will submit (step 0 and its n_steps - 1
+    perturbations), generated up front: the stream is replayed from this
+    trace, so the timed loop measures the server, not the client's random
+    number generation (~1 ms of host time per solve of the mean grid)."""
+    out = {}
+    for r in requests:
+        rho = r.rho0
+        seq = [rho]
+        for step in range(1, r.n_steps):
+            rho = I.perturb(rho, r.factor(step))
+            seq.append(rho)
+        out[r.rid] = seq
+    return out
+
+
 def run_stream(requests, budget_bytes: int, max_active: int = 64, opts=None,
-               realtime: bool = True):
+               realtime: bool = True, densities=None):
     """Drive the request stream; returns per-solve and per-request records.
 
     realtime: submit each request at its arrival time (wall clock since the
-    start); False submits everything at once (saturation)."""
+    start); False submits everything at once (saturation).  densities: the
+    trace of every request's densities (default: made here, before the
+    clock starts)."""
+    if densities is None:
+        densities = trace(requests)
     server = topo.Server(budget_bytes, max_active, opts=opts)
     pending = sorted(requests, key=lambda r: r.arrival)
     state = {}          # design -> [request, step, rho, arrival wall time]
@@ -60,7 +81,7 @@ def run_stream(requests, budget_bytes: int, max_active: int = 64, opts=None,
                                "n_dof": 3 * (r.nx + 1) * (r.ny + 1) * (r.nz + 1)})
                 step += 1
                 if step < r.n_steps:
-                    rho = I.perturb(rho, r.factor(step))
+                    rho = densities[r.rid][step]
                     server.submit(res.design, rho)
                     state[res.design] = [r, step, rho, t_arr]
                 else:

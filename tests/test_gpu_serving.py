@@ -169,3 +169,33 @@ def test_server_staggered_admission_matches_alone(topo):
                     finished += 1
     for r in reqs:
         assert got[r.rid] == alone[r.rid], r.rid
+
+
+def test_server_rejects_invalid_densities_per_job_and_recovers(topo):
+    """A job whose densities hold a NaN or a value above 1 fails with
+    TOPO_ERR_NAN, detail 1 (the density check, which the server reads with
+    the solve's first scalars instead of waiting on the host), and the same
+    design's next valid job solves as on a fresh mesh."""
+    nx, ny, nz = 24, 12, 12
+    rho = I.density_cone_smoothed(nx, ny, nz, 5)
+    with topo.Mesh(nx, ny, nz) as m:
+        m.set_density(rho)
+        m.solve(topo.default_opts())
+        c_ref = m.compliance()
+    srv = topo.Server(1 << 32, max_active=4)
+    try:
+        d = srv.open(nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM)
+        bad_nan = rho.copy()
+        bad_nan[17] = np.nan
+        bad_big = rho.copy()
+        bad_big[3] = 1.5
+        for bad in (bad_nan, bad_big):
+            srv.submit(d, bad)
+            res = [r for r in srv.poll(wait=True)]
+            assert len(res) == 1 and res[0].status == topo.ERR_NAN and res[0].detail == 1
+        srv.submit(d, rho)
+        res = [r for r in srv.poll(wait=True)]
+        assert len(res) == 1 and res[0].status == 0
+        assert res[0].compliance == pytest.approx(c_ref, rel=1e-8)
+    finally:
+        srv.close()
