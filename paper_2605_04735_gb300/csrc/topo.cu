@@ -807,6 +807,7 @@ struct ServerDesign {
   float* pinned = nullptr;
   int* h_bad = nullptr;
   bool check_bad = false;
+  bool finishing = false;  // the solve is done; its compliance is on the way
 };
 
 struct topo_server {
@@ -919,21 +920,59 @@ bool server_step(topo_server* s) {
     if (d.running) {
       cudaSetDevice(d.mesh->dev);
       const cudaError_t q = cudaEventQuery(d.mesh->ev_poll);
-      if (q == cudaSuccess) {
-        if (d.check_bad) {  // the job's densities were checked before these scalars
-          d.check_bad = false;
-          if (*d.h_bad) {
-            d.mesh->has_density = false;
-            task_finish(d.task, TOPO_ERR_NAN);
+      bool report = false;
+      if (d.finishing) {  // f^T u (enqueued when the solve ended) has arrived
+        if (q == cudaSuccess) {
+          d.finishing = false;
+          report = true;
+        } else if (q != cudaErrorNotReady) {
+          cudaGetLastError();
+          d.finishing = false;
+          d.task.st = cuda_status(q);
+          d.info.status = d.task.st;
+          d.info.detail = TOPO_FAIL_DEVICE;
+          report = true;
+        }
+      } else {
+        if (q == cudaSuccess) {
+          if (d.check_bad) {  // the job's densities were checked before these scalars
+            d.check_bad = false;
+            if (*d.h_bad) {
+              d.mesh->has_density = false;
+              task_finish(d.task, TOPO_ERR_NAN);
+            }
+          }
+          if (d.task.phase != SolveTask::P_FINISHED) task_advance(d.task);
+          moved = true;
+        } else if (q != cudaErrorNotReady) {
+          cudaGetLastError();
+          task_finish(d.task, cuda_status(q));
+        }
+        if (d.task.phase == SolveTask::P_FINISHED) {
+          moved = true;
+          topo_mesh* m = d.mesh;
+          // compliance J = f^T u (Eq. (2)) without a host wait: the dot and its
+          // copy follow the solve on the design's stream, reported when they land
+          if (d.task.st == TOPO_OK &&
+              launch_dot<double>(m->f64, m->u64, m->nvec, red_of(m, FIN_AUX), m->stream) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(m->h_sc, m->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
+                              m->stream) == cudaSuccess &&
+              cudaEventRecord(m->ev_poll, m->stream) == cudaSuccess) {
+            ++m->launches;
+            d.finishing = true;
+          } else {
+            if (d.task.st == TOPO_OK) {  // the enqueue failed
+              cudaGetLastError();
+              d.task.st = TOPO_ERR_CUDA;
+              d.info.status = TOPO_ERR_CUDA;
+              d.info.detail = TOPO_FAIL_DEVICE;
+            }
+            report = true;
           }
         }
-        if (d.task.phase != SolveTask::P_FINISHED) task_advance(d.task);
-        moved = true;
-      } else if (q != cudaErrorNotReady) {
-        cudaGetLastError();
-        task_finish(d.task, cuda_status(q));
       }
-      if (d.task.phase == SolveTask::P_FINISHED) {
+      if (report) {
         d.running = false;
         moved = true;
         topo_job_result r{};
@@ -947,7 +986,7 @@ bool server_step(topo_server* s) {
         r.submit_s = d.current.submit_s;
         r.start_s = d.current.start_s;
         if (r.status == TOPO_OK) {
-          topo_compliance(d.mesh, &r.compliance);
+          r.compliance = d.mesh->h_sc->aux[0];
           d.solved = true;
         }
         {
