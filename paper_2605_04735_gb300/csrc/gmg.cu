@@ -783,7 +783,8 @@ cudaError_t level_op(const float* x, const GmgLevel& L, const K0<float>& k0f,
   // the smoother's operator: one TF32 pass on the tensor-core form (a fixed
   // approximation of the level operator is all a smoother needs)
   if (mcf)
-    return launch_modal_any<1, float>(x, L.E, L.d, *mcf, k0f, ep, red, done, errflag, s, bt);
+    return launch_modal_any<TOPO_TC_SMOOTH_PASSES, float>(x, L.E, L.d, *mcf, k0f, ep, red, done,
+                                                         errflag, s, bt);
   if (bt.nb != 1) return cudaErrorInvalidValue;  // the gather kernels run one design
   return launch_stencil<float>(x, L.E, L.d, k0f, ep, red, done, errflag, s);
 }

@@ -16,9 +16,11 @@
 //
 // Precision: PASSES = 1 is a single TF32 product (k0 and the shifted values
 // rounded to TF32: ~2^-11 relative), for the multigrid smoother, which only
-// has to be a fixed approximation; PASSES = 3 splits both operands into a
-// TF32 high part and an FP32 remainder and accumulates hi*hi + hi*lo + lo*hi
-// (~2^-21 relative, FP32 level), for the CG operator and residuals.
+// has to be an approximation; PASSES = 2 splits the values into a TF32 high
+// part and an FP32 remainder (hi*k0 + lo*k0, k0 in TF32): the exact product
+// with a TF32-rounded k0, linear in the values; PASSES = 3 splits both
+// operands and accumulates hi*hi + hi*lo + lo*hi (~2^-21 relative, FP32
+// level), for the CG operator and residuals.
 //
 // Work split and data movement are those of k_modal_tma (modal.cuh): a CTA
 // is kTcTX x kTcTY = 16 x 8 threads, thread (tx, ty) owns the element column
@@ -42,6 +44,11 @@ namespace topo {
 constexpr int kTcTX = kModalTX;  // 16: must equal the exchange's x tile
 constexpr int kTcTY = 8;         // 16 x 8 = 128 threads = the MMA's M
 static_assert(kTcTX * kTcTY == 128, "one MMA row per thread");
+// TF32 passes of the smoother's operator (1: one pass; 2: values split, the
+// linear form)
+#ifndef TOPO_TC_SMOOTH_PASSES
+#define TOPO_TC_SMOOTH_PASSES 1
+#endif
 constexpr int kTcN = 32;          // MMA N (24 results padded)
 constexpr int kTcCols = 32;       // TMEM columns allocated per CTA
 constexpr uint32_t kTcIdesc =     // kind::tf32: D f32, A/B tf32, K-major, N = 32, M = 128
@@ -120,7 +127,7 @@ template <int PASSES>
 struct TcSmem {
   static constexpr int ATile = 128 * 24;            // floats
   static constexpr int BTile = kTcN * 24;           // floats
-  static constexpr int NP = PASSES == 3 ? 2 : 1;    // parts (high, low)
+  static constexpr int NP = PASSES >= 2 ? 2 : 1;    // parts (high, low)
   static constexpr size_t bytes() {
     return sizeof(float) * (NP * ATile + NP * BTile) + 16 + 128;  // + barrier, slot, alignment
   }
@@ -203,9 +210,9 @@ __global__ void __launch_bounds__(128)
   for (int q = tid; q < Ts::BTile; q += 128) {
     const int n = q / 24, k = q - 24 * (q / 24);
     const float v = n < 24 ? k0.v[24 * n + k] : 0.0f;
-    const float hi = PASSES == 3 ? to_tf32(v) : v;
+    const float hi = PASSES >= 2 ? to_tf32(v) : v;
     sb[tc_koff(n, k)] = hi;
-    if (PASSES == 3) sb[Ts::BTile + tc_koff(n, k)] = v - hi;
+    if (PASSES >= 2) sb[Ts::BTile + tc_koff(n, k)] = v - hi;
   }
   auto issue = [&](int t) {
     const int slot = t % kModalStages;
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int kc = 0; kc < 6; ++kc) {
         float4 h = make_float4(a[4 * kc], a[4 * kc + 1], a[4 * kc + 2], a[4 * kc + 3]);
-        if (PASSES == 3) {
+        if (PASSES >= 2) {
           const float4 v = h;
           h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
           *reinterpret_cast<float4*>(sa + Ts::ATile + tc_koff(tid, 4 * kc)) =
@@ -306,8 +313,9 @@ __global__ void __launch_bounds__(128)
       const uint32_t ah = sa_u, al = sa_u + 4u * Ts::ATile;
       const uint32_t bh = sb_u, bl = sb_u + 4u * Ts::BTile;
 #pragma unroll
-      for (int p = 0; p < PASSES; ++p) {
-        const uint32_t pa = p == 2 ? al : ah, pb = p == 1 ? bl : bh;
+      for (int p = 0; p < PASSES; ++p) {  // 1: hi hi; 2: + lo hi; 3: + hi lo, lo hi
+        const uint32_t pa = (PASSES == 2 ? p == 1 : p == 2) ? al : ah;
+        const uint32_t pb = (PASSES == 3 && p == 1) ? bl : bh;
 #pragma unroll
         for (int s = 0; s < 3; ++s)
           tc_mma(tmem, tc_sdesc(pa + 256u * s, 128u, 768u), tc_sdesc(pb + 256u * s, 128u, 768u),
