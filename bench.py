@@ -301,6 +301,47 @@ def run_reference(args, workload):
     print(json.dumps(line), flush=True)
 
 
+def serving_cpu_baseline(reqs) -> dict:
+    """The oracle on a bounded sample of the serving stream's designs: one
+    cold FP64 solve (density, solve, compliance, sensitivities) of the
+    smallest grid (direct Cholesky) and of the median grid (the oracle's
+    matrix-free Jacobi-PCG to 1e-8: a direct band would need ~9 GB), on all
+    host cores; a power law in the DOF count through the two times gives
+    the mean time per solve over the stream's grid mix."""
+    from oracle import fem
+    from oracle import fullsize as FS
+    by_ny = sorted(reqs, key=lambda r: r.ny)
+    picks = [by_ny[0], by_ny[len(by_ny) // 2]]
+    pts = []
+    for r in picks:
+        t0 = time.perf_counter()
+        g = fem.Grid(r.nx, r.ny, r.nz)
+        if r.ny <= 16:
+            P = fem.Problem(r.nx, r.ny, r.nz, r.bc, r.load, r.rho0)
+            u = P.solve()
+            P.compliance(u)
+            P.sensitivity(u)
+            how = "banded Cholesky"
+        else:
+            E = fem.simp_modulus(r.rho0)
+            k0 = fem.element_stiffness(1.0, 0.3)
+            f = fem.load_vector(g, r.load)
+            fixed = fem.fixed_dofs(g, r.bc)
+            u, it, rel = FS.cg(g, E, k0, f, fixed, rtol=1e-8)
+            fem.sensitivity(g, u, r.rho0, k0)
+            how = f"Jacobi-PCG, {it} iterations"
+        pts.append((g.n_dof, time.perf_counter() - t0, f"{r.nx}x{r.ny}x{r.nz} ({how})"))
+    (n0, t0_, _), (n1, t1_, _) = pts
+    b = np.log(t1_ / t0_) / np.log(n1 / n0) if n1 != n0 else 1.0
+    mean_t = float(np.mean([t0_ * (3 * (r.nx + 1) * (r.ny + 1) * (r.nz + 1) / n0) ** b
+                            for r in reqs]))
+    cores = os.cpu_count() or 1
+    return {"value": 1.0 / mean_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "; ".join(f"{name}: {t:.2f} s" for _, t, name in pts)
+                      + f"; mean over the stream's grids by t ~ DOF^{b:.2f}: {mean_t:.2f} s per "
+                        "cold solve (the GPU's solves are warm-started)"}
+
+
 def serving_summary(budget_gb: float = 40.0, loads=(0.5, 0.8, 1.0)):
     """The serving workload (64 requests x 30 solves, grids 24x12x12 ..
     128x64x64, half cantilever / half MBB) through the continuous-batching
@@ -314,8 +355,9 @@ def serving_summary(budget_gb: float = 40.0, loads=(0.5, 0.8, 1.0)):
                        "cantilever / half MBB, densities perturbed +-5 % per solve",
            "budget_gb": budget_gb, "saturated": sat, "lambda_sat_req_per_s": lam, "runs": {}}
     for f in loads:
-        reqs = I.serving_stream(64, 30, rate=f * lam)
-        out["runs"][f"{f:.2f}x"] = SV.summarize(*SV.run_stream(reqs, budget, 64))
+        reqs_f = I.serving_stream(64, 30, rate=f * lam)
+        out["runs"][f"{f:.2f}x"] = SV.summarize(*SV.run_stream(reqs_f, budget, 64))
+    out["cpu_baseline"] = serving_cpu_baseline(reqs)
     return out
 
 
