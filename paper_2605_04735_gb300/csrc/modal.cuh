@@ -199,7 +199,12 @@ static_assert(32 % kModalTX == 0 && kModalTX >= 8, "x tile: 8, 16 or 32 threads"
 static_assert(kModalTX * kModalTY % 32 == 0 && kModalTX * kModalTY <= 512, "whole warps");
 
 // exchange a finished plane's corners with the neighbours: res = the sums at
-// the node (ex, ey) of the plane (includes the CTA barrier)
+// the node (ex, ey) of the plane (includes the CTA barrier).  Only threads
+// with tx, ty >= 1 own a node: what the others receive (a tx = 0 lane gets
+// the previous thread row's last lane, or its own value) and the slot they
+// write (read only by the tx = 0 thread of the next row) is never used, so
+// no select guards the shuffled values; the row above is guarded (ty = 0
+// has none).
 template <typename T>
 __device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[kModalTX][3], int tx,
                                                int ty, T (&res)[3]) {
@@ -208,8 +213,8 @@ __device__ __forceinline__ void modal_exchange(const T (&plane)[3][4], T (*xch)[
   for (int c = 0; c < 3; ++c) {
     const T r1 = shfl_up1(plane[c][1]);
     const T r3 = shfl_up1(plane[c][3]);
-    n0[c] = plane[c][0] + (tx > 0 ? r1 : T(0));
-    xch[ty][tx][c] = plane[c][2] + (tx > 0 ? r3 : T(0));
+    n0[c] = plane[c][0] + r1;
+    xch[ty][tx][c] = plane[c][2] + r3;
   }
   __syncthreads();
 #pragma unroll
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(kModalTX* TY)
     mbar_wait_bounded(&bar[r], ph, errflag);
     const float* nd = stg + r * SF;
     es = 0.f;
-    if (DI >= 0 && own) {
+    if (DI >= 0) {  // used by owned nodes only; the others read inside the stage too
       const float* e0 = nd + Tl::ElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
       es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
     }

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(128)
     mbar_wait_bounded(&bar[r], ph, errflag);
     const float* nd = stg + r * SF;
     es = 0.f;
-    if (DI >= 0 && own) {
+    if (DI >= 0) {  // used by owned nodes only; the others read inside the stage too
       const float* e0 = nd + Tl::ElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
       es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
     }
