@@ -412,6 +412,20 @@ topo_status topo_element_energy(topo_mesh* m, double* w, size_t n_elem, int on_d
  * (TOPO_OPERATOR_*); synchronises the mesh's stream.  Cites Eq. (2). */
 topo_status topo_set_operator(topo_mesh* m, int kind);
 
+/* Throughput form of the multigrid hierarchy (no counterpart in the paper),
+ * for meshes that share the GPU with many others (the solve server turns it
+ * on for every design it admits): the coarse levels of at most 1024 nodes
+ * and the coarsest solve run as one kernel per V-cycle, and the coarsest grid
+ * is chosen within 222 DOF so that its FP64 inverse is formed by one kernel
+ * instead of one kernel per pivot.  Fewer, longer launches per solve: more
+ * solves per second when many meshes run at once, more latency for a mesh
+ * alone.  Results differ from the default form by rounding and by the
+ * hierarchy's depth (both stop on the same true FP64 residual).  enable: 1
+ * or 0; the hierarchy is rebuilt at the next solve.  TOPO_ERR_INVALID for a
+ * mesh of a mesh group (its batched solves run their coarse end that way
+ * already).  Synchronises the mesh's stream. */
+topo_status topo_set_throughput_mode(topo_mesh* m, int enable);
+
 /* Change the caller stream the mesh orders its calls against. */
 topo_status topo_set_stream(topo_mesh* m, void* stream);
 

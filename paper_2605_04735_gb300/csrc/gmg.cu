@@ -638,13 +638,13 @@ double k0_jacobi_bound(const double* k0) {
   return lam;
 }
 
-std::vector<Dims> gmg_plan(const Dims& fine, int max_levels) {
+std::vector<Dims> gmg_plan(const Dims& fine, int max_levels, int max_dof) {
   std::vector<Dims> out;
   Dims d = fine;
   for (;;) {
     out.push_back(d);
     const long long dof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
-    if (dof <= kCoarseMaxDof) break;
+    if (dof <= max_dof) break;
     if (max_levels > 0 && (int)out.size() >= max_levels) break;
     const int nx = (d.nx + 1) / 2, ny = (d.ny + 1) / 2, nz = (d.nz + 1) / 2;
     if (nx == d.nx && ny == d.ny && nz == d.nz) break;
@@ -669,12 +669,13 @@ long long gmg_footprint(const Dims& fine, int max_levels) {
 }
 
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
-                       cudaStream_t s, const GmgAlloc* alloc) {
+                       cudaStream_t s, const GmgAlloc* alloc, bool throughput) {
   g.arena = (alloc != nullptr);
   g.degree = std::max(1, degree);
   g.lam_max = lam_max;
+  g.throughput = throughput;
   g.lv.clear();
-  for (const Dims& d : gmg_plan(fine, max_levels)) {
+  for (const Dims& d : gmg_plan(fine, max_levels, throughput ? kSweepMaxN : kCoarseMaxDof)) {
     GmgLevel L;
     L.d = d;
     L.nvec = 3 * d.comp;
@@ -725,7 +726,8 @@ cudaError_t gmg_setup(Gmg& g, const float* E0, const float* dinv0, const K0<floa
   const long long nn = (long long)g.nc * g.nc;
   GCK(launch_pdl(k_dense_assemble, dim3(grid1d(nn, bt.nb), bt.nb), dim3(kPT), 0, s, g.Ainv, Lc.d,
                  Lc.E, k0d, bt.sel()));
-  if (bt.nb > 1 && g.nc <= kSweepMaxN) {  // a batch: the whole inverse in one kernel per design
+  // a batch, or the throughput form: the whole inverse in one kernel per design
+  if ((bt.nb > 1 || g.throughput) && g.nc <= kSweepMaxN) {
     const size_t smem = sizeof(double) * ((size_t)g.nc * (g.nc + 1) / 2 + 2 * g.nc);
     static bool attr = false;
     if (!attr) {
@@ -816,7 +818,7 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   // designs share the launch: one SM per design is then the better use of the
   // GPU than a few-microsecond launch per coarse step.  A single design keeps
   // the per-level kernels, which spread each level over many SMs.
-  const bool tail = g.tail_l0 > 0 && bt.nb > 1;
+  const bool tail = g.tail_l0 > 0 && (bt.nb > 1 || g.throughput);
   const int l_end = tail ? g.tail_l0 : nl - 1;
   // down
   for (int l = 0; l < l_end; ++l) {

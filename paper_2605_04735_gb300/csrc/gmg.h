@@ -44,6 +44,9 @@ struct Gmg {
   int tail_l0 = -1;          // levels tail_l0 .. coarsest run as one kernel per design (-1: none)
   bool ready = false;        // set up for the current densities
   bool arena = false;        // buffers come from a mesh group's arena (not freed here)
+  // throughput form (many meshes sharing the GPU): the coarse end runs as one
+  // kernel per V-cycle and the coarsest inverse is formed by one kernel
+  bool throughput = false;
 };
 
 // Optional allocator for the hierarchy's buffers (a mesh group's arena).
@@ -53,12 +56,15 @@ struct GmgAlloc {
 };
 
 // The level grids a fine grid coarsens to, and the bytes a hierarchy holds.
-std::vector<Dims> gmg_plan(const Dims& fine, int max_levels);
+// max_dof: the coarsest grid's size limit (DOF, fixed ones included)
+std::vector<Dims> gmg_plan(const Dims& fine, int max_levels, int max_dof = 400);
 long long gmg_footprint(const Dims& fine, int max_levels);
 // Choose levels for a fine grid and allocate them (fine-level E/dinv/b/x are
 // bound later, per call).  max_levels <= 0: automatic.
+// throughput: the throughput form (see Gmg::throughput); its coarsest grid
+// is kept within the single-kernel inverse's size (222 DOF)
 cudaError_t gmg_create(Gmg& g, const Dims& fine, int max_levels, int degree, double lam_max,
-                       cudaStream_t s, const GmgAlloc* alloc = nullptr);
+                       cudaStream_t s, const GmgAlloc* alloc = nullptr, bool throughput = false);
 // Per-density setup: coarse moduli, Jacobi diagonals, coarsest inverse.
 // bt: the designs of a mesh group (pointers are design 0's; each design's
 // hierarchy sits at the group's design stride from design 0's).

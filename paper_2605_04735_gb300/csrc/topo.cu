@@ -195,6 +195,7 @@ struct topo_mesh {
   // multigrid hierarchy (built on the first GMG solve, set up per density)
   Gmg gmg;
   bool gmg_built = false;
+  bool throughput = false;  // build the hierarchy in its throughput form
   int gmg_levels_req = -1, gmg_degree = -1;
   double lam_max = 0.0;
 };
@@ -496,7 +497,8 @@ topo_status ensure_gmg(topo_mesh* m, const topo_solve_opts* o) {
     m->gmg_built = false;
   }
   if (!m->gmg_built) {
-    cudaError_t e = gmg_create(m->gmg, m->d, o->gmg_levels, o->smooth_degree, m->lam_max, m->stream);
+    cudaError_t e = gmg_create(m->gmg, m->d, o->gmg_levels, o->smooth_degree, m->lam_max,
+                               m->stream, nullptr, m->throughput);
     m->bytes += m->gmg.bytes;
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -875,6 +877,10 @@ bool server_step(topo_server* s) {
     if (s->active < s->max_active && s->in_use + d.footprint <= s->budget) {
       topo_mesh* m = nullptr;
       topo_status st = topo_create_mesh(d.nx, d.ny, d.nz, d.bc, d.load, &s->prm, s->user, &m);
+      if (st == TOPO_OK) {
+        st = topo_set_throughput_mode(m, 1);
+        if (st != TOPO_OK) topo_free(m);
+      }
       if (st == TOPO_OK &&
           (cudaMallocHost(&d.pinned, sizeof(float) * (size_t)d.nx * d.ny * d.nz) != cudaSuccess ||
            cudaMallocHost(&d.h_bad, sizeof(int)) != cudaSuccess)) {
@@ -2682,6 +2688,23 @@ topo_status topo_set_stream(topo_mesh* m, void* stream) {
 topo_status topo_profile_enable(topo_mesh* m, int enable) {
   if (!m) return TOPO_ERR_INVALID;
   m->prof = enable != 0;
+  return TOPO_OK;
+}
+
+topo_status topo_set_throughput_mode(topo_mesh* m, int enable) {
+  if (!m || (enable != 0 && enable != 1)) return TOPO_ERR_INVALID;
+  if (m->group) return TOPO_ERR_INVALID;  // mesh groups run their coarse end batched anyway
+  if ((enable != 0) == m->throughput) return TOPO_OK;
+  CK(cudaSetDevice(m->dev));
+  CK(cudaStreamSynchronize(m->stream));
+  clear_graphs(m);  // the captured chunks hold the old hierarchy
+  if (m->gmg_built) {
+    m->bytes -= m->gmg.bytes;
+    gmg_free(m->gmg);
+    m->gmg = Gmg();
+    m->gmg_built = false;
+  }
+  m->throughput = enable != 0;
   return TOPO_OK;
 }
 

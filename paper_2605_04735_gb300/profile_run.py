@@ -21,6 +21,10 @@
         entry points (densities, solve, compliances, sensitivities): the
         launch list of a batched step.
 
+    python -m paper_2605_04735_gb300.profile_run serving <requests> [steps]
+        a saturated serving stream (every request at once) of `requests`
+        seeded requests x `steps` solves through the solve server.
+
 Workloads are the seeded recipes of `inputs.WORKLOADS`; nothing is read
 from disk.  Each command prints one line starting with "ok".
 """
@@ -37,6 +41,15 @@ def main(argv):
     from . import topo
 
     mode = argv[0] if argv else "apply"
+    if mode == "serving":
+        from . import serving as SV
+        torch.cuda.set_device(0)
+        n = int(argv[1]) if len(argv) > 1 else 8
+        steps = int(argv[2]) if len(argv) > 2 else 5
+        reqs = I.serving_stream(n, steps, rate=0.0)
+        res = SV.summarize(*SV.run_stream(reqs, 1 << 35, 64, realtime=False))
+        print("ok", mode, n, steps, res["solves"], round(res["solves_per_s"], 1))
+        return
     name = argv[1] if len(argv) > 1 else "cantilever_voids_320x160x160"
     reps = int(argv[2]) if len(argv) > 2 else (1 if mode.startswith("apply") else 3)
     op = int(argv[3]) if len(argv) > 3 else 0

@@ -115,6 +115,7 @@ def lib():
             "topo_profile_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), i]),
             "topo_debug_inject_timeout": (i, [vp, i]),
+            "topo_set_throughput_mode": (i, [vp, i]),
             "topo_profile_read_smoother": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                                C.POINTER(d), i]),
             "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
@@ -520,6 +521,12 @@ class Mesh:
         _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(a), int(reset)),
                "topo_profile_read")
         return ms.value, n.value, a.value
+
+    def set_throughput_mode(self, enable: bool = True):
+        """The multigrid's throughput form (topo_set_throughput_mode), as the
+        solve server uses for its designs."""
+        _check(lib().topo_set_throughput_mode(self._h, int(bool(enable))),
+               "topo_set_throughput_mode")
 
     def debug_inject_timeout(self, count: int = 1):
         """Arm (1) or disarm (0) the test hook of topo_debug_inject_timeout."""

@@ -25,9 +25,11 @@ def topo():
 
 
 def _alone(topo, r, steps):
-    """The request's solves on its own mesh, one after the other."""
+    """The request's solves on its own mesh, one after the other (in the
+    multigrid's throughput form, which the server uses for its designs)."""
     out = []
     with topo.Mesh(r.nx, r.ny, r.nz, r.bc, r.load) as m:
+        m.set_throughput_mode(True)
         rho = r.rho0
         for s in range(steps):
             if s:
@@ -112,6 +114,7 @@ def test_server_many_concurrent_setups_match_alone(topo):
     alone = {}
     for r in reqs:
         with topo.Mesh(r.nx, r.ny, r.nz, r.bc, r.load) as m:
+            m.set_throughput_mode(True)  # the server's form of the hierarchy
             m.set_density(r.rho0)
             info = m.solve()
             alone[r.rid] = (info.iters, m.compliance())
@@ -179,6 +182,7 @@ def test_server_rejects_invalid_densities_per_job_and_recovers(topo):
     nx, ny, nz = 24, 12, 12
     rho = I.density_cone_smoothed(nx, ny, nz, 5)
     with topo.Mesh(nx, ny, nz) as m:
+        m.set_throughput_mode(True)
         m.set_density(rho)
         m.solve(topo.default_opts())
         c_ref = m.compliance()
@@ -199,3 +203,31 @@ def test_server_rejects_invalid_densities_per_job_and_recovers(topo):
         assert res[0].compliance == pytest.approx(c_ref, rel=1e-8)
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("nx,ny,nz,bc,load", [
+    (24, 12, 12, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM),   # coarsest 3x2x2 instead of 6x3x3
+    (48, 24, 24, I.BC_MBB, I.LOAD_EDGE_X0_TOP),
+    (33, 9, 7, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM),
+])
+def test_throughput_form_matches_the_direct_oracle(topo, nx, ny, nz, bc, load):
+    """The server's form of the multigrid hierarchy (coarse end in one kernel,
+    coarsest inverse in one kernel) solves to the same true residual and
+    matches the direct solution like the default form."""
+    rho = I.density_cone_smoothed(nx, ny, nz, 31)
+    P = fem.Problem(nx, ny, nz, bc, load, rho)
+    u_ref = P.solve()
+    opts = topo.default_opts(rtol=1e-10)
+    with topo.Mesh(nx, ny, nz, bc, load) as m:
+        m.set_throughput_mode(True)
+        m.set_density(rho)
+        info = m.solve(opts)
+        u, c = m.displacement(), m.compliance()
+        m.set_throughput_mode(False)  # back to the default form: rebuilt, same answer
+        info0 = m.solve(opts)
+        u0 = m.displacement()
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    assert np.linalg.norm(u - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    assert c == pytest.approx(P.compliance(u_ref), rel=1e-8)
+    assert np.linalg.norm(u0 - u_ref) <= 1e-8 * np.linalg.norm(u_ref)
+    assert info.iters <= 1.3 * info0.iters + 3
