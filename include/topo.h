@@ -72,7 +72,10 @@ enum {
   /* the paper's problems (Sec. 4.2, 4.3) on a 2:1:1 domain, sizes relative to
    * the unit cross-section of ny x nz elements: */
   TOPO_BC_CORNERS = 3,   /* i = 0 fixed on four corner squares j, k <= 0.3 n or >= 0.7 n */
-  TOPO_BC_MBB_STRIP = 4  /* u_x on i = 0; u_z on the bottom strip i >= nx-1; u_y pin; ny even */
+  TOPO_BC_MBB_STRIP = 4, /* u_x on i = 0; u_z on the bottom strip i >= nx-1; u_y pin; ny even */
+  TOPO_BC_NONE = 5       /* no support: a slab of a larger grid whose supports the caller
+                            applies (K is singular: for topo_apply and topo_jacobi_inverse,
+                            not for solves) */
 };
 
 /* Loads (consistent nodal forces; total magnitude params.load). */
@@ -251,6 +254,13 @@ topo_status topo_sensitivity_many(topo_mesh* const* meshes, int n, double* dc, s
 
 /* Copy the stored FP64 displacement out (n_dof = 3 * nodes, DOF order). */
 topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_device);
+
+/* The inverse Jacobi diagonal of K (Eq. (2)) from the current densities, in
+ * FP64, DOF order: 1 / K_ii on free DOFs, 1 on fixed DOFs and where K_ii
+ * vanishes.  n_dof = 3 * nodes.  TOPO_ERR_NO_DENSITY before set_density.
+ * (With TOPO_BC_NONE, the diagonal of a slab: the caller's x-slab
+ * decomposition supplies its supports.) */
+topo_status topo_jacobi_inverse(topo_mesh* m, double* dinv, size_t n_dof, int on_device);
 
 /* Replace the stored displacement (warm start, checkpoint restore).
  * Entries on fixed DOFs are ignored (held at zero). */

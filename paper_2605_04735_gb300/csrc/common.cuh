@@ -19,7 +19,14 @@
 
 namespace topo {
 
-enum Bc { BC_CANTILEVER = 0, BC_MBB = 1, BC_ROLLER_BOX = 2, BC_CORNERS = 3, BC_MBB_STRIP = 4 };
+enum Bc {
+  BC_CANTILEVER = 0,
+  BC_MBB = 1,
+  BC_ROLLER_BOX = 2,
+  BC_CORNERS = 3,
+  BC_MBB_STRIP = 4,
+  BC_NONE = 5  // no support: a slab of a larger grid (operator applications only)
+};
 
 // k0 as a kernel parameter: 24x24 row-major, unit Young's modulus.  Read
 // with compile-time indices only, so every access is a constant-bank
@@ -60,6 +67,8 @@ struct Dims {
         return i0 <= 0 || (i1 >= nx && k0 <= 0);
       case BC_MBB_STRIP:
         return i0 <= 0 || (i1 >= nx - 1 && k0 <= 0);
+      case BC_NONE:
+        return false;
       default:
         return i0 <= 0 || j0 <= 0 || k0 <= 0;
     }
@@ -78,6 +87,8 @@ struct Dims {
       case BC_MBB_STRIP:
         return (c == 0 && i == 0) || (c == 2 && i >= nx - 1 && k == 0) ||
                (c == 1 && i == nx && k == 0 && j == pin_j);
+      case BC_NONE:
+        return false;
       default:
         return (c == 0 && i == 0) || (c == 1 && j == 0) || (c == 2 && k == 0);
     }

@@ -1225,7 +1225,7 @@ topo_status topo_create_mesh(int nx, int ny, int nz, int bc, int load, const top
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
   if ((long long)(nx + 1) * (ny + 1) * (nz + 1) >= (1LL << 31)) return TOPO_ERR_INVALID;
-  if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if (bc < 0 || bc > 5 || load < 0 || load > 4) return TOPO_ERR_INVALID;
   if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
               !(prm->E0 > 0.0) || !(prm->Emin >= 0.0) || !(prm->Emin < prm->E0)))
@@ -1285,7 +1285,7 @@ topo_status topo_create_batch(int nx, int ny, int nz, int bc, int load, const to
   for (int b = 0; b < n_designs; ++b) out[b] = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096) return TOPO_ERR_INVALID;
   if ((long long)(nx + 1) * (ny + 1) * (nz + 1) >= (1LL << 31)) return TOPO_ERR_INVALID;
-  if (bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if (bc < 0 || bc > 5 || load < 0 || load > 4) return TOPO_ERR_INVALID;
   if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   if (prm && (!(prm->nu >= 0.0 && prm->nu < 0.5) || !(prm->penal >= 1.0) || !(prm->h > 0.0) ||
               !(prm->E0 > 0.0) || !(prm->Emin >= 0.0) || !(prm->Emin < prm->E0)))
@@ -2439,6 +2439,27 @@ topo_status topo_get_displacement(topo_mesh* m, double* u, size_t n_dof, int on_
   return TOPO_OK;
 }
 
+topo_status topo_jacobi_inverse(topo_mesh* m, double* dinv, size_t n_dof, int on_device) {
+  if (!m || !dinv) return TOPO_ERR_INVALID;
+  if (!m->has_density) return TOPO_ERR_NO_DENSITY;
+  const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
+  if ((long long)n_dof != nd) return TOPO_ERR_INVALID;
+  Fence fence(m);
+  if (fence.st != TOPO_OK) return fence.st;
+  CKS(ensure_fp64_inner(m));
+  if (!m->diag64) {
+    LK(m, launch_diag_inv<double>(m->dinv64, m->E64, m->d, m->k0d, m->stream));
+    m->diag64 = true;
+  }
+  double* dst = on_device ? dinv : m->aos;
+  LK(m, launch_pack<double>(m->dinv64, dst, m->d, m->stream));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(dinv, m->aos, nd * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+  }
+  return TOPO_OK;
+}
+
 topo_status topo_set_displacement(topo_mesh* m, const double* u, size_t n_dof, int on_device) {
   if (!m || !u) return TOPO_ERR_INVALID;
   const long long nd = 3LL * (m->d.nx + 1) * (m->d.ny + 1) * (m->d.nz + 1);
@@ -2531,6 +2552,8 @@ topo_status topo_mesh_info(const topo_mesh* m, long long* n_nodes, long long* n_
     fixed = face + (d.ny + 1) + 1;
   else if (d.bc == BC_MBB_STRIP)
     fixed = face + 2 * (d.ny + 1) + 1;
+  else if (d.bc == BC_NONE)
+    fixed = 0;
   else if (d.bc == BC_CORNERS)  // supported rows x supported layers on x = 0, all components
     fixed = 3LL * std::min(2 * (d.corner_j + 1), d.ny + 1) *
             (long long)std::min(2 * (d.corner_k + 1), d.nz + 1);
@@ -2768,7 +2791,7 @@ topo_status topo_server_create(long long mem_budget_bytes, int max_active, const
 topo_status topo_server_open(topo_server* s, int nx, int ny, int nz, int bc, int load,
                              int* design) {
   if (!s || !design) return TOPO_ERR_INVALID;
-  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 4 || load < 0 || load > 4) return TOPO_ERR_INVALID;
+  if (nx < 1 || ny < 1 || nz < 1 || bc < 0 || bc > 5 || load < 0 || load > 4) return TOPO_ERR_INVALID;
   if ((bc == TOPO_BC_MBB || bc == TOPO_BC_MBB_STRIP) && (ny % 2)) return TOPO_ERR_INVALID;
   const long long fp = topo_footprint_bytes(nx, ny, nz, &s->opts);
   if (fp > s->budget) return TOPO_ERR_OOM;  // could never be admitted

@@ -268,3 +268,42 @@ def jacobi_pcg(slab: Slab, comm, apply_local, dinv_local: np.ndarray, f_local: n
         if record is not None:
             record.append(x[o].copy())
     return x, it, float(np.sqrt(rr) / fn) if fn > 0 else 0.0
+
+
+class DeviceSlabOperator:
+    """The library's operator on one rank's slab: a mesh of the slab's element
+    layers [e_lo, e_hi) with no support (TOPO_BC_NONE; the decomposition
+    applies the global supports), whose densities are the slab of the global
+    densities (Eq. (1) on the device).  apply_local(u) gives K u on the local
+    planes (correct on the owned ones once the ghosts are exchanged);
+    dinv_local() the Jacobi inverse on the local planes (exact on the owned
+    ones: every element around an owned node is held).  precision:
+    topo.PREC_FP64 or topo.PREC_FP32 (the operator kernels of the library)."""
+
+    def __init__(self, slab: Slab, rho_global: np.ndarray, precision: int = 0, params=None,
+                 stream=None):
+        from . import topo
+        self.slab, self.precision, self.topo = slab, precision, topo
+        self.mesh = topo.Mesh(slab.e_hi - slab.e_lo, slab.ny, slab.nz, topo.BC_NONE,
+                              topo.LOAD_EDGE_XL_BOTTOM, params=params, stream=stream)
+        self.mesh.set_density(np.ascontiguousarray(slab.local_elements(rho_global),
+                                                   dtype=np.float32))
+        self.shape = (slab.n_local_planes, slab.nz + 1, slab.ny + 1, 3)
+
+    def _to_mesh(self, v_local):
+        return np.ascontiguousarray(np.asarray(v_local).transpose(1, 2, 0, 3)).reshape(-1)
+
+    def _from_mesh(self, flat):
+        s = self.slab
+        return np.ascontiguousarray(flat.reshape(s.nz + 1, s.ny + 1, s.n_local_planes, 3)
+                                    .transpose(2, 0, 1, 3))
+
+    def apply_local(self, u_local: np.ndarray) -> np.ndarray:
+        y = self.mesh.apply(self._to_mesh(u_local), precision=self.precision)
+        return self._from_mesh(y)
+
+    def dinv_local(self) -> np.ndarray:
+        return self._from_mesh(self.mesh.jacobi_inverse())
+
+    def close(self):
+        self.mesh.close()

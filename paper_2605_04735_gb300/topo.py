@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libtopo.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NO_DENSITY, ERR_NOT_SOLVED, ERR_NOT_CONVERGED, \
     ERR_NAN, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
-BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX, BC_CORNERS, BC_MBB_STRIP = 0, 1, 2, 3, 4
+BC_CANTILEVER, BC_MBB, BC_ROLLER_BOX, BC_CORNERS, BC_MBB_STRIP, BC_NONE = 0, 1, 2, 3, 4, 5
 LOAD_EDGE_XL_BOTTOM, LOAD_EDGE_X0_TOP, LOAD_FACE_XL_TRACTION = 0, 1, 2
 LOAD_DISC_XL, LOAD_HALFDISC_X0_TOP = 3, 4
 PREC_FP64, PREC_FP32, PREC_DWORD = 0, 1, 2
@@ -116,6 +116,7 @@ def lib():
                                       C.POINTER(C.c_longlong), i]),
             "topo_debug_inject_timeout": (i, [vp, i]),
             "topo_set_throughput_mode": (i, [vp, i]),
+            "topo_jacobi_inverse": (i, [vp, vp, sz, i]),
             "topo_profile_read_smoother": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong),
                                                C.POINTER(d), i]),
             "topo_sensitivity_noalloc": (i, [i, i, i, C.POINTER(Params), vp, vp, vp, vp, vp]),
@@ -521,6 +522,14 @@ class Mesh:
         _check(lib().topo_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(a), int(reset)),
                "topo_profile_read")
         return ms.value, n.value, a.value
+
+    def jacobi_inverse(self, out=None):
+        """1 / diag(K) in FP64, DOF order (topo_jacobi_inverse)."""
+        if out is None:
+            out = np.empty(self.n_dof, dtype=np.float64)
+        p, n, dev = _ptr(out, np.float64)
+        _check(lib().topo_jacobi_inverse(self._h, p, n, dev), "topo_jacobi_inverse")
+        return out
 
     def set_throughput_mode(self, enable: bool = True):
         """The multigrid's throughput form (topo_set_throughput_mode), as the
