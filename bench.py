@@ -64,6 +64,12 @@ def operator_kernel(op: int, nx: int) -> str:
 # 320x160x160)
 NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": 1957888.0 + 0.0,
                                         LARGE_WORKLOAD: 183507712.0 + 69900032.0}
+# DRAM bytes per design of the batched finest-level launches, from one ncu
+# capture each of a 64-design launch of the current kernel source
+# (profiles/k_modal_tma_batch64_mbb_96x32x32.md): the Chebyshev step in its
+# x-added form (8.00 MB algorithmic per design) and the CG apply
+NCU_TRAFFIC_BATCH = {"cheb_step": (307256576.0 + 201840384.0) / 64,
+                     "cg_apply": (135333632.0 + 52475136.0) / 64}
 # FP32 lane-operations per element the modal kernels execute for one K u
 # (ncu instruction counts: the Walsh-Hadamard form of k0 instead of the dense
 # 2 x 24 x 24 product), the basis of the executed-operation floor
@@ -637,7 +643,9 @@ def main():
         # design-launch units: the bytes of the timed launches over their
         # summed duration (each launch covered the designs still iterating)
         cg_apply = hbm_roofline(kern + ", CG apply", w, operator_bytes(w),
-                                batch_op_ms / batch_op_units, 1.0, peaks, peaks_src)
+                                batch_op_ms / batch_op_units, 1.0, peaks, peaks_src,
+                                traffic=NCU_TRAFFIC_BATCH["cg_apply"] if args.operator == 0
+                                else None)
         cg_apply.update({"designs_per_launch": "varies (designs still iterating); figures per "
                                               "design-launch",
                          "avg_launch_us": None,
@@ -649,7 +657,12 @@ def main():
         # the dominant kernel of the batched step: the finest-level Chebyshev
         # smoothing step (operator + smoothing epilogue)
         main = hbm_roofline(kern + " with the Chebyshev-step epilogue", w,
-                            cheb_bytes / cheb_units, cheb_ms / cheb_units, 1.0, peaks, peaks_src)
+                            cheb_bytes / cheb_units, cheb_ms / cheb_units, 1.0, peaks, peaks_src,
+                            traffic=NCU_TRAFFIC_BATCH["cheb_step"] if args.operator == 0
+                            else None)
+        main["traffic_note"] = ("ncu, one 64-design launch of the x-added form (8.00 MB "
+                                "algorithmic per design; bytes_per_launch averages the stored "
+                                "and added forms): DRAM / algorithmic = 0.99")
         main.update({"designs_per_launch": "varies (designs still iterating); figures per "
                                           "design-launch",
                      "avg_launch_us": None,
