@@ -13,6 +13,7 @@ result (u, c = f^T u, dc of Eq. (3)), on every DOF.
 Each comparison prints one `ACCURACY {...}` line (pytest -s shows them)."""
 import dataclasses
 import json
+import os
 
 import numpy as np
 import pytest
@@ -129,3 +130,37 @@ def test_cantilever_voids_192x96x96_against_the_cg_reference(topo):
         assert e["err_c"] <= 1e-8 and e["err_dc"] <= 1e-6
         if rtol <= 1e-10:
             assert e["err_u"] <= 1e-8
+
+
+@pytest.mark.skipif(os.environ.get("TOPO_LONG_TESTS") != "1",
+                    reason="15-20 minutes of host time for the oracle's reference solve; "
+                           "run with TOPO_LONG_TESTS=1")
+def test_cantilever_voids_320x160x160_against_the_cg_reference(topo):
+    """24.9 M DOFs: the oracle's matrix-free FP64 Jacobi-PCG to its FP64 floor
+    as the reference (several thousand iterations on the host's cores)."""
+    w = I.WORKLOADS["cantilever_voids_320x160x160"]
+    rho = w.density()
+    g = fem.Grid(w.nx, w.ny, w.nz)
+    E = fem.simp_modulus(rho)
+    k0 = fem.element_stiffness(1.0, 0.3)
+    f = fem.load_vector(g, w.load)
+    fixed = fem.fixed_dofs(g, w.bc)
+    f[fixed] = 0.0
+    with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load) as m:
+        m.set_density(rho)
+        info = m.solve(topo.default_opts())
+        assert info.status == 0 and info.rel_residual <= 1e-8
+        u, c, dc = m.displacement(), m.compliance(), m.sensitivity()
+    u_ref, it, rel = FS.cg(g, E, k0, f, fixed, rtol=1e-12)
+    assert rel <= 2e-12
+    c_ref = float(f @ u_ref)
+    dc_ref = -3.0 * rho.astype(np.float64) ** 2 * (1 - 1e-9) * FS.element_energies(g, k0, u_ref)
+    e = {"rel_residual_oracle": FS.rel_residual(g, E, k0, f, fixed, u),
+         "err_u": float(np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref)),
+         "err_c": float(abs(c - c_ref) / abs(c_ref)),
+         "err_dc": float(np.abs(dc - dc_ref).max() / np.abs(dc_ref).max()), "c": c, "c_ref": c_ref}
+    print("ACCURACY " + json.dumps({"workload": w.name, "rtol": 1e-8, "iters": info.iters,
+                                    "outer": info.outer, "ref": "oracle CG", "ref_iters": it,
+                                    "ref_rel_residual": rel, **e}))
+    assert e["rel_residual_oracle"] <= 1.01e-8
+    assert e["err_c"] <= 1e-8 and e["err_dc"] <= 1e-6
