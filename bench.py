@@ -354,15 +354,16 @@ def serving_summary(budget_gb: float = 40.0, loads=(0.5, 0.8, 1.0)):
     server: saturated throughput, then Poisson arrivals at fractions of it."""
     from paper_2605_04735_gb300 import serving as SV
     budget = int(budget_gb * 2**30)
+    opts = SV.server_opts()
     reqs = I.serving_stream(64, 30, rate=0.0)
-    sat = SV.summarize(*SV.run_stream(reqs, budget, 64, realtime=False))
+    sat = SV.summarize(*SV.run_stream(reqs, budget, 64, opts=opts, realtime=False))
     lam = sat["solves_per_s"] / 30
     out = {"workload": "64 requests x 30 solves, grids 2n x n x n, n in 12..64 step 4, half "
                        "cantilever / half MBB, densities perturbed +-5 % per solve",
-           "budget_gb": budget_gb, "saturated": sat, "lambda_sat_req_per_s": lam, "runs": {}}
+           "budget_gb": budget_gb, "check_every": opts.check_every, "saturated": sat, "lambda_sat_req_per_s": lam, "runs": {}}
     for f in loads:
         reqs_f = I.serving_stream(64, 30, rate=f * lam)
-        out["runs"][f"{f:.2f}x"] = SV.summarize(*SV.run_stream(reqs_f, budget, 64))
+        out["runs"][f"{f:.2f}x"] = SV.summarize(*SV.run_stream(reqs_f, budget, 64, opts=opts))
     out["cpu_baseline"] = serving_cpu_baseline(reqs)
     return out
 
