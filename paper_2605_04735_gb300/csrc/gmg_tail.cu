@@ -129,7 +129,7 @@ __device__ __forceinline__ LevelView tail_view(const TailPlan& p, float* smem, i
 }
 
 __device__ __forceinline__ float tail_dinv(float kdiag, float esum) {
-  return esum > 0.f ? 1.0f / (kdiag * esum) : 1.0f;
+  return esum > 0.f ? jacobi_rcp(kdiag * esum) : 1.0f;
 }
 
 }  // namespace

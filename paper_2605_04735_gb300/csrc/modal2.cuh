@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(kPairTX* kPairTY, 2)
           }
         if constexpr (DI >= 0) {  // D^-1 of the masked operator, 1 where no stiffness
           const float sa = es_prev.x + es.x, sb = es_prev.y + es.y;
-          const float da = sa > 0.f ? __frcp_rn(kc.kdiag * sa) : 1.0f;
-          const float db = sb > 0.f ? __frcp_rn(kc.kdiag * sb) : 1.0f;
+          const float da = sa > 0.f ? jacobi_rcp(kc.kdiag * sa) : 1.0f;
+          const float db = sb > 0.f ? jacobi_rcp(kc.kdiag * sb) : 1.0f;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             av[DI][0][c] = da;

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(128)
         for (int c = 0; c < 3; ++c) av[q][0][c] = ap[q * Tl::AuxStride + c * (Tl::AuxY * kMAuxX)];
       if constexpr (DI >= 0) {  // D^-1 of the masked operator, 1 where no stiffness
         const float sum = es_prev + es;
-        const float dv = sum > 0.f ? __frcp_rn(kdiag * sum) : 1.0f;
+        const float dv = sum > 0.f ? jacobi_rcp(kdiag * sum) : 1.0f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) av[DI][0][c] = dv;
       }

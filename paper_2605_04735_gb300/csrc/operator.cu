@@ -77,6 +77,11 @@ struct EpiResid {
   }
 };
 
+// 1 / x of a diagonal entry: FP32 through the same reciprocal as the kernels
+// that form D^-1 on the fly from the element moduli
+__device__ __forceinline__ float inv_diag(float x) { return jacobi_rcp(x); }
+__device__ __forceinline__ double inv_diag(double x) { return 1.0 / x; }
+
 // D^-1 of the masked operator: 1 / sum_{e owns n} E_e k0[3 ln + c][3 ln + c],
 // and 1 on fixed DOFs (and on nodes that touch no stiffness at all).
 template <typename T>
@@ -105,7 +110,7 @@ __global__ void k_diag_inv(T* __restrict__ dinv, const T* __restrict__ E, const 
   const long long o = d.node(i, j, k);
 #pragma unroll
   for (int r = 0; r < 3; ++r)
-    dinv[r * d.comp + o] = (d.fixed(r, i, j, k) || !(acc[r] > T(0))) ? T(1) : T(1) / acc[r];
+    dinv[r * d.comp + o] = (d.fixed(r, i, j, k) || !(acc[r] > T(0))) ? T(1) : inv_diag(acc[r]);
 }
 
 }  // namespace
