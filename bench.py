@@ -45,6 +45,17 @@ LARGE_WORKLOAD = "cantilever_voids_320x160x160"
 PAIR_AUTO_MIN_NX = 150  # the library's automatic modal form pairs columns from this nx on
 
 
+def exec_ops(op: int, nx: int, role: str) -> float | None:
+    """FP32 lane-operations per element executed by the default operator
+    kernels in `role` ("cheb_step" or "cg_apply"); None for the other forms
+    (not counted)."""
+    if op != 0:
+        return None
+    if role == "cheb_step":
+        return None if nx >= PAIR_AUTO_MIN_NX else EXEC_FP32_OPS_PER_ELEM["cheb_step"]
+    return EXEC_FP32_OPS_PER_ELEM["cg_apply_pair" if nx >= PAIR_AUTO_MIN_NX else "cg_apply_tma"]
+
+
 def operator_kernel(op: int, nx: int) -> str:
     """The FP32 operator kernel that runs for operator choice `op` on a grid
     of nx elements in x (topo.OPERATOR_*)."""
@@ -68,12 +79,16 @@ NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": 1960704.0 + 0.0,
 # capture each of a 64-design launch of the current kernel source
 # (profiles/k_modal_tma_batch64_mbb_96x32x32.md): the Chebyshev step in its
 # x-added form (8.00 MB algorithmic per design) and the CG apply
-NCU_TRAFFIC_BATCH = {"cheb_step": (307256576.0 + 201840384.0) / 64,
+NCU_TRAFFIC_BATCH = {"cheb_step": (306157056.0 + 201122304.0) / 64,
                      "cg_apply": (135333632.0 + 52475136.0) / 64}
-# FP32 lane-operations per element the modal kernels execute for one K u
-# (ncu instruction counts: the Walsh-Hadamard form of k0 instead of the dense
-# 2 x 24 x 24 product), the basis of the executed-operation floor
-EXEC_FP32_OPS_PER_ELEM = {"k_modal_pair": 165.0, "k_modal_tma": 200.0}
+# FP32 lane-operations the modal kernels execute per element of the grid
+# (ncu smsp__sass_thread_inst_executed_op_fp32_pred_on, a packed f32x2
+# instruction counted as two; halo columns and idle thread slots included),
+# the basis of the executed-operation floor: the Chebyshev step and the CG
+# apply of k_modal_tma in a 64-design 96x32x32 launch (1.744 G and 1.615 G
+# for 6.29 M elements), k_modal_pair's CG apply at 320x160x160 (2.125 G for
+# 8.19 M elements)
+EXEC_FP32_OPS_PER_ELEM = {"cheb_step": 277.1, "cg_apply_tma": 256.7, "cg_apply_pair": 259.4}
 FLOP_PER_ELEM = 2 * 24 * 24  # the dense K0 U_e product per element (multiply + add)
 
 
@@ -90,19 +105,18 @@ def fp32_lane_ops_per_s(sm_mhz: float) -> float:
 
 
 def hbm_roofline(kernel: str, w: I.Workload, bytes_per_launch: float, avg_ms: float,
-                 designs: float, peaks: dict, peaks_src: str, traffic: float | None = None) -> dict:
+                 designs: float, peaks: dict, peaks_src: str, traffic: float | None = None,
+                 ops: float | None = None) -> dict:
     """An operator kernel against the HBM roofline: achieved = its
     algorithmic bytes per launch / its average launch time (CUDA events),
     peak = the measured copy bandwidth.  Beside it the arithmetic view: the
-    dense-equivalent rate (1152 flop per element) and the floor the FP32
-    pipe sets for the operations the kernel actually executes."""
+    dense-equivalent rate (1152 flop per element) and, given `ops` (FP32
+    lane-operations executed per element), the floor the FP32 pipe sets."""
     t = avg_ms * 1e-3
     peak = float(peaks["hbm_gbs"])
     achieved = bytes_per_launch / t / 1e9
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     elems = w.n_elem * designs
-    name = kernel.split(" ")[0]
-    ops = EXEC_FP32_OPS_PER_ELEM.get(name)
     alu = {"dense_equivalent_tflops": FLOP_PER_ELEM * elems / t / 1e12,
            "note": "1152 flop per element is the dense K0.U_e product; the modal kernels reach "
                    "the same result with fewer executed operations"}
@@ -629,14 +643,17 @@ def main():
     avg_ms = prof_ms / max(prof_n, 1)
     lw = I.WORKLOADS[LARGE_WORKLOAD]
     kern = operator_kernel(args.operator, w.nx)
-    large = hbm_roofline(operator_kernel(args.operator, lw.nx) + ", CG apply", lw,
+    large_kern = operator_kernel(args.operator, lw.nx)
+    large = hbm_roofline(large_kern + ", CG apply", lw,
                          operator_bytes(lw), large_operator(topo, stream, flush, args.operator),
                          1.0, peaks, peaks_src,
-                         traffic=NCU_TRAFFIC.get(lw.name) if args.operator == 0 else None)
+                         traffic=NCU_TRAFFIC.get(lw.name) if args.operator == 0 else None,
+                         ops=exec_ops(args.operator, lw.nx, "cg_apply"))
     large["timed"] = "20 back-to-back CG applies, CUDA events, inputs above L2"
     single = hbm_roofline(kern + ", CG apply", w, operator_bytes(w), avg_ms, 1.0, peaks,
                           peaks_src,
-                          traffic=NCU_TRAFFIC.get(w.name) if args.operator == 0 else None)
+                          traffic=NCU_TRAFFIC.get(w.name) if args.operator == 0 else None,
+                          ops=exec_ops(args.operator, w.nx, "cg_apply"))
     single["timed"] = "CG applies of the single-design loop (one design alone, 2.9 MB: L2-resident)"
     single["launches"] = prof_n
     cg_apply = None
@@ -646,7 +663,7 @@ def main():
         cg_apply = hbm_roofline(kern + ", CG apply", w, operator_bytes(w),
                                 batch_op_ms / batch_op_units, 1.0, peaks, peaks_src,
                                 traffic=NCU_TRAFFIC_BATCH["cg_apply"] if args.operator == 0
-                                else None)
+                                else None, ops=exec_ops(args.operator, w.nx, "cg_apply"))
         cg_apply.update({"designs_per_launch": "varies (designs still iterating); figures per "
                                               "design-launch",
                          "avg_launch_us": None,
@@ -660,7 +677,7 @@ def main():
         main = hbm_roofline(kern + " with the Chebyshev-step epilogue", w,
                             cheb_bytes / cheb_units, cheb_ms / cheb_units, 1.0, peaks, peaks_src,
                             traffic=NCU_TRAFFIC_BATCH["cheb_step"] if args.operator == 0
-                            else None)
+                            else None, ops=exec_ops(args.operator, w.nx, "cheb_step"))
         main["traffic_note"] = ("ncu, one 64-design launch of the x-added form (8.00 MB "
                                 "algorithmic per design; bytes_per_launch averages the stored "
                                 "and added forms): DRAM / algorithmic = 0.99")

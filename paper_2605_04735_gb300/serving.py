@@ -113,6 +113,8 @@ def summarize(solves, reqs, wall, stats):
             "solves_per_s": len(solves) / wall,
             "solve_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "request_latency_ms": {"p50": float(np.percentile(rl, 50)), "p99": float(np.percentile(rl, 99))},
+            "iters_mean": float(np.mean([s["iters"] for s in solves])),
+            "dof_mean": float(np.mean([s["n_dof"] for s in solves])),
             "max_rel_residual": float(max(s["rel_residual"] for s in solves)),
             "peak_device_bytes": stats["peak_bytes"]}
 
