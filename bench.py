@@ -362,6 +362,81 @@ def serving_cpu_baseline(reqs) -> dict:
                         "cold solve (the GPU's solves are warm-started)"}
 
 
+def large_configs(topo, stream, flush, steps: int = 3, cpu_iters: int = 10) -> dict:
+    """The full-size cantilevers with voids (192x96x96: 5.4 M DOF, 40 voids;
+    320x160x160: 25.0 M DOF, 120 voids), one design each, through the public
+    API: the mixed-precision GMG-PCG step (density, solve to a true FP64
+    relative residual of 1e-8, compliance, sensitivities) timed with CUDA
+    events over `steps` steps after one warm-up step; one solve of the plain
+    FP64 Jacobi-PCG GPU path to the same residual; and the oracle's FP64
+    matrix-free Jacobi-PCG on the host, `cpu_iters` iterations timed on all
+    cores, its solve estimated at the iteration count the GPU's FP64
+    Jacobi-PCG needed (the same algorithm in the same arithmetic)."""
+    import torch
+    from oracle import fem
+    from oracle import fullsize as FS
+    out = {}
+    for name in ("cantilever_voids_192x96x96", LARGE_WORKLOAD):
+        w = I.WORKLOADS[name]
+        rho = w.density()
+        rec = {"dof": 3 * w.n_nodes}
+        with topo.Mesh(w.nx, w.ny, w.nz, w.bc, w.load, stream=stream) as m:
+            rd = torch.from_numpy(rho).cuda()
+            dc = torch.empty(w.n_elem, dtype=torch.float64, device="cuda")
+
+            def step(o):
+                m.set_density(rd)
+                info = m.solve(o)
+                m.compliance()
+                m.sensitivity(dc)
+                return info
+
+            opts = topo.default_opts(rtol=1e-8)
+            step(opts)  # hierarchy and graphs
+            ts, its = [], []
+            for k in range(steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                info = step(opts)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+                its.append((info.iters, info.outer, info.rel_residual))
+            rec["mixed_gmg"] = {"solves_per_s": 1e3 / float(np.mean(ts)),
+                                "ms_per_step": float(np.mean(ts)),
+                                "iters": its[-1][0], "outer": its[-1][1],
+                                "rel_residual": its[-1][2]}
+            o64 = topo.default_opts(precision=topo.PREC_FP64, precond=topo.PRECOND_JACOBI,
+                                    rtol=1e-8)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info = step(o64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms64 = a.elapsed_time(b)
+            rec["fp64_jacobi_pcg"] = {"solves_per_s": 1e3 / ms64, "ms_per_step": ms64,
+                                      "iters": info.iters, "rel_residual": info.rel_residual}
+            rec["gain_over_fp64_jacobi"] = ms64 / rec["mixed_gmg"]["ms_per_step"]
+        g = fem.Grid(w.nx, w.ny, w.nz)
+        E = fem.simp_modulus(rho)
+        k0 = fem.element_stiffness(1.0, 0.3)
+        f = fem.load_vector(g, w.load)
+        fixed = fem.fixed_dofs(g, w.bc)
+        t0 = time.perf_counter()
+        _, it, _ = FS.cg(g, E, k0, f, fixed, rtol=0.0, maxiter=cpu_iters)
+        per_it = (time.perf_counter() - t0) / max(it, 1)
+        n64 = rec["fp64_jacobi_pcg"]["iters"]
+        rec["cpu_baseline"] = {"value": 1.0 / (per_it * n64), "unit": UNIT,
+                               "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"{it} iterations of the oracle's FP64 matrix-free "
+                                         f"Jacobi-PCG: {per_it * 1e3:.1f} ms each; a solve "
+                                         f"to 1e-8 = {n64} iterations (the GPU FP64 "
+                                         f"Jacobi-PCG's count): {per_it * n64:.1f} s"}
+        out[name] = rec
+    return out
+
+
 def serving_summary(budget_gb: float = 40.0, loads=(0.5, 0.8, 1.0)):
     """The serving workload (64 requests x 30 solves, grids 24x12x12 ..
     128x64x64, half cantilever / half MBB) through the continuous-batching
@@ -410,6 +485,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--large", type=int, default=1,
+                    help="1: also time one design of 192x96x96 and of 320x160x160 (mixed GMG, "
+                         "plain FP64 Jacobi-PCG, the oracle's per-iteration time on the host)")
     ap.add_argument("--same-batch", type=int, default=1,
                     help="1: also time one step of the same batch with FP32 Jacobi-PCG + FP64 "
                          "refinement and with plain FP64 Jacobi-PCG")
@@ -735,6 +813,8 @@ def main():
         pool.shutdown()
     for m in meshes:
         m.close()
+    if args.large and ws == 1 and args.operator == 0:
+        line["large_configs"] = large_configs(topo, stream, flush)
     if args.serving and ws == 1:
         line["serving"] = serving_summary()
     print(json.dumps(line), flush=True)
