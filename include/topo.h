@@ -110,6 +110,12 @@ enum {
                                accuracy), the multigrid smoother's operator in one TF32 pass;
                                FP64 kernels and grids too small for the tiles (ny < 6) keep
                                the modal SIMT kernels */
+  ,
+  TOPO_OPERATOR_MODAL_CLUSTER = 5 /* modal, one element column per thread, the x tiles of a
+                                     grid row as one thread-block cluster passing the halo
+                                     column's sums through distributed shared memory (no
+                                     recomputed halo column); FP32 grids with nx <= 128 (others
+                                     use the tiled one-column kernel) */
 };
 
 enum {

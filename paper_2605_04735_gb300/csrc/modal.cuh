@@ -46,7 +46,8 @@ struct ModalCoef {
   T D[3][8];     // diagonal of K~ per component and mode (mode 0 unused)
   T C[3][3][8];  // coupling of (p, m) with (q, m ^ (1<<p) ^ (1<<q)), bits p, q of m differ
   T kdiag;       // every diagonal entry of k0 (the cube's symmetry makes them equal)
-  int form;  // FP32 kernel form: 0 automatic, 1 one column per thread, 2 two columns (packed)
+  int form;  // FP32 kernel form: 0 automatic, 1 one column per thread, 2 two columns (packed),
+             // 3 tensor cores, 4 one column per thread with the x tiles in a cluster
 };
 
 // a * b + c (overloaded for the double-word type)
@@ -237,6 +238,40 @@ __device__ __forceinline__ T modal_finish(const T (&plane)[3][4], T (*xch)[kModa
 
 constexpr int kModalOwnX = kModalTX - 1, kModalOwnY = kModalTY - 1;
 constexpr int kModalStages = 4;
+constexpr int kClRing = 4;       // halo-ring slots of the cluster form
+constexpr int kClMaxCtas = 8;    // portable cluster size: x extents up to 8 x 16 elements
+
+// The cluster form's exchange: as modal_exchange, but lane 0's left
+// neighbour corners (h1, h3) come from the CTA on the left instead of the
+// shuffle, and with `xn` (lane 15 of the last CTA when nx is a multiple of
+// 16) the +x corners of the thread's element also make the node column
+// x = nx: resX = its (1,0) corner plus the (1,1) corner of the row below,
+// passed through xchx.
+__device__ __forceinline__ void modal_exchange_cl(const float (&plane)[3][4],
+                                                  float (*xch)[kModalTX][3], float* xchx, int tx,
+                                                  int ty, const float (&h1)[3],
+                                                  const float (&h3)[3], bool xn, float (&res)[3],
+                                                  float (&resx)[3]) {
+  float n0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float r1 = shfl_up1(plane[c][1]);
+    float r3 = shfl_up1(plane[c][3]);
+    if (tx == 0) {
+      r1 = h1[c];
+      r3 = h3[c];
+    }
+    n0[c] = plane[c][0] + r1;
+    xch[ty][tx][c] = plane[c][2] + r3;
+    if (xn) xchx[ty * 3 + c] = plane[c][3];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    res[c] = n0[c] + (ty > 0 ? xch[ty - 1][tx][c] : 0.f);
+    if (xn) resx[c] = plane[c][1] + (ty > 0 ? xchx[(ty - 1) * 3 + c] : 0.f);
+  }
+}
 // node box columns: >= 3 (alignment slack) + kModalTX + 1, a multiple of 4
 constexpr int kMBoxX = kModalTX == 32 ? 40 : (kModalTX + 4 + 3) / 4 * 4;
 constexpr int kMAuxX = (kModalTX + 3 + 3) / 4 * 4;  // >= 3 (alignment slack) + kModalTX columns
@@ -261,20 +296,40 @@ struct MTile {
   static constexpr int AuxStride = (Aux + 31) / 32 * 32;
   static constexpr uint32_t AuxTx = (uint32_t)Aux * 4u;
   static constexpr size_t XchBytes = sizeof(float) * 2 * TY * kModalTX * 3;
+  // cluster form: the halo ring (kClRing slots of TY rows x 6 values, written
+  // by the CTA on the left), the exchange slot of the extra node column, and
+  // the ring's full and empty mbarriers
+  static constexpr int ClRingFloats = kClRing * TY * 6;
+  static constexpr int ClXchXFloats = 2 * TY * 3;
   __host__ __device__ static constexpr int stage_floats(int naux) {
     return StageBase + naux * AuxStride;
   }
-  __host__ __device__ static constexpr size_t smem(int naux) {
+  __host__ __device__ static constexpr size_t smem(int naux, bool cl = false) {
     return sizeof(float) * stage_floats(naux) * kModalStages + XchBytes +
-           sizeof(uint64_t) * kModalStages + 128;  // + alignment slack
+           sizeof(uint64_t) * kModalStages + 128 +  // + alignment slack
+           (cl ? sizeof(uint64_t) * 2 * kClRing + sizeof(float) * (ClRingFloats + ClXchXFloats)
+               : 0);
   }
 };
 
 // Grid: (x tiles, y tiles, zc z-chunks x designs); design b reads and writes
 // its own buffers at b * S bytes from design 0's (the TMA maps carry the
 // design as their outermost dimension).
-template <class Epi, int TY>
-__global__ void __launch_bounds__(kModalTX* TY)
+//
+// CL (the cluster form): the x tiles of a (y tile, z chunk, design) are one
+// thread-block cluster of gridDim.x CTAs, CTA k covering element columns
+// 16 k .. 16 k + 15 with no halo column: lane tx owns the corner-0 node of
+// its own element, and the +x corners of the left neighbour element (lane 15
+// of CTA k - 1) come through a ring of kClRing slots in this CTA's shared
+// memory that CTA k - 1 writes with st.async, each store completing its
+// bytes on the slot's full mbarrier here (armed with the slot's TY x 24
+// bytes by thread 0 per use; no fence on the writer's side).  Thread 0 (row
+// 0 owns no node, so it has no global stores in flight) frees a slot for the
+// writer by a release arrival on the writer's empty mbarrier once the
+// layer's barrier shows every row has read it.  When nx = 16 x (CTAs), lane
+// 15 of the last CTA also finishes node column nx.
+template <class Epi, int TY, bool CL = false>
+__global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
                 const __grid_constant__ CUtensorMap amap0,
                 const __grid_constant__ CUtensorMap amap1, const Dims d,
@@ -304,9 +359,17 @@ __global__ void __launch_bounds__(kModalTX* TY)
       base + sizeof(float) * SF * kModalStages);
   uint64_t* bar =
       reinterpret_cast<uint64_t*>(base + sizeof(float) * SF * kModalStages + Tl::XchBytes);
+  // cluster form: ring mbarriers, ring values, the extra column's exchange
+  uint64_t* cl_full = bar + kModalStages;
+  uint64_t* cl_empty = cl_full + kClRing;
+  float* ring = reinterpret_cast<float*>(cl_empty + kClRing);
+  float* xchx = ring + Tl::ClRingFloats;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kModalTX + tx;
-  const int x0 = blockIdx.x * kModalOwnX, y0 = blockIdx.y * Tl::OwnY;
+  const int crank = CL ? (int)blockIdx.x : 0, ncl = CL ? (int)gridDim.x : 1;
+  // x0 - 1: the first element column (the halo's in the tiled form); CL: 16 k
+  const int x0 = CL ? crank * kModalTX + 1 : blockIdx.x * kModalOwnX;
+  const int y0 = blockIdx.y * Tl::OwnY;
   const int ex = x0 - 1 + tx, ey = y0 - 1 + ty;
   const int bx = x0 & ~3;  // 16-byte aligned box start (storage x of node x0-1 is x0)
   const int ox = x0 - bx;
@@ -315,7 +378,15 @@ __global__ void __launch_bounds__(kModalTX* TY)
   const int nst = (ke - kb) + 2;  // stage t: node plane kb-2+t+1, element layer kb-2+t
   if (tid == 0) {
     for (int q = 0; q < kModalStages; ++q) mbar_init(&bar[q], 1);
+    if constexpr (CL)
+      for (int q = 0; q < kClRing; ++q) {
+        mbar_init(&cl_full[q], 1);
+        mbar_init(&cl_empty[q], 1);
+      }
     fence_mbar_init();
+    if constexpr (CL)
+      if (crank > 0)  // every slot armed for its first use
+        for (int q = 0; q < kClRing; ++q) mbar_arrive_expect_tx(&cl_full[q], TY * 24u);
     tma_prefetch_desc(&xmap);
     tma_prefetch_desc(&emap);
     if (NA > 0) tma_prefetch_desc(&amap0);
@@ -332,7 +403,10 @@ __global__ void __launch_bounds__(kModalTX* TY)
       mbar_wait_bounded(&never_bar, 0u, errflag, 64u);
     }
   }
-  __syncthreads();
+  if constexpr (CL)
+    cluster_sync();  // every CTA's ring barriers exist before any remote arrival
+  else
+    __syncthreads();
   // stage t: node plane kb-1+t, element layer kb-2+t and, once that plane
   // has an epilogue (t >= 2), the operand planes of node plane kb-2+t
   auto issue = [&](int t) {
@@ -351,22 +425,32 @@ __global__ void __launch_bounds__(kModalTX* TY)
   };
   if (tid == 0)
     for (int t = 0; t < kModalStages && t < nst; ++t) issue(t);
-  const bool own = tx > 0 && ty > 0 && ex <= d.nx && ey <= d.ny;
+  const bool own = (CL || tx > 0) && ty > 0 && ex <= d.nx && ey <= d.ny;
+  // CL: lane 15 of the last CTA also owns node column nx when no lane's
+  // element column is nx
+  const bool xn = CL && crank == ncl - 1 && tx == kModalTX - 1 && d.nx == ncl * kModalTX;
+  const bool xown = xn && ty > 0 && ey <= d.ny;
   // tiles without any fixed DOF run the epilogue without the per-DOF support test
-  const bool clean = !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
+  const bool clean = CL ? !d.box_may_fix(x0 - 1, min(x0 + kModalTX - 1, d.nx), y0, kb)
+                        : !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
   const FreeDims fd{d.comp};
   ModalColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   float es_prev = 0.f;  // (DI) moduli of the 2 x 2 elements below node (ex, ey), layer before
+  float esx_prev = 0.f;  // the same for node (nx, ey) (xn)
+  float xr[3] = {0.f, 0.f, 0.f};  // (xn) raw node (nx, ey) of the last plane read
   // stage (slot, phase) -> registers: the top node plane, the element
   // modulus and (DI) the moduli of the 2 x 2 elements around (ex, ey)
-  auto read_stage = [&](int r, uint32_t ph, float(&top)[2][2][3], float& E, float& es) {
+  auto read_stage = [&](int r, uint32_t ph, float(&top)[2][2][3], float& E, float& es,
+                        float& esx) {
     mbar_wait_bounded(&bar[r], ph, errflag);
     const float* nd = stg + r * SF;
     es = 0.f;
+    esx = 0.f;
     if (DI >= 0) {  // used by owned nodes only; the others read inside the stage too
       const float* e0 = nd + Tl::ElemOff + (ty - 1) * kMBoxX + ox + tx - 1;
       es = (e0[0] + e0[1]) + (e0[kMBoxX] + e0[kMBoxX + 1]);
+      if (xn) esx = (e0[1] + e0[2]) + (e0[kMBoxX + 1] + e0[kMBoxX + 2]);
     }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
@@ -379,7 +463,9 @@ __global__ void __launch_bounds__(kModalTX* TY)
   };
   {  // the first node plane only seeds the march
     float top[2][2][3], E;
-    read_stage(0, 0u, top, E, es_prev);
+    read_stage(0, 0u, top, E, es_prev, esx_prev);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) xr[c] = top[0][1][c];
     __syncthreads();
     if (tid == 0 && kModalStages < nst) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -392,13 +478,49 @@ __global__ void __launch_bounds__(kModalTX* TY)
   uint32_t phase = 0u;
   for (int t = 1; t < nst; ++t) {
     const float* nd = stg + rs * SF;
-    float top[2][2][3], E, es;
-    read_stage(rs, phase, top, E, es);
+    float top[2][2][3], E, es, esx;
+    read_stage(rs, phase, top, E, es, esx);
     float plane[3][4], ctr[3];
     modal_layer<float>(col, top, E, kc, plane, ctr);
     const int ez = kb - 2 + t;
-    float res[3];
-    modal_exchange<float>(plane, xch[t & 1], tx, ty, res);
+    float res[3], resx[3], ctrx[3];
+    if constexpr (CL) {
+      // layer t - 1 (from 0) uses halo-ring slot (t - 1) % kClRing for the
+      // (t - 1) / kClRing-th time
+      const int hs = (t - 1) % kClRing;
+      const uint32_t use = (uint32_t)(t - 1) / kClRing;
+      if (tx == kModalTX - 1 && crank + 1 < ncl) {  // this row's +x corners to the right
+        if (use > 0) mbar_wait_cluster_bounded(&cl_empty[hs], (use - 1u) & 1u, errflag);
+        const uint32_t dst = cluster_map(smem_u32(ring + (hs * TY + ty) * 6), crank + 1);
+        const uint32_t rb = cluster_map(smem_u32(&cl_full[hs]), crank + 1);
+        cluster_st_async_v2(dst, plane[0][1], plane[1][1], rb);
+        cluster_st_async_v2(dst + 8u, plane[2][1], plane[0][3], rb);
+        cluster_st_async_v2(dst + 16u, plane[1][3], plane[2][3], rb);
+      }
+      float h1[3] = {0.f, 0.f, 0.f}, h3[3] = {0.f, 0.f, 0.f};  // the left element's corners
+      if (tx == 0 && crank > 0) {
+        mbar_wait_bounded(&cl_full[hs], use & 1u, errflag);
+        const float* src = ring + (hs * TY + ty) * 6;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          h1[c] = src[c];
+          h3[c] = src[3 + c];
+        }
+      }
+      modal_exchange_cl(plane, xch[t & 1], xchx + (t & 1) * (TY * 3), tx, ty, h1, h3, xn, res,
+                        resx);
+      if (tid == 0 && crank > 0) {  // every row has read slot hs: re-arm it, free it
+        mbar_arrive_expect_tx(&cl_full[hs], TY * 24u);
+        mbar_arrive_remote(cluster_map(smem_u32(&cl_empty[hs]), crank - 1));
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {  // raw node (nx, ey, ez), then the top plane's
+        ctrx[c] = xr[c];
+        xr[c] = top[0][1][c];
+      }
+    } else {
+      modal_exchange<float>(plane, xch[t & 1], tx, ty, res);
+    }
     // the slot the exchange barrier retires: stage t's (its node data is
     // read), or with staged operands stage t-1's (its epilogue, before this
     // barrier, was the last reader; stage 0's slot was refilled after the seed)
@@ -430,6 +552,33 @@ __global__ void __launch_bounds__(kModalTX* TY)
       else
         part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
     }
+    if constexpr (CL) {
+      if (xown && t >= 2) {  // node column nx (lane 15 of the last CTA)
+        const int ii[1] = {d.nx};
+        const long long oo[1] = {d.node(d.nx, ey, ez)};
+        const bool ow[1] = {true};
+        const float rr[1][3] = {{resx[0], resx[1], resx[2]}};
+        const float cc[1][3] = {{ctrx[0], ctrx[1], ctrx[2]}};
+        float av[epi_slots<Epi>()][1][3];
+        const float* ap = nd + Tl::StageBase + (ty - 1) * kMAuxX + ox + tx + 1;
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            av[q][0][c] = ap[q * Tl::AuxStride + c * (Tl::AuxY * kMAuxX)];
+        if constexpr (DI >= 0) {
+          const float sum = esx_prev + esx;
+          const float dv = sum > 0.f ? jacobi_rcp(kc.kdiag * sum) : 1.0f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) av[DI][0][c] = dv;
+        }
+        if (clean)
+          part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, fd);
+        else
+          part += epi.template finish<1>(ii, ey, ez, oo, ow, rr, cc, av, d);
+      }
+      esx_prev = esx;
+    }
     es_prev = es;
     if (++rs == kModalStages) {
       rs = 0;
@@ -441,6 +590,7 @@ __global__ void __launch_bounds__(kModalTX* TY)
     reduce_finalize<1>(v, red, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * chunk),
                        gridDim.x * gridDim.y * zc);
   }
+  if constexpr (CL) cluster_sync();  // no CTA leaves while a neighbour may reach its ring
 }
 
 // Plain-load variant (FP64, and FP32 grids too small for the TMA boxes):
@@ -559,6 +709,58 @@ inline int modal_pick_ty(const Dims& d, int nb) {
   return best < 0 ? kModalTY : best;
 }
 
+// Use the cluster form?  form 4 asks for it; the automatic form takes it
+// with TOPO_MODAL_CLUSTER_AUTO.  It needs the x extent within one portable
+// cluster (nx <= 8 x 16).
+#ifndef TOPO_MODAL_CLUSTER_AUTO
+#define TOPO_MODAL_CLUSTER_AUTO 0
+#endif
+inline bool modal_use_cluster(const Dims& d, int form) {
+  const int ncl = (d.nx + kModalTX - 1) / kModalTX;
+  return (form == 4 || (form == 0 && TOPO_MODAL_CLUSTER_AUTO)) && ncl <= kClMaxCtas;
+}
+
+template <class Epi, int TY, bool CL>
+cudaError_t launch_modal_tma_form(const CUtensorMap& xm, const CUtensorMap& em,
+                                  const CUtensorMap (&am)[2], const Dims& d,
+                                  const ModalCoef<float>& kc, const Epi& epi, const Red& red,
+                                  const int* done, int* errflag, cudaStream_t s, const Bat& bt) {
+  constexpr size_t smem = MTile<TY>::smem(epi_staged<Epi>(), CL);
+  static bool attr = false;  // per instantiation; setting it twice is harmless
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_modal_tma<Epi, TY, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int z = modal_zchunk(d, bt.nb, TY - 1);
+  const int zc = (d.nz + z) / z;
+  dim3 block(kModalTX, TY, 1);
+  const int gx = CL ? (d.nx + kModalTX - 1) / kModalTX : (d.nx + kModalOwnX) / kModalOwnX;
+  dim3 grid(gx, (d.ny + TY - 1) / (TY - 1), zc * bt.nb);
+  if constexpr (CL) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)gx;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_modal_tma<Epi, TY, true>, xm, em, am[0], am[1], d, kc, epi,
+                              red, z, zc, bt.sel(), done, errflag);
+  } else {
+    return launch_pdl(k_modal_tma<Epi, TY, false>, grid, block, smem, s, xm, em, am[0], am[1], d,
+                      kc, epi, red, z, zc, bt.sel(), done, errflag);
+  }
+}
+
 template <class Epi, int TY>
 cudaError_t launch_modal_tma(const float* x, const float* E, const Dims& d,
                              const ModalCoef<float>& kc, const Epi& epi, const Red& red,
@@ -571,21 +773,11 @@ cudaError_t launch_modal_tma(const float* x, const float* E, const Dims& d,
   for (int q = 0; q < epi_staged<Epi>() && ok; ++q)
     ok = modal_aux_map(epi.aux(q), d, bt, TY, &am[q]);
   if (!ok) return cudaSuccess;  // the boxes do not fit: the plain kernel
-  constexpr size_t smem = MTile<TY>::smem(epi_staged<Epi>());
-  static bool attr = false;  // per instantiation; setting it twice is harmless
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_modal_tma<Epi, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int z = modal_zchunk(d, bt.nb, TY - 1);
-  const int zc = (d.nz + z) / z;
-  dim3 block(kModalTX, TY, 1);
-  dim3 grid((d.nx + kModalOwnX) / kModalOwnX, (d.ny + TY - 1) / (TY - 1), zc * bt.nb);
   *launched = true;
-  return launch_pdl(k_modal_tma<Epi, TY>, grid, block, smem, s, xm, em, am[0], am[1], d, kc, epi,
-                    red, z, zc, bt.sel(), done, errflag);
+  if (modal_use_cluster(d, kc.form))
+    return launch_modal_tma_form<Epi, TY, true>(xm, em, am, d, kc, epi, red, done, errflag, s,
+                                                bt);
+  return launch_modal_tma_form<Epi, TY, false>(xm, em, am, d, kc, epi, red, done, errflag, s, bt);
 }
 
 template <typename T, class Epi>

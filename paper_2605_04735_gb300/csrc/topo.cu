@@ -2680,12 +2680,14 @@ topo_status topo_get_density(topo_mesh* m, float* rho, size_t n_elem, int on_dev
 }
 
 topo_status topo_set_operator(topo_mesh* m, int kind) {
-  if (!m || kind < TOPO_OPERATOR_MODAL || kind > TOPO_OPERATOR_TENSOR) return TOPO_ERR_INVALID;
+  if (!m || kind < TOPO_OPERATOR_MODAL || kind > TOPO_OPERATOR_MODAL_CLUSTER)
+    return TOPO_ERR_INVALID;
   const bool modal = (kind != TOPO_OPERATOR_GATHER);
-  const int form = kind == TOPO_OPERATOR_MODAL_SINGLE ? 1
-                   : kind == TOPO_OPERATOR_MODAL_PAIR ? 2
-                   : kind == TOPO_OPERATOR_TENSOR     ? 3
-                                                      : 0;
+  const int form = kind == TOPO_OPERATOR_MODAL_SINGLE    ? 1
+                   : kind == TOPO_OPERATOR_MODAL_PAIR    ? 2
+                   : kind == TOPO_OPERATOR_TENSOR        ? 3
+                   : kind == TOPO_OPERATOR_MODAL_CLUSTER ? 4
+                                                         : 0;
   if (modal != m->use_modal || form != m->mcf.form) {
     CK(cudaSetDevice(m->dev));
     CK(cudaStreamSynchronize(m->stream));

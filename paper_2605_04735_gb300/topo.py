@@ -26,6 +26,7 @@ RESIDUAL_DWORD, RESIDUAL_FP64 = 0, 1
 PRECOND_JACOBI, PRECOND_GMG = 0, 1
 OPERATOR_MODAL, OPERATOR_GATHER, OPERATOR_MODAL_SINGLE, OPERATOR_MODAL_PAIR = 0, 1, 2, 3
 OPERATOR_TENSOR = 4
+OPERATOR_MODAL_CLUSTER = 5
 
 
 class Params(C.Structure):
@@ -500,7 +501,8 @@ class Mesh:
 
     def set_operator(self, kind):
         """OPERATOR_MODAL (default, automatic FP32 kernel form), OPERATOR_GATHER,
-        OPERATOR_MODAL_SINGLE or OPERATOR_MODAL_PAIR for all later calls."""
+        OPERATOR_MODAL_SINGLE, OPERATOR_MODAL_PAIR, OPERATOR_TENSOR or
+        OPERATOR_MODAL_CLUSTER for all later calls."""
         _check(lib().topo_set_operator(self._h, kind), "topo_set_operator")
 
     def set_stream(self, stream):

@@ -58,7 +58,9 @@ PAIR_CASES = [
     (80, 12, 12, I.BC_CORNERS, I.LOAD_DISC_XL),
     (128, 16, 9, I.BC_MBB_STRIP, I.LOAD_HALFDISC_X0_TOP),
 ]
-OPS = [0, 1, 2, 3]  # modal (automatic form), node-centric gather, modal one column, modal paired
+# modal (automatic form), node-centric gather, modal one column, modal paired,
+# modal one column with the x tiles as one thread-block cluster
+OPS = [0, 1, 2, 3, 5]
 
 
 @pytest.mark.parametrize("case", CASES + PAIR_CASES)
