@@ -63,6 +63,9 @@ def operator_kernel(op: int, nx: int) -> str:
         return "k_stencil_tma (FP32 node-centric 27-node gather)"
     if op == 4:
         return "k_tc_tma (tensor cores: K0.U_e as TF32 tcgen05 GEMMs, accumulator in TMEM)"
+    if op == 5 and nx <= 128:
+        return ("k_modal_tma, cluster form (FP32 modal operator, one element column per thread, "
+                "the x tiles of a grid row as one thread-block cluster)")
     if op == 3 or (op == 0 and nx >= PAIR_AUTO_MIN_NX):
         return "k_modal_pair (FP32 modal operator, two element columns per thread, packed f32x2)"
     return "k_modal_tma (FP32 modal operator, one element column per thread)"
@@ -484,7 +487,7 @@ def main():
                     help="Chebyshev smoothing degree of the V-cycle (0: the library's default)")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--precond", type=int, default=1)
-    ap.add_argument("--operator", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--operator", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="operator kernel family (topo.OPERATOR_*)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the plain FP64 Jacobi-PCG path timed for comparison")
