@@ -831,10 +831,18 @@ def main():
         pool.shutdown()
     for m in meshes:
         m.close()
+    # the side measurements after the headline: a failure there is reported
+    # in its own key and does not lose the headline line
     if args.large and ws == 1 and args.operator == 0:
-        line["large_configs"] = large_configs(topo, stream, flush)
+        try:
+            line["large_configs"] = large_configs(topo, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            line["large_configs"] = {"error": f"{type(e).__name__}: {e}"}
     if args.serving and ws == 1:
-        line["serving"] = serving_summary()
+        try:
+            line["serving"] = serving_summary()
+        except Exception as e:  # noqa: BLE001
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
