@@ -1,0 +1,47 @@
+"""The benchmark's roofline arithmetic on CPU: the algorithmic bytes of a CG
+apply (read x, write y: 24 B per node; the modulus: 4 B per element), the
+achieved bandwidth and its fraction of the peak, the executed-operation FP32
+floor, and which kernel and operation count each operator choice reports."""
+import pytest
+
+import bench
+from paper_2605_04735_gb300 import inputs as I
+
+
+def test_operator_bytes_count_nodes_and_elements():
+    w = I.WORKLOADS["mbb_96x32x32"]
+    assert w.n_nodes == 97 * 33 * 33 and w.n_elem == 96 * 32 * 32
+    assert bench.operator_bytes(w) == 24 * 97 * 33 * 33 + 4 * 96 * 32 * 32
+
+
+def test_hbm_roofline_is_bytes_over_time_over_peak():
+    w = I.WORKLOADS["mbb_96x32x32"]
+    peaks = {"hbm_gbs": 6000.0, "sm_max_mhz": 2000.0}
+    nbytes, ms = 3.0e6, 0.002  # 3 MB in 2 us: 1.5 TB/s
+    r = bench.hbm_roofline("k", w, nbytes, ms, 1.0, peaks, "measured", traffic=3.1e6, ops=250.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(1500.0)
+    assert r["frac"] == pytest.approx(0.25)
+    assert r["hbm_floor_us"] == pytest.approx(0.5)
+    assert r["traffic"] == 3.1e6
+    # 98,304 elements x 250 lane-operations over 152 SMs x 128 lanes x 2 GHz
+    floor_us = w.n_elem * 250.0 / (152 * 128 * 2.0e9) * 1e6
+    assert r["alu_view"]["executed_floor_us"] == pytest.approx(floor_us)
+    assert r["alu_view"]["executed_frac_of_fp32_pipe"] == pytest.approx(floor_us / 2.0)
+    # no operation count: no executed floor
+    assert "executed_floor_us" not in bench.hbm_roofline("k", w, nbytes, ms, 1.0, peaks,
+                                                         "measured")["alu_view"]
+
+
+def test_executed_operation_counts_follow_the_kernel_choice():
+    small, large = 96, 320  # the one-column and the paired kernel (nx >= 150)
+    assert bench.exec_ops(0, small, "cheb_step") == bench.EXEC_FP32_OPS_PER_ELEM["cheb_step"]
+    assert bench.exec_ops(0, small, "cg_apply") == bench.EXEC_FP32_OPS_PER_ELEM["cg_apply_tma"]
+    assert bench.exec_ops(0, large, "cg_apply") == bench.EXEC_FP32_OPS_PER_ELEM["cg_apply_pair"]
+    assert bench.exec_ops(0, large, "cheb_step") is None  # not counted for the paired kernel
+    for op in (1, 2, 3, 4, 5):  # the other forms are not counted
+        assert bench.exec_ops(op, small, "cg_apply") is None
+    assert bench.operator_kernel(0, small).startswith("k_modal_tma")
+    assert bench.operator_kernel(0, large).startswith("k_modal_pair")
+    assert bench.operator_kernel(4, small).startswith("k_tc_tma")
+    assert "cluster" in bench.operator_kernel(5, small)
