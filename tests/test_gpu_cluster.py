@@ -115,3 +115,33 @@ def test_cluster_batch_matches_tiled_batch(topo):
         assert i2.rel_residual <= 1e-10
         assert _rel(u2, u1) <= 1e-8
         assert c2 == pytest.approx(c1, rel=1e-8)
+
+
+def test_cluster_batch_designs_sit_out_after_converging(topo):
+    """Designs of a group that converge at different outer steps: the ones
+    done early sit out the later launches (whole clusters return at once) and
+    keep their results; each design matches its own solve alone."""
+    nx, ny, nz, nb = 48, 12, 12, 4
+    opts = topo.default_opts(rtol=1e-10)
+    rhos = [np.ones(nx * ny * nz, np.float32)] + \
+           [I.density_voids(nx, ny, nz, 8, seed=s, rmin=2.0, rmax=4.0) for s in range(nb - 1)]
+    meshes = topo.create_batch(nb, nx, ny, nz, opts=opts)
+    try:
+        for m, r in zip(meshes, rhos):
+            m.set_operator(topo.OPERATOR_MODAL_CLUSTER)
+            m.set_density(r)
+        infos = topo.solve_many(meshes, opts)
+        us = [m.displacement() for m in meshes]
+    finally:
+        for m in meshes:
+            m.close()
+    assert len({i.outer for i in infos}) > 1  # they do finish at different steps
+    for b in range(nb):
+        with topo.Mesh(nx, ny, nz, I.BC_CANTILEVER, I.LOAD_EDGE_XL_BOTTOM) as m:
+            m.set_operator(topo.OPERATOR_MODAL_CLUSTER)
+            m.set_density(rhos[b])
+            info1 = m.solve(opts)
+            u1 = m.displacement()
+        assert infos[b].status == 0 and infos[b].rel_residual <= 1e-10
+        assert infos[b].outer == info1.outer
+        assert _rel(us[b], u1) <= 1e-8
