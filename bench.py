@@ -670,7 +670,7 @@ def main():
     step_batch(rho_host.numpy(), dc_host.numpy(), opts)
     torch.cuda.synchronize()
     e2e_t = []
-    for k in range(max(3, args.steps // 2)):
+    for k in range(max(5, args.steps)):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()

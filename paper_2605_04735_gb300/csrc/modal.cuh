@@ -671,11 +671,20 @@ __global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAI
 // whole columns (up to 64 planes), and the chunks of a column are equal
 // (a floor of 8 or 16 planes measured 1-5 % more solves/s with 64 designs in
 // flight on 96x32x32 but 57-147 % more latency for one design: 4 it is)
+// z chunks per launch: planes per CTA column ~ the launch's (tiles x planes
+// x designs) over 152 SMs x 2 x TOPO_ZCHUNK_WAVES (at least 4, at most 64);
+// full 256-design batches of 96x32x32 keep whole columns, narrower launches
+// (the lockstep tail, where few designs still iterate) split them.  Measured
+// on the batched 96x32x32 Chebyshev step: 4 -> 2.003, 8 -> 1.987 us per
+// design and launch.
+#ifndef TOPO_ZCHUNK_WAVES
+#define TOPO_ZCHUNK_WAVES 8
+#endif
 inline int modal_zchunk(const Dims& d, int nb = 1, int own_y = kModalOwnY) {
   const long long xy = (long long)((d.nx + kModalOwnX) / kModalOwnX) *
                        ((d.ny + own_y) / own_y);
   const int planes = d.nz + 1;
-  int z = (int)((xy * planes * nb) / (152 * 2 * 4));
+  int z = (int)((xy * planes * nb) / (152 * 2 * TOPO_ZCHUNK_WAVES));
   if (z < 4) z = 4;
   if (z > 64) z = 64;
   while (xy * ((planes + z - 1) / z) > kMaxPartials) ++z;
