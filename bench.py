@@ -42,6 +42,7 @@ from paper_2605_04735_gb300 import inputs as I  # noqa: E402
 METRIC = "PCG state solves/s at true FP64 rel. residual 1e-8 (solve + compliance + sensitivity)"
 UNIT = "solves/s"
 LARGE_WORKLOAD = "cantilever_voids_320x160x160"
+SAME_BATCH = 256  # designs of the precision / preconditioner comparison group
 PAIR_AUTO_MIN_NX = 150  # the library's automatic modal form pairs columns from this nx on
 
 
@@ -369,7 +370,8 @@ def serving_cpu_baseline(reqs) -> dict:
                         "cold solve (the GPU's solves are warm-started)"}
 
 
-def large_configs(topo, stream, flush, steps: int = 3, cpu_iters: int = 10) -> dict:
+def large_configs(topo, stream, flush, steps: int = 3, cpu_iters: int = 10,
+                  peaks: dict | None = None, peaks_src: str = "") -> dict:
     """The full-size cantilevers with voids (192x96x96: 5.4 M DOF, 40 voids;
     320x160x160: 25.0 M DOF, 120 voids), one design each, through the public
     API: the mixed-precision GMG-PCG step (density, solve to a true FP64
@@ -414,6 +416,31 @@ def large_configs(topo, stream, flush, steps: int = 3, cpu_iters: int = 10) -> d
                                 "ms_per_step": float(np.mean(ts)),
                                 "iters": its[-1][0], "outer": its[-1][1],
                                 "rel_residual": its[-1][2]}
+            if name == LARGE_WORKLOAD and peaks:
+                # the step's largest kernel, the finest-level Chebyshev step,
+                # timed live by the library's event pair around each launch
+                # (in separate steps: the events ride in the captured graphs,
+                # whose first profiled use captures them again)
+                m.profile(True)
+                step(opts)
+                m.profile_read_smoother(reset=True)
+                for k in range(steps):
+                    flush.fill_(float(k))
+                    step(opts)
+                torch.cuda.synchronize()
+                cms, cn, cb = m.profile_read_smoother(reset=True)
+                m.profile(False)
+                if cn > 0:
+                    r = hbm_roofline(operator_kernel(0, w.nx) + " with the Chebyshev-step "
+                                     "epilogue, finest level", w, cb / cn, cms / cn, 1.0, peaks,
+                                     peaks_src)
+                    r.update({"bytes_rule": "per node 60 B (x stored) or 72 B (x added), per "
+                                            "element 4 B",
+                              "launches": cn,
+                              "timed": f"every finest-level Chebyshev step of {steps} full "
+                                       "steps of one design, CUDA events on the library's "
+                                       "stream; inputs above L2"})
+                    rec["roofline_cheb_step"] = r
             o64 = topo.default_opts(precision=topo.PREC_FP64, precond=topo.PRECOND_JACOBI,
                                     rtol=1e-8)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -471,7 +498,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mbb_96x32x32", choices=sorted(I.WORKLOADS))
-    ap.add_argument("--batch", type=int, default=256,
+    ap.add_argument("--batch", type=int, default=1024,
                     help="independent designs solved concurrently per step")
     ap.add_argument("--check-every", type=int, default=0,
                     help="CG iterations between host convergence checks (0: the library's "
@@ -697,35 +724,54 @@ def main():
         fp64 = {"solves_per_s": 1e3 / float(np.mean(ts)), "ms_per_solve": float(np.mean(ts)),
                 "iters": int(np.mean(its)), "batch": 1}
 
-    # ---- the same batch (one step of every design, same group, same
-    # accuracy) with the plain FP64 Jacobi-PCG path and with FP32 Jacobi-PCG
-    # inside FP64 refinement: the precision and preconditioner gains apart ----
+    # ---- the same designs (the first SAME_BATCH of the batch, one mesh group
+    # of their own, same accuracy) with the mixed GMG path, with FP32
+    # Jacobi-PCG inside FP64 refinement and with the plain FP64 Jacobi-PCG
+    # path: the precision and preconditioner gains apart ----
     same_batch = None
     if args.same_batch and batched and rank == 0:
-        same_batch = {"what": "one step of the same batch (densities, solve to true rel. "
-                              "residual 1e-8, compliances, sensitivities), one mesh group in "
-                              "lockstep, CUDA events, L2 flushed; graph capture included",
-                      "fp32_gmg_ir": {"solves_per_s": value,
-                                      "iters_mean": float(np.mean([r[0] for r in recs]))}}
-        for key, prec in (("fp32_jacobi_ir", topo.PREC_FP32), ("fp64_jacobi_pcg", topo.PREC_FP64)):
-            oj = topo.default_opts(precision=prec, precond=topo.PRECOND_JACOBI, rtol=1e-8)
+        nb = min(B, SAME_BATCH)
+        sub = topo.create_batch(nb, w.nx, w.ny, w.nz, w.bc, w.load, stream=stream, opts=opts)
+        r_sub, d_sub = rho_dev[:nb], dc_dev[:nb]
+
+        def step_sub(o):
+            topo.set_density_many(sub, r_sub)
+            infos_s = topo.solve_many(sub, o)
+            topo.compliance_many(sub)
+            topo.sensitivity_many(sub, d_sub)
+            return infos_s
+
+        same_batch = {"what": f"one step of the first {nb} designs of the batch as one mesh "
+                              "group (densities, solve to true rel. residual 1e-8, "
+                              "compliances, sensitivities), lockstep, CUDA events, L2 flushed; "
+                              "the Jacobi paths' graph capture included",
+                      "designs": nb}
+        for key, prec, pc in (("fp32_gmg_ir", topo.PREC_FP32, topo.PRECOND_GMG),
+                              ("fp32_jacobi_ir", topo.PREC_FP32, topo.PRECOND_JACOBI),
+                              ("fp64_jacobi_pcg", topo.PREC_FP64, topo.PRECOND_JACOBI)):
+            oj = opts if pc == topo.PRECOND_GMG else topo.default_opts(
+                precision=prec, precond=pc, rtol=1e-8)
+            if pc == topo.PRECOND_GMG:
+                step_sub(oj)  # hierarchy and graphs
             flush.fill_(3.0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            infos_j, _ = step_batch(rho_dev, dc_dev, oj)
+            infos_j = step_sub(oj)
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
-            same_batch[key] = {"solves_per_s": B * 1e3 / ms, "ms_per_step": ms,
+            same_batch[key] = {"solves_per_s": nb * 1e3 / ms, "ms_per_step": ms,
                                "iters_mean": float(np.mean([i.iters for i in infos_j])),
                                "outer_mean": float(np.mean([i.outer for i in infos_j])),
                                "rel_residual_max": float(max(i.rel_residual for i in infos_j))}
-        same_batch["gain_fp32_over_fp64_jacobi"] = (same_batch["fp32_jacobi_ir"]["solves_per_s"] /
-                                                    same_batch["fp64_jacobi_pcg"]["solves_per_s"])
-        same_batch["gain_gmg_over_jacobi_fp32"] = (value /
-                                                   same_batch["fp32_jacobi_ir"]["solves_per_s"])
-        same_batch["gain_total_over_fp64_jacobi"] = (value /
-                                                     same_batch["fp64_jacobi_pcg"]["solves_per_s"])
+        for m in sub:
+            m.close()
+        g32, g64 = same_batch["fp32_jacobi_ir"], same_batch["fp64_jacobi_pcg"]
+        same_batch["gain_fp32_over_fp64_jacobi"] = g32["solves_per_s"] / g64["solves_per_s"]
+        same_batch["gain_gmg_over_jacobi_fp32"] = (same_batch["fp32_gmg_ir"]["solves_per_s"] /
+                                                   g32["solves_per_s"])
+        same_batch["gain_total_over_fp64_jacobi"] = (same_batch["fp32_gmg_ir"]["solves_per_s"] /
+                                                     g64["solves_per_s"])
 
     if rank != 0:
         if pool is not None:
@@ -838,7 +884,11 @@ def main():
     # in its own key and does not lose the headline line
     if args.large and ws == 1 and args.operator == 0:
         try:
-            line["large_configs"] = large_configs(topo, stream, flush)
+            line["large_configs"] = large_configs(topo, stream, flush, peaks=peaks,
+                                                  peaks_src=peaks_src)
+            cheb_large = line["large_configs"].get(LARGE_WORKLOAD, {}).get("roofline_cheb_step")
+            if cheb_large:
+                line["roofline_large_cheb_step"] = cheb_large
         except Exception as e:  # noqa: BLE001
             line["large_configs"] = {"error": f"{type(e).__name__}: {e}"}
     if args.serving and ws == 1:
