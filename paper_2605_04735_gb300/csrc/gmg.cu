@@ -20,6 +20,11 @@ namespace topo {
 namespace {
 
 constexpr int kCoarseMaxDof = 400;  // target size of the dense coarsest problem
+// prolongation: four fine nodes of a row per thread (k_prolong_add4); 0 keeps
+// one node per thread (k_prolong_add)
+#ifndef TOPO_PROLONG4
+#define TOPO_PROLONG4 1
+#endif
 constexpr int kPT = 256;
 
 // blocks per design: one item per thread up to 16 blocks per SM in all,
@@ -362,6 +367,69 @@ __global__ void k_prolong_add(const float* __restrict__ xc, const Dims dc, float
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (!df.fixed(c, i, j, k)) xf[c * df.comp + o] += s[c];
+  }
+}
+
+// The same update, four fine nodes of a row per thread: storage entries
+// 4q .. 4q+3 of a node row (i = 4q-1 .. 4q+2; rows are 16-byte aligned) are
+// read and written as one float4 per component, and the three coarse
+// columns 2q-1 .. 2q+1 that interpolate them are read once per coarse row.
+// Per node the arithmetic is k_prolong_add's, in its order (the clamp of
+// the odd nodes' right neighbour never acts on a node of the grid: odd
+// i <= nx - 1 has i/2 + 1 <= nx/2 <= the coarse nx).  Ghost entries keep 0.
+__global__ void k_prolong_add4(const float* __restrict__ xc, const Dims dc,
+                               float* __restrict__ xf, const Dims df,
+                               const int* __restrict__ done, const DSel S) {
+  pdl_start();
+  const long long off = S.off(blockIdx.y);
+  done = bshift(done, off);
+  if (*done) return;
+  xc = bshift(xc, off);
+  xf = bshift(xf, off);
+  const int nq = (df.nx + 2 + 3) / 4;  // quads of a row holding i = -1 .. nx
+  const int nrow = (df.ny + 1) * (df.nz + 1);
+  const int total = nq * nrow;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int row = t / nq, q = t - row * nq;
+    const int j = row % (df.ny + 1), k = row / (df.ny + 1);
+    const int j0 = j >> 1, k0 = k >> 1;
+    const bool oj = j & 1, ok = k & 1;
+    const long long dy = (long long)(min(j0 + 1, dc.ny) - j0) * dc.row_stride();
+    const long long dz = (long long)(min(k0 + 1, dc.nz) - k0) * dc.plane_stride();
+    const long long cb = dc.node(2 * q - 1, j0, k0);  // coarse column 2q - 1 (a ghost for q = 0)
+    const float wjk = (oj ? 0.5f : 1.0f) * (ok ? 0.5f : 1.0f);
+    float s[3][4] = {};
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      if (c2 && !ok) break;
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2) {
+        if (b2 && !oj) break;
+        const long long o = cb + (b2 ? dy : 0) + (c2 ? dz : 0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* p = xc + c * dc.comp + o;
+          const float a = p[0], b = p[1], e = p[2];
+          s[c][0] = fmaf(wjk, 0.5f * (a + b), s[c][0]);  // i = 4q - 1 (odd)
+          s[c][1] = fmaf(wjk, b, s[c][1]);                // i = 4q
+          s[c][2] = fmaf(wjk, 0.5f * (b + e), s[c][2]);  // i = 4q + 1 (odd)
+          s[c][3] = fmaf(wjk, e, s[c][3]);                // i = 4q + 2
+        }
+      }
+    }
+    const long long o = df.node(4 * q - 1, j, k);  // storage entry 4q: 16-byte aligned
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4* px = reinterpret_cast<float4*>(xf + c * df.comp + o);
+      float4 v = *px;
+      float* vv = reinterpret_cast<float*>(&v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 4 * q - 1 + e;
+        if (i >= 0 && i <= df.nx && !df.fixed(c, i, j, k)) vv[e] += s[c][e];
+      }
+      *px = v;
+    }
   }
 }
 
@@ -883,9 +951,17 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
   for (int l = l_end - 1; l >= 0; --l) {
     GmgLevel& L = g.lv[l];
     const GmgLevel& C = g.lv[l + 1];
+#if TOPO_PROLONG4
+    {
+      const long long nq4 = (long long)((L.d.nx + 5) / 4) * (L.d.ny + 1) * (L.d.nz + 1);
+      GCK(launch_pdl(k_prolong_add4, dim3(grid1d(nq4, bt.nb), bt.nb), dim3(kPT), 0, s, X(l + 1),
+                     C.d, X(l), L.d, done, bt.sel()));
+    }
+#else
     const long long nnf = (long long)(L.d.nx + 1) * (L.d.ny + 1) * (L.d.nz + 1);
     GCK(launch_pdl(k_prolong_add, dim3(grid1d(nnf, bt.nb), bt.nb), dim3(kPT), 0, s, X(l + 1), C.d,
                    X(l), L.d, done, bt.sel()));
+#endif
     EpiChebResid er{B(l), L.r, L.dv[0], L.dinv, cc.inv_theta};
     GCK(level_op(X(l), L, k0f, mcf, er, done, errflag, s, bt));
     *launches += 2;

@@ -35,11 +35,19 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tma.cuh"
 
 namespace topo {
+
+// The FP32 one-column kernels march with components 0 and 1 packed
+// (ModalColumnP: fewer issued instructions); 0 keeps the scalar march of
+// modal_layer for comparison.
+#ifndef TOPO_MODAL_PACKED
+#define TOPO_MODAL_PACKED 1
+#endif
 
 template <typename T>
 struct ModalCoef {
@@ -178,6 +186,195 @@ __device__ __forceinline__ void modal_layer(ModalColumn<T>& col, const T (&top)[
   }
 }
 
+// Packed two-wide FP32 arithmetic (add/sub/mul/fma .f32x2, sm_100+): each
+// half rounds exactly as the scalar instruction does, so a computation moved
+// onto pairs keeps every bit of its scalar result.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+  return *reinterpret_cast<const float2*>(&r);
+}
+
+// in-place 4-point (x-y) Walsh-Hadamard transform on pairs
+__device__ __forceinline__ void pfwht4(float2 (&v)[4]) {
+  const float2 a = padd(v[0], v[1]), b = psub(v[0], v[1]);
+  const float2 c = padd(v[2], v[3]), e = psub(v[2], v[3]);
+  v[0] = padd(a, c);
+  v[1] = padd(b, e);
+  v[2] = psub(a, c);
+  v[3] = psub(b, e);
+}
+
+// The FP32 z march with components 0 and 1 of every per-component quantity
+// held as one pair (.x = component 0, .y = component 1) and component 2 as a
+// scalar: the shift, the x-y and z transforms, the face sums with E and the
+// inverse transform of components 0 and 1 then issue as one packed
+// instruction each.  The operations and their order are modal_layer's; the
+// K~ product stays scalar, its operands read from the halves.  The results
+// agree with modal_layer<float> to FP32 rounding, not to the bit: there the
+// compiler may fuse the lone product of mode 7 (no coupling term) into the
+// face sums, which the packed sums do not.
+struct ModalColumnP {
+  float2 bxy01[4];
+  float bxy2[4];
+  float2 ref01;
+  float ref2;
+  float2 carry01[4];
+  float carry2[4];
+};
+
+__device__ __forceinline__ void modal_seed_p(ModalColumnP& col, const float (&raw)[2][2][3]) {
+  col.ref01 = make_float2(raw[0][0][0], raw[0][0][1]);
+  col.ref2 = raw[0][0][2];
+  float2 v[4] = {make_float2(0.f, 0.f),
+                 psub(make_float2(raw[0][1][0], raw[0][1][1]), col.ref01),
+                 psub(make_float2(raw[1][0][0], raw[1][0][1]), col.ref01),
+                 psub(make_float2(raw[1][1][0], raw[1][1][1]), col.ref01)};
+  pfwht4(v);
+  float u[4] = {0.f, raw[0][1][2] - col.ref2, raw[1][0][2] - col.ref2, raw[1][1][2] - col.ref2};
+  fwht4(u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    col.bxy01[q] = v[q];
+    col.bxy2[q] = u[q];
+    col.carry01[q] = make_float2(0.f, 0.f);
+    col.carry2[q] = 0.f;
+  }
+}
+
+__device__ __forceinline__ void modal_layer_p(ModalColumnP& col, const float (&top)[2][2][3],
+                                              float E, const ModalCoef<float>& kc,
+                                              float (&plane)[3][4], float (&ctr)[3]) {
+  // x-y transform of the top plane (shifted by corner 0) and the z butterfly
+  float2 uh01[8];  // [m] = (component 0, component 1) of mode m; [0] never formed
+  float uh2[8];
+  float2 t01[4];
+  float t2[4];
+  {
+    const float2 r = col.ref01;
+    ctr[0] = r.x;
+    ctr[1] = r.y;
+    ctr[2] = col.ref2;
+    t01[0] = psub(make_float2(top[0][0][0], top[0][0][1]), r);
+    t01[1] = psub(make_float2(top[0][1][0], top[0][1][1]), r);
+    t01[2] = psub(make_float2(top[1][0][0], top[1][0][1]), r);
+    t01[3] = psub(make_float2(top[1][1][0], top[1][1][1]), r);
+    pfwht4(t01);
+    t2[0] = top[0][0][2] - col.ref2;
+    t2[1] = top[0][1][2] - col.ref2;
+    t2[2] = top[1][0][2] - col.ref2;
+    t2[3] = top[1][1][2] - col.ref2;
+    fwht4(t2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q > 0) {
+        uh01[q] = padd(col.bxy01[q], t01[q]);
+        uh2[q] = col.bxy2[q] + t2[q];
+      }
+      uh01[q + 4] = psub(col.bxy01[q], t01[q]);
+      uh2[q + 4] = col.bxy2[q] - t2[q];
+    }
+  }
+  // the 45 entries of K~ (scalar; components 0 and 1 land in one pair)
+  auto uh = [&](int c, int m) -> float { return c == 0 ? uh01[m].x : (c == 1 ? uh01[m].y : uh2[m]); };
+  float2 yh01[8];
+  float yh2[8];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+      float acc = kc.D[p][m] * uh(p, m);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q == p) continue;
+        if (((m >> p) & 1) == ((m >> q) & 1)) continue;
+        acc = fmaf(kc.C[p][q][m], uh(q, m ^ (1 << p) ^ (1 << q)), acc);
+      }
+      if (p == 0)
+        yh01[m].x = acc;
+      else if (p == 1)
+        yh01[m].y = acc;
+      else
+        yh2[m] = acc;
+    }
+  }
+  // E on the two z faces, the previous element's top face, inverse x-y transform
+  const float nE = -E;
+  {
+    const float2 E2 = make_float2(E, E), nE2 = make_float2(nE, nE);
+    float2 w[4];
+    w[0] = pfma(E2, yh01[4], col.carry01[0]);
+    col.carry01[0] = pmul(nE2, yh01[4]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      w[q] = pfma(E2, padd(yh01[q], yh01[q + 4]), col.carry01[q]);
+      col.carry01[q] = pmul(E2, psub(yh01[q], yh01[q + 4]));
+    }
+    pfwht4(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      plane[0][q] = w[q].x;
+      plane[1][q] = w[q].y;
+    }
+    const float2 nref = make_float2(top[0][0][0], top[0][0][1]);
+    col.bxy01[0] = pfma(make_float2(4.f, 4.f), psub(col.ref01, nref), t01[0]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) col.bxy01[q] = t01[q];
+    col.ref01 = nref;
+  }
+  {
+    float w[4];
+    w[0] = fmaf(E, yh2[4], col.carry2[0]);
+    col.carry2[0] = nE * yh2[4];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      w[q] = fmaf(E, yh2[q] + yh2[q + 4], col.carry2[q]);
+      col.carry2[q] = E * (yh2[q] - yh2[q + 4]);
+    }
+    fwht4(w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) plane[2][q] = w[q];
+    const float nref = top[0][0][2];
+    col.bxy2[0] = fmaf(4.f, col.ref2 - nref, t2[0]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) col.bxy2[q] = t2[q];
+    col.ref2 = nref;
+  }
+}
+
+// The z march of the one-column kernels: the packed form for FP32 (every
+// FP32 one-column kernel, TMA-staged or plain, so that they agree to the
+// bit), the scalar template for FP64 and the double-word type.
+template <typename T>
+using MarchColumn = typename std::conditional<TOPO_MODAL_PACKED && std::is_same<T, float>::value,
+                                              ModalColumnP, ModalColumn<T>>::type;
+template <typename T>
+__device__ __forceinline__ void march_seed(ModalColumn<T>& col, const T (&raw)[2][2][3]) {
+  modal_seed<T>(col, raw);
+}
+__device__ __forceinline__ void march_seed(ModalColumnP& col, const float (&raw)[2][2][3]) {
+  modal_seed_p(col, raw);
+}
+template <typename T>
+__device__ __forceinline__ void march_layer(ModalColumn<T>& col, const T (&top)[2][2][3], T E,
+                                            const ModalCoef<T>& kc, T (&plane)[3][4],
+                                            T (&ctr)[3], T* dot = nullptr) {
+  modal_layer<T>(col, top, E, kc, plane, ctr, dot);
+}
+// (the FP32 kernels form no element energies: `dot` is never requested)
+__device__ __forceinline__ void march_layer(ModalColumnP& col, const float (&top)[2][2][3],
+                                            float E, const ModalCoef<float>& kc,
+                                            float (&plane)[3][4], float (&ctr)[3],
+                                            float* = nullptr) {
+  modal_layer_p(col, top, E, kc, plane, ctr);
+}
+
 // the value of lane - 1 (overloaded for the double-word type)
 template <typename T>
 __device__ __forceinline__ T shfl_up1(T v) {
@@ -196,6 +393,12 @@ __device__ __forceinline__ T shfl_up1(T v) {
 #define TOPO_MODAL_TY 12
 #endif
 constexpr int kModalTX = TOPO_MODAL_TX, kModalTY = TOPO_MODAL_TY;
+// CTAs per SM the TMA kernels ask the register allocator to fit (the packed
+// march holds pairs in aligned register pairs): 3 of the 18-row tiles, 4 of
+// the 12-row and 5 of the 10-row ones, as the scalar march reached.
+#ifndef TOPO_MODAL_MINB
+#define TOPO_MODAL_MINB(ty) ((ty) == 18 ? 3 : ((ty) == 12 ? 4 : 5))
+#endif
 static_assert(32 % kModalTX == 0 && kModalTX >= 8, "x tile: 8, 16 or 32 threads");
 static_assert(kModalTX * kModalTY % 32 == 0 && kModalTX * kModalTY <= 512, "whole warps");
 
@@ -329,7 +532,7 @@ struct MTile {
 // layer's barrier shows every row has read it.  When nx = 16 x (CTAs), lane
 // 15 of the last CTA also finishes node column nx.
 template <class Epi, int TY, bool CL = false>
-__global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
+__global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : TOPO_MODAL_MINB(TY))
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
                 const __grid_constant__ CUtensorMap amap0,
                 const __grid_constant__ CUtensorMap amap1, const Dims d,
@@ -434,7 +637,7 @@ __global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
   const bool clean = CL ? !d.box_may_fix(x0 - 1, min(x0 + kModalTX - 1, d.nx), y0, kb)
                         : !d.box_may_fix(x0, x0 + kModalOwnX - 1, y0, kb);
   const FreeDims fd{d.comp};
-  ModalColumn<float> col;
+  MarchColumn<float> col;
   float part = 0.f;  // this thread's nodes only (at most zchunk); widened to FP64 below
   float es_prev = 0.f;  // (DI) moduli of the 2 x 2 elements below node (ex, ey), layer before
   float esx_prev = 0.f;  // the same for node (nx, ey) (xn)
@@ -471,7 +674,7 @@ __global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(kModalStages);
     }
-    modal_seed<float>(col, top);
+    march_seed(col, top);
   }
   const long long o_col = d.node(ex, ey, 0), ps = d.plane_stride();  // node (ex, ey, ez): + ez ps
   int rs = 1;  // stage t's ring slot t % kModalStages, and its mbarrier phase
@@ -481,7 +684,7 @@ __global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
     float top[2][2][3], E, es, esx;
     read_stage(rs, phase, top, E, es, esx);
     float plane[3][4], ctr[3];
-    modal_layer<float>(col, top, E, kc, plane, ctr);
+    march_layer(col, top, E, kc, plane, ctr);
     const int ez = kb - 2 + t;
     float res[3], resx[3], ctrx[3];
     if constexpr (CL) {
@@ -628,7 +831,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAI
     if (i > d.nx + 1 || j > d.ny + 1 || k > d.nz + 1) return T(0);  // beyond the ghost ring
     return __ldg(x + c * d.comp + d.node(i, j, k));
   };
-  ModalColumn<T> col;
+  MarchColumn<T> col;
   {
     T raw[2][2][3];
 #pragma unroll
@@ -637,7 +840,7 @@ __global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAI
       for (int dx = 0; dx < 2; ++dx)
 #pragma unroll
         for (int c = 0; c < 3; ++c) raw[dy][dx][c] = node_val(ex + dx, ey + dy, kb - 1, c);
-    modal_seed<T>(col, raw);
+    march_seed(col, raw);
   }
   T part = T(0);
   for (int ez = kb - 1; ez < ke; ++ez) {
@@ -649,8 +852,8 @@ __global__ void __launch_bounds__(kModalTX* kModalTY, sizeof(T) == 8 ? TOPO_PLAI
 #pragma unroll
         for (int c = 0; c < 3; ++c) top[dy][dx][c] = node_val(ex + dx, ey + dy, ez + 1, c);
     const T Ee = (ex <= d.nx && ey <= d.ny && ez <= d.nz) ? __ldg(E + d.elem(ex, ey, ez)) : T(0);
-    T plane[3][4], ctr[3], dot;
-    modal_layer<T>(col, top, Ee, kc, plane, ctr, energy ? &dot : nullptr);
+    T plane[3][4], ctr[3], dot = T(0);
+    march_layer(col, top, Ee, kc, plane, ctr, energy ? &dot : nullptr);
     // element energies (u_e - u_0)^T k0 (u_e - u_0), written by the CTA and
     // z-chunk that own the element (the others compute it as halo / warm-up)
     if (energy && tx > 0 && ty > 0 && ex < d.nx && ey < d.ny && ez >= kb && ez < d.nz)

@@ -34,28 +34,6 @@
 
 namespace topo {
 
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;"
-      : "=l"(r)
-      : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
-        "l"(*reinterpret_cast<const unsigned long long*>(&b)));
-  return *reinterpret_cast<const float2*>(&r);
-}
-
-// in-place 4-point (x-y) Walsh-Hadamard transform on pairs
-__device__ __forceinline__ void pfwht4(float2 (&v)[4]) {
-  const float2 a = padd(v[0], v[1]), b = psub(v[0], v[1]);
-  const float2 c = padd(v[2], v[3]), e = psub(v[2], v[3]);
-  v[0] = padd(a, c);
-  v[1] = padd(b, e);
-  v[2] = psub(a, c);
-  v[3] = psub(b, e);
-}
-
 // ModalCoef<float> with every coefficient duplicated into both halves
 struct ModalCoef2 {
   float2 D[3][8];
