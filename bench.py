@@ -74,24 +74,25 @@ def operator_kernel(op: int, nx: int) -> str:
 
 # DRAM bytes (read + write) per launch of the CG apply (operator + p.Ap) from
 # one ncu capture of the same kernel source, by workload; None until captured
-# (k_modal_tma on one 96x32x32 design: its 2.9 MB working set stays in L2, so
-# the output is never written back during the launch; k_modal_pair on
-# 320x160x160)
-NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": 1960704.0 + 0.0,
+# on the current source (k_modal_tma on one 96x32x32 design, not recaptured
+# since its march was packed; k_modal_pair on 320x160x160)
+NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": None,
                                         LARGE_WORKLOAD: 183507712.0 + 69900032.0}
 # DRAM bytes per design of the batched finest-level launches, from one ncu
-# capture each of a 64-design launch of the current kernel source
+# capture of a 64-design launch of the current kernel source
 # (profiles/k_modal_tma_batch64_mbb_96x32x32.md): the Chebyshev step in its
-# x-added form (8.00 MB algorithmic per design) and the CG apply
-NCU_TRAFFIC_BATCH = {"cheb_step": (306157056.0 + 201122304.0) / 64,
-                     "cg_apply": (135333632.0 + 52475136.0) / 64}
+# x-added form (8.00 MB algorithmic per design); the CG apply not recaptured
+# since its march was packed
+NCU_TRAFFIC_BATCH: dict[str, float | None] = {"cheb_step": (303777536.0 + 197783808.0) / 64,
+                                              "cg_apply": None}
 # FP32 lane-operations the modal kernels execute per element of the grid
 # (ncu smsp__sass_thread_inst_executed_op_fp32_pred_on, a packed f32x2
 # instruction counted as two; halo columns and idle thread slots included),
 # the basis of the executed-operation floor: the Chebyshev step and the CG
 # apply of k_modal_tma in a 64-design 96x32x32 launch (1.744 G and 1.615 G
-# for 6.29 M elements), k_modal_pair's CG apply at 320x160x160 (2.125 G for
-# 8.19 M elements)
+# for 6.29 M elements; counted on the scalar march, which executes the same
+# FP32 lane-operations as the packed one), k_modal_pair's CG apply at
+# 320x160x160 (2.125 G for 8.19 M elements)
 EXEC_FP32_OPS_PER_ELEM = {"cheb_step": 277.1, "cg_apply_tma": 256.7, "cg_apply_pair": 259.4}
 FLOP_PER_ELEM = 2 * 24 * 24  # the dense K0 U_e product per element (multiply + add)
 
@@ -257,8 +258,19 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        pw = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                pw.append(float(f[3]))
+            except (ValueError, IndexError):
+                pass
+        out = {"sm_mhz": float(np.median(sm)), "sm_min_mhz": min(sm), "sm_max_mhz": max(mx),
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if pw:
+            out["power_w_median"] = float(np.median(pw))
+            out["power_w_max"] = max(pw)
+        return out
 
 
 def oracle_step(workload: I.Workload, rho: np.ndarray) -> float:
@@ -697,13 +709,14 @@ def main():
     step_batch(rho_host.numpy(), dc_host.numpy(), opts)
     torch.cuda.synchronize()
     e2e_t = []
-    for k in range(max(5, args.steps)):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        step_batch(rho_host.numpy(), dc_host.numpy(), opts)
-        torch.cuda.synchronize()
-        e2e_t.append(time.perf_counter() - t0)
+    with ClockSampler(local) as clk_e2e:
+        for k in range(max(5, args.steps)):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_batch(rho_host.numpy(), dc_host.numpy(), opts)
+            torch.cuda.synchronize()
+            e2e_t.append(time.perf_counter() - t0)
     e2e_value = ws * B / float(np.mean(e2e_t))
 
     # ---- the plain FP64 Jacobi-PCG GPU path on design 0 (comparison) ----
@@ -825,7 +838,7 @@ def main():
                             else None, ops=exec_ops(args.operator, w.nx, "cheb_step"))
         main["traffic_note"] = ("ncu, one 64-design launch of the x-added form (8.00 MB "
                                 "algorithmic per design; bytes_per_launch averages the stored "
-                                "and added forms): DRAM / algorithmic = 0.99")
+                                "and added forms): DRAM / algorithmic = 0.98")
         main.update({"designs_per_launch": "varies (designs still iterating); figures per "
                                           "design-launch",
                      "avg_launch_us": None,
@@ -871,7 +884,8 @@ def main():
         "roofline_large": large,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem * B,
-                "d2h_bytes_per_step": (8 * w.n_elem + 8) * B},
+                "d2h_bytes_per_step": (8 * w.n_elem + 8) * B,
+                "steps_ms": [round(1e3 * t, 2) for t in e2e_t], "clocks": clk_e2e.summary()},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s": wall,
