@@ -708,6 +708,17 @@ def main():
     dc_host = torch.empty((B, w.n_elem), dtype=torch.float64).pin_memory()
     step_batch(rho_host.numpy(), dc_host.numpy(), opts)
     torch.cuda.synchronize()
+
+    def copy_gbs(dst, src):
+        """GB/s of one copy of the pinned e2e buffers (CUDA events)."""
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dst.copy_(src, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return src.numel() * src.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9
+
+    copies = {"h2d_before": copy_gbs(rho_dev, rho_host), "d2h_before": copy_gbs(dc_host, dc_dev)}
     e2e_t = []
     with ClockSampler(local) as clk_e2e:
         for k in range(max(5, args.steps)):
@@ -718,6 +729,8 @@ def main():
             torch.cuda.synchronize()
             e2e_t.append(time.perf_counter() - t0)
     e2e_value = ws * B / float(np.mean(e2e_t))
+    copies.update({"h2d_after": copy_gbs(rho_dev, rho_host),
+                   "d2h_after": copy_gbs(dc_host, dc_dev)})
 
     # ---- the plain FP64 Jacobi-PCG GPU path on design 0 (comparison) ----
     fp64 = None
@@ -885,7 +898,10 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n_elem * B,
                 "d2h_bytes_per_step": (8 * w.n_elem + 8) * B,
-                "steps_ms": [round(1e3 * t, 2) for t in e2e_t], "clocks": clk_e2e.summary()},
+                "steps_ms": [round(1e3 * t, 2) for t in e2e_t], "clocks": clk_e2e.summary(),
+                "copy_gbs": {k: round(v, 1) for k, v in copies.items()},
+                "host_cpus": sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                else None},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s": wall,
