@@ -25,11 +25,6 @@ constexpr int kCoarseMaxDof = 400;  // target size of the dense coarsest problem
 #ifndef TOPO_PROLONG4
 #define TOPO_PROLONG4 1
 #endif
-// restriction: four coarse nodes of a row per thread (k_restrict4); 0 keeps
-// one node per thread (k_restrict)
-#ifndef TOPO_RESTRICT4
-#define TOPO_RESTRICT4 1
-#endif
 constexpr int kPT = 256;
 
 // blocks per design: one item per thread up to 16 blocks per SM in all,
@@ -323,82 +318,6 @@ __global__ void k_restrict(const float* __restrict__ rf, const Dims df, float* _
     const long long o = dc.node(I, J, K);
 #pragma unroll
     for (int c = 0; c < 3; ++c) bc[c * dc.comp + o] = dc.fixed(c, I, J, K) ? 0.0f : s[c];
-  }
-}
-
-// The same restriction, four coarse nodes of a row per thread: coarse
-// storage entries 4q .. 4q+3 (I = 4q-1 .. 4q+2) gather the fine columns
-// 8q-3 .. 8q+5 of each fine row, read as three aligned float4 (storage
-// entries 8q-4 .. 8q+7; the first is not needed for q = 0 and is not read,
-// the last may reach the next row's head, inside the array since every
-// fine row used has ghost rows after it); the four results go out as one
-// float4 per component, 0 on the ghost and padding entries (which hold 0).
-// Per node the terms, their weights, order and skips are k_restrict's.
-__global__ void k_restrict4(const float* __restrict__ rf, const Dims df, float* __restrict__ bc,
-                            const Dims dc, const int* __restrict__ done, const DSel S) {
-  pdl_start();
-  const long long off = S.off(blockIdx.y);
-  done = bshift(done, off);
-  if (*done) return;
-  rf = bshift(rf, off);
-  bc = bshift(bc, off);
-  const int nq = (dc.nx + 2 + 3) / 4;  // quads of a coarse row holding I = -1 .. nx
-  const int nrow = (dc.ny + 1) * (dc.nz + 1);
-  const int total = nq * nrow;
-  const long long px = df.row_stride(), pz = df.plane_stride();
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int row = t / nq, q = t - row * nq;
-    const int J = row % (dc.ny + 1), K = row / (dc.ny + 1);
-    float s[3][4] = {};
-#pragma unroll
-    for (int dk = -1; dk <= 1; ++dk) {
-      const int k = 2 * K + dk;
-      if (k < 0 || k > df.nz) continue;
-      const float wk = dk ? 0.5f : 1.0f;
-#pragma unroll
-      for (int dj = -1; dj <= 1; ++dj) {
-        const int j = 2 * J + dj;
-        if (j < 0 || j > df.ny) continue;
-        const float wjk = wk * (dj ? 0.5f : 1.0f);
-        // storage entry 8q of fine row (j, k): fine column i = 8q - 1
-        const long long base = df.node(-1, j, k) + 8LL * q;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float* p = rf + c * df.comp + base;
-          const float4 v0 = q > 0 ? *reinterpret_cast<const float4*>(p - 4)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 v1 = *reinterpret_cast<const float4*>(p);
-          const float4 v2 = *reinterpret_cast<const float4*>(p + 4);
-          // f[n] is fine column 8q - 5 + n (storage entries 8q - 4 .. 8q + 7)
-          const float f[12] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y,
-                               v1.z, v1.w, v2.x, v2.y, v2.z, v2.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int I = 4 * q - 1 + e;  // lane e's coarse column
-#pragma unroll
-            for (int di = -1; di <= 1; ++di) {
-              const int i = 2 * I + di;
-              if (I < 0 || I > dc.nx || i < 0 || i > df.nx) continue;
-              const float wt = wjk * (di ? 0.5f : 1.0f);
-              // fine column i = 8q - 2 + 2e + di: f index 2e + di + 3
-              s[c][e] = fmaf(wt, f[2 * e + di + 3], s[c][e]);
-            }
-          }
-        }
-      }
-    }
-    const long long o = dc.node(4 * q - 1, J, K);  // storage entry 4q: 16-byte aligned
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float4 v;
-      float* vv = reinterpret_cast<float*>(&v);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int I = 4 * q - 1 + e;
-        vv[e] = (I < 0 || I > dc.nx || dc.fixed(c, I, J, K)) ? 0.0f : s[c][e];
-      }
-      *reinterpret_cast<float4*>(bc + c * dc.comp + o) = v;
-    }
   }
 }
 
@@ -991,15 +910,9 @@ cudaError_t gmg_vcycle(Gmg& g, const float* b0, float* x0, const K0<float>& k0f,
     }
     GCK(level_op(L.dv[(m - 1) & 1], L, k0f, mcf, EpiChebLast{L.r}, done, errflag, s, bt));
     const GmgLevel& C = g.lv[l + 1];
-#if TOPO_RESTRICT4
-    const long long nq4 = (long long)((C.d.nx + 5) / 4) * (C.d.ny + 1) * (C.d.nz + 1);
-    GCK(launch_pdl(k_restrict4, dim3(grid1d(nq4, bt.nb), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b,
-                   C.d, done, bt.sel()));
-#else
     const long long nnc = (long long)(C.d.nx + 1) * (C.d.ny + 1) * (C.d.nz + 1);
     GCK(launch_pdl(k_restrict, dim3(grid1d(nnc, bt.nb), bt.nb), dim3(kPT), 0, s, L.r, L.d, C.b,
                    C.d, done, bt.sel()));
-#endif
     *launches += 2;
   }
   if (tail) {  // levels l_end .. coarsest in one kernel per design
