@@ -393,12 +393,7 @@ __device__ __forceinline__ T shfl_up1(T v) {
 #define TOPO_MODAL_TY 12
 #endif
 constexpr int kModalTX = TOPO_MODAL_TX, kModalTY = TOPO_MODAL_TY;
-// CTAs per SM the TMA kernels ask the register allocator to fit (the packed
-// march holds pairs in aligned register pairs): 3 of the 18-row tiles, 4 of
-// the 12-row and 5 of the 10-row ones, as the scalar march reached.
-#ifndef TOPO_MODAL_MINB
-#define TOPO_MODAL_MINB(ty) ((ty) == 18 ? 3 : ((ty) == 12 ? 4 : 5))
-#endif
+
 static_assert(32 % kModalTX == 0 && kModalTX >= 8, "x tile: 8, 16 or 32 threads");
 static_assert(kModalTX * kModalTY % 32 == 0 && kModalTX * kModalTY <= 512, "whole warps");
 
@@ -532,7 +527,7 @@ struct MTile {
 // layer's barrier shows every row has read it.  When nx = 16 x (CTAs), lane
 // 15 of the last CTA also finishes node column nx.
 template <class Epi, int TY, bool CL = false>
-__global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : TOPO_MODAL_MINB(TY))
+__global__ void __launch_bounds__(kModalTX* TY, CL ? 4 : 0)
     k_modal_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap emap,
                 const __grid_constant__ CUtensorMap amap0,
                 const __grid_constant__ CUtensorMap amap1, const Dims d,
