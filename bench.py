@@ -83,7 +83,7 @@ NCU_TRAFFIC: dict[str, float | None] = {"mbb_96x32x32": None,
 # (profiles/k_modal_tma_batch64_mbb_96x32x32.md): the Chebyshev step in its
 # x-added form (8.00 MB algorithmic per design); the CG apply not recaptured
 # since its march was packed
-NCU_TRAFFIC_BATCH: dict[str, float | None] = {"cheb_step": (303777536.0 + 197783808.0) / 64,
+NCU_TRAFFIC_BATCH: dict[str, float | None] = {"cheb_step": (303747840.0 + 198051328.0) / 64,
                                               "cg_apply": None}
 # FP32 lane-operations the modal kernels execute per element of the grid
 # (ncu smsp__sass_thread_inst_executed_op_fp32_pred_on, a packed f32x2
