@@ -45,3 +45,23 @@ def test_executed_operation_counts_follow_the_kernel_choice():
     assert bench.operator_kernel(0, large).startswith("k_modal_pair")
     assert bench.operator_kernel(4, small).startswith("k_tc_tma")
     assert "cluster" in bench.operator_kernel(5, small)
+
+
+def test_clock_summary_reads_clocks_reasons_and_power():
+    """nvidia-smi CSV rows (index, SM clock, max SM clock, power, active
+    reasons, then the four reasons the timing rules name) become the median
+    and minimum SM clock, the reasons seen active and the power figures;
+    malformed rows are skipped."""
+    clk = bench.ClockSampler(0)
+    clk.lines = [
+        "0, 2070, 2070, 800.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 850.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1965, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    s = clk.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_min_mhz"] == 1965.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+    assert s["power_w_median"] == pytest.approx(850.0) and s["power_w_max"] == 900.0
+    empty = bench.ClockSampler(0).summary()
+    assert empty["reasons"] == ["unsampled"] and empty["sm_mhz"] is None
