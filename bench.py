@@ -170,10 +170,15 @@ def _dist():
     return ws, rank, local
 
 
+SEED_STRIDE = 1_000_000  # seeds per rank: ranks' batches never overlap (batch < stride)
+
+
 def design_seeds(base_seed: int, rank: int, batch: int):
     """Seeds of the independent designs rank `rank` solves: disjoint across
     ranks (weak scaling: every rank gets its own batch, no data exchange)."""
-    return [base_seed + 1000 * rank + b for b in range(batch)]
+    if batch > SEED_STRIDE:
+        raise ValueError(f"at most {SEED_STRIDE} designs per rank")
+    return [base_seed + SEED_STRIDE * rank + b for b in range(batch)]
 
 
 def job_throughput(local_ms: float, units_per_rank: int, dist_mod=None, device=None):

@@ -52,3 +52,14 @@ def test_two_gloo_ranks_shard_designs_and_take_the_slowest_time():
 def test_single_process_throughput():
     v, t = bench.job_throughput(50.0, 10)
     assert t == 50.0 and v == pytest.approx(200.0)
+
+
+def test_design_seeds_stay_disjoint_at_the_default_batch():
+    """Every rank of an 8-GPU run solves its own 1024 designs: no seed repeats
+    across ranks (the per-rank stride exceeds the batch)."""
+    seen = set()
+    for r in range(8):
+        s = bench.design_seeds(2605_04735 + 1, r, 1024)
+        assert len(set(s)) == 1024 and not seen & set(s)
+        seen |= set(s)
+    assert bench.design_seeds(2605_04735 + 1, 0, 3) == [2605_04736, 2605_04737, 2605_04738]
