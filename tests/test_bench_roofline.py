@@ -65,3 +65,22 @@ def test_clock_summary_reads_clocks_reasons_and_power():
     assert s["power_w_median"] == pytest.approx(850.0) and s["power_w_max"] == 900.0
     empty = bench.ClockSampler(0).summary()
     assert empty["reasons"] == ["unsampled"] and empty["sm_mhz"] is None
+
+
+def test_reference_arm_prints_one_line_of_the_contract(capsys):
+    """`bench.py --impl reference` on the smallest workload: one JSON line
+    with the metric, unit and config of our arm, the oracle as its
+    cpu_baseline, an e2e of the same value with no host-device bytes, and
+    no GPU launch (the oracle is host code)."""
+    import argparse
+    import json
+    w = I.WORKLOADS["cantilever_24x12x12"]
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0), w)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["gpu_launches"] == 0
+    assert line["config"]["workload"] == w.name
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
